@@ -1,0 +1,191 @@
+/*
+ * cavity.h -- C ABI of the GB300 (sm_103a) buoyancy-driven-cavity step.
+ *
+ * One explicit time step of the artificial-compressibility Boussinesq solver
+ * of Xue & Roy (arXiv 2006.02602): fields p, u, v, w, T on a unit cube with n
+ * interior nodes per axis, walls at the nodes 0 and n+1 (h = 1/(n+1)), a
+ * pressure ghost beyond every wall.  Per step (Section 2, Eqs. 1-3; Section
+ * 3.1, Fig. 1; Section 4.5, Listings 1-2):
+ *   dt from the previous step's spectral-radius max-reduce,
+ *   fused residual + explicit Euler update of every interior node (13-point
+ *   pressure star, 7-point star for u, v, w, T),
+ *   FP64 residual sums, centre-pressure rescale, wall conditions,
+ *   ghost-face pack/unpack between the blocks of a decomposition held on one
+ *   device (p at depth 2, u, v, w, T at depth 1), hot/cold wall Nusselt.
+ *
+ * Nondimensional (thermal) scaling: rho = 1, alpha = 1, nu = Pr,
+ * g sigma = Ra Pr.  Hot wall x = 0, cold wall x = 1, other walls adiabatic,
+ * no slip everywhere; buoyancy along +gravity_axis.
+ *
+ * Conventions for every entry point:
+ *  - return 0 (CAVITY_OK) or a negative CAVITY_ERR_* code; cavity_strerror()
+ *    names a code, cavity_last_error() gives the last message of a handle;
+ *  - the library owns all device memory of a handle; the caller owns every
+ *    host buffer and must keep it valid for the duration of the call;
+ *  - host arrays of interior fields are FP64, ordered (f, k, j, i) with i
+ *    fastest and f in p, u, v, w, T order restricted to the mask;
+ *  - cavity_step() only enqueues work on the handle's stream; every getter
+ *    synchronises that stream first;
+ *  - a handle is not thread safe; distinct handles are independent.
+ */
+#ifndef BDC_CAVITY_H
+#define BDC_CAVITY_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CAVITY_API __attribute__((visibility("default")))
+#else
+#define CAVITY_API
+#endif
+
+/* status codes */
+#define CAVITY_OK 0
+#define CAVITY_ERR_INVALID_ARG (-1) /* bad pointer, size, mask or parameter */
+#define CAVITY_ERR_OOM (-2)         /* device or host allocation failed */
+#define CAVITY_ERR_CUDA (-3)        /* a CUDA runtime call failed (see cavity_last_error) */
+#define CAVITY_ERR_NONFINITE (-4)   /* a residual or the spectral radius became NaN/Inf */
+#define CAVITY_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define CAVITY_ERR_UNSUPPORTED (-6) /* valid request this build does not implement */
+
+/* arithmetic forms */
+#define CAVITY_FP64 0       /* every field and every operation in FP64 */
+#define CAVITY_FP32_MIXED 1 /* u, v, w, T in FP32; p as an FP32 hi/lo pair; FP64 reductions */
+
+/* field masks */
+#define CAVITY_FIELD_P 1
+#define CAVITY_FIELD_U 2
+#define CAVITY_FIELD_V 4
+#define CAVITY_FIELD_W 8
+#define CAVITY_FIELD_T 16
+#define CAVITY_FIELD_ALL 31
+
+typedef struct cavity cavity_t; /* opaque, library owned */
+
+/* Geometry, decomposition and initial condition.
+ *  nx, ny, nz   interior nodes per axis (h_d = 1/(n_d+1));
+ *  px, py, pz   block grid; the cavity is split as evenly as possible along
+ *               each axis (Section 3.2), every block at least 2 nodes thick;
+ *               1,1,1 = a single block;
+ *  precision    CAVITY_FP64 or CAVITY_FP32_MIXED;
+ *  seed, noise_amp  initial T = t_hot + (t_cold - t_hot) x + noise_amp (2U - 1),
+ *               U from splitmix64(seed * 2^40 + global interior index);
+ *               u = v = w = p = 0;
+ *  device       CUDA device ordinal;
+ *  stream       cudaStream_t to run on, or NULL for a stream the handle owns. */
+typedef struct {
+  int nx, ny, nz;
+  int px, py, pz;
+  int precision;
+  unsigned long long seed;
+  double noise_amp;
+  int device;
+  void *stream;
+} cavity_desc;
+
+/* Physical and numerical parameters (Section 2; the paper gives no formula for
+ * beta, eps or dt, so the forms below are readings of its text).  Negative
+ * u_ref or NaN t_inf select their defaults:
+ * u_ref = max(1, sqrt(Ra Pr)), t_inf = (t_hot + t_cold) / 2.
+ *  beta^2 = max(|V|^2, kappa u_ref^2)                 (Section 2)
+ *  eps_d  = c4 lambda_d h_d^3 / beta^2                 (Eq. 1 dissipation)
+ *  dt     = cfl / max[sum_d lambda_d/h_d + 2 max(nu,alpha) sum_d 1/h_d^2]
+ *  gravity_axis 1 (y) or 2 (z). */
+typedef struct {
+  double Ra, Pr, cfl, kappa, c4, u_ref, t_inf, t_hot, t_cold;
+  int gravity_axis;
+} cavity_params;
+
+/* Fill *p with the default parameters (Ra 1e5, Pr 0.71, cfl 0.5, kappa 0.1,
+ * c4 1/32, u_ref and t_inf defaulted, t_hot 1, t_cold 0, gravity_axis 2). */
+CAVITY_API int cavity_default_params(cavity_params *p);
+
+/* Allocate the handle and its device state, initialise the fields from desc
+ * (Section 2 problem statement), apply the walls, exchange ghosts and compute
+ * the first dt.  Uses the default parameters until cavity_set_params().
+ * On error *out is NULL and nothing is leaked. */
+CAVITY_API int cavity_create(const cavity_desc *desc, cavity_t **out);
+
+/* Set the parameters.  Before the first step the state is re-initialised
+ * from the descriptor's seed and noise under the new parameters; after it the
+ * fields are kept and only the walls and the next dt are recomputed. */
+CAVITY_API int cavity_set_params(cavity_t *h, const cavity_params *p);
+
+/* Temperature of an isothermal wall: wall 0 = hot (x = 0), 1 = cold (x = 1).
+ * host holds ny*nz values, (j-1) + ny (k-1) order; n must equal ny*nz.
+ * Replaces the uniform t_hot / t_cold on that wall; walls are re-applied. */
+CAVITY_API int cavity_set_wall_temperature(cavity_t *h, int wall, const double *host, size_t n);
+
+/* Enqueue nsteps explicit steps (nsteps >= 0) on the handle's stream. */
+CAVITY_API int cavity_step(cavity_t *h, int nsteps);
+
+/* RMS over the interior of dq/dt of the last step, p, u, v, w, T
+ * (Section 4.2 residual norms).  Zeros before the first step.
+ * Returns CAVITY_ERR_NONFINITE (after filling out) once a step produced
+ * a NaN/Inf residual or spectral radius. */
+CAVITY_API int cavity_residual(cavity_t *h, double out[5]);
+
+/* Hot- and cold-wall Nusselt numbers of the current state: mean over the
+ * ny*nz wall nodes of the one-sided second-order wall heat flux divided by
+ * (t_hot - t_cold).  Either pointer may be NULL. */
+CAVITY_API int cavity_nusselt(cavity_t *h, double *hot, double *cold);
+
+/* Copy interior fields of the whole cavity to host (FP64; FP32 fields
+ * widened, the p pair summed).  count must equal popcount(mask)*nx*ny*nz. */
+CAVITY_API int cavity_get_fields(cavity_t *h, int field_mask, double *host, size_t count);
+
+/* Overwrite interior fields from host (layout as cavity_get_fields), then
+ * re-apply walls, exchange ghosts and recompute dt.  Step count and time
+ * are kept. */
+CAVITY_API int cavity_set_fields(cavity_t *h, int field_mask, const double *host, size_t count);
+
+/* Step counter, simulated time and the dt the next step will use. */
+CAVITY_API int cavity_get_time(cavity_t *h, long long *step, double *t, double *dt);
+
+/* Number of blocks (px*py*pz). */
+CAVITY_API int cavity_num_blocks(cavity_t *h);
+
+/* Whole array of one field of one block, walls and ghosts included, as
+ * stored (p before the pending centre shift), (k, j, i) order over local
+ * nodes -1 .. n+2 of each axis: count = (nx_b+4)(ny_b+4)(nz_b+4).
+ * dims (optional) receives nx_b, ny_b, nz_b, ox, oy, oz (global node index
+ * = o + local index).  For checks of the ghost exchange. */
+CAVITY_API int cavity_get_block_array(cavity_t *h, int block, int field, double *host, size_t count, int dims[6]);
+
+/* The last packed buffer of one cut face of one block (Section 4.5 layout:
+ * p at depth 2 with depth fastest, then u, v, w, T at depth 1), widened to
+ * FP64; count must equal 6*nb*nc.  CAVITY_ERR_INVALID_ARG if the face is a
+ * wall. */
+CAVITY_API int cavity_get_face_buffer(cavity_t *h, int block, int face, double *host, size_t count);
+
+/* Pack and unpack every cut face of the current state (a7, a8 alone). */
+CAVITY_API int cavity_exchange(cavity_t *h);
+
+/* Measurement: run nsteps steps as plain launches (no graph replay) with CUDA
+ * events around every kernel on the handle's stream.  ms[0..3] receive the
+ * mean duration per launch of the fused step kernel, the wall/finalise
+ * kernel, the pack kernel and the unpack kernel (0 where a kernel does not
+ * run).  The steps are real steps of the state. */
+CAVITY_API int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]);
+
+/* Synchronise the handle's stream; returns the sticky non-finite status. */
+CAVITY_API int cavity_sync(cavity_t *h);
+
+/* Release everything the handle owns.  NULL is accepted. */
+CAVITY_API int cavity_destroy(cavity_t *h);
+
+/* Static description of a status code. */
+CAVITY_API const char *cavity_strerror(int code);
+
+/* Last error message recorded on a handle (empty string if none). */
+CAVITY_API const char *cavity_last_error(cavity_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDC_CAVITY_H */

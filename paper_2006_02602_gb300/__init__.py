@@ -1,0 +1,296 @@
+"""GB300 (sm_103a) buoyancy-driven-cavity step of Xue & Roy (arXiv 2006.02602).
+
+Thin ctypes binding of the C ABI declared in ``include/cavity.h``: every
+function below has the name of the C entry point it marshals arguments for,
+and every step of the computation runs in the CUDA kernels of
+``libbdc_cavity.so``.  There is no CPU fallback: importing the binding without
+the built library raises, and so does every call that returns an error code.
+
+Build the library with ``python -m paper_2006_02602_gb300.build`` (nvcc,
+``-gencode arch=compute_103a,code=sm_103a``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libbdc_cavity.so")
+
+CAVITY_OK = 0
+CAVITY_ERR_INVALID_ARG = -1
+CAVITY_ERR_OOM = -2
+CAVITY_ERR_CUDA = -3
+CAVITY_ERR_NONFINITE = -4
+CAVITY_ERR_TIMEOUT = -5
+CAVITY_ERR_UNSUPPORTED = -6
+
+CAVITY_FP64 = 0
+CAVITY_FP32_MIXED = 1
+
+CAVITY_FIELD_P, CAVITY_FIELD_U, CAVITY_FIELD_V, CAVITY_FIELD_W, CAVITY_FIELD_T = 1, 2, 4, 8, 16
+CAVITY_FIELD_ALL = 31
+
+EXPORTED = (
+    "cavity_default_params", "cavity_create", "cavity_set_params", "cavity_set_wall_temperature",
+    "cavity_step", "cavity_residual", "cavity_nusselt", "cavity_get_fields", "cavity_set_fields",
+    "cavity_get_time", "cavity_num_blocks", "cavity_get_block_array", "cavity_get_face_buffer",
+    "cavity_exchange", "cavity_time_kernels", "cavity_sync", "cavity_destroy", "cavity_strerror", "cavity_last_error",
+)
+
+
+class CavityError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        self.code = code
+        super().__init__(f"{code}: {msg}")
+
+
+class cavity_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("px", ctypes.c_int), ("py", ctypes.c_int), ("pz", ctypes.c_int),
+                ("precision", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("noise_amp", ctypes.c_double), ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class cavity_params(ctypes.Structure):
+    _fields_ = [("Ra", ctypes.c_double), ("Pr", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("c4", ctypes.c_double), ("u_ref", ctypes.c_double),
+                ("t_inf", ctypes.c_double), ("t_hot", ctypes.c_double), ("t_cold", ctypes.c_double),
+                ("gravity_axis", ctypes.c_int)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libbdc_cavity.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library missing: {path} (build it with python -m paper_2006_02602_gb300.build)")
+    L = ctypes.CDLL(path)
+    sig = {
+        "cavity_default_params": ([ctypes.POINTER(cavity_params)], ctypes.c_int),
+        "cavity_create": ([ctypes.POINTER(cavity_desc), ctypes.POINTER(_H)], ctypes.c_int),
+        "cavity_set_params": ([_H, ctypes.POINTER(cavity_params)], ctypes.c_int),
+        "cavity_set_wall_temperature": ([_H, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+        "cavity_step": ([_H, ctypes.c_int], ctypes.c_int),
+        "cavity_residual": ([_H, _dp], ctypes.c_int),
+        "cavity_nusselt": ([_H, _dp, _dp], ctypes.c_int),
+        "cavity_get_fields": ([_H, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+        "cavity_set_fields": ([_H, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+        "cavity_get_time": ([_H, ctypes.POINTER(ctypes.c_longlong), _dp, _dp], ctypes.c_int),
+        "cavity_num_blocks": ([_H], ctypes.c_int),
+        "cavity_get_block_array": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t,
+                                    ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cavity_get_face_buffer": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+        "cavity_exchange": ([_H], ctypes.c_int),
+        "cavity_time_kernels": ([_H, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_sync": ([_H], ctypes.c_int),
+        "cavity_destroy": ([_H], ctypes.c_int),
+        "cavity_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "cavity_last_error": ([_H], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int, h=None) -> int:
+    if rc < 0:
+        L = load_library()
+        msg = L.cavity_strerror(rc).decode()
+        if h is not None:
+            extra = L.cavity_last_error(h).decode()
+            if extra:
+                msg += f" ({extra})"
+        raise CavityError(rc, msg)
+    return rc
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# -- C-ABI mirrors --------------------------------------------------------------
+
+def cavity_default_params(**overrides) -> cavity_params:
+    p = cavity_params()
+    _check(load_library().cavity_default_params(ctypes.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    if "Ra" in overrides or "Pr" in overrides:
+        if "u_ref" not in overrides:
+            p.u_ref = max(1.0, math.sqrt(p.Ra * p.Pr))
+    if ("t_hot" in overrides or "t_cold" in overrides) and "t_inf" not in overrides:
+        p.t_inf = 0.5 * (p.t_hot + p.t_cold)
+    return p
+
+
+def cavity_create(nx, ny, nz, blocks=(1, 1, 1), precision=CAVITY_FP64, seed=0, noise_amp=0.0,
+                  device=0, stream=None):
+    d = cavity_desc(int(nx), int(ny), int(nz), int(blocks[0]), int(blocks[1]), int(blocks[2]),
+                    int(precision), int(seed), float(noise_amp), int(device), stream)
+    h = _H()
+    _check(load_library().cavity_create(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def cavity_set_params(h, params: cavity_params) -> None:
+    _check(load_library().cavity_set_params(h, ctypes.byref(params)), h)
+
+
+def cavity_set_wall_temperature(h, wall: int, values) -> None:
+    v = _f64(values).reshape(-1)
+    _check(load_library().cavity_set_wall_temperature(h, int(wall), v.ctypes.data_as(_dp), v.size), h)
+
+
+def cavity_step(h, nsteps: int = 1) -> None:
+    _check(load_library().cavity_step(h, int(nsteps)), h)
+
+
+def cavity_residual(h) -> np.ndarray:
+    out = np.zeros(5)
+    _check(load_library().cavity_residual(h, out.ctypes.data_as(_dp)), h)
+    return out
+
+
+def cavity_nusselt(h) -> tuple[float, float]:
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().cavity_nusselt(h, ctypes.byref(a), ctypes.byref(b)), h)
+    return a.value, b.value
+
+
+def _nfields(mask: int) -> int:
+    return bin(mask & CAVITY_FIELD_ALL).count("1")
+
+
+def cavity_get_fields(h, shape: tuple[int, int, int], mask: int = CAVITY_FIELD_ALL) -> np.ndarray:
+    """Interior fields as an array [nf, nz, ny, nx] (shape = (nx, ny, nz))."""
+    nx, ny, nz = shape
+    out = np.empty((_nfields(mask), nz, ny, nx))
+    _check(load_library().cavity_get_fields(h, int(mask), out.ctypes.data_as(_dp), out.size), h)
+    return out
+
+
+def cavity_set_fields(h, values, mask: int = CAVITY_FIELD_ALL) -> None:
+    v = _f64(values)
+    _check(load_library().cavity_set_fields(h, int(mask), v.ctypes.data_as(_dp), v.size), h)
+
+
+def cavity_get_time(h) -> tuple[int, float, float]:
+    s, t, dt = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().cavity_get_time(h, ctypes.byref(s), ctypes.byref(t), ctypes.byref(dt)), h)
+    return s.value, t.value, dt.value
+
+
+def cavity_num_blocks(h) -> int:
+    return _check(load_library().cavity_num_blocks(h), h)
+
+
+def cavity_get_block_array(h, block: int, field: int):
+    """(array [nz+4, ny+4, nx+4] of the block incl. walls/ghosts, (nx, ny, nz, ox, oy, oz))."""
+    dims = (ctypes.c_int * 6)()
+    L = load_library()
+    _check(L.cavity_get_block_array(h, int(block), int(field), None, 0, dims), h)
+    nx, ny, nz = dims[0], dims[1], dims[2]
+    out = np.empty((nz + 4, ny + 4, nx + 4))
+    _check(L.cavity_get_block_array(h, int(block), int(field), out.ctypes.data_as(_dp), out.size, dims), h)
+    return out, tuple(dims)
+
+
+def cavity_get_face_buffer(h, block: int, face: int, nb: int, nc: int) -> np.ndarray:
+    out = np.empty(6 * nb * nc)
+    _check(load_library().cavity_get_face_buffer(h, int(block), int(face), out.ctypes.data_as(_dp), out.size), h)
+    return out
+
+
+def cavity_exchange(h) -> None:
+    _check(load_library().cavity_exchange(h), h)
+
+
+def cavity_time_kernels(h, nsteps: int) -> np.ndarray:
+    """Mean ms per launch of [step, wall/finalise, pack, unpack] over nsteps real steps."""
+    out = np.zeros(4)
+    _check(load_library().cavity_time_kernels(h, int(nsteps), out.ctypes.data_as(_dp)), h)
+    return out
+
+
+def cavity_sync(h) -> int:
+    return load_library().cavity_sync(h)
+
+
+def cavity_destroy(h) -> None:
+    _check(load_library().cavity_destroy(h))
+
+
+def cavity_strerror(code: int) -> str:
+    return load_library().cavity_strerror(int(code)).decode()
+
+
+def cavity_last_error(h) -> str:
+    return load_library().cavity_last_error(h).decode()
+
+
+# -- convenience object -------------------------------------------------------
+
+class Cavity:
+    """Owning wrapper: ``Cavity(32, 32, 32, Ra=1e4, noise_amp=1e-3).step(200)``."""
+
+    def __init__(self, nx, ny, nz, blocks=(1, 1, 1), precision=CAVITY_FP64, seed=0, noise_amp=0.0,
+                 device=0, stream=None, **params):
+        self.shape = (int(nx), int(ny), int(nz))
+        self.h = cavity_create(nx, ny, nz, blocks, precision, seed, noise_amp, device, stream)
+        self.params = cavity_default_params(**params)
+        cavity_set_params(self.h, self.params)
+
+    def step(self, n: int = 1):
+        cavity_step(self.h, n)
+        return self
+
+    def fields(self, mask: int = CAVITY_FIELD_ALL) -> np.ndarray:
+        return cavity_get_fields(self.h, self.shape, mask)
+
+    def set_fields(self, values, mask: int = CAVITY_FIELD_ALL) -> None:
+        cavity_set_fields(self.h, values, mask)
+
+    @property
+    def residual(self) -> np.ndarray:
+        return cavity_residual(self.h)
+
+    @property
+    def nusselt(self) -> tuple[float, float]:
+        return cavity_nusselt(self.h)
+
+    @property
+    def time(self) -> tuple[int, float, float]:
+        return cavity_get_time(self.h)
+
+    def sync(self) -> int:
+        return cavity_sync(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            cavity_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,635 @@
+// Device-side data structures and kernels of the buoyancy-driven-cavity step
+// (Xue & Roy, arXiv 2006.02602).  Shared by the C-ABI translation unit only.
+//
+// Per step, on the handle's stream (one CUDA graph per buffer parity):
+//   k_step      fused residual (Eqs. 1-3) + explicit Euler update of every
+//               interior node of every block, FP64 residual sums and the
+//               spectral-radius max of the new state as per-CTA partials;
+//   k_bc        wall conditions (Section 2) and the hot/cold-wall Nusselt
+//               sums; the last CTA to finish reduces the partials in a
+//               fixed order: residual norms, next dt, centre pressure,
+//               Nusselt numbers, time, step, non-finite flag;
+//   k_pack      cut-face ghost data -> contiguous buffers (Section 4.5,
+//               Listings 1-2, V3): p at depth 2, u, v, w, T at depth 1;
+//   k_unpack    buffers -> the neighbour's ghost layers.
+//
+// Storage: each block holds two buffer sets (ping-pong); a set is NF
+// consecutive padded arrays, x fastest.  Local node (i, j, k), i in
+// [-1, n+2], sits at element (XO1 - 1 + i) + pitch (j + 1) + plane (k + 1)
+// so that node 1 of every row starts on a 32-byte boundary.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bdc {
+
+constexpr int kNF = 5;           // p, u, v, w, T
+constexpr int kMaxCentre = 8;    // 2^3 centre nodes at most
+constexpr int kPartStride = 8;   // doubles per step partial: 5 sums, sr max, pad
+constexpr int kBcThreads = 256;
+
+struct BlockDev {
+  int nx, ny, nz;        // interior nodes of the block
+  int ox, oy, oz;        // global node index = o + local index
+  int pitch;             // elements per row
+  int rows;              // ny + 4
+  long long plane;       // pitch * rows
+  long long fstride;     // elements per field array
+  int wall[6];           // face on a cavity wall (-x, +x, -y, +y, -z, +z)
+  int nbr[6];            // neighbour block across a cut face, -1 on walls
+  int cav;               // cavity this block belongs to
+  int tiles_x, tiles_y, tiles_z;
+  int tile_begin;        // first k_step CTA of this block
+  void *base[2];         // buffer sets (field f at base + f * fstride)
+};
+
+struct CavConst {
+  double h[3], ih[3], ih2[3], ihh[3];
+  double nu, alpha, gs, t_inf, b2min, c4, cfl, diffsr, inv_dT;
+  double inv_nint, inv_nwall;
+  int gaxis;
+  int gn[3];
+  int ncentre;
+  int centre_blk[kMaxCentre];
+  long long centre_off[kMaxCentre];  // element offset of the node in its field array
+  int tile_begin, tile_end;          // k_step CTAs of this cavity
+  int bc_begin, bc_end;              // k_bc CTAs of this cavity
+  long long wall_off;                // offset of this cavity's wall temperatures
+};
+
+struct CavState {
+  double dt;         // dt of the next step
+  double c;          // pending centre-pressure shift of the stored p
+  double t;          // simulated time
+  long long step;    // steps taken
+  double res[5];     // RMS dq/dt of the last step
+  double nu_hot, nu_cold;
+  int flags;         // bit 0: non-finite residual or spectral radius
+  int pad;
+};
+
+struct WallFace {     // one wall face of one block, processed by k_bc
+  int block, face;
+  int n1, n2;         // face interior extents (faster, slower face axis)
+  int cta_begin;      // first k_bc CTA
+  int cav;
+};
+
+struct CutFace {      // one cut face of one block, processed by k_pack / k_unpack
+  int src, face, dst;
+  int nb, nc;         // face extents (faster, slower face axis)
+  int cta_begin;
+  long long buf_off;  // element offset into the exchange buffer
+};
+
+// ---------------------------------------------------------------------------
+// storage traits
+
+template <class S> struct XO;
+template <> struct XO<double> { static constexpr int v = 4; };
+template <> struct XO<float> { static constexpr int v = 8; };
+
+template <class S>
+__device__ __forceinline__ long long node_index(const BlockDev &B, int i, int j, int k) {
+  return (long long)(XO<S>::v - 1 + i) + (long long)B.pitch * (j + 1) + B.plane * (k + 1);
+}
+
+// ---------------------------------------------------------------------------
+// deterministic block reductions (fixed shuffle tree, fixed warp order)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Per-node rates, Eqs. 1-3, FP64.  Star values: c, x-, x+, y-, y+, z-, z+.
+// Rearranged for few FP64 operations: beta^2 eps_d / h_d^4 = c4 lambda_d / h_d,
+// so the continuity rate needs no division.
+
+struct NodeF64 {
+  double p[13];  // c, x-, x+, y-, y+, z-, z+, x-2, x+2, y-2, y+2, z-2, z+2
+  double u[7], v[7], w[7], T[7];
+};
+
+__device__ __forceinline__ void rates_f64(const CavConst &C, const NodeF64 &n, double r[5]) {
+  const double u0 = n.u[0], v0 = n.v[0], w0 = n.w[0];
+  const double b2 = fmax(u0 * u0 + v0 * v0 + w0 * w0, C.b2min);
+  const double f4 = 4.0 * b2;
+  const double lx = 0.5 * (fabs(u0) + sqrt(u0 * u0 + f4));
+  const double ly = 0.5 * (fabs(v0) + sqrt(v0 * v0 + f4));
+  const double lz = 0.5 * (fabs(w0) + sqrt(w0 * w0 + f4));
+  const double p0 = n.p[0];
+  const double d4x = (n.p[8] + n.p[7]) - 4.0 * (n.p[2] + n.p[1]) + 6.0 * p0;
+  const double d4y = (n.p[10] + n.p[9]) - 4.0 * (n.p[4] + n.p[3]) + 6.0 * p0;
+  const double d4z = (n.p[12] + n.p[11]) - 4.0 * (n.p[6] + n.p[5]) + 6.0 * p0;
+  const double diss = C.c4 * (lx * C.ih[0] * d4x + ly * C.ih[1] * d4y + lz * C.ih[2] * d4z);
+  const double divV = (n.u[2] - n.u[1]) * C.ih2[0] + (n.v[4] - n.v[3]) * C.ih2[1] + (n.w[6] - n.w[5]) * C.ih2[2];
+  r[0] = -b2 * divV - diss;
+
+  const double ax = u0 * C.ih2[0], ay = v0 * C.ih2[1], az = w0 * C.ih2[2];
+  const double buoy = C.gs * (n.T[0] - C.t_inf);
+#define BDC_TRANSPORT(q, q0, conv, lap)                                                        \
+  const double conv = ax * (q[2] - q[1]) + ay * (q[4] - q[3]) + az * (q[6] - q[5]);            \
+  const double lap = ((q[2] + q[1]) - 2.0 * q0) * C.ihh[0] + ((q[4] + q[3]) - 2.0 * q0) * C.ihh[1] + \
+                     ((q[6] + q[5]) - 2.0 * q0) * C.ihh[2];
+  BDC_TRANSPORT(n.u, u0, cu, lu)
+  BDC_TRANSPORT(n.v, v0, cv, lv)
+  BDC_TRANSPORT(n.w, w0, cw, lw)
+  BDC_TRANSPORT(n.T, n.T[0], cT, lT)
+#undef BDC_TRANSPORT
+  r[1] = -cu - (n.p[2] - n.p[1]) * C.ih2[0] + C.nu * lu;
+  r[2] = -cv - (n.p[4] - n.p[3]) * C.ih2[1] + C.nu * lv + (C.gaxis == 1 ? buoy : 0.0);
+  r[3] = -cw - (n.p[6] - n.p[5]) * C.ih2[2] + C.nu * lw + (C.gaxis == 2 ? buoy : 0.0);
+  r[4] = -cT + C.alpha * lT;
+}
+
+// spectral-radius bound of one node's state (the dt denominator)
+__device__ __forceinline__ double spectral_f64(const CavConst &C, double u, double v, double w) {
+  const double b2 = fmax(u * u + v * v + w * w, C.b2min);
+  const double f4 = 4.0 * b2;
+  const double sx = fabs(u) + sqrt(u * u + f4);
+  const double sy = fabs(v) + sqrt(v * v + f4);
+  const double sz = fabs(w) + sqrt(w * w + f4);
+  return 0.5 * (sx * C.ih[0] + sy * C.ih[1] + sz * C.ih[2]) + C.diffsr;
+}
+
+// ---------------------------------------------------------------------------
+// k_step, FP64: one thread per (i, j) column of a TX x TY tile, sweeping a
+// chunk of KC planes in k.  The z-neighbours live in register queues
+// (5 deep for p, 3 deep for u, v, w, T); x/y neighbours come through L1.
+
+struct StepArgs {
+  const BlockDev *blocks;
+  int nblocks;
+  const CavConst *cc;
+  const CavState *cs;
+  double *partials;  // [cta][kPartStride]
+  int parity;        // read base[parity], write base[parity ^ 1]
+  int mode;          // 0 = step, 1 = spectral radius of the current state only
+};
+
+__device__ __forceinline__ int find_block(const BlockDev *blocks, int nblocks, int cta) {
+  int lo = 0, hi = nblocks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (blocks[mid].tile_begin <= cta) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int TX, int TY, int KC>
+__global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
+  constexpr int NT = TX * TY;
+  const int cta = blockIdx.x;
+  const int b = find_block(a.blocks, a.nblocks, cta);
+  const BlockDev &B = a.blocks[b];
+  const CavConst &C = a.cc[B.cav];
+  const int t = cta - B.tile_begin;
+  const int tx = t % B.tiles_x, ty = (t / B.tiles_x) % B.tiles_y, tz = t / (B.tiles_x * B.tiles_y);
+  const int i = tx * TX + threadIdx.x + 1;
+  const int j = ty * TY + threadIdx.y + 1;
+  const int k0 = tz * KC + 1;
+  const int k1 = min(k0 + KC - 1, B.nz);
+  const bool active = (i <= B.nx) && (j <= B.ny);
+  const double dt = a.cs[B.cav].dt;
+  const double cshift = a.cs[B.cav].c;
+
+  const double *__restrict__ src = (const double *)B.base[a.parity];
+  double *__restrict__ dst = (double *)B.base[a.parity ^ 1];
+  const long long fs = B.fstride;
+  const double *__restrict__ P = src;
+  const double *__restrict__ U = src + fs;
+  const double *__restrict__ V = src + 2 * fs;
+  const double *__restrict__ W = src + 3 * fs;
+  const double *__restrict__ TT = src + 4 * fs;
+  const long long pl = B.plane, pt = B.pitch;
+
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, smax = 0;
+  if (active) {
+    long long o = node_index<double>(B, i, j, k0);
+    // z queues: p at k-2..k+1, the others at k-1..k
+    double pq0 = __ldg(P + o - 2 * pl), pq1 = __ldg(P + o - pl), pq2 = __ldg(P + o), pq3 = __ldg(P + o + pl);
+    double uq0 = __ldg(U + o - pl), uq1 = __ldg(U + o);
+    double vq0 = __ldg(V + o - pl), vq1 = __ldg(V + o);
+    double wq0 = __ldg(W + o - pl), wq1 = __ldg(W + o);
+    double Tq0 = __ldg(TT + o - pl), Tq1 = __ldg(TT + o);
+    for (int k = k0; k <= k1; ++k, o += pl) {
+      NodeF64 n;
+      const double pq4 = __ldg(P + o + 2 * pl);
+      const double uq2 = __ldg(U + o + pl), vq2 = __ldg(V + o + pl), wq2 = __ldg(W + o + pl), Tq2 = __ldg(TT + o + pl);
+      if (a.mode == 0) {
+        n.p[0] = pq2; n.p[5] = pq1; n.p[6] = pq3; n.p[11] = pq0; n.p[12] = pq4;
+        n.p[1] = __ldg(P + o - 1); n.p[2] = __ldg(P + o + 1);
+        n.p[7] = __ldg(P + o - 2); n.p[8] = __ldg(P + o + 2);
+        n.p[3] = __ldg(P + o - pt); n.p[4] = __ldg(P + o + pt);
+        n.p[9] = __ldg(P + o - 2 * pt); n.p[10] = __ldg(P + o + 2 * pt);
+#define BDC_LOAD7(arr, F, q0, q1, q2)                                           \
+  arr[0] = q1; arr[5] = q0; arr[6] = q2;                                        \
+  arr[1] = __ldg(F + o - 1); arr[2] = __ldg(F + o + 1);                         \
+  arr[3] = __ldg(F + o - pt); arr[4] = __ldg(F + o + pt);
+        BDC_LOAD7(n.u, U, uq0, uq1, uq2)
+        BDC_LOAD7(n.v, V, vq0, vq1, vq2)
+        BDC_LOAD7(n.w, W, wq0, wq1, wq2)
+        BDC_LOAD7(n.T, TT, Tq0, Tq1, Tq2)
+#undef BDC_LOAD7
+        double r[5];
+        rates_f64(C, n, r);
+        const double pn = (pq2 - cshift) + dt * r[0];
+        const double un = uq1 + dt * r[1];
+        const double vn = vq1 + dt * r[2];
+        const double wn = wq1 + dt * r[3];
+        const double Tn = Tq1 + dt * r[4];
+        dst[o] = pn;
+        dst[o + fs] = un;
+        dst[o + 2 * fs] = vn;
+        dst[o + 3 * fs] = wn;
+        dst[o + 4 * fs] = Tn;
+        s0 += r[0] * r[0]; s1 += r[1] * r[1]; s2 += r[2] * r[2]; s3 += r[3] * r[3]; s4 += r[4] * r[4];
+        smax = fmax(smax, spectral_f64(C, un, vn, wn));
+      } else {
+        smax = fmax(smax, spectral_f64(C, uq1, vq1, wq1));
+      }
+      pq0 = pq1; pq1 = pq2; pq2 = pq3; pq3 = pq4;
+      uq0 = uq1; uq1 = uq2; vq0 = vq1; vq1 = vq2; wq0 = wq1; wq1 = wq2; Tq0 = Tq1; Tq1 = Tq2;
+    }
+  }
+  // deterministic CTA reduction of the six partials
+  __shared__ double red[NT / 32][6];
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3); s4 = warp_sum(s4);
+  smax = warp_max(smax);
+  if (lane == 0) {
+    red[wid][0] = s0; red[wid][1] = s1; red[wid][2] = s2; red[wid][3] = s3; red[wid][4] = s4; red[wid][5] = smax;
+  }
+  __syncthreads();
+  if (tid < 6) {
+    double acc = red[0][tid];
+    for (int q = 1; q < NT / 32; ++q) acc = (tid == 5) ? fmax(acc, red[q][tid]) : acc + red[q][tid];
+    a.partials[(long long)cta * kPartStride + tid] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_bc: wall conditions + Nusselt partials; the last CTA finalises.
+
+struct BcArgs {
+  const BlockDev *blocks;
+  const WallFace *faces;
+  int nfaces;
+  const CavConst *cc;
+  CavState *cs;
+  int ncav;
+  const double *step_partials;
+  double *bc_partials;        // [cta][2]
+  unsigned int *counter;
+  const double *t_wall;       // hot walls then cold walls, per cavity at wall_off
+  int parity;                 // buffer set holding the new state
+  int mode;                   // 0 after a step, 1 after init / set_fields
+};
+
+template <class S>
+__device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C, S *base, int face,
+                                           int c1, int c2, const double *t_wall, double &nu_h,
+                                           double &nu_c) {
+  const int axis = face >> 1, high = face & 1;
+  const int n[3] = {B.nx, B.ny, B.nz};
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+  const int w = high ? n[axis] + 1 : 0;
+  const int s = high ? -1 : 1;
+  int iw[3];
+  iw[axis] = w; iw[a1] = c1; iw[a2] = c2;
+  const long long W = node_index<S>(B, iw[0], iw[1], iw[2]);
+  const long long step = axis == 0 ? 1 : (axis == 1 ? (long long)B.pitch : B.plane);
+  const long long N1 = W + s * step, N2 = W + 2 * s * step, G = W - s * step;
+  const long long fs = B.fstride;
+  S *P = base, *U = base + fs, *V = base + 2 * fs, *Wv = base + 3 * fs, *T = base + 4 * fs;
+  U[W] = S(0); V[W] = S(0); Wv[W] = S(0);
+  const double p1 = (double)P[N1], p2 = (double)P[N2];
+  const double pw = 2.0 * p1 - p2;
+  P[W] = (S)pw;
+  P[G] = (S)(2.0 * pw - p1);
+  if (axis == 0) {
+    const int J = B.oy + iw[1], K = B.oz + iw[2];
+    const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
+    const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
+    T[W] = (S)tw;
+    const double T1 = (double)T[N1], T2 = (double)T[N2];
+    const double flux = (3.0 * tw - 4.0 * T1 + T2) * (0.5 * C.ih[0]) * C.inv_dT;
+    if (high) nu_c += -flux; else nu_h += flux;
+  } else {
+    const double T1 = (double)T[N1], T2 = (double)T[N2];
+    T[W] = (S)((4.0 * T1 - T2) / 3.0);
+  }
+}
+
+template <class S>
+__device__ void finalize_cavity(const BcArgs &a, int cv, double *sh) {
+  const CavConst &C = a.cc[cv];
+  CavState &st = a.cs[cv];
+  const int tid = threadIdx.x;
+  // residual sums and spectral max over this cavity's k_step CTAs, fixed order
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int q = C.tile_begin + tid; q < C.tile_end; q += kBcThreads) {
+    const double *pp = a.step_partials + (long long)q * kPartStride;
+    for (int f = 0; f < 5; ++f) acc[f] += pp[f];
+    acc[5] = fmax(acc[5], pp[5]);
+  }
+  double nh = 0, nc = 0;
+  for (int q = C.bc_begin + tid; q < C.bc_end; q += kBcThreads) {
+    nh += a.bc_partials[2LL * q];
+    nc += a.bc_partials[2LL * q + 1];
+  }
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int f = 0; f < 5; ++f) acc[f] = warp_sum(acc[f]);
+  acc[5] = warp_max(acc[5]);
+  nh = warp_sum(nh);
+  nc = warp_sum(nc);
+  __syncthreads();
+  if (lane == 0) {
+    for (int f = 0; f < 6; ++f) sh[wid * 8 + f] = acc[f];
+    sh[wid * 8 + 6] = nh;
+    sh[wid * 8 + 7] = nc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tot[8];
+    for (int f = 0; f < 8; ++f) tot[f] = sh[f];
+    for (int q = 1; q < kBcThreads / 32; ++q)
+      for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], sh[q * 8 + f]) : tot[f] + sh[q * 8 + f];
+    bool bad = !isfinite(tot[5]);
+    if (a.mode == 0) {
+      for (int f = 0; f < 5; ++f) {
+        st.res[f] = sqrt(tot[f] * C.inv_nint);
+        bad = bad || !isfinite(tot[f]);
+      }
+      st.t += st.dt;
+      st.step += 1;
+      // centre pressure of the new state, lexicographic (k, j, i) order
+      double csum = 0.0;
+      for (int m = 0; m < C.ncentre; ++m) {
+        const BlockDev &B = a.blocks[C.centre_blk[m]];
+        const S *Pp = (const S *)B.base[a.parity];
+        csum += (double)Pp[C.centre_off[m]];
+      }
+      st.c = csum / (double)C.ncentre;
+    }
+    st.dt = C.cfl / tot[5];
+    st.nu_hot = tot[6] * C.inv_nwall;
+    st.nu_cold = tot[7] * C.inv_nwall;
+    if (bad) st.flags |= 1;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int find_face(const WallFace *faces, int nfaces, int cta) {
+  int lo = 0, hi = nfaces - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (faces[mid].cta_begin <= cta) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
+  __shared__ double sh[(kBcThreads / 32) * 8];
+  __shared__ bool am_last;
+  const int cta = blockIdx.x, tid = threadIdx.x;
+  double nu_h = 0.0, nu_c = 0.0;
+  if (a.nfaces > 0) {
+    const int fi = find_face(a.faces, a.nfaces, cta);
+    const WallFace &F = a.faces[fi];
+    const int e = (cta - F.cta_begin) * kBcThreads + tid;
+    if (e < F.n1 * F.n2) {
+      const BlockDev &B = a.blocks[F.block];
+      apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
+                    nu_h, nu_c);
+    }
+  }
+  nu_h = warp_sum(nu_h);
+  nu_c = warp_sum(nu_c);
+  if ((tid & 31) == 0) { sh[(tid >> 5) * 2] = nu_h; sh[(tid >> 5) * 2 + 1] = nu_c; }
+  __syncthreads();
+  if (tid == 0) {
+    double h = 0, c = 0;
+    for (int q = 0; q < kBcThreads / 32; ++q) { h += sh[2 * q]; c += sh[2 * q + 1]; }
+    a.bc_partials[2LL * cta] = h;
+    a.bc_partials[2LL * cta + 1] = c;
+    __threadfence();
+    const unsigned int prev = atomicAdd(a.counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int cv = 0; cv < a.ncav; ++cv) finalize_cavity<S>(a, cv, sh);
+  if (tid == 0) *a.counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// k_pack / k_unpack (Section 4.5, Listings 1-2, Optimized V3).  One thread per
+// (ib, ic) face position; buffer layout p[(ic nb + ib) 2 + d], then
+// var[2 nb nc + v nb nc + ic nb + ib].  Depth d counts layers in increasing
+// index order.  Pure copies: bit exact.
+
+struct ExchArgs {
+  const BlockDev *blocks;
+  const CutFace *faces;
+  int nfaces;
+  double *buf;   // FP64 storage: values; FP32 storage: reinterpreted as float
+  int parity;
+};
+
+__device__ __forceinline__ int find_cut(const CutFace *faces, int nfaces, int cta) {
+  int lo = 0, hi = nfaces - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (faces[mid].cta_begin <= cta) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class S>
+__device__ __forceinline__ void face_geometry(const BlockDev &B, int face, int ib, int ic, bool ghost,
+                                              long long &p_first, long long &v_node, long long &dstep) {
+  const int a = face >> 1, high = face & 1;
+  const int n[3] = {B.nx, B.ny, B.nz};
+  const int bb = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+  int idx[3];
+  idx[bb] = ib + 1;
+  idx[cc] = ic + 1;
+  int pl, vl;
+  if (!ghost) { pl = high ? n[a] - 1 : 1; vl = high ? n[a] : 1; }
+  else { pl = high ? n[a] + 1 : -1; vl = high ? n[a] + 1 : 0; }
+  idx[a] = pl;
+  p_first = node_index<S>(B, idx[0], idx[1], idx[2]);
+  idx[a] = vl;
+  v_node = node_index<S>(B, idx[0], idx[1], idx[2]);
+  dstep = a == 0 ? 1 : (a == 1 ? (long long)B.pitch : B.plane);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_pack(ExchArgs a) {
+  const int fi = find_cut(a.faces, a.nfaces, blockIdx.x);
+  const CutFace &F = a.faces[fi];
+  const int e = (blockIdx.x - F.cta_begin) * 256 + threadIdx.x;
+  const int plane = F.nb * F.nc;
+  if (e >= plane) return;
+  const int ib = e % F.nb, ic = e / F.nb;
+  const BlockDev &B = a.blocks[F.src];
+  const S *q = (const S *)B.base[a.parity];
+  long long p_first, v_node, dstep;
+  face_geometry<S>(B, F.face, ib, ic, false, p_first, v_node, dstep);
+  S *buf = (S *)a.buf + F.buf_off;
+  buf[2LL * e] = q[p_first];
+  buf[2LL * e + 1] = q[p_first + dstep];
+  for (int v = 0; v < 4; ++v) buf[2LL * plane + (long long)v * plane + e] = q[(long long)(v + 1) * B.fstride + v_node];
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_unpack(ExchArgs a) {
+  const int fi = find_cut(a.faces, a.nfaces, blockIdx.x);
+  const CutFace &F = a.faces[fi];
+  const int e = (blockIdx.x - F.cta_begin) * 256 + threadIdx.x;
+  const int plane = F.nb * F.nc;
+  if (e >= plane) return;
+  const int ib = e % F.nb, ic = e / F.nb;
+  const BlockDev &B = a.blocks[F.dst];
+  S *q = (S *)B.base[a.parity];
+  long long p_first, v_node, dstep;
+  face_geometry<S>(B, F.face ^ 1, ib, ic, true, p_first, v_node, dstep);
+  const S *buf = (const S *)a.buf + F.buf_off;
+  q[p_first] = buf[2LL * e];
+  q[p_first + dstep] = buf[2LL * e + 1];
+  for (int v = 0; v < 4; ++v) q[(long long)(v + 1) * B.fstride + v_node] = buf[2LL * plane + (long long)v * plane + e];
+}
+
+// ---------------------------------------------------------------------------
+// initial state, gather / scatter of the interior
+
+// splitmix64 (Steele, Lea & Flood 2014): finaliser of state x + golden gamma
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+struct InitArgs {
+  const BlockDev *blocks;
+  const CavConst *cc;
+  int block;
+  int parity;
+  unsigned long long seed;
+  double noise;
+  double t_hot, t_cold;
+};
+
+template <class S>
+__global__ void k_init(InitArgs a) {
+  const BlockDev &B = a.blocks[a.block];
+  const long long n = (long long)B.nx * B.ny * B.nz;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int i = (int)(e % B.nx) + 1, j = (int)((e / B.nx) % B.ny) + 1, k = (int)(e / ((long long)B.nx * B.ny)) + 1;
+  const CavConst &C = a.cc[B.cav];
+  const int I = B.ox + i, J = B.oy + j, K = B.oz + k;
+  const uint64_t gidx = (uint64_t)(I - 1) + (uint64_t)C.gn[0] * ((uint64_t)(J - 1) + (uint64_t)C.gn[1] * (uint64_t)(K - 1));
+  const double U = (double)(splitmix64(a.seed * (1ULL << 40) + gidx) >> 11) * (1.0 / 9007199254740992.0);
+  // explicit round-to-nearest operations (no contraction): the initial state is
+  // reproducible bit for bit by any IEEE implementation of the same formula
+  const double x = __dmul_rn((double)I, C.h[0]);
+  const double lin = __dadd_rn(a.t_hot, __dmul_rn(__dsub_rn(a.t_cold, a.t_hot), x));
+  const double pert = __dmul_rn(a.noise, __dsub_rn(__dmul_rn(2.0, U), 1.0));
+  S *T = (S *)B.base[a.parity] + 4 * B.fstride;
+  T[node_index<S>(B, i, j, k)] = (S)__dadd_rn(lin, pert);
+}
+
+struct MoveArgs {
+  const BlockDev *blocks;
+  int block;
+  int parity;
+  int mask;
+  int gn[3];
+  double *stage;       // [nf][gnz][gny][gnx] FP64, fields of the mask in order
+  double pshift;       // subtracted from p on gather
+};
+
+template <class S>
+__global__ void k_gather(MoveArgs a) {
+  const BlockDev &B = a.blocks[a.block];
+  const long long n = (long long)B.nx * B.ny * B.nz;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int i = (int)(e % B.nx) + 1, j = (int)((e / B.nx) % B.ny) + 1, k = (int)(e / ((long long)B.nx * B.ny)) + 1;
+  const long long g = (long long)(B.ox + i - 1) + (long long)a.gn[0] * ((B.oy + j - 1) + (long long)a.gn[1] * (B.oz + k - 1));
+  const long long gN = (long long)a.gn[0] * a.gn[1] * a.gn[2];
+  const S *q = (const S *)B.base[a.parity];
+  const long long o = node_index<S>(B, i, j, k);
+  int slot = 0;
+  for (int f = 0; f < kNF; ++f) {
+    if (!(a.mask & (1 << f))) continue;
+    double v = (double)q[f * B.fstride + o];
+    if (f == 0) v -= a.pshift;
+    a.stage[slot * gN + g] = v;
+    ++slot;
+  }
+}
+
+template <class S>
+__global__ void k_scatter(MoveArgs a) {
+  const BlockDev &B = a.blocks[a.block];
+  const long long n = (long long)B.nx * B.ny * B.nz;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int i = (int)(e % B.nx) + 1, j = (int)((e / B.nx) % B.ny) + 1, k = (int)(e / ((long long)B.nx * B.ny)) + 1;
+  const long long g = (long long)(B.ox + i - 1) + (long long)a.gn[0] * ((B.oy + j - 1) + (long long)a.gn[1] * (B.oz + k - 1));
+  const long long gN = (long long)a.gn[0] * a.gn[1] * a.gn[2];
+  S *q = (S *)B.base[a.parity];
+  const long long o = node_index<S>(B, i, j, k);
+  int slot = 0;
+  for (int f = 0; f < kNF; ++f) {
+    if (!(a.mask & (1 << f))) continue;
+    q[f * B.fstride + o] = (S)a.stage[slot * gN + g];
+    ++slot;
+  }
+}
+
+// p of the stored state is p_true + c: fold a pending shift into the array
+// (used before overwriting other fields from the host, so that c can be reset)
+template <class S>
+__global__ void k_shift_p(const BlockDev *blocks, int block, int parity, double c) {
+  const BlockDev &B = blocks[block];
+  const long long n = (long long)(B.nx + 4) * (B.ny + 4) * (B.nz + 4);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int i = (int)(e % (B.nx + 4)) - 1, j = (int)((e / (B.nx + 4)) % (B.ny + 4)) - 1;
+  const int k = (int)(e / ((long long)(B.nx + 4) * (B.ny + 4))) - 1;
+  S *q = (S *)B.base[parity];
+  const long long o = node_index<S>(B, i, j, k);
+  q[o] = (S)((double)q[o] - c);
+}
+
+// copy of a whole block array (walls and ghosts included) to a dense stage
+template <class S>
+__global__ void k_copy_block(const BlockDev *blocks, int block, int parity, int field, double *stage) {
+  const BlockDev &B = blocks[block];
+  const long long n = (long long)(B.nx + 4) * (B.ny + 4) * (B.nz + 4);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int i = (int)(e % (B.nx + 4)) - 1, j = (int)((e / (B.nx + 4)) % (B.ny + 4)) - 1;
+  const int k = (int)(e / ((long long)(B.nx + 4) * (B.ny + 4))) - 1;
+  const S *q = (const S *)B.base[parity];
+  stage[e] = (double)q[field * B.fstride + node_index<S>(B, i, j, k)];
+}
+
+}  // namespace bdc

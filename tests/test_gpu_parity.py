@@ -1,0 +1,253 @@
+"""GPU (sm_103a) FP64 step against the FP64 oracle, through the C ABI.
+
+Tolerances: fields <= 1e-12 relative max-norm per field (FP64 form), Nusselt
+and dt <= 1e-12 relative, residual norms <= 1e-10 relative (sums in another
+order); initial state and pack/unpack bit exact; decompositions bit exact
+against the single block.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_02602_gb300 import build
+    build.build()
+    import paper_2006_02602_gb300 as mod
+    mod.load_library()
+    return mod
+
+
+def relmax(a, b):
+    s = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / (s if s > 0 else 1.0)
+
+
+def assert_fields_close(g, o, tol, what=""):
+    for f, name in enumerate(oracle.FIELDS):
+        e = relmax(g[f], o[f])
+        assert e <= tol, f"{what} field {name}: rel max err {e:.3e} > {tol:.1e}"
+
+
+def run_pair(m, n, Ra, steps, blocks=(1, 1, 1), noise=1e-3, seed=0, **kw):
+    o = oracle.OracleCavity(*n, dict(Ra=Ra, **kw), noise=noise, seed=seed)
+    c = m.Cavity(*n, blocks=blocks, seed=seed, noise_amp=noise, Ra=Ra, **kw)
+    o.step(steps)
+    c.step(steps)
+    return o, c
+
+
+# ---------------------------------------------------------------------------
+def test_initial_state_bit_exact(m):
+    n = (37, 21, 18)
+    o = oracle.OracleCavity(*n, dict(Ra=1e4), noise=1e-3, seed=5)
+    with m.Cavity(*n, seed=5, noise_amp=1e-3, Ra=1e4) as c:
+        assert np.array_equal(c.fields(), o.fields())
+        s, t, dt = c.time
+        assert s == 0 and t == 0.0
+        assert dt == pytest.approx(o.p["cfl"] / o.spectral_max(), rel=1e-14)
+        h, cold = c.nusselt
+        assert h == pytest.approx(o.nusselt[0], rel=1e-12)
+        assert cold == pytest.approx(o.nusselt[1], rel=1e-12)
+
+
+def test_config1_32cube_200_steps(m):
+    cfg = workloads.CFG1
+    o, c = run_pair(m, cfg["n"], cfg["Ra"], cfg["steps"], noise=cfg["noise"], seed=cfg["seed"], Pr=cfg["Pr"])
+    with c:
+        assert_fields_close(c.fields(), o.fields(), FP64_TOL, "cfg1")
+        assert np.allclose(c.residual, o.residual, rtol=1e-10, atol=0)
+        h, cold = c.nusselt
+        assert abs(h - o.nusselt[0]) <= FP64_TOL * abs(o.nusselt[0])
+        assert abs(cold - o.nusselt[1]) <= FP64_TOL * abs(o.nusselt[1])
+        s, t, dt = c.time
+        assert s == 200
+        assert t == pytest.approx(o.t, rel=1e-13)
+        assert dt == pytest.approx(o.p["cfl"] / o.spectral_max(), rel=1e-13)
+
+
+@pytest.mark.parametrize("n", [(37, 21, 18), (2, 2, 2), (3, 40, 5), (65, 9, 33)])
+def test_ragged_and_degenerate_sizes(m, n):
+    o, c = run_pair(m, n, 3e4, 25, noise=1e-3, seed=11)
+    with c:
+        assert_fields_close(c.fields(), o.fields(), FP64_TOL, f"n={n}")
+        assert np.allclose(c.residual, o.residual, rtol=1e-10, atol=1e-300)
+
+
+@pytest.mark.parametrize("gaxis", [1, 2])
+def test_gravity_axis_and_params(m, gaxis):
+    kw = dict(gravity_axis=gaxis, Pr=2.0, cfl=0.4, kappa=0.2, c4=0.05, t_hot=2.0, t_cold=0.5)
+    o, c = run_pair(m, (20, 24, 22), 2e4, 40, noise=1e-3, seed=2, **kw)
+    with c:
+        assert_fields_close(c.fields(), o.fields(), FP64_TOL, f"g={gaxis}")
+
+
+def test_zero_steps_is_noop(m):
+    with m.Cavity(12, 10, 8, seed=1, noise_amp=1e-3, Ra=1e4) as c:
+        f0 = c.fields()
+        c.step(0)
+        assert np.array_equal(c.fields(), f0)
+        assert c.time[0] == 0
+
+
+def test_conduction_state_fixed_point(m):
+    with m.Cavity(24, 20, 16, noise_amp=0.0, Ra=0.0) as c:
+        f0 = c.fields()
+        c.step(50)
+        f = c.fields()
+        assert np.max(np.abs(f[1:4])) < 1e-9
+        assert np.max(np.abs(f[4] - f0[4])) < 1e-12
+        h, cold = c.nusselt
+        assert h == pytest.approx(1.0, abs=1e-10) and cold == pytest.approx(1.0, abs=1e-10)
+
+
+def test_set_fields_then_step(m):
+    n = (28, 22, 19)
+    q = workloads.smooth_state(n, seed=3)
+    o = oracle.OracleCavity(*n, dict(Ra=5e4))
+    o.set_fields(q)
+    with m.Cavity(*n, Ra=5e4) as c:
+        c.set_fields(q)
+        assert np.array_equal(c.fields(), q)
+        o.step(30)
+        c.step(30)
+        assert_fields_close(c.fields(), o.fields(), FP64_TOL, "set_fields")
+        # partial masks: p alone and T alone round-trip, others untouched
+        f = c.fields()
+        c.set_fields(q[0:1], mask=m.CAVITY_FIELD_P)
+        g = c.fields()
+        assert np.array_equal(g[0], q[0]) and np.array_equal(g[1:], f[1:])
+
+
+def test_wall_temperature_field(m):
+    n = (20, 18, 16)
+    th = workloads.wall_temperature(n[1], n[2], seed=4)
+    o = oracle.OracleCavity(*n, dict(Ra=1e5), noise=1e-3, seed=0, t_hot_wall=th)
+    with m.Cavity(*n, seed=0, noise_amp=1e-3, Ra=1e5) as c:
+        m.cavity_set_wall_temperature(c.h, 0, th)
+        h0, _ = c.nusselt
+        assert h0 == pytest.approx(o.nusselt[0], rel=1e-12)
+        o.step(40)
+        c.step(40)
+        assert_fields_close(c.fields(), o.fields(), FP64_TOL, "wall T")
+        assert c.nusselt[0] == pytest.approx(o.nusselt[0], rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# decomposition: bit exact against one block; ghosts and buffers vs brute force
+
+DECOMPS = [(8, 1, 1), (4, 2, 1), (2, 2, 2), (1, 1, 8), (3, 2, 2)]
+
+
+@pytest.fixture(scope="module")
+def single_48(m):
+    c = m.Cavity(48, 40, 44, seed=9, noise_amp=1e-3, Ra=1e5)
+    c.step(60)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("blocks", DECOMPS)
+def test_blocks_bit_identical(m, single_48, blocks):
+    with m.Cavity(48, 40, 44, blocks=blocks, seed=9, noise_amp=1e-3, Ra=1e5) as c:
+        assert m.cavity_num_blocks(c.h) == blocks[0] * blocks[1] * blocks[2]
+        c.step(60)
+        assert np.array_equal(c.fields(), single_48.fields())
+        assert c.time == single_48.time
+        assert np.allclose(c.residual, single_48.residual, rtol=1e-13)
+
+
+def test_blocks_match_oracle(m):
+    n = (30, 26, 22)
+    o = oracle.OracleCavity(*n, dict(Ra=1e5), blocks=(2, 2, 2), noise=1e-3, seed=3)
+    with m.Cavity(*n, blocks=(2, 2, 2), seed=3, noise_amp=1e-3, Ra=1e5) as c:
+        o.step(20)
+        c.step(20)
+        assert_fields_close(c.fields(), o.fields(), FP64_TOL, "2x2x2")
+
+
+@pytest.mark.parametrize("blocks", [(2, 2, 2), (4, 2, 1), (8, 1, 1)])
+def test_ghosts_and_buffers_bit_exact(m, single_48, blocks):
+    """Every ghost layer equals the single-block array at the same global node,
+    and every face buffer equals a brute-force read of the sending block."""
+    with m.Cavity(48, 40, 44, blocks=blocks, seed=9, noise_amp=1e-3, Ra=1e5) as c:
+        c.step(60)
+        G = [m.cavity_get_block_array(single_48.h, 0, f)[0] for f in range(5)]
+        nb_total = m.cavity_num_blocks(c.h)
+        arrays = [[m.cavity_get_block_array(c.h, b, f)[0] for f in range(5)] for b in range(nb_total)]
+        dims = [m.cavity_get_block_array(c.h, b, 0)[1] for b in range(nb_total)]
+        ncut = 0
+        for b in range(nb_total):
+            nx, ny, nz, ox, oy, oz = dims[b]
+            n, org = (nx, ny, nz), (ox, oy, oz)
+            for face in range(6):
+                a, hi = face // 2, face % 2
+                coords = [b % blocks[0], (b // blocks[0]) % blocks[1], b // (blocks[0] * blocks[1])]
+                nbc = coords[a] + (1 if hi else -1)
+                if not (0 <= nbc < blocks[a]):
+                    with pytest.raises(m.CavityError):
+                        m.cavity_get_face_buffer(c.h, b, face, 1, 1)
+                    continue
+                ncut += 1
+                # ghosts of this face (filled by the neighbour's pack + this unpack)
+                layers_p = [n[a] + 1, n[a] + 2] if hi else [-1, 0]
+                layers_v = [n[a] + 1] if hi else [0]
+                for f in range(5):
+                    for L in (layers_p if f == 0 else layers_v):
+                        idx = [slice(2, 2 + n[d]) for d in range(3)]
+                        gidx = [slice(org[d] + 2, org[d] + 2 + n[d]) for d in range(3)]
+                        idx[a] = L + 1
+                        gidx[a] = org[a] + L + 1
+                        mine = arrays[b][f][idx[2], idx[1], idx[0]]
+                        glob = G[f][gidx[2], gidx[1], gidx[0]]
+                        assert np.array_equal(mine, glob), (b, face, f, L)
+                # the face buffer this block packed, vs its own array
+                bax, cax = [d for d in range(3) if d != a]
+                nb, nc = n[bax], n[cax]
+                buf = m.cavity_get_face_buffer(c.h, b, face, nb, nc)
+                A = arrays[b]
+                exp = np.empty(6 * nb * nc)
+                for d in range(2):
+                    idx = [slice(2, 2 + n[0]), slice(2, 2 + n[1]), slice(2, 2 + n[2])]
+                    idx[a] = (n[a] - 1 + d if hi else 1 + d) + 1
+                    layer = A[0][idx[2], idx[1], idx[0]]  # [c, b]: flat index ic*nb + ib
+                    exp[d:2 * nb * nc:2] = layer.reshape(-1)
+                for v in range(4):
+                    idx = [slice(2, 2 + n[0]), slice(2, 2 + n[1]), slice(2, 2 + n[2])]
+                    idx[a] = (n[a] if hi else 1) + 1
+                    layer = A[1 + v][idx[2], idx[1], idx[0]]
+                    exp[2 * nb * nc + v * nb * nc: 2 * nb * nc + (v + 1) * nb * nc] = layer.reshape(-1)
+                assert np.array_equal(buf, exp), (b, face)
+        assert ncut > 0
+
+
+# ---------------------------------------------------------------------------
+def test_invalid_arguments_and_nonfinite(m):
+    with m.Cavity(10, 10, 10, Ra=1e4) as c:
+        with pytest.raises(m.CavityError) as e:
+            m.cavity_get_fields(c.h, (10, 10, 11))
+        assert e.value.code == m.CAVITY_ERR_INVALID_ARG
+        bad = m.cavity_default_params(Ra=1e4, gravity_axis=0)
+        with pytest.raises(m.CavityError):
+            m.cavity_set_params(c.h, bad)
+        with pytest.raises(m.CavityError):
+            m.cavity_step(c.h, -1)
+        # host-side injection of a non-finite value: the step flags it
+        q = c.fields()
+        q[1, 5, 5, 5] = np.inf
+        c.set_fields(q)
+        c.step(1)
+        with pytest.raises(m.CavityError) as e:
+            c.residual
+        assert e.value.code == m.CAVITY_ERR_NONFINITE
+        assert c.sync() == m.CAVITY_ERR_NONFINITE
