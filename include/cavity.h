@@ -172,6 +172,42 @@ CAVITY_API int cavity_exchange(cavity_t *h);
  * run).  The steps are real steps of the state. */
 CAVITY_API int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]);
 
+/* Allocation-free step of one caller-held block.  The paper has no
+ * counterpart; this exists for callers that must not call cudaMalloc, such as
+ * code running inside another framework's caching allocator or a fixed,
+ * pre-sized memory arena, where a driver allocation behind the allocator's
+ * back would break its accounting and its out-of-memory handling.
+ *
+ * Runs the fused residual + explicit-update kernel (the one cavity_step uses)
+ * once over a single block whose walls and ghosts the caller has already
+ * filled, then reduces the rates:
+ *  q_in   device, 5 fields (p, u, v, w, T) one after another, each a dense
+ *         (nz+4)(ny+4)(nx+4) FP64 array over local nodes -1 .. n+2 with x
+ *         fastest (the layout cavity_get_block_array returns); read only;
+ *  q_out  device, same layout, distinct from q_in; the interior nodes are
+ *         written (p_new = p - pshift + dt dp/dt, q_new = q + dt dq/dt),
+ *         walls and ghosts are left untouched;
+ *  p      parameters (defaults resolved as in cavity_set_params);
+ *  dt     the time step; pshift a pending centre-pressure shift (0 if none);
+ *  out6   device, 6 doubles: RMS dq/dt of p, u, v, w, T and the next dt;
+ *  stream cudaStream_t (NULL = the legacy default stream); the call only
+ *         enqueues work.
+ * Nothing is allocated: the per-CTA reduction partials and the kernel
+ * descriptors live in one fixed array compiled into the library, about
+ * 1 MiB, held on every GPU that loads the library until the process exits.
+ * Limit: ceil(nx/32) ceil(ny/8) ceil(nz/16) <= CAVITY_NOALLOC_MAX_TILES
+ * (e.g. 256^3 fits, 512^3 does not); larger blocks return
+ * CAVITY_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (each call rewrites all it reads): calls
+ * that overlap on the GPU (other streams, other threads) race and must not
+ * be issued. */
+#define CAVITY_NOALLOC_MAX_TILES 16384
+CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *q_out, int nx, int ny, int nz,
+                                         const cavity_params *p, double dt, double pshift, double *out6,
+                                         void *stream);
+
 /* Synchronise the handle's stream; returns the sticky non-finite status. */
 CAVITY_API int cavity_sync(cavity_t *h);
 

@@ -38,7 +38,8 @@ EXPORTED = (
     "cavity_default_params", "cavity_create", "cavity_set_params", "cavity_set_wall_temperature",
     "cavity_step", "cavity_residual", "cavity_nusselt", "cavity_get_fields", "cavity_set_fields",
     "cavity_get_time", "cavity_num_blocks", "cavity_get_block_array", "cavity_get_face_buffer",
-    "cavity_exchange", "cavity_time_kernels", "cavity_sync", "cavity_destroy", "cavity_strerror", "cavity_last_error",
+    "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
+    "cavity_strerror", "cavity_last_error",
 )
 
 
@@ -92,6 +93,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_get_face_buffer": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
         "cavity_exchange": ([_H], ctypes.c_int),
         "cavity_time_kernels": ([_H, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_step_block_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(cavity_params), ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
         "cavity_sync": ([_H], ctypes.c_int),
         "cavity_destroy": ([_H], ctypes.c_int),
         "cavity_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -223,6 +227,17 @@ def cavity_time_kernels(h, nsteps: int) -> np.ndarray:
     out = np.zeros(4)
     _check(load_library().cavity_time_kernels(h, int(nsteps), out.ctypes.data_as(_dp)), h)
     return out
+
+
+def cavity_step_block_noalloc(q_in_ptr: int, q_out_ptr: int, shape, params: cavity_params, dt: float,
+                              pshift: float, out6_ptr: int, stream=None) -> None:
+    """Allocation-free fused step of one caller-held block (device pointers
+    given as integers, e.g. tensor.data_ptr()); for callers that must not
+    allocate device memory.  See include/cavity.h."""
+    nx, ny, nz = shape
+    _check(load_library().cavity_step_block_noalloc(q_in_ptr, q_out_ptr, int(nx), int(ny), int(nz),
+                                                    ctypes.byref(params), float(dt), float(pshift),
+                                                    out6_ptr, stream))
 
 
 def cavity_sync(h) -> int:

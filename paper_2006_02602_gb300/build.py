@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libbdc_cavity.so")
-SOURCES = [os.path.join(CSRC, "cavity_capi.cu")]
+SOURCES = [os.path.join(CSRC, "cavity_capi.cu"), os.path.join(CSRC, "noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(ROOT, "include", "cavity.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
