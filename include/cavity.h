@@ -138,6 +138,13 @@ CAVITY_API int cavity_nusselt(cavity_t *h, double *hot, double *cold);
  * widened, the p pair summed).  count must equal popcount(mask)*nx*ny*nz. */
 CAVITY_API int cavity_get_fields(cavity_t *h, int field_mask, double *host, size_t count);
 
+/* Copy a box of interior nodes (global 1-based node ranges i0 .. i0+ni-1,
+ * j0 .. j0+nj-1, k0 .. k0+nk-1) of the fields in the mask to host, FP64,
+ * ordered (f, k, j, i); count must equal popcount(mask)*ni*nj*nk.  For
+ * probes and sampled checks of cavities too large to copy whole. */
+CAVITY_API int cavity_get_fields_box(cavity_t *h, int field_mask, int i0, int j0, int k0, int ni, int nj, int nk,
+                                     double *host, size_t count);
+
 /* Overwrite interior fields from host (layout as cavity_get_fields), then
  * re-apply walls, exchange ghosts and recompute dt.  Step count and time
  * are kept. */

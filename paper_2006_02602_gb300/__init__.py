@@ -36,7 +36,8 @@ CAVITY_FIELD_ALL = 31
 
 EXPORTED = (
     "cavity_default_params", "cavity_create", "cavity_set_params", "cavity_set_wall_temperature",
-    "cavity_step", "cavity_residual", "cavity_nusselt", "cavity_get_fields", "cavity_set_fields",
+    "cavity_step", "cavity_residual", "cavity_nusselt", "cavity_get_fields", "cavity_get_fields_box",
+    "cavity_set_fields",
     "cavity_get_time", "cavity_num_blocks", "cavity_get_block_array", "cavity_get_face_buffer",
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
     "cavity_strerror", "cavity_last_error",
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_residual": ([_H, _dp], ctypes.c_int),
         "cavity_nusselt": ([_H, _dp, _dp], ctypes.c_int),
         "cavity_get_fields": ([_H, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+        "cavity_get_fields_box": ([_H, ctypes.c_int] + [ctypes.c_int] * 6 + [_dp, ctypes.c_size_t], ctypes.c_int),
         "cavity_set_fields": ([_H, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
         "cavity_get_time": ([_H, ctypes.POINTER(ctypes.c_longlong), _dp, _dp], ctypes.c_int),
         "cavity_num_blocks": ([_H], ctypes.c_int),
@@ -183,6 +185,16 @@ def cavity_get_fields(h, shape: tuple[int, int, int], mask: int = CAVITY_FIELD_A
     nx, ny, nz = shape
     out = np.empty((_nfields(mask), nz, ny, nx))
     _check(load_library().cavity_get_fields(h, int(mask), out.ctypes.data_as(_dp), out.size), h)
+    return out
+
+
+def cavity_get_fields_box(h, lo: tuple[int, int, int], size: tuple[int, int, int],
+                          mask: int = CAVITY_FIELD_ALL) -> np.ndarray:
+    """Fields on the global 1-based node box lo .. lo+size-1 as [nf, nk, nj, ni]."""
+    (i0, j0, k0), (ni, nj, nk) = lo, size
+    out = np.empty((_nfields(mask), nk, nj, ni))
+    _check(load_library().cavity_get_fields_box(h, int(mask), int(i0), int(j0), int(k0), int(ni), int(nj), int(nk),
+                                                out.ctypes.data_as(_dp), out.size), h)
     return out
 
 

@@ -585,6 +585,39 @@ __global__ void k_gather(MoveArgs a) {
   }
 }
 
+struct BoxArgs {
+  const BlockDev *blocks;
+  int nblocks;
+  int parity;
+  int mask;
+  int i0, j0, k0, ni, nj, nk;  // global 1-based node box
+  double *stage;               // [nf][nk][nj][ni]
+  double pshift;
+};
+
+template <class S>
+__global__ void k_gather_box(BoxArgs a) {
+  const long long n = (long long)a.ni * a.nj * a.nk;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int I = a.i0 + (int)(e % a.ni), J = a.j0 + (int)((e / a.ni) % a.nj), K = a.k0 + (int)(e / ((long long)a.ni * a.nj));
+  for (int b = 0; b < a.nblocks; ++b) {
+    const BlockDev &B = a.blocks[b];
+    if (I <= B.ox || I > B.ox + B.nx || J <= B.oy || J > B.oy + B.ny || K <= B.oz || K > B.oz + B.nz) continue;
+    const S *q = (const S *)B.base[a.parity];
+    const long long o = node_index<S>(B, I - B.ox, J - B.oy, K - B.oz);
+    int slot = 0;
+    for (int f = 0; f < kNF; ++f) {
+      if (!(a.mask & (1 << f))) continue;
+      double v = (double)q[f * B.fstride + o];
+      if (f == 0) v -= a.pshift;
+      a.stage[slot * n + e] = v;
+      ++slot;
+    }
+    return;
+  }
+}
+
 template <class S>
 __global__ void k_scatter(MoveArgs a) {
   const BlockDev &B = a.blocks[a.block];

@@ -368,12 +368,17 @@ int init_state(cavity *h) {
   return refresh_state(h);
 }
 
-int ensure_stage(cavity *h) {
-  if (h->d_stage) return CAVITY_OK;
-  size_t n = (size_t)kNF * h->desc.nx * h->desc.ny * h->desc.nz;
-  for (const BlockDev &B : h->hb) n = std::max(n, (size_t)(B.nx + 4) * (B.ny + 4) * (B.nz + 4));
-  h->stage_elems = n;
+// device staging buffer of at least n doubles for host transfers (grown on demand)
+int ensure_stage(cavity *h, size_t n) {
+  if (h->d_stage && h->stage_elems >= n) return CAVITY_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->d_stage) {
+    cudaFree(h->d_stage);
+    h->d_stage = nullptr;
+    h->stage_elems = 0;
+  }
   CK(cudaMalloc(&h->d_stage, n * sizeof(double)));
+  h->stage_elems = n;
   return CAVITY_OK;
 }
 
@@ -535,7 +540,7 @@ int cavity_get_fields(cavity_t *h, int mask, double *host, size_t count) {
   const size_t N = (size_t)h->desc.nx * h->desc.ny * h->desc.nz;
   if (count != (size_t)popcount5(mask) * N) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
   DeviceGuard g(h->dev);
-  int rc = ensure_stage(h);
+  int rc = ensure_stage(h, count);
   if (rc != CAVITY_OK) return rc;
   CavState st;
   rc = read_state(h, &st);
@@ -551,12 +556,34 @@ int cavity_get_fields(cavity_t *h, int mask, double *host, size_t count) {
   return CAVITY_OK;
 }
 
+int cavity_get_fields_box(cavity_t *h, int mask, int i0, int j0, int k0, int ni, int nj, int nk, double *host,
+                          size_t count) {
+  if (!h || !host || mask <= 0 || mask > CAVITY_FIELD_ALL) return CAVITY_ERR_INVALID_ARG;
+  if (ni < 1 || nj < 1 || nk < 1 || i0 < 1 || j0 < 1 || k0 < 1 || i0 + ni - 1 > h->desc.nx ||
+      j0 + nj - 1 > h->desc.ny || k0 + nk - 1 > h->desc.nz)
+    return fail(h, CAVITY_ERR_INVALID_ARG, "box outside the interior");
+  const size_t n = (size_t)ni * nj * nk;
+  if (count != (size_t)popcount5(mask) * n) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
+  DeviceGuard g(h->dev);
+  int rc = ensure_stage(h, count);
+  if (rc != CAVITY_OK) return rc;
+  CavState st;
+  rc = read_state(h, &st);
+  if (rc != CAVITY_OK) return rc;
+  BoxArgs a{h->d_blocks, h->nblocks, h->parity, mask, i0, j0, k0, ni, nj, nk, h->d_stage, st.c};
+  k_gather_box<double><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(a);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(host, h->d_stage, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CAVITY_OK;
+}
+
 int cavity_set_fields(cavity_t *h, int mask, const double *host, size_t count) {
   if (!h || !host || mask <= 0 || mask > CAVITY_FIELD_ALL) return CAVITY_ERR_INVALID_ARG;
   const size_t N = (size_t)h->desc.nx * h->desc.ny * h->desc.nz;
   if (count != (size_t)popcount5(mask) * N) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
   DeviceGuard g(h->dev);
-  int rc = ensure_stage(h);
+  int rc = ensure_stage(h, count);
   if (rc != CAVITY_OK) return rc;
   CavState st;
   rc = read_state(h, &st);
@@ -594,7 +621,7 @@ int cavity_get_block_array(cavity_t *h, int block, int field, double *host, size
   if (!host) return count == 0 ? CAVITY_OK : CAVITY_ERR_INVALID_ARG;
   if (count != n) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
   DeviceGuard g(h->dev);
-  int rc = ensure_stage(h);
+  int rc = ensure_stage(h, count);
   if (rc != CAVITY_OK) return rc;
   k_copy_block<double><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(h->d_blocks, block, h->parity, field, h->d_stage);
   CK(cudaGetLastError());
