@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the buoyancy-driven-cavity step on GB300.
 
-Workload (default): the 128^3 cavity at Ra 1e5, Pr 0.71, initial T linear in
+Headline workload: the 128^3 cavity at Ra 1e5, Pr 0.71, initial T linear in
 x plus U(-1e-3, 1e-3) noise (seed 0), split on one GPU into 2x2x2 blocks that
-exchange ghost faces every step; FP64.  One bench step = one explicit step of
-the whole hot path: fused residual + update with residual / spectral-radius
-reductions, wall conditions + finalise (dt, centre pressure, Nusselt), face
-pack and unpack.  Metric: grid-point updates per second (interior nodes x
-steps / time), whole job.
+exchange ghost faces every step, FP64.  One bench step = one explicit step
+of the whole hot path: fused residual + update with residual /
+spectral-radius reductions, wall conditions + finalise (dt, centre pressure,
+Nusselt), face pack and unpack.  Metric: grid-point updates per second
+(interior nodes x steps / time), whole job.  The same line carries the
+FP32-mixed form of the same workload and of the 256^3, Ra 1e6 cavity as
+"variants".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64|fp32] [--workload cfg2|cfg3] [--no-variants]
 
 Under torchrun every rank advances its own independent cavity (replicas; the
 step has no data-path collective); rank 0 prints one JSON line.
@@ -34,15 +37,17 @@ import workloads  # noqa: E402
 
 METRIC = "grid-point updates/s per step"
 UNIT = "point-updates/s"
-# FP64 operations per interior point of the fused step (adds, multiplies,
+# FP64 operations per interior point of the fused FP64 step (adds, multiplies,
 # compares = 1, FMA = 2, sqrt = 1), counted on the kernel's formulation: rates
 # 166, update 11, residual sums 10, spectral radius of the new state 25
 FP64_FLOP_PER_POINT = 212
-# algorithmic HBM bytes per interior point-update of one fused pass: read
-# and write the five FP64 fields once
-FP64_BYTES_PER_POINT = 80
+# algorithmic HBM bytes per interior point-update of one fused pass: every
+# stored array read once and written once (FP64: 5 x 8 B; FP32-mixed: 6 x 4 B)
+BYTES_PER_POINT = {"fp64": 80, "fp32": 48}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_BYTES = 129e6
+WORKLOADS = {"cfg2": workloads.CFG2, "cfg3": workloads.CFG3}
 
 
 def parse():
@@ -51,8 +56,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--blocks", default="2,2,2")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
+    ap.add_argument("--blocks", default=None, help="px,py,pz (default 2,2,2 for cfg2, 1,1,1 for cfg3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -126,11 +134,18 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(n, blocks, params, min_seconds=10.0, max_steps=200):
+def default_blocks(workload: str, blocks: str | None):
+    if blocks:
+        return tuple(int(v) for v in blocks.split(","))
+    return (2, 2, 2) if workload == "cfg2" else (1, 1, 1)
+
+
+def cpu_baseline(cfg, blocks, min_seconds=10.0, max_steps=200):
     """The oracle as it stands on a bounded sample: steps of the same workload
     until about min_seconds of CPU work."""
     import oracle
-    o = oracle.OracleCavity(*n, params, blocks=blocks, noise=workloads.CFG2["noise"], seed=workloads.CFG2["seed"])
+    n = cfg["n"]
+    o = oracle.OracleCavity(*n, dict(Ra=cfg["Ra"], Pr=cfg["Pr"]), blocks=blocks, noise=cfg["noise"], seed=cfg["seed"])
     o.step(1)
     t0 = time.perf_counter()
     steps = 0
@@ -149,11 +164,11 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    n = workloads.CFG2["n"]
-    blocks = tuple(int(v) for v in args.blocks.split(","))
-    params = dict(Ra=workloads.CFG2["Ra"], Pr=workloads.CFG2["Pr"])
+    cfg = WORKLOADS[args.workload]
+    n = cfg["n"]
+    blocks = default_blocks(args.workload, args.blocks)
     import oracle
-    o = oracle.OracleCavity(*n, params, blocks=blocks, noise=workloads.CFG2["noise"], seed=workloads.CFG2["seed"])
+    o = oracle.OracleCavity(*n, dict(Ra=cfg["Ra"], Pr=cfg["Pr"]), blocks=blocks, noise=cfg["noise"], seed=cfg["seed"])
     o.step(args.warmup)
     t0 = time.perf_counter()
     o.step(args.steps)
@@ -166,14 +181,114 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded initial state; no dataset)",
-        "config": {"workload": f"cavity {n[0]}^3 Ra 1e5 Pr 0.71 noise 1e-3 seed 0, blocks {blocks}, FP64",
-                   "blocks": list(blocks)},
+        "config": {"workload": f"cavity {n[0]}^3 Ra {cfg['Ra']:g} Pr {cfg['Pr']} noise {cfg['noise']:g} seed "
+                               f"{cfg['seed']}, blocks {blocks}, FP64 oracle", "blocks": list(blocks)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} timed oracle steps after {args.warmup} warm-up steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def roofline_for(precision, pts, step_ms, hbm):
+    step_s = step_ms / 1e3
+    bpp = BYTES_PER_POINT[precision]
+    gbs = bpp * pts / step_s / 1e9
+    hbm_obj = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if hbm else None,
+               "bytes_per_point": bpp, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if precision == "fp32":
+        return dict(kernel="k_step_f32 (TMA-staged fused residual + update + reductions)", traffic=None,
+                    kernel_ms=step_ms, **hbm_obj)
+    tf = FP64_FLOP_PER_POINT * pts / step_s / 1e12
+    return {"kernel": "k_step_f64 (fused residual + update + reductions)", "bound": "alu", "achieved": tf,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure measured)",
+            "kernel_ms": step_ms, "flop_per_point": FP64_FLOP_PER_POINT, "hbm_view": hbm_obj}
+
+
+def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, local, stream, e2e=True):
+    """Device time of `steps` steps (and optionally e2e) of one workload."""
+    cfg = WORKLOADS[workload]
+    n = cfg["n"]
+    pts = n[0] * n[1] * n[2]
+    prec = m.CAVITY_FP64 if precision == "fp64" else m.CAVITY_FP32_MIXED
+    c = m.Cavity(*n, blocks=blocks, precision=prec, seed=cfg["seed"] + rank, noise_amp=cfg["noise"],
+                 device=local, stream=stream.cuda_stream, Ra=cfg["Ra"], Pr=cfg["Pr"])
+    nb = blocks[0] * blocks[1] * blocks[2]
+    launches_per_step = 2 + (2 if nb > 1 else 0)
+    both_buffers = pts * BYTES_PER_POINT[precision]  # the two buffer sets of the state
+    flush = both_buffers < 1.2 * L2_BYTES
+    scratch = torch.empty(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=f"cuda:{local}") if flush else None
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    c.step(warmup)
+    c.sync()
+    kms = m.cavity_time_kernels(c.h, 20)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        if not flush:
+            # K graph-replayed steps, inputs resident in HBM (state larger than L2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        else:
+            # state fits in L2: write a 2xL2 buffer before every timed step
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                for a, b in ev:
+                    scratch.fill_(1.0)
+                    a.record(stream)
+                    c.step(1)
+                    b.record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev)
+    barrier()
+    rc = c.sync()
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    out = {"value": pts * steps * world / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+           "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
+           "gpu_launches": launches_per_step * steps, "clocks": clk.summary(), "status": rc,
+           "l2": ("L2 flushed (2 x L2 buffer written) before every timed step: the state fits in L2" if flush else
+                  f"no flush: the two state buffers ({both_buffers / 1e6:.0f} MB) exceed the 129 MB L2"),
+           "roofline": roofline_for(precision, pts, kms[0], measured_peaks().get("hbm_gbs"))}
+    if e2e:
+        # end to end through the public API with host buffers: initial state
+        # from host, every step followed by the residual + Nusselt read, final
+        # fields back to host
+        host0 = c.fields()
+        e2e_steps = max(1, min(steps, 500))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.set_fields(host0)
+        for _ in range(e2e_steps):
+            c.step(1)
+            _ = c.residual
+            _ = c.nusselt
+        res = c.fields()
+        t1 = time.perf_counter()
+        barrier()
+        e2e_s = t1 - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=f"cuda:{local}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        out["e2e"] = {"value": pts * e2e_steps * world / e2e_s, "unit": UNIT, "steps": e2e_steps,
+                      "h2d_bytes_per_step": host0.nbytes / e2e_steps,
+                      "d2h_bytes_per_step": res.nbytes / e2e_steps + 7 * 8}
+    c.close()
+    return out
 
 
 def run_ours(args):
@@ -185,99 +300,36 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_2006_02602_gb300 as m
     m.load_library()
-
-    cfg = workloads.CFG2
-    n = cfg["n"]
-    blocks = tuple(int(v) for v in args.blocks.split(","))
-    pts = n[0] * n[1] * n[2]
     stream = torch.cuda.Stream(device=local)
-    c = m.Cavity(*n, blocks=blocks, precision=m.CAVITY_FP64, seed=cfg["seed"] + rank, noise_amp=cfg["noise"],
-                 device=local, stream=stream.cuda_stream, Ra=cfg["Ra"], Pr=cfg["Pr"])
-    nb = blocks[0] * blocks[1] * blocks[2]
-    launches_per_step = 2 + (2 if nb > 1 else 0)
 
-    # per-kernel durations (CUDA events around each launch on the handle's stream)
-    c.step(args.warmup)
-    c.sync()
-    kms = m.cavity_time_kernels(c.h, 20)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    # device-timed region: K graph-replayed steps, inputs resident in HBM
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        c.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
-    rc = c.sync()
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = pts * args.steps * world / (ms / 1e3)
-
-    # end to end through the public API with host buffers: initial state from
-    # host, every step followed by the residual + Nusselt read, final fields
-    # back to host
-    host0 = c.fields()
-    e2e_steps = max(1, min(args.steps, 500))
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    c.set_fields(host0)
-    for _ in range(e2e_steps):
-        c.step(1)
-        _ = c.residual
-        _ = c.nusselt
-    out = c.fields()
-    t1 = time.perf_counter()
-    barrier()
-    e2e_s = t1 - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = pts * e2e_steps * world / e2e_s
-    field_bytes = host0.nbytes
-    e2e = {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
-           "h2d_bytes_per_step": field_bytes / e2e_steps,
-           "d2h_bytes_per_step": (out.nbytes / e2e_steps) + 7 * 8}
-
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs")
-    step_s = kms[0] / 1e3
-    achieved_tflops = FP64_FLOP_PER_POINT * pts / step_s / 1e12
-    roofline = {"kernel": "k_step_f64 (fused residual + update + reductions)", "bound": "alu",
-                "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure measured)",
-                "kernel_ms": kms[0], "flop_per_point": FP64_FLOP_PER_POINT,
-                "hbm_view": {"bytes_per_point": FP64_BYTES_PER_POINT,
-                             "achieved_gbs": FP64_BYTES_PER_POINT * pts / step_s / 1e9,
-                             "peak_gbs": hbm, "frac": (FP64_BYTES_PER_POINT * pts / step_s / 1e9 / hbm) if hbm else None,
-                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+    cfg = WORKLOADS[args.workload]
+    n = cfg["n"]
+    blocks = default_blocks(args.workload, args.blocks)
+    r = measure(m, torch, args.precision, args.workload, blocks, args.steps, args.warmup, rank, world, local, stream)
+    dtype = "f64" if args.precision == "fp64" else "f32 (p as f32 hi/lo pair, f64 reductions)"
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded initial state; no dataset)",
-        "config": {"workload": f"cavity {n[0]}^3 Ra 1e5 Pr 0.71 noise 1e-3, blocks {blocks}, FP64, "
-                               "all hot-path rows per step",
-                   "blocks": list(blocks), "parallelism": f"replicas x{world}",
-                   "l2": "no flush: the two FP64 state buffers (2 x 84 MB) exceed the 129 MB L2"},
-        "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
-        "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
-        "clocks": clk.summary(), "status": rc,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded initial state; no dataset)",
+        "config": {"workload": f"cavity {n[0]}^3 Ra {cfg['Ra']:g} Pr {cfg['Pr']} noise {cfg['noise']:g}, "
+                               f"blocks {blocks}, {args.precision.upper()}, all hot-path rows per step",
+                   "blocks": list(blocks), "parallelism": f"replicas x{world}", "l2": r["l2"]},
+        "kernel_ms": r["kernel_ms"], "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
+        "roofline": r["roofline"], "clocks": r["clocks"], "status": r["status"],
     }
+    if not args.no_variants and args.workload == "cfg2" and args.precision == "fp64":
+        variants = {}
+        for name, prec, wl, blk, steps in (("fp32_mixed_cfg2", "fp32", "cfg2", (2, 2, 2), min(args.steps, 500)),
+                                           ("fp32_mixed_cfg3", "fp32", "cfg3", (1, 1, 1), min(args.steps, 500))):
+            v = measure(m, torch, prec, wl, blk, steps, args.warmup, rank, world, local, stream, e2e=False)
+            wcfg = WORKLOADS[wl]
+            v["config"] = {"workload": f"cavity {wcfg['n'][0]}^3 Ra {wcfg['Ra']:g} blocks {blk} FP32-mixed",
+                           "l2": v.pop("l2")}
+            v["dtype"] = "f32 (p as f32 hi/lo pair, f64 reductions)"
+            variants[name] = v
+        line["variants"] = variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(n, blocks, dict(Ra=cfg["Ra"], Pr=cfg["Pr"]))
-    c.close()
+        line["cpu_baseline"] = cpu_baseline(cfg, blocks)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -54,7 +54,8 @@ struct CavConst {
   int centre_blk[kMaxCentre];
   long long centre_off[kMaxCentre];  // element offset of the node in its field array
   int tile_begin, tile_end;          // k_step CTAs of this cavity
-  int bc_begin, bc_end;              // k_bc CTAs of this cavity
+  int bc_begin, bc_end;              // k_bc CTAs of this cavity (all wall faces)
+  int nus_begin, nus_end;            // k_bc CTAs of this cavity in the Nusselt-only mode (x walls)
   long long wall_off;                // offset of this cavity's wall temperatures
 };
 
@@ -93,6 +94,31 @@ template <> struct XO<float> { static constexpr int v = 8; };
 template <class S>
 __device__ __forceinline__ long long node_index(const BlockDev &B, int i, int j, int k) {
   return (long long)(XO<S>::v - 1 + i) + (long long)B.pitch * (j + 1) + B.plane * (k + 1);
+}
+
+// Arrays of one buffer set.  FP64 form: p, u, v, w, T.  FP32-mixed form:
+// p_hi, p_lo, u, v, w, T (p = p_hi + p_lo, an unevaluated FP32 pair).
+template <class S> struct Store;
+template <> struct Store<double> { static constexpr int NA = 5, NP = 1; };
+template <> struct Store<float> { static constexpr int NA = 6, NP = 2; };
+
+template <class S>
+__device__ __forceinline__ double load_p(const S *base, long long fs, long long o);
+template <>
+__device__ __forceinline__ double load_p<double>(const double *base, long long, long long o) { return base[o]; }
+template <>
+__device__ __forceinline__ double load_p<float>(const float *base, long long fs, long long o) {
+  return (double)base[o] + (double)base[fs + o];
+}
+template <class S>
+__device__ __forceinline__ void store_p(S *base, long long fs, long long o, double v);
+template <>
+__device__ __forceinline__ void store_p<double>(double *base, long long, long long o, double v) { base[o] = v; }
+template <>
+__device__ __forceinline__ void store_p<float>(float *base, long long fs, long long o, double v) {
+  const float hi = (float)v;
+  base[o] = hi;
+  base[fs + o] = (float)(v - (double)hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -293,13 +319,35 @@ struct BcArgs {
   unsigned int *counter;
   const double *t_wall;       // hot walls then cold walls, per cavity at wall_off
   int parity;                 // buffer set holding the new state
-  int mode;                   // 0 after a step, 1 after init / set_fields
+  int mode;                   // 0 after a step, 1 after init / set_fields,
+                              // 2 after a step whose kernel applied the walls itself:
+                              //   Nusselt sums over the x-wall faces only
 };
 
+// Nusselt sums of one x-wall node (no writes)
+template <class S>
+__device__ __forceinline__ void nusselt_node(const BlockDev &B, const CavConst &C, const S *base, int face, int c1,
+                                             int c2, const double *t_wall, double &nu_h, double &nu_c) {
+  const int high = face & 1;
+  const int w = high ? B.nx + 1 : 0, s = high ? -1 : 1;
+  const long long W = node_index<S>(B, w, c1, c2);
+  const S *T = base + (Store<S>::NP + 3) * B.fstride;
+  const int J = B.oy + c1, K = B.oz + c2;
+  const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
+  const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
+  const double T1 = (double)T[W + s], T2 = (double)T[W + 2 * s];
+  const double flux = (3.0 * tw - 4.0 * T1 + T2) * (0.5 * C.ih[0]) * C.inv_dT;
+  if (high) nu_c += -flux; else nu_h += flux;
+}
+
+// Walls of one face node.  u = v = w = 0 and the isothermal T never change
+// between steps: they are written (into both buffer sets) only when `other`
+// is given (state refresh); every step rewrites p's wall and ghost values and
+// the adiabatic T, and reads T next to the x walls for the Nusselt sums.
 template <class S>
 __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C, S *base, int face,
                                            int c1, int c2, const double *t_wall, double &nu_h,
-                                           double &nu_c) {
+                                           double &nu_c, S *other = nullptr) {
   const int axis = face >> 1, high = face & 1;
   const int n[3] = {B.nx, B.ny, B.nz};
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
@@ -311,17 +359,24 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
   const long long step = axis == 0 ? 1 : (axis == 1 ? (long long)B.pitch : B.plane);
   const long long N1 = W + s * step, N2 = W + 2 * s * step, G = W - s * step;
   const long long fs = B.fstride;
-  S *P = base, *U = base + fs, *V = base + 2 * fs, *Wv = base + 3 * fs, *T = base + 4 * fs;
-  U[W] = S(0); V[W] = S(0); Wv[W] = S(0);
-  const double p1 = (double)P[N1], p2 = (double)P[N2];
+  constexpr int NP = Store<S>::NP;
+  S *T = base + (NP + 3) * fs;
+  if (other) {
+    base[NP * fs + W] = S(0); base[(NP + 1) * fs + W] = S(0); base[(NP + 2) * fs + W] = S(0);
+    other[NP * fs + W] = S(0); other[(NP + 1) * fs + W] = S(0); other[(NP + 2) * fs + W] = S(0);
+  }
+  const double p1 = load_p<S>(base, fs, N1), p2 = load_p<S>(base, fs, N2);
   const double pw = 2.0 * p1 - p2;
-  P[W] = (S)pw;
-  P[G] = (S)(2.0 * pw - p1);
+  store_p<S>(base, fs, W, pw);
+  store_p<S>(base, fs, G, 2.0 * pw - p1);
   if (axis == 0) {
     const int J = B.oy + iw[1], K = B.oz + iw[2];
     const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
     const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
-    T[W] = (S)tw;
+    if (other) {
+      T[W] = (S)tw;
+      other[(NP + 3) * fs + W] = (S)tw;
+    }
     const double T1 = (double)T[N1], T2 = (double)T[N2];
     const double flux = (3.0 * tw - 4.0 * T1 + T2) * (0.5 * C.ih[0]) * C.inv_dT;
     if (high) nu_c += -flux; else nu_h += flux;
@@ -344,7 +399,8 @@ __device__ void finalize_cavity(const BcArgs &a, int cv, double *sh) {
     acc[5] = fmax(acc[5], pp[5]);
   }
   double nh = 0, nc = 0;
-  for (int q = C.bc_begin + tid; q < C.bc_end; q += kBcThreads) {
+  const int qb = a.mode == 2 ? C.nus_begin : C.bc_begin, qe = a.mode == 2 ? C.nus_end : C.bc_end;
+  for (int q = qb + tid; q < qe; q += kBcThreads) {
     nh += a.bc_partials[2LL * q];
     nc += a.bc_partials[2LL * q + 1];
   }
@@ -366,7 +422,7 @@ __device__ void finalize_cavity(const BcArgs &a, int cv, double *sh) {
     for (int q = 1; q < kBcThreads / 32; ++q)
       for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], sh[q * 8 + f]) : tot[f] + sh[q * 8 + f];
     bool bad = !isfinite(tot[5]);
-    if (a.mode == 0) {
+    if (a.mode != 1) {
       for (int f = 0; f < 5; ++f) {
         st.res[f] = sqrt(tot[f] * C.inv_nint);
         bad = bad || !isfinite(tot[f]);
@@ -377,8 +433,7 @@ __device__ void finalize_cavity(const BcArgs &a, int cv, double *sh) {
       double csum = 0.0;
       for (int m = 0; m < C.ncentre; ++m) {
         const BlockDev &B = a.blocks[C.centre_blk[m]];
-        const S *Pp = (const S *)B.base[a.parity];
-        csum += (double)Pp[C.centre_off[m]];
+        csum += load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[m]);
       }
       st.c = csum / (double)C.ncentre;
     }
@@ -411,8 +466,12 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
     const int e = (cta - F.cta_begin) * kBcThreads + tid;
     if (e < F.n1 * F.n2) {
       const BlockDev &B = a.blocks[F.block];
-      apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
-                    nu_h, nu_c);
+      if (a.mode == 2)
+        nusselt_node<S>(B, a.cc[F.cav], (const S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
+                        nu_h, nu_c);
+      else
+        apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
+                      nu_h, nu_c, a.mode == 1 ? (S *)B.base[a.parity ^ 1] : nullptr);
     }
   }
   nu_h = warp_sum(nu_h);
@@ -490,9 +549,14 @@ __global__ void __launch_bounds__(256) k_pack(ExchArgs a) {
   long long p_first, v_node, dstep;
   face_geometry<S>(B, F.face, ib, ic, false, p_first, v_node, dstep);
   S *buf = (S *)a.buf + F.buf_off;
-  buf[2LL * e] = q[p_first];
-  buf[2LL * e + 1] = q[p_first + dstep];
-  for (int v = 0; v < 4; ++v) buf[2LL * plane + (long long)v * plane + e] = q[(long long)(v + 1) * B.fstride + v_node];
+  constexpr int NP = Store<S>::NP;  // pressure arrays (FP32-mixed: hi, then lo section)
+  for (int pa = 0; pa < NP; ++pa) {
+    const S *pq = q + (long long)pa * B.fstride;
+    buf[2LL * pa * plane + 2LL * e] = pq[p_first];
+    buf[2LL * pa * plane + 2LL * e + 1] = pq[p_first + dstep];
+  }
+  for (int v = 0; v < 4; ++v)
+    buf[2LL * NP * plane + (long long)v * plane + e] = q[(long long)(NP + v) * B.fstride + v_node];
 }
 
 template <class S>
@@ -508,9 +572,14 @@ __global__ void __launch_bounds__(256) k_unpack(ExchArgs a) {
   long long p_first, v_node, dstep;
   face_geometry<S>(B, F.face ^ 1, ib, ic, true, p_first, v_node, dstep);
   const S *buf = (const S *)a.buf + F.buf_off;
-  q[p_first] = buf[2LL * e];
-  q[p_first + dstep] = buf[2LL * e + 1];
-  for (int v = 0; v < 4; ++v) q[(long long)(v + 1) * B.fstride + v_node] = buf[2LL * plane + (long long)v * plane + e];
+  constexpr int NP = Store<S>::NP;
+  for (int pa = 0; pa < NP; ++pa) {
+    S *pq = q + (long long)pa * B.fstride;
+    pq[p_first] = buf[2LL * pa * plane + 2LL * e];
+    pq[p_first + dstep] = buf[2LL * pa * plane + 2LL * e + 1];
+  }
+  for (int v = 0; v < 4; ++v)
+    q[(long long)(NP + v) * B.fstride + v_node] = buf[2LL * NP * plane + (long long)v * plane + e];
 }
 
 // ---------------------------------------------------------------------------
@@ -550,8 +619,19 @@ __global__ void k_init(InitArgs a) {
   const double x = __dmul_rn((double)I, C.h[0]);
   const double lin = __dadd_rn(a.t_hot, __dmul_rn(__dsub_rn(a.t_cold, a.t_hot), x));
   const double pert = __dmul_rn(a.noise, __dsub_rn(__dmul_rn(2.0, U), 1.0));
-  S *T = (S *)B.base[a.parity] + 4 * B.fstride;
+  S *T = (S *)B.base[a.parity] + (Store<S>::NP + 3) * B.fstride;
   T[node_index<S>(B, i, j, k)] = (S)__dadd_rn(lin, pert);
+}
+
+// field f (0 = p, 1..4 = u, v, w, T) of node offset o, widened to FP64
+template <class S>
+__device__ __forceinline__ double get_field(const S *q, long long fs, int f, long long o) {
+  return f == 0 ? load_p<S>(q, fs, o) : (double)q[(long long)(Store<S>::NP + f - 1) * fs + o];
+}
+template <class S>
+__device__ __forceinline__ void put_field(S *q, long long fs, int f, long long o, double v) {
+  if (f == 0) store_p<S>(q, fs, o, v);
+  else q[(long long)(Store<S>::NP + f - 1) * fs + o] = (S)v;
 }
 
 struct MoveArgs {
@@ -578,7 +658,7 @@ __global__ void k_gather(MoveArgs a) {
   int slot = 0;
   for (int f = 0; f < kNF; ++f) {
     if (!(a.mask & (1 << f))) continue;
-    double v = (double)q[f * B.fstride + o];
+    double v = get_field<S>(q, B.fstride, f, o);
     if (f == 0) v -= a.pshift;
     a.stage[slot * gN + g] = v;
     ++slot;
@@ -609,7 +689,7 @@ __global__ void k_gather_box(BoxArgs a) {
     int slot = 0;
     for (int f = 0; f < kNF; ++f) {
       if (!(a.mask & (1 << f))) continue;
-      double v = (double)q[f * B.fstride + o];
+      double v = get_field<S>(q, B.fstride, f, o);
       if (f == 0) v -= a.pshift;
       a.stage[slot * n + e] = v;
       ++slot;
@@ -632,7 +712,7 @@ __global__ void k_scatter(MoveArgs a) {
   int slot = 0;
   for (int f = 0; f < kNF; ++f) {
     if (!(a.mask & (1 << f))) continue;
-    q[f * B.fstride + o] = (S)a.stage[slot * gN + g];
+    put_field<S>(q, B.fstride, f, o, a.stage[slot * gN + g]);
     ++slot;
   }
 }
@@ -649,10 +729,11 @@ __global__ void k_shift_p(const BlockDev *blocks, int block, int parity, double 
   const int k = (int)(e / ((long long)(B.nx + 4) * (B.ny + 4))) - 1;
   S *q = (S *)B.base[parity];
   const long long o = node_index<S>(B, i, j, k);
-  q[o] = (S)((double)q[o] - c);
+  store_p<S>(q, B.fstride, o, load_p<S>(q, B.fstride, o) - c);
 }
 
-// copy of a whole block array (walls and ghosts included) to a dense stage
+// copy of one stored array of a block (walls and ghosts included) to a dense
+// stage; `field` is the array index (FP32-mixed: 0 = p_hi, 1 = p_lo, 2.. = u..T)
 template <class S>
 __global__ void k_copy_block(const BlockDev *blocks, int block, int parity, int field, double *stage) {
   const BlockDev &B = blocks[block];

@@ -1,11 +1,16 @@
 // C ABI of the buoyancy-driven-cavity step (include/cavity.h): host runtime
 // that lays out the blocks in HBM, builds the work lists of the kernels in
-// bdc_device.cuh, captures one CUDA graph per buffer parity and replays it.
+// bdc_device.cuh / bdc_step_f32.cuh, captures one CUDA graph per buffer
+// parity and replays it.  Two arithmetic forms share the runtime: FP64
+// (five FP64 arrays per buffer set) and FP32-mixed (p_hi, p_lo, u, v, w, T in
+// FP32, read by the step kernel through TMA tensor maps).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -13,6 +18,7 @@
 
 #include "../../include/cavity.h"
 #include "bdc_device.cuh"
+#include "bdc_step_f32.cuh"
 
 using namespace bdc;
 
@@ -28,6 +34,10 @@ std::vector<int> split_sizes(int n, int parts) {  // Section 3.2: as even as pos
   return s;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
 }  // namespace
 
 struct cavity {
@@ -36,20 +46,28 @@ struct cavity {
   bool own_stream = false;
   cavity_desc desc{};
   cavity_params prm{};
+  bool f32 = false;  // FP32-mixed form
   size_t esize = 8;  // bytes per stored element
+  int na = 5;        // stored arrays per buffer set
+  int np = 1;        // pressure arrays
+  int tx = kTX, ty = kTY, kc = kKC;
+  int f32_r = 0;  // ring depth of the FP32 step kernel
   int nblocks = 0;
   std::vector<BlockDev> hb;
   std::vector<WallFace> hwall;
+  std::vector<WallFace> hnus;  // x-wall faces (Nusselt-only wall pass)
   std::vector<CutFace> hcut;
   CavConst hcc{};
   long long xbuf_elems = 0;
-  int n_step = 0, n_bc = 0, n_cut = 0;
+  int n_step = 0, n_bc = 0, n_cut = 0, n_nus = 0;
+  WallFace *d_nus = nullptr;
 
   BlockDev *d_blocks = nullptr;
   CavConst *d_cc = nullptr;
   CavState *d_cs = nullptr;
   WallFace *d_wall = nullptr;
   CutFace *d_cut = nullptr;
+  CUtensorMap *d_maps = nullptr;
   double *d_step_part = nullptr, *d_bc_part = nullptr, *d_twall = nullptr, *d_stage = nullptr;
   unsigned int *d_counter = nullptr;
   void *d_fields = nullptr, *d_xbuf = nullptr;
@@ -175,12 +193,12 @@ int build_layout(cavity *h) {
           B.nbr[f] = inside ? cc[0] + pg[0] * (cc[1] + pg[1] * cc[2]) : -1;
         }
         B.cav = 0;
-        B.tiles_x = ceil_div(B.nx, kTX);
-        B.tiles_y = ceil_div(B.ny, kTY);
-        B.tiles_z = ceil_div(B.nz, kKC);
+        B.tiles_x = ceil_div(B.nx, h->tx);
+        B.tiles_y = ceil_div(B.ny, h->ty);
+        B.tiles_z = ceil_div(B.nz, h->kc);
         B.tile_begin = tile;
         tile += B.tiles_x * B.tiles_y * B.tiles_z;
-        total_elems += 2 * kNF * (size_t)B.fstride;
+        total_elems += 2 * (size_t)h->na * (size_t)B.fstride;
       }
   h->n_step = tile;
   h->field_bytes = total_elems * es;
@@ -203,17 +221,28 @@ int build_layout(cavity *h) {
         CutFace c{id, f, B.nbr[f], n1, n2, cut, xoff};
         h->hcut.push_back(c);
         cut += ceil_div((long long)n1 * n2, 256);
-        xoff += 6LL * n1 * n2;
+        xoff += (long long)(2 * h->np + 4) * n1 * n2;
       }
     }
   }
   h->n_bc = bc;
   h->n_cut = cut;
   h->xbuf_elems = xoff;
+  int nus = 0;
+  h->hnus.clear();
+  for (const WallFace &w : h->hwall) {
+    if (w.face / 2 != 0) continue;
+    WallFace x = w;
+    x.cta_begin = nus;
+    h->hnus.push_back(x);
+    nus += ceil_div((long long)w.n1 * w.n2, kBcThreads);
+  }
+  h->n_nus = nus;
   // cavity constants: work ranges and centre nodes
   CavConst &C = h->hcc;
   C.tile_begin = 0; C.tile_end = h->n_step;
   C.bc_begin = 0; C.bc_end = h->n_bc;
+  C.nus_begin = 0; C.nus_end = h->n_nus;
   C.wall_off = 0;
   std::vector<int> ax[3];
   for (int a = 0; a < 3; ++a) {
@@ -237,6 +266,54 @@ int build_layout(cavity *h) {
   return CAVITY_OK;
 }
 
+// FP32 step-kernel variants compiled in: (z chunk KC, ring depth R)
+#define BDC_F32_VARIANTS(X) X(16, 8) X(32, 8) X(64, 4) X(64, 8)
+
+bool f32_variant_ok(int kc, int r) {
+#define BDC_OK(KC, R) if (kc == KC && r == R) return true;
+  BDC_F32_VARIANTS(BDC_OK)
+#undef BDC_OK
+  return false;
+}
+
+cudaError_t f32_set_smem(int kc, int r) {
+#define BDC_ATTR(KC, R)                                                                                   \
+  if (kc == KC && r == R)                                                                                 \
+    return cudaFuncSetAttribute(k_step_f32<KC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                f32_smem_bytes(R));
+  BDC_F32_VARIANTS(BDC_ATTR)
+#undef BDC_ATTR
+  return cudaErrorInvalidValue;
+}
+
+// TMA descriptors of the FP32-mixed step kernel: one 4-D map per block and
+// buffer set over (x, y, z, array), box = one tile plane with its halo for
+// all six arrays
+int encode_maps(cavity *h) {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (q != cudaDriverEntryPointSuccess || !fn) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  EncodeTiledFn encode = (EncodeTiledFn)fn;
+  std::vector<CUtensorMap> maps(2 * h->nblocks);
+  for (int id = 0; id < h->nblocks; ++id) {
+    const BlockDev &B = h->hb[id];
+    for (int s = 0; s < 2; ++s) {
+      const cuuint64_t dims[4] = {(cuuint64_t)B.pitch, (cuuint64_t)B.rows, (cuuint64_t)(B.nz + 4), (cuuint64_t)kF32NA};
+      const cuuint64_t strides[3] = {(cuuint64_t)B.pitch * 4, (cuuint64_t)B.plane * 4, (cuuint64_t)B.fstride * 4};
+      const cuuint32_t box[4] = {(cuuint32_t)kF32BX, (cuuint32_t)kF32BY, 1, (cuuint32_t)kF32NA};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      const CUresult r = encode(&maps[2 * id + s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.base[s], dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+  }
+  CK(cudaMalloc(&h->d_maps, sizeof(CUtensorMap) * maps.size()));
+  CK(cudaMemcpy(h->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+  return CAVITY_OK;
+}
+
 int alloc_device(cavity *h) {
   CK(cudaMalloc(&h->d_fields, h->field_bytes));
   CK(cudaMemsetAsync(h->d_fields, 0, h->field_bytes, h->stream));
@@ -244,7 +321,7 @@ int alloc_device(cavity *h) {
   for (auto &B : h->hb) {
     for (int s = 0; s < 2; ++s) {
       B.base[s] = base;
-      base += kNF * (size_t)B.fstride * h->esize;
+      base += (size_t)h->na * (size_t)B.fstride * h->esize;
     }
   }
   CK(cudaMalloc(&h->d_blocks, sizeof(BlockDev) * h->nblocks));
@@ -253,6 +330,9 @@ int alloc_device(cavity *h) {
   CK(cudaMemsetAsync(h->d_cs, 0, sizeof(CavState), h->stream));
   CK(cudaMalloc(&h->d_wall, sizeof(WallFace) * std::max<size_t>(1, h->hwall.size())));
   CK(cudaMalloc(&h->d_cut, sizeof(CutFace) * std::max<size_t>(1, h->hcut.size())));
+  CK(cudaMalloc(&h->d_nus, sizeof(WallFace) * std::max<size_t>(1, h->hnus.size())));
+  if (!h->hnus.empty())
+    CK(cudaMemcpyAsync(h->d_nus, h->hnus.data(), sizeof(WallFace) * h->hnus.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMalloc(&h->d_step_part, sizeof(double) * kPartStride * std::max(1, h->n_step)));
   CK(cudaMalloc(&h->d_bc_part, sizeof(double) * 2 * std::max(1, h->n_bc)));
   CK(cudaMalloc(&h->d_counter, sizeof(unsigned int)));
@@ -264,6 +344,11 @@ int alloc_device(cavity *h) {
     CK(cudaMemcpyAsync(h->d_wall, h->hwall.data(), sizeof(WallFace) * h->hwall.size(), cudaMemcpyHostToDevice, h->stream));
   if (!h->hcut.empty())
     CK(cudaMemcpyAsync(h->d_cut, h->hcut.data(), sizeof(CutFace) * h->hcut.size(), cudaMemcpyHostToDevice, h->stream));
+  if (h->f32) {
+    int rc = encode_maps(h);
+    if (rc != CAVITY_OK) return rc;
+    CK(f32_set_smem(h->kc, h->f32_r));
+  }
   return CAVITY_OK;
 }
 
@@ -289,9 +374,18 @@ StepArgs step_args(cavity *h, int parity, int mode) {
   return a;
 }
 
+StepF32Args step_f32_args(cavity *h, int parity) {
+  StepF32Args a;
+  a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
+  a.maps = h->d_maps; a.partials = h->d_step_part; a.parity = parity;
+  return a;
+}
+
 BcArgs bc_args(cavity *h, int parity, int mode) {
   BcArgs a;
-  a.blocks = h->d_blocks; a.faces = h->d_wall; a.nfaces = (int)h->hwall.size();
+  a.blocks = h->d_blocks;
+  a.faces = mode == 2 ? h->d_nus : h->d_wall;
+  a.nfaces = (int)(mode == 2 ? h->hnus.size() : h->hwall.size());
   a.cc = h->d_cc; a.cs = h->d_cs; a.ncav = 1;
   a.step_partials = h->d_step_part; a.bc_partials = h->d_bc_part; a.counter = h->d_counter;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
@@ -305,29 +399,69 @@ ExchArgs exch_args(cavity *h, int parity) {
   return a;
 }
 
+void launch_step_kernel(cavity *h, int parity) {
+  if (h->f32) {
+#define BDC_LAUNCH(KC, R)                                                                                   \
+  if (h->kc == KC && h->f32_r == R)                                                                         \
+    k_step_f32<KC, R><<<h->n_step, dim3(kF32TX, kF32TY), f32_smem_bytes(R), h->stream>>>( \
+        step_f32_args(h, parity));
+    BDC_F32_VARIANTS(BDC_LAUNCH)
+#undef BDC_LAUNCH
+  } else {
+    k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, parity, 0));
+  }
+}
+
+// mode 0: after a step; mode 1: state refresh.  The FP32 step kernel applies
+// the walls itself, so after its steps only the Nusselt sums remain (mode 2).
+void launch_bc_kernel(cavity *h, int parity, int mode) {
+  if (h->f32) {
+    if (mode == 0) k_bc<float><<<h->n_nus, kBcThreads, 0, h->stream>>>(bc_args(h, parity, 2));
+    else k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
+  } else {
+    k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
+  }
+}
+
+void launch_pack(cavity *h, int parity) {
+  if (h->f32) k_pack<float><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+  else k_pack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+}
+
+void launch_unpack(cavity *h, int parity) {
+  if (h->f32) k_unpack<float><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+  else k_unpack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+}
+
 int launch_exchange(cavity *h, int parity) {
   if (h->n_cut == 0) return CAVITY_OK;
-  k_pack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+  launch_pack(h, parity);
   CK(cudaGetLastError());
-  k_unpack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+  launch_unpack(h, parity);
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
 
 // one explicit step reading buffer set `parity`, leaving the new state in parity ^ 1
 int launch_step(cavity *h, int parity) {
-  k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, parity, 0));
+  launch_step_kernel(h, parity);
   CK(cudaGetLastError());
-  k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0));
+  launch_bc_kernel(h, parity ^ 1, 0);
   CK(cudaGetLastError());
   return launch_exchange(h, parity ^ 1);
 }
 
 // walls, ghosts, dt and Nusselt of the state in the current buffer set (no step)
 int refresh_state(cavity *h) {
-  k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, h->parity, 1));
+  if (h->f32) {
+    const StepArgs sa = step_args(h, h->parity, 1);
+    if (h->kc == 16) k_spectral<float, kF32TX, kF32TY, 16><<<h->n_step, dim3(kF32TX, kF32TY), 0, h->stream>>>(sa);
+    else if (h->kc == 32) k_spectral<float, kF32TX, kF32TY, 32><<<h->n_step, dim3(kF32TX, kF32TY), 0, h->stream>>>(sa);
+    else k_spectral<float, kF32TX, kF32TY, 64><<<h->n_step, dim3(kF32TX, kF32TY), 0, h->stream>>>(sa);
+  } else
+    k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, h->parity, 1));
   CK(cudaGetLastError());
-  k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, h->parity, 1));
+  launch_bc_kernel(h, h->parity, 1);
   CK(cudaGetLastError());
   return launch_exchange(h, h->parity);
 }
@@ -362,7 +496,8 @@ int init_state(cavity *h) {
     const BlockDev &B = h->hb[id];
     InitArgs a{h->d_blocks, h->d_cc, id, 0, h->desc.seed, h->desc.noise_amp, h->prm.t_hot, h->prm.t_cold};
     const long long n = (long long)B.nx * B.ny * B.nz;
-    k_init<double><<<ceil_div(n, 256), 256, 0, h->stream>>>(a);
+    if (h->f32) k_init<float><<<ceil_div(n, 256), 256, 0, h->stream>>>(a);
+    else k_init<double><<<ceil_div(n, 256), 256, 0, h->stream>>>(a);
     CK(cudaGetLastError());
   }
   return refresh_state(h);
@@ -394,12 +529,18 @@ int read_state(cavity *h, CavState *st) {
   return CAVITY_OK;
 }
 
+int state_status(const CavState &st) {
+  if (st.flags & 2) return CAVITY_ERR_TIMEOUT;
+  if (st.flags & 1) return CAVITY_ERR_NONFINITE;
+  return CAVITY_OK;
+}
+
 void release(cavity *h) {
   DeviceGuard g(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   void *ptrs[] = {h->d_fields, h->d_blocks, h->d_cc, h->d_cs, h->d_wall, h->d_cut, h->d_step_part,
-                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage};
+                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps, h->d_nus};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -428,14 +569,30 @@ int cavity_create(const cavity_desc *desc, cavity_t **out) {
   if ((long long)d.nx * d.ny * d.nz > (1LL << 34)) return CAVITY_ERR_INVALID_ARG;
   if (!(d.noise_amp >= 0.0) || !std::isfinite(d.noise_amp)) return CAVITY_ERR_INVALID_ARG;
   if (d.precision != CAVITY_FP64 && d.precision != CAVITY_FP32_MIXED) return CAVITY_ERR_INVALID_ARG;
-  if (d.precision != CAVITY_FP64) return CAVITY_ERR_UNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || d.device < 0 || d.device >= ndev) return CAVITY_ERR_CUDA;
   cavity *h = new (std::nothrow) cavity();
   if (!h) return CAVITY_ERR_OOM;
   h->desc = d;
   h->dev = d.device;
-  h->esize = 8;
+  h->f32 = d.precision == CAVITY_FP32_MIXED;
+  h->esize = h->f32 ? 4 : 8;
+  h->na = h->f32 ? Store<float>::NA : Store<double>::NA;
+  h->np = h->f32 ? Store<float>::NP : Store<double>::NP;
+  if (h->f32) {
+    h->tx = kF32TX;
+    h->ty = kF32TY;
+    h->kc = kF32KC;
+    h->f32_r = kF32R;
+    // tile override for tuning sweeps: BDC_F32_TILE="KC,R" (a compiled variant)
+    if (const char *env = std::getenv("BDC_F32_TILE")) {
+      int kc = 0, r = 0;
+      if (std::sscanf(env, "%d,%d", &kc, &r) == 2 && f32_variant_ok(kc, r)) {
+        h->kc = kc;
+        h->f32_r = r;
+      }
+    }
+  }
   cavity_default_params(&h->prm);
   int rc = CAVITY_OK;
   {
@@ -509,7 +666,7 @@ int cavity_residual(cavity_t *h, double out[5]) {
   int rc = read_state(h, &st);
   if (rc != CAVITY_OK) return rc;
   for (int f = 0; f < 5; ++f) out[f] = st.res[f];
-  return (st.flags & 1) ? CAVITY_ERR_NONFINITE : CAVITY_OK;
+  return state_status(st);
 }
 
 int cavity_nusselt(cavity_t *h, double *hot, double *cold) {
@@ -520,7 +677,7 @@ int cavity_nusselt(cavity_t *h, double *hot, double *cold) {
   if (rc != CAVITY_OK) return rc;
   if (hot) *hot = st.nu_hot;
   if (cold) *cold = st.nu_cold;
-  return (st.flags & 1) ? CAVITY_ERR_NONFINITE : CAVITY_OK;
+  return state_status(st);
 }
 
 int cavity_get_time(cavity_t *h, long long *step, double *t, double *dt) {
@@ -532,7 +689,7 @@ int cavity_get_time(cavity_t *h, long long *step, double *t, double *dt) {
   if (step) *step = st.step;
   if (t) *t = st.t;
   if (dt) *dt = st.dt;
-  return (st.flags & 1) ? CAVITY_ERR_NONFINITE : CAVITY_OK;
+  return state_status(st);
 }
 
 int cavity_get_fields(cavity_t *h, int mask, double *host, size_t count) {
@@ -548,7 +705,9 @@ int cavity_get_fields(cavity_t *h, int mask, double *host, size_t count) {
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
     MoveArgs a{h->d_blocks, id, h->parity, mask, {h->desc.nx, h->desc.ny, h->desc.nz}, h->d_stage, st.c};
-    k_gather<double><<<ceil_div((long long)B.nx * B.ny * B.nz, 256), 256, 0, h->stream>>>(a);
+    const int grid = ceil_div((long long)B.nx * B.ny * B.nz, 256);
+    if (h->f32) k_gather<float><<<grid, 256, 0, h->stream>>>(a);
+    else k_gather<double><<<grid, 256, 0, h->stream>>>(a);
     CK(cudaGetLastError());
   }
   CK(cudaMemcpyAsync(host, h->d_stage, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -571,7 +730,8 @@ int cavity_get_fields_box(cavity_t *h, int mask, int i0, int j0, int k0, int ni,
   rc = read_state(h, &st);
   if (rc != CAVITY_OK) return rc;
   BoxArgs a{h->d_blocks, h->nblocks, h->parity, mask, i0, j0, k0, ni, nj, nk, h->d_stage, st.c};
-  k_gather_box<double><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(a);
+  if (h->f32) k_gather_box<float><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(a);
+  else k_gather_box<double><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(a);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(host, h->d_stage, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -592,8 +752,9 @@ int cavity_set_fields(cavity_t *h, int mask, const double *host, size_t count) {
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
     if (st.c != 0.0 && !(mask & CAVITY_FIELD_P)) {
-      k_shift_p<double><<<ceil_div((long long)(B.nx + 4) * (B.ny + 4) * (B.nz + 4), 256), 256, 0, h->stream>>>(
-          h->d_blocks, id, h->parity, st.c);
+      const int grid = ceil_div((long long)(B.nx + 4) * (B.ny + 4) * (B.nz + 4), 256);
+      if (h->f32) k_shift_p<float><<<grid, 256, 0, h->stream>>>(h->d_blocks, id, h->parity, st.c);
+      else k_shift_p<double><<<grid, 256, 0, h->stream>>>(h->d_blocks, id, h->parity, st.c);
       CK(cudaGetLastError());
     }
   }
@@ -602,7 +763,9 @@ int cavity_set_fields(cavity_t *h, int mask, const double *host, size_t count) {
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
     MoveArgs a{h->d_blocks, id, h->parity, mask, {h->desc.nx, h->desc.ny, h->desc.nz}, h->d_stage, 0.0};
-    k_scatter<double><<<ceil_div((long long)B.nx * B.ny * B.nz, 256), 256, 0, h->stream>>>(a);
+    const int grid = ceil_div((long long)B.nx * B.ny * B.nz, 256);
+    if (h->f32) k_scatter<float><<<grid, 256, 0, h->stream>>>(a);
+    else k_scatter<double><<<grid, 256, 0, h->stream>>>(a);
     CK(cudaGetLastError());
   }
   rc = refresh_state(h);
@@ -614,7 +777,7 @@ int cavity_set_fields(cavity_t *h, int mask, const double *host, size_t count) {
 int cavity_num_blocks(cavity_t *h) { return h ? h->nblocks : CAVITY_ERR_INVALID_ARG; }
 
 int cavity_get_block_array(cavity_t *h, int block, int field, double *host, size_t count, int dims[6]) {
-  if (!h || block < 0 || block >= h->nblocks || field < 0 || field >= kNF) return CAVITY_ERR_INVALID_ARG;
+  if (!h || block < 0 || block >= h->nblocks || field < 0 || field >= h->na) return CAVITY_ERR_INVALID_ARG;
   const BlockDev &B = h->hb[block];
   const size_t n = (size_t)(B.nx + 4) * (B.ny + 4) * (B.nz + 4);
   if (dims) { dims[0] = B.nx; dims[1] = B.ny; dims[2] = B.nz; dims[3] = B.ox; dims[4] = B.oy; dims[5] = B.oz; }
@@ -623,7 +786,8 @@ int cavity_get_block_array(cavity_t *h, int block, int field, double *host, size
   DeviceGuard g(h->dev);
   int rc = ensure_stage(h, count);
   if (rc != CAVITY_OK) return rc;
-  k_copy_block<double><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(h->d_blocks, block, h->parity, field, h->d_stage);
+  if (h->f32) k_copy_block<float><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(h->d_blocks, block, h->parity, field, h->d_stage);
+  else k_copy_block<double><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(h->d_blocks, block, h->parity, field, h->d_stage);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(host, h->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -634,11 +798,20 @@ int cavity_get_face_buffer(cavity_t *h, int block, int face, double *host, size_
   if (!h || !host || block < 0 || block >= h->nblocks || face < 0 || face > 5) return CAVITY_ERR_INVALID_ARG;
   for (const CutFace &c : h->hcut) {
     if (c.src != block || c.face != face) continue;
-    const size_t n = 6 * (size_t)c.nb * c.nc;
+    const size_t n = (size_t)(2 * h->np + 4) * c.nb * c.nc;
     if (count != n) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
     DeviceGuard g(h->dev);
-    CK(cudaMemcpyAsync(host, (double *)h->d_xbuf + c.buf_off, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    if (h->f32) {
+      std::vector<float> tmp(n);
+      CK(cudaMemcpyAsync(tmp.data(), (float *)h->d_xbuf + c.buf_off, n * sizeof(float), cudaMemcpyDeviceToHost,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (size_t q = 0; q < n; ++q) host[q] = (double)tmp[q];
+    } else {
+      CK(cudaMemcpyAsync(host, (double *)h->d_xbuf + c.buf_off, n * sizeof(double), cudaMemcpyDeviceToHost,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
     return CAVITY_OK;
   }
   return fail(h, CAVITY_ERR_INVALID_ARG, "face is a wall");
@@ -660,13 +833,13 @@ int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
   for (int s = 0; s < nsteps && rc == CAVITY_OK; ++s) {
     const int par = h->parity;
     cudaEventRecord(ev[0], h->stream);
-    k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, par, 0));
+    launch_step_kernel(h, par);
     cudaEventRecord(ev[1], h->stream);
-    k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, par ^ 1, 0));
+    launch_bc_kernel(h, par ^ 1, 0);
     cudaEventRecord(ev[2], h->stream);
-    if (h->n_cut > 0) k_pack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, par ^ 1));
+    if (h->n_cut > 0) launch_pack(h, par ^ 1);
     cudaEventRecord(ev[3], h->stream);
-    if (h->n_cut > 0) k_unpack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, par ^ 1));
+    if (h->n_cut > 0) launch_unpack(h, par ^ 1);
     cudaEventRecord(ev[4], h->stream);
     cudaError_t e = cudaEventSynchronize(ev[4]);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -691,7 +864,7 @@ int cavity_sync(cavity_t *h) {
   CavState st;
   int rc = read_state(h, &st);
   if (rc != CAVITY_OK) return rc;
-  return (st.flags & 1) ? CAVITY_ERR_NONFINITE : CAVITY_OK;
+  return state_status(st);
 }
 
 int cavity_destroy(cavity_t *h) {

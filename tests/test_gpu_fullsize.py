@@ -68,6 +68,36 @@ def test_cfg2_fp64_2x2x2_vs_oracle(m, cfg2_oracle):
         assert s == 2000 and t == pytest.approx(o.t, rel=1e-12)
 
 
+def test_cfg2_fp32_mixed_2x2x2_vs_fp64_oracle(m, cfg2_oracle):
+    """Configuration 2 in the FP32-mixed form: every field within 1e-5
+    relative max-norm and Nusselt within 1e-4 of the FP64 oracle."""
+    cfg = workloads.CFG2
+    o = cfg2_oracle
+    with m.Cavity(*cfg["n"], blocks=(2, 2, 2), precision=m.CAVITY_FP32_MIXED, seed=cfg["seed"],
+                  noise_amp=cfg["noise"], Ra=cfg["Ra"], Pr=cfg["Pr"]) as c:
+        c.step(cfg["steps"])
+        g = c.fields()
+        ref = o.fields()
+        for f, name in enumerate(oracle.FIELDS):
+            e = relmax(g[f], ref[f])
+            assert e <= 1e-5, (name, e)
+        h, cold = c.nusselt
+        assert abs(h - o.nusselt[0]) <= 1e-4 * abs(o.nusselt[0])
+        assert abs(cold - o.nusselt[1]) <= 1e-4 * abs(o.nusselt[1])
+
+
+def test_cfg2_fp32_decompositions_bit_identical(m):
+    cfg = workloads.CFG2
+    kw = dict(precision=m.CAVITY_FP32_MIXED, seed=cfg["seed"], noise_amp=cfg["noise"], Ra=cfg["Ra"], Pr=cfg["Pr"])
+    with m.Cavity(*cfg["n"], **kw) as ref:
+        ref.step(cfg["steps"])
+        f0 = ref.fields()
+        for blocks in cfg["decomps"]:
+            with m.Cavity(*cfg["n"], blocks=blocks, **kw) as c:
+                c.step(cfg["steps"])
+                assert np.array_equal(c.fields(), f0), blocks
+
+
 def test_cfg2_decompositions_bit_identical(m):
     with _cfg2(m, (1, 1, 1)) as ref:
         f0 = ref.fields()

@@ -251,3 +251,130 @@ def test_invalid_arguments_and_nonfinite(m):
             c.residual
         assert e.value.code == m.CAVITY_ERR_NONFINITE
         assert c.sync() == m.CAVITY_ERR_NONFINITE
+
+
+# ---------------------------------------------------------------------------
+# FP32-mixed form: u, v, w, T in FP32, p as an FP32 hi/lo pair, FP64 reductions.
+# Against the FP64 oracle: fields <= 1e-5 relative max-norm, Nusselt <= 1e-4.
+
+FP32_TOL = 1e-5
+NU32_TOL = 1e-4
+
+
+def run_pair32(m, n, Ra, steps, blocks=(1, 1, 1), noise=1e-3, seed=0, **kw):
+    o = oracle.OracleCavity(*n, dict(Ra=Ra, **kw), noise=noise, seed=seed)
+    c = m.Cavity(*n, blocks=blocks, precision=m.CAVITY_FP32_MIXED, seed=seed, noise_amp=noise, Ra=Ra, **kw)
+    o.step(steps)
+    c.step(steps)
+    return o, c
+
+
+def test_fp32_initial_state(m):
+    n = (37, 21, 18)
+    o = oracle.OracleCavity(*n, dict(Ra=1e4), noise=1e-3, seed=5)
+    with m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=5, noise_amp=1e-3, Ra=1e4) as c:
+        g, ref = c.fields(), o.fields()
+        assert np.array_equal(g[4], ref[4].astype(np.float32).astype(np.float64))
+        assert np.all(g[:4] == 0)
+
+
+def test_fp32_config1_32cube_200_steps(m):
+    cfg = workloads.CFG1
+    o, c = run_pair32(m, cfg["n"], cfg["Ra"], cfg["steps"], noise=cfg["noise"], seed=cfg["seed"], Pr=cfg["Pr"])
+    with c:
+        assert_fields_close(c.fields(), o.fields(), FP32_TOL, "fp32 cfg1")
+        h, cold = c.nusselt
+        assert abs(h - o.nusselt[0]) <= NU32_TOL * abs(o.nusselt[0])
+        assert abs(cold - o.nusselt[1]) <= NU32_TOL * abs(o.nusselt[1])
+        assert np.allclose(c.residual, o.residual, rtol=1e-4)
+        assert c.time[2] == pytest.approx(o.p["cfl"] / o.spectral_max(), rel=1e-5)
+
+
+@pytest.mark.parametrize("n", [(37, 21, 18), (2, 2, 2), (65, 9, 40), (33, 17, 70)])
+def test_fp32_ragged_and_degenerate_sizes(m, n):
+    """Small and ragged cavities: p and T against their own max-norm, each
+    velocity component against the maximum speed (a component that the
+    y-mirror symmetry keeps near zero has no scale of its own)."""
+    o, c = run_pair32(m, n, 3e4, 25, noise=1e-3, seed=11)
+    with c:
+        g, ref = c.fields(), o.fields()
+        speed = max(np.max(np.abs(ref[f])) for f in (1, 2, 3))
+        for f, name in enumerate(oracle.FIELDS):
+            scale = speed if f in (1, 2, 3) else np.max(np.abs(ref[f]))
+            e = np.max(np.abs(g[f] - ref[f])) / scale
+            assert e <= FP32_TOL, f"fp32 n={n} field {name}: {e:.3e}"
+
+
+@pytest.mark.parametrize("blocks", DECOMPS)
+def test_fp32_blocks_bit_identical(m, blocks):
+    kw = dict(precision=m.CAVITY_FP32_MIXED, seed=9, noise_amp=1e-3, Ra=1e5)
+    with m.Cavity(48, 40, 44, **kw) as ref, m.Cavity(48, 40, 44, blocks=blocks, **kw) as c:
+        ref.step(60)
+        c.step(60)
+        assert np.array_equal(c.fields(), ref.fields())
+        assert c.time == ref.time
+
+
+def test_fp32_ghosts_and_buffers_bit_exact(m):
+    blocks = (2, 2, 2)
+    kw = dict(precision=m.CAVITY_FP32_MIXED, seed=9, noise_amp=1e-3, Ra=1e5)
+    with m.Cavity(48, 40, 44, **kw) as ref, m.Cavity(48, 40, 44, blocks=blocks, **kw) as c:
+        ref.step(30)
+        c.step(30)
+        NA = 6  # p_hi, p_lo, u, v, w, T
+        G = [m.cavity_get_block_array(ref.h, 0, f)[0] for f in range(NA)]
+        for b in range(8):
+            arrs = [m.cavity_get_block_array(c.h, b, f)[0] for f in range(NA)]
+            nx, ny, nz, ox, oy, oz = m.cavity_get_block_array(c.h, b, 0)[1]
+            n, org = (nx, ny, nz), (ox, oy, oz)
+            coords = [b % 2, (b // 2) % 2, b // 4]
+            for face in range(6):
+                a, hi = face // 2, face % 2
+                if not (0 <= coords[a] + (1 if hi else -1) < 2):
+                    continue
+                for f in range(NA):
+                    for L in ([n[a] + 1, n[a] + 2] if hi else [-1, 0]) if f < 2 else ([n[a] + 1] if hi else [0]):
+                        idx = [slice(2, 2 + n[d]) for d in range(3)]
+                        gidx = [slice(org[d] + 2, org[d] + 2 + n[d]) for d in range(3)]
+                        idx[a], gidx[a] = L + 1, org[a] + L + 1
+                        assert np.array_equal(arrs[f][idx[2], idx[1], idx[0]], G[f][gidx[2], gidx[1], gidx[0]])
+                bax, cax = [d for d in range(3) if d != a]
+                nb, nc = n[bax], n[cax]
+                buf = m.load_library()
+                out = np.empty(8 * nb * nc)
+                rc = buf.cavity_get_face_buffer(c.h, b, face, out.ctypes.data_as(m._dp), out.size)
+                assert rc == 0
+                exp = np.empty(8 * nb * nc)
+                for pa in range(2):
+                    for d in range(2):
+                        idx = [slice(2, 2 + n[0]), slice(2, 2 + n[1]), slice(2, 2 + n[2])]
+                        idx[a] = (n[a] - 1 + d if hi else 1 + d) + 1
+                        exp[2 * pa * nb * nc + d:2 * (pa + 1) * nb * nc:2] = arrs[pa][idx[2], idx[1], idx[0]].reshape(-1)
+                for v in range(4):
+                    idx = [slice(2, 2 + n[0]), slice(2, 2 + n[1]), slice(2, 2 + n[2])]
+                    idx[a] = (n[a] if hi else 1) + 1
+                    exp[4 * nb * nc + v * nb * nc:4 * nb * nc + (v + 1) * nb * nc] = \
+                        arrs[2 + v][idx[2], idx[1], idx[0]].reshape(-1)
+                assert np.array_equal(out, exp), (b, face)
+
+
+def test_fp32_set_fields_wall_field_and_nonfinite(m):
+    n = (28, 22, 19)
+    q = workloads.smooth_state(n, seed=3)
+    th = workloads.wall_temperature(n[1], n[2], seed=4)
+    o = oracle.OracleCavity(*n, dict(Ra=5e4), t_hot_wall=th)
+    o.set_fields(q)
+    with m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, Ra=5e4) as c:
+        m.cavity_set_wall_temperature(c.h, 0, th)
+        c.set_fields(q)
+        g = c.fields()
+        assert np.max(np.abs(g[0] - q[0])) <= 1e-12 * np.max(np.abs(q[0]))  # the hi/lo pair keeps p
+        assert np.array_equal(g[1:], q[1:].astype(np.float32).astype(np.float64))
+        o.step(30)
+        c.step(30)
+        assert_fields_close(c.fields(), o.fields(), FP32_TOL, "fp32 set_fields")
+        q2 = c.fields()
+        q2[3, 4, 4, 4] = np.nan
+        c.set_fields(q2)
+        c.step(1)
+        assert c.sync() == m.CAVITY_ERR_NONFINITE
