@@ -172,6 +172,38 @@ CAVITY_API int cavity_get_face_buffer(cavity_t *h, int block, int face, double *
 /* Pack and unpack every cut face of the current state (a7, a8 alone). */
 CAVITY_API int cavity_exchange(cavity_t *h);
 
+/* Batch of independent cavities advanced together (the batched form of the
+ * step): every launch covers all cavities through one block descriptor table
+ * and one work list per kernel, and each cavity's reductions finalise in
+ * parallel (one last-CTA counter per cavity).  descs[i] gives cavity i's size,
+ * seed and noise; each member is a single block (px = py = pz = 1); precision,
+ * device and stream come from descs[0].  params[i] are cavity i's parameters
+ * (params may be NULL for the defaults).  The single-cavity getters and
+ * cavity_set_wall_temperature address cavity 0; cavity_set_params sets every
+ * cavity. */
+CAVITY_API int cavity_create_batch(const cavity_desc *descs, const cavity_params *params, int n, cavity_t **out);
+
+/* Number of cavities of a handle (1 for cavity_create). */
+CAVITY_API int cavity_batch_size(cavity_t *h);
+
+/* State of cavity `cav`: out[0] step, out[1] t, out[2] next dt, out[3..7]
+ * RMS dq/dt of p, u, v, w, T of the last step, out[8] hot- and out[9]
+ * cold-wall Nusselt number. */
+CAVITY_API int cavity_batch_state(cavity_t *h, int cav, double out[10]);
+
+/* Interior fields of cavity `cav` (layout of cavity_get_fields, that
+ * cavity's nx, ny, nz). */
+CAVITY_API int cavity_batch_get_fields(cavity_t *h, int cav, int field_mask, double *host, size_t count);
+
+/* Autotuner of the FP32-mixed step kernel: times every compiled tile shape
+ * (x-y tile extent, z-chunk length, ring depth) for `steps` graph-replayed
+ * steps on this handle's own cavities and keeps the fastest.  The state is
+ * saved before the trials and restored after them (the step counter and the
+ * fields are as before the call).  out (optional) receives the chosen tile
+ * height, z-chunk, ring depth and microseconds per step.  FP64 handles have a
+ * single shape: CAVITY_ERR_UNSUPPORTED. */
+CAVITY_API int cavity_autotune(cavity_t *h, int steps, double out[4]);
+
 /* Measurement: run nsteps steps as plain launches (no graph replay) with CUDA
  * events around every kernel on the handle's stream.  ms[0..3] receive the
  * mean duration per launch of the fused step kernel, the wall/finalise

@@ -40,7 +40,8 @@ EXPORTED = (
     "cavity_set_fields",
     "cavity_get_time", "cavity_num_blocks", "cavity_get_block_array", "cavity_get_face_buffer",
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
-    "cavity_strerror", "cavity_last_error",
+    "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
+    "cavity_batch_get_fields", "cavity_autotune",
 )
 
 
@@ -95,6 +96,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_get_face_buffer": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
         "cavity_exchange": ([_H], ctypes.c_int),
         "cavity_time_kernels": ([_H, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_create_batch": ([ctypes.POINTER(cavity_desc), ctypes.POINTER(cavity_params), ctypes.c_int,
+                                 ctypes.POINTER(_H)], ctypes.c_int),
+        "cavity_batch_size": ([_H], ctypes.c_int),
+        "cavity_batch_state": ([_H, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_batch_get_fields": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
+        "cavity_autotune": ([_H, ctypes.c_int, _dp], ctypes.c_int),
         "cavity_step_block_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(cavity_params), ctypes.c_double, ctypes.c_double,
                                        ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
@@ -258,6 +265,47 @@ def cavity_sync(h) -> int:
 
 def cavity_destroy(h) -> None:
     _check(load_library().cavity_destroy(h))
+
+
+def cavity_create_batch(sizes, params_list=None, precision=CAVITY_FP32_MIXED, seeds=None, noise_amp=0.0,
+                        device=0, stream=None):
+    """Batch handle of len(sizes) single-block cavities; sizes = [(nx, ny, nz), ...]."""
+    n = len(sizes)
+    seeds = list(range(n)) if seeds is None else list(seeds)
+    noise = [noise_amp] * n if np.isscalar(noise_amp) else list(noise_amp)
+    descs = (cavity_desc * n)(*[cavity_desc(int(s[0]), int(s[1]), int(s[2]), 1, 1, 1, int(precision),
+                                            int(seeds[c]), float(noise[c]), int(device), stream)
+                                for c, s in enumerate(sizes)])
+    prm = None
+    if params_list is not None:
+        prm = (cavity_params * n)(*params_list)
+    h = _H()
+    _check(load_library().cavity_create_batch(descs, prm, n, ctypes.byref(h)))
+    return h
+
+
+def cavity_batch_size(h) -> int:
+    return _check(load_library().cavity_batch_size(h), h)
+
+
+def cavity_batch_state(h, cav: int) -> dict:
+    out = np.zeros(10)
+    _check(load_library().cavity_batch_state(h, int(cav), out.ctypes.data_as(_dp)), h)
+    return {"step": int(out[0]), "t": out[1], "dt": out[2], "residual": out[3:8].copy(),
+            "nusselt": (out[8], out[9])}
+
+
+def cavity_batch_get_fields(h, cav: int, shape, mask: int = CAVITY_FIELD_ALL) -> np.ndarray:
+    nx, ny, nz = shape
+    out = np.empty((_nfields(mask), nz, ny, nx))
+    _check(load_library().cavity_batch_get_fields(h, int(cav), int(mask), out.ctypes.data_as(_dp), out.size), h)
+    return out
+
+
+def cavity_autotune(h, steps: int = 20) -> dict:
+    out = np.zeros(4)
+    _check(load_library().cavity_autotune(h, int(steps), out.ctypes.data_as(_dp)), h)
+    return {"tile_y": int(out[0]), "kc": int(out[1]), "ring": int(out[2]), "us_per_step": out[3]}
 
 
 def cavity_strerror(code: int) -> str:

@@ -460,9 +460,11 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
   __shared__ bool am_last;
   const int cta = blockIdx.x, tid = threadIdx.x;
   double nu_h = 0.0, nu_c = 0.0;
+  int cav = 0;
   if (a.nfaces > 0) {
     const int fi = find_face(a.faces, a.nfaces, cta);
     const WallFace &F = a.faces[fi];
+    cav = F.cav;
     const int e = (cta - F.cta_begin) * kBcThreads + tid;
     if (e < F.n1 * F.n2) {
       const BlockDev &B = a.blocks[F.block];
@@ -483,15 +485,19 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
     for (int q = 0; q < kBcThreads / 32; ++q) { h += sh[2 * q]; c += sh[2 * q + 1]; }
     a.bc_partials[2LL * cta] = h;
     a.bc_partials[2LL * cta + 1] = c;
+    // the last of this cavity's CTAs to finish reduces the cavity (one
+    // counter per cavity, so the cavities of a batch finalise in parallel)
     __threadfence();
-    const unsigned int prev = atomicAdd(a.counter, 1u);
-    am_last = (prev == gridDim.x - 1);
+    const CavConst &C = a.cc[cav];
+    const unsigned int nct = (unsigned int)(a.mode == 2 ? C.nus_end - C.nus_begin : C.bc_end - C.bc_begin);
+    const unsigned int prev = atomicAdd(a.counter + cav, 1u);
+    am_last = (prev == nct - 1);
   }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  for (int cv = 0; cv < a.ncav; ++cv) finalize_cavity<S>(a, cv, sh);
-  if (tid == 0) *a.counter = 0u;
+  finalize_cavity<S>(a, cav, sh);
+  if (tid == 0) a.counter[cav] = 0u;
 }
 
 // ---------------------------------------------------------------------------

@@ -28,13 +28,12 @@
 
 namespace bdc {
 
-constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 64, kF32R = 8;  // default z chunk and ring depth
+constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 64, kF32R = 8;  // default tile height, z chunk, ring depth
 constexpr int kF32BX = kF32TX + 8;  // x halo 4 on each side: the box starts on a 16-byte boundary
-constexpr int kF32BY = kF32TY + 4;  // y halo 2 (pressure star)
 constexpr int kF32NA = 6;           // p_hi, p_lo, u, v, w, T
-constexpr int kF32SlotFloats = kF32NA * kF32BY * kF32BX;
-constexpr int kF32SlotBytes = kF32SlotFloats * 4;
-constexpr int f32_smem_bytes(int R) { return R * kF32SlotBytes + R * 8; }
+__host__ __device__ constexpr int f32_box_y(int TY) { return TY + 4; }  // y halo 2 (pressure star)
+__host__ __device__ constexpr int f32_slot_floats(int TY) { return kF32NA * f32_box_y(TY) * kF32BX; }
+__host__ __device__ constexpr int f32_smem_bytes(int TY, int R) { return R * f32_slot_floats(TY) * 4 + R * 8; }
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier wait, about 2 s
 
 struct StepF32Args {
@@ -124,36 +123,37 @@ __device__ __forceinline__ float wall_temperature(float t1, float t2) {
 }
 
 // Apply the x and y wall conditions to one freshly loaded plane slot.
-// Slot coordinates: lx = i - i0 + 4, ly = j - j0 + 2.  Threads 0..BX-1 take
-// the low y wall, 64.. the high y wall, 128.. the low x wall, 192.. the high
-// x wall (x walls: pressure only; their temperature is prescribed and stored).
-template <int NT>
+// Slot coordinates: lx = i - i0 + 4, ly = j - j0 + 2.  Threads [0, BX) take
+// the low y wall, [BX, 2BX) the high y wall, the next BY the low x wall and
+// the next BY the high x wall (x walls: pressure only; their temperature is
+// prescribed and stored).
+template <int NT, int BY>
 __device__ __forceinline__ void fix_plane_walls(float *s, int tid, bool wxl, bool wxh, bool wyl, bool wyh,
                                                 int lxh, int lyh) {
-  constexpr int BX = kF32BX, BY = kF32BY, AS = BX * BY;
+  constexpr int BX = kF32BX, AS = BX * BY;
   float *H = s, *L = s + AS, *T = s + 5 * AS;
-  static_assert(NT >= 192 + BY, "thread groups");
+  static_assert(NT >= 2 * (BX + BY), "thread groups");
   if (wyl && tid < BX) {
     const int x = tid;
     float hw, lw, hg, lg;
     wall_pressure(H[2 * BX + x], L[2 * BX + x], H[3 * BX + x], L[3 * BX + x], hw, lw, hg, lg);
     H[BX + x] = hw; L[BX + x] = lw; H[x] = hg; L[x] = lg;
     T[BX + x] = wall_temperature(T[2 * BX + x], T[3 * BX + x]);
-  } else if (wyh && tid >= 64 && tid < 64 + BX) {
-    const int x = tid - 64;
+  } else if (wyh && tid >= BX && tid < 2 * BX) {
+    const int x = tid - BX;
     const int r1 = lyh, r2 = lyh - 1;  // rows of nodes ny and ny - 1
     float hw, lw, hg, lg;
     wall_pressure(H[r1 * BX + x], L[r1 * BX + x], H[r2 * BX + x], L[r2 * BX + x], hw, lw, hg, lg);
     H[(r1 + 1) * BX + x] = hw; L[(r1 + 1) * BX + x] = lw;
     if (r1 + 2 < BY) { H[(r1 + 2) * BX + x] = hg; L[(r1 + 2) * BX + x] = lg; }
     T[(r1 + 1) * BX + x] = wall_temperature(T[r1 * BX + x], T[r2 * BX + x]);
-  } else if (wxl && tid >= 128 && tid < 128 + BY) {
-    const int y = tid - 128;
+  } else if (wxl && tid >= 2 * BX && tid < 2 * BX + BY) {
+    const int y = tid - 2 * BX;
     float hw, lw, hg, lg;
     wall_pressure(H[y * BX + 4], L[y * BX + 4], H[y * BX + 5], L[y * BX + 5], hw, lw, hg, lg);
     H[y * BX + 3] = hw; L[y * BX + 3] = lw; H[y * BX + 2] = hg; L[y * BX + 2] = lg;
-  } else if (wxh && tid >= 192 && tid < 192 + BY) {
-    const int y = tid - 192;
+  } else if (wxh && tid >= 2 * BX + BY && tid < 2 * (BX + BY)) {
+    const int y = tid - 2 * BX - BY;
     const int c1 = lxh, c2 = lxh - 1;  // columns of nodes nx and nx - 1
     float hw, lw, hg, lg;
     wall_pressure(H[y * BX + c1], L[y * BX + c1], H[y * BX + c2], L[y * BX + c2], hw, lw, hg, lg);
@@ -173,14 +173,15 @@ __device__ __forceinline__ float warp_max_f(float v) {
   return v;
 }
 
-template <int KC, int R>
-__global__ void __launch_bounds__(kF32TX *kF32TY, 2) k_step_f32(StepF32Args a) {
+template <int TY, int KC, int R>
+__global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(StepF32Args a) {
   static_assert(R >= 4 && (R & (R - 1)) == 0, "ring depth: a power of two >= 4");
-  constexpr int TX = kF32TX, TY = kF32TY, NT = TX * TY;
-  constexpr int BX = kF32BX, BY = kF32BY, AS = BX * BY;  // array stride inside a slot
+  constexpr int TX = kF32TX, NT = TX * TY;
+  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;  // array stride inside a slot
+  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float *ring = reinterpret_cast<float *>(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * kF32SlotBytes);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
 
   const int cta = blockIdx.x;
   const int b = find_block(a.blocks, a.nblocks, cta);
@@ -214,14 +215,14 @@ __global__ void __launch_bounds__(kF32TX *kF32TY, 2) k_step_f32(StepF32Args a) {
   int issued = 0;
   auto issue = [&](int pl) {
     const int s = pl & (R - 1);
-    mbar_expect_tx(&bars[s], kF32SlotBytes);
-    tma_load_4d(ring + s * kF32SlotFloats, map, &bars[s], x0, y0, zbase + pl, 0);
+    mbar_expect_tx(&bars[s], SB);
+    tma_load_4d(ring + s * SF, map, &bars[s], x0, y0, zbase + pl, 0);
   };
   if (tid == 0) {
     for (; issued < min(R, nplanes); ++issued) issue(issued);
   }
   auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1)); };
-  auto slot = [&](int pl) { return ring + (pl & (R - 1)) * kF32SlotFloats; };
+  auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
   const int col = (lj + 2) * BX + (li + 4);  // own column inside a slot
 
   // constants in FP32
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kF32TX *kF32TY, 2) k_step_f32(StepF32Args a) {
         Tq[pl - 1] = s[5 * AS + col];
       }
       if (pl == 3) T2next = s[5 * AS + col];
-      if (fix && pl >= 2) fix_plane_walls<NT>(s, tid, wxl, wxh, wyl, wyh, lxh, lyh);
+      if (fix && pl >= 2) fix_plane_walls<NT, BY>(s, tid, wxl, wxh, wyl, wyh, lxh, lyh);
     }
   }
   // bottom z wall inside the queue (queue slot q holds plane k0 - 2 + q);
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kF32TX *kF32TY, 2) k_step_f32(StepF32Args a) {
         }
         if (k + 1 == B.nz + 1) Tq[2] = wall_temperature(Tq[1], Tq[0]);
       }
-      if (fix) fix_plane_walls<NT>(sk2, tid, wxl, wxh, wyl, wyh, lxh, lyh);
+      if (fix) fix_plane_walls<NT, BY>(sk2, tid, wxl, wxh, wyl, wyh, lxh, lyh);
       if (active) {
         const float p0h = ph[2], p0l = pq[2];
         const float *H = sk, *L = sk + AS;

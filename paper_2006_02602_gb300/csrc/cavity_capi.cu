@@ -1,9 +1,11 @@
 // C ABI of the buoyancy-driven-cavity step (include/cavity.h): host runtime
-// that lays out the blocks in HBM, builds the work lists of the kernels in
-// bdc_device.cuh / bdc_step_f32.cuh, captures one CUDA graph per buffer
-// parity and replays it.  Two arithmetic forms share the runtime: FP64
-// (five FP64 arrays per buffer set) and FP32-mixed (p_hi, p_lo, u, v, w, T in
-// FP32, read by the step kernel through TMA tensor maps).
+// that lays out the blocks of one or many cavities in HBM, builds the work
+// lists of the kernels in bdc_device.cuh / bdc_step_f32.cuh, captures one CUDA
+// graph per buffer parity and replays it.  Two arithmetic forms share the
+// runtime: FP64 (five FP64 arrays per buffer set) and FP32-mixed (p_hi, p_lo,
+// u, v, w, T in FP32, read by the step kernel through TMA tensor maps).  A
+// handle holds either one cavity split into blocks (Section 3.2
+// decomposition) or a batch of single-block cavities.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -38,34 +40,54 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// FP32 step-kernel tile shapes compiled in: (tile height TY, z chunk KC, ring depth R)
+#define BDC_F32_VARIANTS(X) X(8, 16, 8) X(8, 32, 8) X(8, 64, 8) X(4, 32, 8) X(4, 64, 8)
+struct F32Shape {
+  int ty, kc, r;
+};
+const F32Shape kF32Shapes[] = {
+#define BDC_SHAPE(TY, KC, R) {TY, KC, R},
+    BDC_F32_VARIANTS(BDC_SHAPE)
+#undef BDC_SHAPE
+};
+
+bool f32_variant_ok(int ty, int kc, int r) {
+  for (const F32Shape &s : kF32Shapes)
+    if (s.ty == ty && s.kc == kc && s.r == r) return true;
+  return false;
+}
+
 }  // namespace
 
 struct cavity {
   int dev = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cavity_desc desc{};
-  cavity_params prm{};
-  bool f32 = false;  // FP32-mixed form
-  size_t esize = 8;  // bytes per stored element
-  int na = 5;        // stored arrays per buffer set
-  int np = 1;        // pressure arrays
+  int ncav = 1;
+  std::vector<cavity_desc> descs;
+  std::vector<cavity_params> prms;
+  std::vector<CavConst> hcc;
+  std::vector<char> wall_custom;  // 2 per cavity
+  std::vector<double> twall;      // per cavity: hot wall then cold wall (ny*nz each) at wall_off
+  bool f32 = false;               // FP32-mixed form
+  size_t esize = 8;               // bytes per stored element
+  int na = 5;                     // stored arrays per buffer set
+  int np = 1;                     // pressure arrays
   int tx = kTX, ty = kTY, kc = kKC;
-  int f32_r = 0;  // ring depth of the FP32 step kernel
+  int f32_r = 0;                  // ring depth of the FP32 step kernel
   int nblocks = 0;
   std::vector<BlockDev> hb;
   std::vector<WallFace> hwall;
   std::vector<WallFace> hnus;  // x-wall faces (Nusselt-only wall pass)
   std::vector<CutFace> hcut;
-  CavConst hcc{};
   long long xbuf_elems = 0;
   int n_step = 0, n_bc = 0, n_cut = 0, n_nus = 0;
-  WallFace *d_nus = nullptr;
+  int part_cap = 0;  // step partials allocated (CTAs)
 
   BlockDev *d_blocks = nullptr;
   CavConst *d_cc = nullptr;
   CavState *d_cs = nullptr;
-  WallFace *d_wall = nullptr;
+  WallFace *d_wall = nullptr, *d_nus = nullptr;
   CutFace *d_cut = nullptr;
   CUtensorMap *d_maps = nullptr;
   double *d_step_part = nullptr, *d_bc_part = nullptr, *d_twall = nullptr, *d_stage = nullptr;
@@ -74,8 +96,6 @@ struct cavity {
   size_t field_bytes = 0;
   size_t stage_elems = 0;
 
-  std::vector<double> twall;  // hot wall then cold wall, gny*gnz each
-  bool wall_custom[2] = {false, false};
   int parity = 0;
   long long steps_taken = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -114,10 +134,10 @@ long long host_node_index(const BlockDev &B, size_t esize, int i, int j, int k) 
   return (long long)(xo1(esize) - 1 + i) + (long long)B.pitch * (j + 1) + B.plane * (k + 1);
 }
 
-void fill_consts(cavity *h) {
-  CavConst &C = h->hcc;
-  const cavity_params &p = h->prm;
-  const int gn[3] = {h->desc.nx, h->desc.ny, h->desc.nz};
+void fill_consts(cavity *h, int c) {
+  CavConst &C = h->hcc[c];
+  const cavity_params &p = h->prms[c];
+  const int gn[3] = {h->descs[c].nx, h->descs[c].ny, h->descs[c].nz};
   double sih = 0.0;
   for (int d = 0; d < 3; ++d) {
     const double np1 = (double)gn[d] + 1.0;
@@ -155,71 +175,131 @@ int check_params(const cavity_params &p) {
   return CAVITY_OK;
 }
 
+int check_desc(const cavity_desc &d) {
+  if (d.nx < 2 || d.ny < 2 || d.nz < 2 || d.px < 1 || d.py < 1 || d.pz < 1) return CAVITY_ERR_INVALID_ARG;
+  if (d.nx / d.px < 2 || d.ny / d.py < 2 || d.nz / d.pz < 2) return CAVITY_ERR_INVALID_ARG;
+  if ((long long)d.nx * d.ny * d.nz > (1LL << 34)) return CAVITY_ERR_INVALID_ARG;
+  if (!(d.noise_amp >= 0.0) || !std::isfinite(d.noise_amp)) return CAVITY_ERR_INVALID_ARG;
+  if (d.precision != CAVITY_FP64 && d.precision != CAVITY_FP32_MIXED) return CAVITY_ERR_INVALID_ARG;
+  return CAVITY_OK;
+}
+
 // ---------------------------------------------------------------------------
-int build_layout(cavity *h) {
-  const cavity_desc &d = h->desc;
-  const int gn[3] = {d.nx, d.ny, d.nz};
-  const int pg[3] = {d.px, d.py, d.pz};
-  std::vector<int> sz[3], org[3];
-  for (int a = 0; a < 3; ++a) {
-    sz[a] = split_sizes(gn[a], pg[a]);
-    int o = 0;
-    for (int s : sz[a]) { org[a].push_back(o); o += s; }
+// layout: blocks of every cavity, wall / cut face lists, centre nodes
+
+void assign_tiles(cavity *h) {
+  int tile = 0;
+  for (int c = 0; c < h->ncav; ++c) h->hcc[c].tile_begin = -1;
+  for (BlockDev &B : h->hb) {
+    B.tiles_x = ceil_div(B.nx, h->tx);
+    B.tiles_y = ceil_div(B.ny, h->ty);
+    B.tiles_z = ceil_div(B.nz, h->kc);
+    B.tile_begin = tile;
+    CavConst &C = h->hcc[B.cav];
+    if (C.tile_begin < 0) C.tile_begin = tile;
+    tile += B.tiles_x * B.tiles_y * B.tiles_z;
+    C.tile_end = tile;
   }
+  h->n_step = tile;
+}
+
+int build_layout(cavity *h) {
   const size_t es = h->esize;
   const int row_align = (int)(128 / es);
-  h->nblocks = pg[0] * pg[1] * pg[2];
-  h->hb.assign(h->nblocks, BlockDev{});
+  h->hb.clear();
   size_t total_elems = 0;
-  int tile = 0;
-  for (int bz = 0; bz < pg[2]; ++bz)
-    for (int by = 0; by < pg[1]; ++by)
-      for (int bx = 0; bx < pg[0]; ++bx) {
-        const int id = bx + pg[0] * (by + pg[1] * bz);
-        BlockDev &B = h->hb[id];
-        B.nx = sz[0][bx]; B.ny = sz[1][by]; B.nz = sz[2][bz];
-        B.ox = org[0][bx]; B.oy = org[1][by]; B.oz = org[2][bz];
-        B.pitch = ((xo1(es) + B.nx + 2 + row_align - 1) / row_align) * row_align;
-        B.rows = B.ny + 4;
-        B.plane = (long long)B.pitch * B.rows;
-        B.fstride = ((B.plane * (B.nz + 4) + 63) / 64) * 64;
-        const int c[3] = {bx, by, bz};
-        for (int f = 0; f < 6; ++f) {
-          const int a = f / 2, hi = f % 2;
-          int cc[3] = {c[0], c[1], c[2]};
-          cc[a] += hi ? 1 : -1;
-          const bool inside = cc[a] >= 0 && cc[a] < pg[a];
-          B.wall[f] = inside ? 0 : 1;
-          B.nbr[f] = inside ? cc[0] + pg[0] * (cc[1] + pg[1] * cc[2]) : -1;
+  long long wall_off = 0;
+  for (int cv = 0; cv < h->ncav; ++cv) {
+    const cavity_desc &d = h->descs[cv];
+    const int pg[3] = {d.px, d.py, d.pz};
+    const int gn[3] = {d.nx, d.ny, d.nz};
+    std::vector<int> sz[3], org[3];
+    for (int a = 0; a < 3; ++a) {
+      sz[a] = split_sizes(gn[a], pg[a]);
+      int o = 0;
+      for (int s : sz[a]) { org[a].push_back(o); o += s; }
+    }
+    const int first = (int)h->hb.size();
+    for (int bz = 0; bz < pg[2]; ++bz)
+      for (int by = 0; by < pg[1]; ++by)
+        for (int bx = 0; bx < pg[0]; ++bx) {
+          BlockDev B{};
+          B.nx = sz[0][bx]; B.ny = sz[1][by]; B.nz = sz[2][bz];
+          B.ox = org[0][bx]; B.oy = org[1][by]; B.oz = org[2][bz];
+          B.pitch = ((xo1(es) + B.nx + 2 + row_align - 1) / row_align) * row_align;
+          B.rows = B.ny + 4;
+          B.plane = (long long)B.pitch * B.rows;
+          B.fstride = ((B.plane * (B.nz + 4) + 63) / 64) * 64;
+          const int c3[3] = {bx, by, bz};
+          for (int f = 0; f < 6; ++f) {
+            const int a = f / 2, hi = f % 2;
+            int cc[3] = {c3[0], c3[1], c3[2]};
+            cc[a] += hi ? 1 : -1;
+            const bool inside = cc[a] >= 0 && cc[a] < pg[a];
+            B.wall[f] = inside ? 0 : 1;
+            B.nbr[f] = inside ? first + cc[0] + pg[0] * (cc[1] + pg[1] * cc[2]) : -1;
+          }
+          B.cav = cv;
+          h->hb.push_back(B);
+          total_elems += 2 * (size_t)h->na * (size_t)B.fstride;
         }
-        B.cav = 0;
-        B.tiles_x = ceil_div(B.nx, h->tx);
-        B.tiles_y = ceil_div(B.ny, h->ty);
-        B.tiles_z = ceil_div(B.nz, h->kc);
-        B.tile_begin = tile;
-        tile += B.tiles_x * B.tiles_y * B.tiles_z;
-        total_elems += 2 * (size_t)h->na * (size_t)B.fstride;
-      }
-  h->n_step = tile;
+    CavConst &C = h->hcc[cv];
+    C.wall_off = wall_off;
+    wall_off += 2LL * d.ny * d.nz;
+    // centre nodes in (k, j, i) lexicographic order
+    std::vector<int> ax[3];
+    for (int a = 0; a < 3; ++a) {
+      if (gn[a] % 2 == 1) ax[a] = {(gn[a] + 1) / 2};
+      else ax[a] = {gn[a] / 2, gn[a] / 2 + 1};
+    }
+    int m = 0;
+    for (int K : ax[2])
+      for (int J : ax[1])
+        for (int I : ax[0]) {
+          for (int id = first; id < (int)h->hb.size(); ++id) {
+            const BlockDev &B = h->hb[id];
+            if (I > B.ox && I <= B.ox + B.nx && J > B.oy && J <= B.oy + B.ny && K > B.oz && K <= B.oz + B.nz) {
+              C.centre_blk[m] = id;
+              C.centre_off[m] = host_node_index(B, es, I - B.ox, J - B.oy, K - B.oz);
+            }
+          }
+          ++m;
+        }
+    C.ncentre = m;
+  }
+  h->nblocks = (int)h->hb.size();
   h->field_bytes = total_elems * es;
-  // wall and cut faces
-  int bc = 0, cut = 0;
+  h->twall.assign((size_t)wall_off, 0.0);
+  assign_tiles(h);
+  // wall faces (all, and the x walls alone), cut faces; contiguous per cavity
+  int bc = 0, cut = 0, nus = 0;
   long long xoff = 0;
   h->hwall.clear();
   h->hcut.clear();
+  h->hnus.clear();
+  for (int c = 0; c < h->ncav; ++c) {
+    h->hcc[c].bc_begin = h->hcc[c].nus_begin = -1;
+  }
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
+    CavConst &C = h->hcc[B.cav];
     const int n[3] = {B.nx, B.ny, B.nz};
     for (int f = 0; f < 6; ++f) {
       const int a = f / 2;
       const int n1 = n[a == 0 ? 1 : 0], n2 = n[a == 2 ? 1 : 2];
       if (B.wall[f]) {
-        WallFace w{id, f, n1, n2, bc, 0};
-        h->hwall.push_back(w);
+        h->hwall.push_back(WallFace{id, f, n1, n2, bc, B.cav});
+        if (C.bc_begin < 0) C.bc_begin = bc;
         bc += ceil_div((long long)n1 * n2, kBcThreads);
+        C.bc_end = bc;
+        if (a == 0) {
+          h->hnus.push_back(WallFace{id, f, n1, n2, nus, B.cav});
+          if (C.nus_begin < 0) C.nus_begin = nus;
+          nus += ceil_div((long long)n1 * n2, kBcThreads);
+          C.nus_end = nus;
+        }
       } else {
-        CutFace c{id, f, B.nbr[f], n1, n2, cut, xoff};
-        h->hcut.push_back(c);
+        h->hcut.push_back(CutFace{id, f, B.nbr[f], n1, n2, cut, xoff});
         cut += ceil_div((long long)n1 * n2, 256);
         xoff += (long long)(2 * h->np + 4) * n1 * n2;
       }
@@ -227,63 +307,9 @@ int build_layout(cavity *h) {
   }
   h->n_bc = bc;
   h->n_cut = cut;
-  h->xbuf_elems = xoff;
-  int nus = 0;
-  h->hnus.clear();
-  for (const WallFace &w : h->hwall) {
-    if (w.face / 2 != 0) continue;
-    WallFace x = w;
-    x.cta_begin = nus;
-    h->hnus.push_back(x);
-    nus += ceil_div((long long)w.n1 * w.n2, kBcThreads);
-  }
   h->n_nus = nus;
-  // cavity constants: work ranges and centre nodes
-  CavConst &C = h->hcc;
-  C.tile_begin = 0; C.tile_end = h->n_step;
-  C.bc_begin = 0; C.bc_end = h->n_bc;
-  C.nus_begin = 0; C.nus_end = h->n_nus;
-  C.wall_off = 0;
-  std::vector<int> ax[3];
-  for (int a = 0; a < 3; ++a) {
-    if (gn[a] % 2 == 1) ax[a] = {(gn[a] + 1) / 2};
-    else ax[a] = {gn[a] / 2, gn[a] / 2 + 1};
-  }
-  int m = 0;
-  for (int K : ax[2])
-    for (int J : ax[1])
-      for (int I : ax[0]) {
-        for (int id = 0; id < h->nblocks; ++id) {
-          const BlockDev &B = h->hb[id];
-          if (I > B.ox && I <= B.ox + B.nx && J > B.oy && J <= B.oy + B.ny && K > B.oz && K <= B.oz + B.nz) {
-            C.centre_blk[m] = id;
-            C.centre_off[m] = host_node_index(B, es, I - B.ox, J - B.oy, K - B.oz);
-          }
-        }
-        ++m;
-      }
-  C.ncentre = m;
+  h->xbuf_elems = xoff;
   return CAVITY_OK;
-}
-
-// FP32 step-kernel variants compiled in: (z chunk KC, ring depth R)
-#define BDC_F32_VARIANTS(X) X(16, 8) X(32, 8) X(64, 4) X(64, 8)
-
-bool f32_variant_ok(int kc, int r) {
-#define BDC_OK(KC, R) if (kc == KC && r == R) return true;
-  BDC_F32_VARIANTS(BDC_OK)
-#undef BDC_OK
-  return false;
-}
-
-cudaError_t f32_set_smem(int kc, int r) {
-#define BDC_ATTR(KC, R)                                                                                   \
-  if (kc == KC && r == R)                                                                                 \
-    return cudaFuncSetAttribute(k_step_f32<KC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                f32_smem_bytes(R));
-  BDC_F32_VARIANTS(BDC_ATTR)
-#undef BDC_ATTR
-  return cudaErrorInvalidValue;
 }
 
 // TMA descriptors of the FP32-mixed step kernel: one 4-D map per block and
@@ -301,7 +327,7 @@ int encode_maps(cavity *h) {
     for (int s = 0; s < 2; ++s) {
       const cuuint64_t dims[4] = {(cuuint64_t)B.pitch, (cuuint64_t)B.rows, (cuuint64_t)(B.nz + 4), (cuuint64_t)kF32NA};
       const cuuint64_t strides[3] = {(cuuint64_t)B.pitch * 4, (cuuint64_t)B.plane * 4, (cuuint64_t)B.fstride * 4};
-      const cuuint32_t box[4] = {(cuuint32_t)kF32BX, (cuuint32_t)kF32BY, 1, (cuuint32_t)kF32NA};
+      const cuuint32_t box[4] = {(cuuint32_t)kF32BX, (cuuint32_t)f32_box_y(h->ty), 1, (cuuint32_t)kF32NA};
       const cuuint32_t estr[4] = {1, 1, 1, 1};
       const CUresult r = encode(&maps[2 * id + s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.base[s], dims, strides, box,
                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -309,8 +335,35 @@ int encode_maps(cavity *h) {
       if (r != CUDA_SUCCESS) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
   }
-  CK(cudaMalloc(&h->d_maps, sizeof(CUtensorMap) * maps.size()));
+  if (!h->d_maps) CK(cudaMalloc(&h->d_maps, sizeof(CUtensorMap) * maps.size()));
   CK(cudaMemcpy(h->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+  return CAVITY_OK;
+}
+
+cudaError_t f32_set_smem(int ty, int kc, int r) {
+#define BDC_ATTR(TY, KC, R)                                                                              \
+  if (ty == TY && kc == KC && r == R)                                                                    \
+    return cudaFuncSetAttribute(k_step_f32<TY, KC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                f32_smem_bytes(TY, R));
+  BDC_F32_VARIANTS(BDC_ATTR)
+#undef BDC_ATTR
+  return cudaErrorInvalidValue;
+}
+
+int upload_tables(cavity *h) {
+  CK(cudaMemcpyAsync(h->d_blocks, h->hb.data(), sizeof(BlockDev) * h->nblocks, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_cc, h->hcc.data(), sizeof(CavConst) * h->ncav, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CAVITY_OK;
+}
+
+int ensure_partials(cavity *h) {
+  if (h->part_cap >= h->n_step) return CAVITY_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->d_step_part) cudaFree(h->d_step_part);
+  h->d_step_part = nullptr;
+  CK(cudaMalloc(&h->d_step_part, sizeof(double) * kPartStride * std::max(1, h->n_step)));
+  h->part_cap = h->n_step;
   return CAVITY_OK;
 }
 
@@ -325,40 +378,43 @@ int alloc_device(cavity *h) {
     }
   }
   CK(cudaMalloc(&h->d_blocks, sizeof(BlockDev) * h->nblocks));
-  CK(cudaMalloc(&h->d_cc, sizeof(CavConst)));
-  CK(cudaMalloc(&h->d_cs, sizeof(CavState)));
-  CK(cudaMemsetAsync(h->d_cs, 0, sizeof(CavState), h->stream));
+  CK(cudaMalloc(&h->d_cc, sizeof(CavConst) * h->ncav));
+  CK(cudaMalloc(&h->d_cs, sizeof(CavState) * h->ncav));
+  CK(cudaMemsetAsync(h->d_cs, 0, sizeof(CavState) * h->ncav, h->stream));
   CK(cudaMalloc(&h->d_wall, sizeof(WallFace) * std::max<size_t>(1, h->hwall.size())));
-  CK(cudaMalloc(&h->d_cut, sizeof(CutFace) * std::max<size_t>(1, h->hcut.size())));
   CK(cudaMalloc(&h->d_nus, sizeof(WallFace) * std::max<size_t>(1, h->hnus.size())));
-  if (!h->hnus.empty())
-    CK(cudaMemcpyAsync(h->d_nus, h->hnus.data(), sizeof(WallFace) * h->hnus.size(), cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMalloc(&h->d_step_part, sizeof(double) * kPartStride * std::max(1, h->n_step)));
+  CK(cudaMalloc(&h->d_cut, sizeof(CutFace) * std::max<size_t>(1, h->hcut.size())));
+  int rc = ensure_partials(h);
+  if (rc != CAVITY_OK) return rc;
   CK(cudaMalloc(&h->d_bc_part, sizeof(double) * 2 * std::max(1, h->n_bc)));
-  CK(cudaMalloc(&h->d_counter, sizeof(unsigned int)));
-  CK(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int), h->stream));
-  CK(cudaMalloc(&h->d_twall, sizeof(double) * 2 * (size_t)h->desc.ny * h->desc.nz));
+  CK(cudaMalloc(&h->d_counter, sizeof(unsigned int) * h->ncav));
+  CK(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int) * h->ncav, h->stream));
+  CK(cudaMalloc(&h->d_twall, sizeof(double) * std::max<size_t>(1, h->twall.size())));
   if (h->xbuf_elems > 0) CK(cudaMalloc(&h->d_xbuf, h->esize * (size_t)h->xbuf_elems));
-  CK(cudaMemcpyAsync(h->d_blocks, h->hb.data(), sizeof(BlockDev) * h->nblocks, cudaMemcpyHostToDevice, h->stream));
   if (!h->hwall.empty())
     CK(cudaMemcpyAsync(h->d_wall, h->hwall.data(), sizeof(WallFace) * h->hwall.size(), cudaMemcpyHostToDevice, h->stream));
+  if (!h->hnus.empty())
+    CK(cudaMemcpyAsync(h->d_nus, h->hnus.data(), sizeof(WallFace) * h->hnus.size(), cudaMemcpyHostToDevice, h->stream));
   if (!h->hcut.empty())
     CK(cudaMemcpyAsync(h->d_cut, h->hcut.data(), sizeof(CutFace) * h->hcut.size(), cudaMemcpyHostToDevice, h->stream));
   if (h->f32) {
-    int rc = encode_maps(h);
+    rc = encode_maps(h);
     if (rc != CAVITY_OK) return rc;
-    CK(f32_set_smem(h->kc, h->f32_r));
+    CK(f32_set_smem(h->ty, h->kc, h->f32_r));
   }
   return CAVITY_OK;
 }
 
 int upload_consts(cavity *h) {
-  fill_consts(h);
-  const size_t nw = (size_t)h->desc.ny * h->desc.nz;
-  if (h->twall.size() != 2 * nw) h->twall.assign(2 * nw, 0.0);
-  if (!h->wall_custom[0]) std::fill(h->twall.begin(), h->twall.begin() + nw, h->prm.t_hot);
-  if (!h->wall_custom[1]) std::fill(h->twall.begin() + nw, h->twall.end(), h->prm.t_cold);
-  CK(cudaMemcpyAsync(h->d_cc, &h->hcc, sizeof(CavConst), cudaMemcpyHostToDevice, h->stream));
+  for (int c = 0; c < h->ncav; ++c) {
+    fill_consts(h, c);
+    const size_t nw = (size_t)h->descs[c].ny * h->descs[c].nz;
+    double *tw = h->twall.data() + h->hcc[c].wall_off;
+    if (!h->wall_custom[2 * c]) std::fill(tw, tw + nw, h->prms[c].t_hot);
+    if (!h->wall_custom[2 * c + 1]) std::fill(tw + nw, tw + 2 * nw, h->prms[c].t_cold);
+  }
+  int rc = upload_tables(h);
+  if (rc != CAVITY_OK) return rc;
   CK(cudaMemcpyAsync(h->d_twall, h->twall.data(), sizeof(double) * h->twall.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));  // the host vectors may change after return
   return CAVITY_OK;
@@ -386,7 +442,7 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.blocks = h->d_blocks;
   a.faces = mode == 2 ? h->d_nus : h->d_wall;
   a.nfaces = (int)(mode == 2 ? h->hnus.size() : h->hwall.size());
-  a.cc = h->d_cc; a.cs = h->d_cs; a.ncav = 1;
+  a.cc = h->d_cc; a.cs = h->d_cs; a.ncav = h->ncav;
   a.step_partials = h->d_step_part; a.bc_partials = h->d_bc_part; a.counter = h->d_counter;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
   return a;
@@ -401,14 +457,27 @@ ExchArgs exch_args(cavity *h, int parity) {
 
 void launch_step_kernel(cavity *h, int parity) {
   if (h->f32) {
-#define BDC_LAUNCH(KC, R)                                                                                   \
-  if (h->kc == KC && h->f32_r == R)                                                                         \
-    k_step_f32<KC, R><<<h->n_step, dim3(kF32TX, kF32TY), f32_smem_bytes(R), h->stream>>>( \
+#define BDC_LAUNCH(TY, KC, R)                                                                          \
+  if (h->ty == TY && h->kc == KC && h->f32_r == R)                                                     \
+    k_step_f32<TY, KC, R><<<h->n_step, dim3(kF32TX, TY), f32_smem_bytes(TY, R), h->stream>>>(          \
         step_f32_args(h, parity));
     BDC_F32_VARIANTS(BDC_LAUNCH)
 #undef BDC_LAUNCH
   } else {
     k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, parity, 0));
+  }
+}
+
+void launch_spectral(cavity *h) {
+  const StepArgs sa = step_args(h, h->parity, 1);
+  if (h->f32) {
+#define BDC_SPEC(TY, KC, R)                                                                                      \
+  if (h->ty == TY && h->kc == KC && h->f32_r == R)                                                               \
+    k_spectral<float, kF32TX, TY, KC><<<h->n_step, dim3(kF32TX, TY), 0, h->stream>>>(sa);
+    BDC_F32_VARIANTS(BDC_SPEC)
+#undef BDC_SPEC
+  } else {
+    k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(sa);
   }
 }
 
@@ -453,13 +522,7 @@ int launch_step(cavity *h, int parity) {
 
 // walls, ghosts, dt and Nusselt of the state in the current buffer set (no step)
 int refresh_state(cavity *h) {
-  if (h->f32) {
-    const StepArgs sa = step_args(h, h->parity, 1);
-    if (h->kc == 16) k_spectral<float, kF32TX, kF32TY, 16><<<h->n_step, dim3(kF32TX, kF32TY), 0, h->stream>>>(sa);
-    else if (h->kc == 32) k_spectral<float, kF32TX, kF32TY, 32><<<h->n_step, dim3(kF32TX, kF32TY), 0, h->stream>>>(sa);
-    else k_spectral<float, kF32TX, kF32TY, 64><<<h->n_step, dim3(kF32TX, kF32TY), 0, h->stream>>>(sa);
-  } else
-    k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, h->parity, 1));
+  launch_spectral(h);
   CK(cudaGetLastError());
   launch_bc_kernel(h, h->parity, 1);
   CK(cudaGetLastError());
@@ -487,14 +550,31 @@ int build_graphs(cavity *h) {
   return CAVITY_OK;
 }
 
+// change the FP32 step kernel's tile shape: work lists, maps, graphs
+int retile(cavity *h, int ty, int kc, int r) {
+  CK(cudaStreamSynchronize(h->stream));
+  h->ty = ty;
+  h->kc = kc;
+  h->f32_r = r;
+  assign_tiles(h);
+  int rc = ensure_partials(h);
+  if (rc == CAVITY_OK) rc = upload_tables(h);
+  if (rc == CAVITY_OK) rc = encode_maps(h);
+  if (rc != CAVITY_OK) return rc;
+  CK(f32_set_smem(ty, kc, r));
+  return build_graphs(h);
+}
+
 int init_state(cavity *h) {
   CK(cudaMemsetAsync(h->d_fields, 0, h->field_bytes, h->stream));
-  CK(cudaMemsetAsync(h->d_cs, 0, sizeof(CavState), h->stream));
+  CK(cudaMemsetAsync(h->d_cs, 0, sizeof(CavState) * h->ncav, h->stream));
   h->parity = 0;
   h->steps_taken = 0;
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
-    InitArgs a{h->d_blocks, h->d_cc, id, 0, h->desc.seed, h->desc.noise_amp, h->prm.t_hot, h->prm.t_cold};
+    const cavity_desc &d = h->descs[B.cav];
+    const cavity_params &p = h->prms[B.cav];
+    InitArgs a{h->d_blocks, h->d_cc, id, 0, d.seed, d.noise_amp, p.t_hot, p.t_cold};
     const long long n = (long long)B.nx * B.ny * B.nz;
     if (h->f32) k_init<float><<<ceil_div(n, 256), 256, 0, h->stream>>>(a);
     else k_init<double><<<ceil_div(n, 256), 256, 0, h->stream>>>(a);
@@ -523,8 +603,15 @@ int popcount5(int m) {
   return c;
 }
 
-int read_state(cavity *h, CavState *st) {
-  CK(cudaMemcpyAsync(st, h->d_cs, sizeof(CavState), cudaMemcpyDeviceToHost, h->stream));
+int read_states(cavity *h, std::vector<CavState> &st) {
+  st.resize(h->ncav);
+  CK(cudaMemcpyAsync(st.data(), h->d_cs, sizeof(CavState) * h->ncav, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CAVITY_OK;
+}
+
+int read_state(cavity *h, int cav, CavState *st) {
+  CK(cudaMemcpyAsync(st, h->d_cs + cav, sizeof(CavState), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return CAVITY_OK;
 }
@@ -532,6 +619,44 @@ int read_state(cavity *h, CavState *st) {
 int state_status(const CavState &st) {
   if (st.flags & 2) return CAVITY_ERR_TIMEOUT;
   if (st.flags & 1) return CAVITY_ERR_NONFINITE;
+  return CAVITY_OK;
+}
+
+int all_status(cavity *h) {
+  std::vector<CavState> st;
+  int rc = read_states(h, st);
+  if (rc != CAVITY_OK) return rc;
+  int worst = CAVITY_OK;
+  for (const CavState &s : st) {
+    const int r = state_status(s);
+    if (r == CAVITY_ERR_TIMEOUT) return r;
+    if (r != CAVITY_OK) worst = r;
+  }
+  return worst;
+}
+
+int get_fields_cav(cavity *h, int cav, int mask, double *host, size_t count) {
+  if (!host || mask <= 0 || mask > CAVITY_FIELD_ALL || cav < 0 || cav >= h->ncav) return CAVITY_ERR_INVALID_ARG;
+  const cavity_desc &d = h->descs[cav];
+  const size_t N = (size_t)d.nx * d.ny * d.nz;
+  if (count != (size_t)popcount5(mask) * N) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
+  DeviceGuard g(h->dev);
+  int rc = ensure_stage(h, count);
+  if (rc != CAVITY_OK) return rc;
+  CavState st;
+  rc = read_state(h, cav, &st);
+  if (rc != CAVITY_OK) return rc;
+  for (int id = 0; id < h->nblocks; ++id) {
+    const BlockDev &B = h->hb[id];
+    if (B.cav != cav) continue;
+    MoveArgs a{h->d_blocks, id, h->parity, mask, {d.nx, d.ny, d.nz}, h->d_stage, st.c};
+    const int grid = ceil_div((long long)B.nx * B.ny * B.nz, 256);
+    if (h->f32) k_gather<float><<<grid, 256, 0, h->stream>>>(a);
+    else k_gather<double><<<grid, 256, 0, h->stream>>>(a);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(host, h->d_stage, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return CAVITY_OK;
 }
 
@@ -546,36 +671,40 @@ void release(cavity *h) {
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
-}  // namespace
-
-// ===========================================================================
-extern "C" {
-
-int cavity_default_params(cavity_params *p) {
-  if (!p) return CAVITY_ERR_INVALID_ARG;
-  p->Ra = 1e5; p->Pr = 0.71; p->cfl = 0.5; p->kappa = 0.1; p->c4 = 1.0 / 32.0;
-  p->u_ref = -1.0; p->t_inf = NAN; p->t_hot = 1.0; p->t_cold = 0.0; p->gravity_axis = 2;
-  resolve_defaults(p);
-  return CAVITY_OK;
-}
-
-int cavity_create(const cavity_desc *desc, cavity_t **out) {
+int create_common(const cavity_desc *descs, const cavity_params *params, int n, cavity_t **out) {
   if (!out) return CAVITY_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!desc) return CAVITY_ERR_INVALID_ARG;
-  const cavity_desc &d = *desc;
-  if (d.nx < 2 || d.ny < 2 || d.nz < 2 || d.px < 1 || d.py < 1 || d.pz < 1) return CAVITY_ERR_INVALID_ARG;
-  if (d.nx / d.px < 2 || d.ny / d.py < 2 || d.nz / d.pz < 2) return CAVITY_ERR_INVALID_ARG;
-  if ((long long)d.nx * d.ny * d.nz > (1LL << 34)) return CAVITY_ERR_INVALID_ARG;
-  if (!(d.noise_amp >= 0.0) || !std::isfinite(d.noise_amp)) return CAVITY_ERR_INVALID_ARG;
-  if (d.precision != CAVITY_FP64 && d.precision != CAVITY_FP32_MIXED) return CAVITY_ERR_INVALID_ARG;
+  if (!descs || n < 1) return CAVITY_ERR_INVALID_ARG;
+  for (int c = 0; c < n; ++c) {
+    if (check_desc(descs[c]) != CAVITY_OK) return CAVITY_ERR_INVALID_ARG;
+    if (n > 1 && (descs[c].px != 1 || descs[c].py != 1 || descs[c].pz != 1)) return CAVITY_ERR_INVALID_ARG;
+    if (descs[c].precision != descs[0].precision) return CAVITY_ERR_INVALID_ARG;
+    if (params) {
+      cavity_params q = params[c];
+      resolve_defaults(&q);
+      if (check_params(q) != CAVITY_OK) return CAVITY_ERR_INVALID_ARG;
+    }
+  }
+  const cavity_desc &d0 = descs[0];
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || d.device < 0 || d.device >= ndev) return CAVITY_ERR_CUDA;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || d0.device < 0 || d0.device >= ndev) return CAVITY_ERR_CUDA;
   cavity *h = new (std::nothrow) cavity();
   if (!h) return CAVITY_ERR_OOM;
-  h->desc = d;
-  h->dev = d.device;
-  h->f32 = d.precision == CAVITY_FP32_MIXED;
+  h->ncav = n;
+  h->descs.assign(descs, descs + n);
+  h->prms.resize(n);
+  for (int c = 0; c < n; ++c) {
+    if (params) {
+      h->prms[c] = params[c];
+      resolve_defaults(&h->prms[c]);
+    } else {
+      cavity_default_params(&h->prms[c]);
+    }
+  }
+  h->hcc.assign(n, CavConst{});
+  h->wall_custom.assign(2 * n, 0);
+  h->dev = d0.device;
+  h->f32 = d0.precision == CAVITY_FP32_MIXED;
   h->esize = h->f32 ? 4 : 8;
   h->na = h->f32 ? Store<float>::NA : Store<double>::NA;
   h->np = h->f32 ? Store<float>::NP : Store<double>::NP;
@@ -584,21 +713,21 @@ int cavity_create(const cavity_desc *desc, cavity_t **out) {
     h->ty = kF32TY;
     h->kc = kF32KC;
     h->f32_r = kF32R;
-    // tile override for tuning sweeps: BDC_F32_TILE="KC,R" (a compiled variant)
+    // tile override for tuning sweeps: BDC_F32_TILE="TY,KC,R" (a compiled shape)
     if (const char *env = std::getenv("BDC_F32_TILE")) {
-      int kc = 0, r = 0;
-      if (std::sscanf(env, "%d,%d", &kc, &r) == 2 && f32_variant_ok(kc, r)) {
+      int ty = 0, kc = 0, r = 0;
+      if (std::sscanf(env, "%d,%d,%d", &ty, &kc, &r) == 3 && f32_variant_ok(ty, kc, r)) {
+        h->ty = ty;
         h->kc = kc;
         h->f32_r = r;
       }
     }
   }
-  cavity_default_params(&h->prm);
   int rc = CAVITY_OK;
   {
     DeviceGuard g(h->dev);
-    if (d.stream) {
-      h->stream = (cudaStream_t)d.stream;
+    if (d0.stream) {
+      h->stream = (cudaStream_t)d0.stream;
     } else {
       if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) rc = CAVITY_ERR_CUDA;
       h->own_stream = true;
@@ -619,6 +748,27 @@ int cavity_create(const cavity_desc *desc, cavity_t **out) {
   return CAVITY_OK;
 }
 
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int cavity_default_params(cavity_params *p) {
+  if (!p) return CAVITY_ERR_INVALID_ARG;
+  p->Ra = 1e5; p->Pr = 0.71; p->cfl = 0.5; p->kappa = 0.1; p->c4 = 1.0 / 32.0;
+  p->u_ref = -1.0; p->t_inf = NAN; p->t_hot = 1.0; p->t_cold = 0.0; p->gravity_axis = 2;
+  resolve_defaults(p);
+  return CAVITY_OK;
+}
+
+int cavity_create(const cavity_desc *desc, cavity_t **out) { return create_common(desc, nullptr, 1, out); }
+
+int cavity_create_batch(const cavity_desc *descs, const cavity_params *params, int n, cavity_t **out) {
+  return create_common(descs, params, n, out);
+}
+
+int cavity_batch_size(cavity_t *h) { return h ? h->ncav : CAVITY_ERR_INVALID_ARG; }
+
 int cavity_set_params(cavity_t *h, const cavity_params *p) {
   if (!h || !p) return CAVITY_ERR_INVALID_ARG;
   cavity_params q = *p;
@@ -626,7 +776,7 @@ int cavity_set_params(cavity_t *h, const cavity_params *p) {
   if (check_params(q) != CAVITY_OK) return fail(h, CAVITY_ERR_INVALID_ARG, "invalid parameters");
   DeviceGuard g(h->dev);
   CK(cudaStreamSynchronize(h->stream));
-  h->prm = q;
+  for (auto &pc : h->prms) pc = q;
   int rc = upload_consts(h);
   if (rc != CAVITY_OK) return rc;
   if (h->steps_taken == 0) return init_state(h);
@@ -635,14 +785,14 @@ int cavity_set_params(cavity_t *h, const cavity_params *p) {
 
 int cavity_set_wall_temperature(cavity_t *h, int wall, const double *host, size_t n) {
   if (!h || !host || (wall != 0 && wall != 1)) return CAVITY_ERR_INVALID_ARG;
-  const size_t nw = (size_t)h->desc.ny * h->desc.nz;
+  const size_t nw = (size_t)h->descs[0].ny * h->descs[0].nz;
   if (n != nw) return fail(h, CAVITY_ERR_INVALID_ARG, "wall temperature count must be ny*nz");
   for (size_t q = 0; q < n; ++q)
     if (!std::isfinite(host[q])) return fail(h, CAVITY_ERR_INVALID_ARG, "non-finite wall temperature");
   DeviceGuard g(h->dev);
   CK(cudaStreamSynchronize(h->stream));
-  std::copy(host, host + n, h->twall.begin() + (wall ? nw : 0));
-  h->wall_custom[wall] = true;
+  std::copy(host, host + n, h->twall.begin() + h->hcc[0].wall_off + (wall ? nw : 0));
+  h->wall_custom[wall] = 1;
   int rc = upload_consts(h);
   if (rc != CAVITY_OK) return rc;
   return refresh_state(h);
@@ -659,11 +809,31 @@ int cavity_step(cavity_t *h, int nsteps) {
   return CAVITY_OK;
 }
 
+int cavity_batch_state(cavity_t *h, int cav, double out[10]) {
+  if (!h || !out || cav < 0 || cav >= h->ncav) return CAVITY_ERR_INVALID_ARG;
+  DeviceGuard g(h->dev);
+  CavState st;
+  int rc = read_state(h, cav, &st);
+  if (rc != CAVITY_OK) return rc;
+  out[0] = (double)st.step;
+  out[1] = st.t;
+  out[2] = st.dt;
+  for (int f = 0; f < 5; ++f) out[3 + f] = st.res[f];
+  out[8] = st.nu_hot;
+  out[9] = st.nu_cold;
+  return state_status(st);
+}
+
+int cavity_batch_get_fields(cavity_t *h, int cav, int mask, double *host, size_t count) {
+  if (!h) return CAVITY_ERR_INVALID_ARG;
+  return get_fields_cav(h, cav, mask, host, count);
+}
+
 int cavity_residual(cavity_t *h, double out[5]) {
   if (!h || !out) return CAVITY_ERR_INVALID_ARG;
   DeviceGuard g(h->dev);
   CavState st;
-  int rc = read_state(h, &st);
+  int rc = read_state(h, 0, &st);
   if (rc != CAVITY_OK) return rc;
   for (int f = 0; f < 5; ++f) out[f] = st.res[f];
   return state_status(st);
@@ -673,7 +843,7 @@ int cavity_nusselt(cavity_t *h, double *hot, double *cold) {
   if (!h) return CAVITY_ERR_INVALID_ARG;
   DeviceGuard g(h->dev);
   CavState st;
-  int rc = read_state(h, &st);
+  int rc = read_state(h, 0, &st);
   if (rc != CAVITY_OK) return rc;
   if (hot) *hot = st.nu_hot;
   if (cold) *cold = st.nu_cold;
@@ -684,7 +854,7 @@ int cavity_get_time(cavity_t *h, long long *step, double *t, double *dt) {
   if (!h) return CAVITY_ERR_INVALID_ARG;
   DeviceGuard g(h->dev);
   CavState st;
-  int rc = read_state(h, &st);
+  int rc = read_state(h, 0, &st);
   if (rc != CAVITY_OK) return rc;
   if (step) *step = st.step;
   if (t) *t = st.t;
@@ -693,33 +863,16 @@ int cavity_get_time(cavity_t *h, long long *step, double *t, double *dt) {
 }
 
 int cavity_get_fields(cavity_t *h, int mask, double *host, size_t count) {
-  if (!h || !host || mask <= 0 || mask > CAVITY_FIELD_ALL) return CAVITY_ERR_INVALID_ARG;
-  const size_t N = (size_t)h->desc.nx * h->desc.ny * h->desc.nz;
-  if (count != (size_t)popcount5(mask) * N) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
-  DeviceGuard g(h->dev);
-  int rc = ensure_stage(h, count);
-  if (rc != CAVITY_OK) return rc;
-  CavState st;
-  rc = read_state(h, &st);
-  if (rc != CAVITY_OK) return rc;
-  for (int id = 0; id < h->nblocks; ++id) {
-    const BlockDev &B = h->hb[id];
-    MoveArgs a{h->d_blocks, id, h->parity, mask, {h->desc.nx, h->desc.ny, h->desc.nz}, h->d_stage, st.c};
-    const int grid = ceil_div((long long)B.nx * B.ny * B.nz, 256);
-    if (h->f32) k_gather<float><<<grid, 256, 0, h->stream>>>(a);
-    else k_gather<double><<<grid, 256, 0, h->stream>>>(a);
-    CK(cudaGetLastError());
-  }
-  CK(cudaMemcpyAsync(host, h->d_stage, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  return CAVITY_OK;
+  if (!h) return CAVITY_ERR_INVALID_ARG;
+  return get_fields_cav(h, 0, mask, host, count);
 }
 
 int cavity_get_fields_box(cavity_t *h, int mask, int i0, int j0, int k0, int ni, int nj, int nk, double *host,
                           size_t count) {
   if (!h || !host || mask <= 0 || mask > CAVITY_FIELD_ALL) return CAVITY_ERR_INVALID_ARG;
-  if (ni < 1 || nj < 1 || nk < 1 || i0 < 1 || j0 < 1 || k0 < 1 || i0 + ni - 1 > h->desc.nx ||
-      j0 + nj - 1 > h->desc.ny || k0 + nk - 1 > h->desc.nz)
+  const cavity_desc &d = h->descs[0];
+  if (ni < 1 || nj < 1 || nk < 1 || i0 < 1 || j0 < 1 || k0 < 1 || i0 + ni - 1 > d.nx || j0 + nj - 1 > d.ny ||
+      k0 + nk - 1 > d.nz)
     return fail(h, CAVITY_ERR_INVALID_ARG, "box outside the interior");
   const size_t n = (size_t)ni * nj * nk;
   if (count != (size_t)popcount5(mask) * n) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
@@ -727,9 +880,11 @@ int cavity_get_fields_box(cavity_t *h, int mask, int i0, int j0, int k0, int ni,
   int rc = ensure_stage(h, count);
   if (rc != CAVITY_OK) return rc;
   CavState st;
-  rc = read_state(h, &st);
+  rc = read_state(h, 0, &st);
   if (rc != CAVITY_OK) return rc;
-  BoxArgs a{h->d_blocks, h->nblocks, h->parity, mask, i0, j0, k0, ni, nj, nk, h->d_stage, st.c};
+  int nb0 = 0;  // blocks of cavity 0
+  while (nb0 < h->nblocks && h->hb[nb0].cav == 0) ++nb0;
+  BoxArgs a{h->d_blocks, nb0, h->parity, mask, i0, j0, k0, ni, nj, nk, h->d_stage, st.c};
   if (h->f32) k_gather_box<float><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(a);
   else k_gather_box<double><<<ceil_div((long long)n, 256), 256, 0, h->stream>>>(a);
   CK(cudaGetLastError());
@@ -740,17 +895,19 @@ int cavity_get_fields_box(cavity_t *h, int mask, int i0, int j0, int k0, int ni,
 
 int cavity_set_fields(cavity_t *h, int mask, const double *host, size_t count) {
   if (!h || !host || mask <= 0 || mask > CAVITY_FIELD_ALL) return CAVITY_ERR_INVALID_ARG;
-  const size_t N = (size_t)h->desc.nx * h->desc.ny * h->desc.nz;
+  const cavity_desc &d = h->descs[0];
+  const size_t N = (size_t)d.nx * d.ny * d.nz;
   if (count != (size_t)popcount5(mask) * N) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
   DeviceGuard g(h->dev);
   int rc = ensure_stage(h, count);
   if (rc != CAVITY_OK) return rc;
   CavState st;
-  rc = read_state(h, &st);
+  rc = read_state(h, 0, &st);
   if (rc != CAVITY_OK) return rc;
   // fold the pending centre shift into the stored p, then c = 0
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
+    if (B.cav != 0) continue;
     if (st.c != 0.0 && !(mask & CAVITY_FIELD_P)) {
       const int grid = ceil_div((long long)(B.nx + 4) * (B.ny + 4) * (B.nz + 4), 256);
       if (h->f32) k_shift_p<float><<<grid, 256, 0, h->stream>>>(h->d_blocks, id, h->parity, st.c);
@@ -758,11 +915,12 @@ int cavity_set_fields(cavity_t *h, int mask, const double *host, size_t count) {
       CK(cudaGetLastError());
     }
   }
-  CK(cudaMemsetAsync(&h->d_cs->c, 0, sizeof(double), h->stream));
+  CK(cudaMemsetAsync(&h->d_cs[0].c, 0, sizeof(double), h->stream));
   CK(cudaMemcpyAsync(h->d_stage, host, count * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
-    MoveArgs a{h->d_blocks, id, h->parity, mask, {h->desc.nx, h->desc.ny, h->desc.nz}, h->d_stage, 0.0};
+    if (B.cav != 0) continue;
+    MoveArgs a{h->d_blocks, id, h->parity, mask, {d.nx, d.ny, d.nz}, h->d_stage, 0.0};
     const int grid = ceil_div((long long)B.nx * B.ny * B.nz, 256);
     if (h->f32) k_scatter<float><<<grid, 256, 0, h->stream>>>(a);
     else k_scatter<double><<<grid, 256, 0, h->stream>>>(a);
@@ -823,6 +981,67 @@ int cavity_exchange(cavity_t *h) {
   return launch_exchange(h, h->parity);
 }
 
+int cavity_autotune(cavity_t *h, int steps, double out[4]) {
+  if (!h || steps < 1) return CAVITY_ERR_INVALID_ARG;
+  if (!h->f32) return fail(h, CAVITY_ERR_UNSUPPORTED, "the FP64 form has one tile shape");
+  DeviceGuard g(h->dev);
+  CK(cudaStreamSynchronize(h->stream));
+  // save the state (fields, per-cavity scalars, ping-pong parity, step count)
+  void *backup = nullptr;
+  CK(cudaMalloc(&backup, h->field_bytes));
+  std::vector<CavState> st0;
+  int rc = read_states(h, st0);
+  const int par0 = h->parity;
+  const long long steps0 = h->steps_taken;
+  auto restore = [&]() -> int {
+    CK(cudaMemcpyAsync(h->d_fields, backup, h->field_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_cs, st0.data(), sizeof(CavState) * h->ncav, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->parity = par0;
+    h->steps_taken = steps0;
+    return CAVITY_OK;
+  };
+  if (rc == CAVITY_OK && cudaMemcpyAsync(backup, h->d_fields, h->field_bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    rc = fail(h, CAVITY_ERR_CUDA, "state backup failed");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == CAVITY_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(h, CAVITY_ERR_CUDA, "event creation failed");
+  double best_us = 1e300;
+  F32Shape best = {h->ty, h->kc, h->f32_r};
+  for (const F32Shape &s : kF32Shapes) {
+    if (rc != CAVITY_OK) break;
+    rc = retile(h, s.ty, s.kc, s.r);
+    if (rc != CAVITY_OK) break;
+    rc = cavity_step(h, 2);  // warm-up
+    if (rc != CAVITY_OK) break;
+    cudaEventRecord(e0, h->stream);
+    rc = cavity_step(h, steps);
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(h, CAVITY_ERR_CUDA, "trial failed");
+    if (rc != CAVITY_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double us = 1e3 * ms / steps;
+    if (us < best_us) {
+      best_us = us;
+      best = s;
+    }
+    rc = restore();
+  }
+  if (rc == CAVITY_OK) rc = retile(h, best.ty, best.kc, best.r);
+  if (rc == CAVITY_OK) rc = restore();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(backup);
+  if (rc == CAVITY_OK && out) {
+    out[0] = best.ty;
+    out[1] = best.kc;
+    out[2] = best.r;
+    out[3] = best_us;
+  }
+  return rc;
+}
+
 int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
   if (!h || !ms || nsteps < 1) return CAVITY_ERR_INVALID_ARG;
   DeviceGuard g(h->dev);
@@ -861,10 +1080,7 @@ int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
 int cavity_sync(cavity_t *h) {
   if (!h) return CAVITY_ERR_INVALID_ARG;
   DeviceGuard g(h->dev);
-  CavState st;
-  int rc = read_state(h, &st);
-  if (rc != CAVITY_OK) return rc;
-  return state_status(st);
+  return all_status(h);
 }
 
 int cavity_destroy(cavity_t *h) {

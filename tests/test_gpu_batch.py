@@ -1,0 +1,142 @@
+"""Batched form: many independent cavities of uneven sizes and Rayleigh
+numbers advanced by the same launches (one descriptor table, one work list
+per kernel, parallel per-cavity finalise), graph-captured, with an autotuner
+over the FP32 step kernel's tile shapes.
+
+ * every member against the FP64 oracle run alone (FP64 batch <= 1e-12,
+   FP32-mixed batch <= 1e-5 relative max-norm, Nusselt <= 1e-4);
+ * every member bit-identical to the same cavity in a handle of its own;
+ * the autotuner restores the state and the tile shape does not change the
+   fields (bit-identical to an untuned handle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_02602_gb300 import build
+    build.build()
+    import paper_2006_02602_gb300 as mod
+    mod.load_library()
+    return mod
+
+
+def relmax(a, b):
+    s = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / (s if s > 0 else 1.0)
+
+
+SMALL = workloads.batch_cavities(ncav=6, nmin=12, nmax=33)
+
+
+def _params(m, cav):
+    return m.cavity_default_params(Ra=cav["Ra"], Pr=0.71)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_members_match_oracle(m, prec):
+    precision = m.CAVITY_FP64 if prec == "fp64" else m.CAVITY_FP32_MIXED
+    steps = 30
+    h = m.cavity_create_batch([c["n"] for c in SMALL], [_params(m, c) for c in SMALL], precision=precision,
+                              seeds=[c["seed"] for c in SMALL], noise_amp=1e-3)
+    try:
+        assert m.cavity_batch_size(h) == len(SMALL)
+        m.cavity_step(h, steps)
+        for b, cav in enumerate(SMALL):
+            o = oracle.OracleCavity(*cav["n"], dict(Ra=cav["Ra"], Pr=0.71), noise=1e-3, seed=cav["seed"])
+            o.step(steps)
+            g = m.cavity_batch_get_fields(h, b, cav["n"])
+            ref = o.fields()
+            tol = 1e-12 if prec == "fp64" else 1e-5
+            speed = max(np.max(np.abs(ref[f])) for f in (1, 2, 3))
+            for f in range(5):
+                scale = speed if (prec == "fp32" and f in (1, 2, 3)) else np.max(np.abs(ref[f]))
+                e = np.max(np.abs(g[f] - ref[f])) / scale
+                assert e <= tol, (b, cav, f, e)
+            st = m.cavity_batch_state(h, b)
+            assert st["step"] == steps
+            assert st["t"] == pytest.approx(o.t, rel=1e-12 if prec == "fp64" else 1e-5)
+            ntol = 1e-12 if prec == "fp64" else 1e-4
+            assert abs(st["nusselt"][0] - o.nusselt[0]) <= ntol * abs(o.nusselt[0])
+            assert abs(st["nusselt"][1] - o.nusselt[1]) <= ntol * abs(o.nusselt[1])
+    finally:
+        m.cavity_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_members_bit_identical_to_single_handles(m, prec):
+    precision = m.CAVITY_FP64 if prec == "fp64" else m.CAVITY_FP32_MIXED
+    steps = 25
+    h = m.cavity_create_batch([c["n"] for c in SMALL], [_params(m, c) for c in SMALL], precision=precision,
+                              seeds=[c["seed"] for c in SMALL], noise_amp=1e-3)
+    try:
+        m.cavity_step(h, steps)
+        for b, cav in enumerate(SMALL):
+            with m.Cavity(*cav["n"], precision=precision, seed=cav["seed"], noise_amp=1e-3, Ra=cav["Ra"],
+                          Pr=0.71) as c:
+                c.step(steps)
+                assert np.array_equal(m.cavity_batch_get_fields(h, b, cav["n"]), c.fields()), b
+                st = m.cavity_batch_state(h, b)
+                assert (st["step"], st["t"], st["dt"]) == c.time
+    finally:
+        m.cavity_destroy(h)
+
+
+def test_autotune_restores_state_and_keeps_fields(m):
+    cavs = workloads.batch_cavities(ncav=8, nmin=24, nmax=64)
+    sizes = [c["n"] for c in cavs]
+    params = [_params(m, c) for c in cavs]
+    seeds = [c["seed"] for c in cavs]
+    h = m.cavity_create_batch(sizes, params, seeds=seeds, noise_amp=1e-3)
+    ref = m.cavity_create_batch(sizes, params, seeds=seeds, noise_amp=1e-3)
+    try:
+        m.cavity_step(h, 3)
+        m.cavity_step(ref, 3)
+        before = [m.cavity_batch_get_fields(h, b, s) for b, s in enumerate(sizes)]
+        choice = m.cavity_autotune(h, 5)
+        assert choice["tile_y"] in (4, 8) and choice["kc"] in (16, 32, 64) and choice["us_per_step"] > 0
+        for b, s in enumerate(sizes):
+            assert np.array_equal(m.cavity_batch_get_fields(h, b, s), before[b])
+            assert m.cavity_batch_state(h, b)["step"] == 3
+        m.cavity_step(h, 20)
+        m.cavity_step(ref, 20)
+        for b, s in enumerate(sizes):
+            assert np.array_equal(m.cavity_batch_get_fields(h, b, s), m.cavity_batch_get_fields(ref, b, s)), b
+    finally:
+        m.cavity_destroy(h)
+        m.cavity_destroy(ref)
+
+
+def test_fp32_tile_shapes_give_identical_fields(m, monkeypatch):
+    """The tile shape changes only the order of the residual sums, never a field."""
+    n = (45, 38, 70)
+    out = []
+    for shape in ("8,16,8", "8,64,8", "4,32,8"):
+        monkeypatch.setenv("BDC_F32_TILE", shape)
+        with m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=4, noise_amp=1e-3, Ra=2e5) as c:
+            c.step(40)
+            out.append((c.fields(), c.time))
+    for f, t in out[1:]:
+        assert np.array_equal(f, out[0][0])
+        assert t == out[0][1]
+
+
+def test_batch_rejects_mixed_precision_and_split_members(m):
+    import ctypes
+    L = m.load_library()
+    d = (m.cavity_desc * 2)(m.cavity_desc(8, 8, 8, 1, 1, 1, 0, 0, 0.0, 0, None),
+                            m.cavity_desc(8, 8, 8, 1, 1, 1, 1, 0, 0.0, 0, None))
+    h = ctypes.c_void_p()
+    assert L.cavity_create_batch(d, None, 2, ctypes.byref(h)) == m.CAVITY_ERR_INVALID_ARG
+    d = (m.cavity_desc * 2)(m.cavity_desc(8, 8, 8, 2, 1, 1, 0, 0, 0.0, 0, None),
+                            m.cavity_desc(8, 8, 8, 1, 1, 1, 0, 0, 0.0, 0, None))
+    assert L.cavity_create_batch(d, None, 2, ctypes.byref(h)) == m.CAVITY_ERR_INVALID_ARG

@@ -24,6 +24,35 @@ CFG2 = dict(name="cavity128_ra1e5", n=(128, 128, 128), Ra=1e5, Pr=0.71, noise=1e
 CFG3 = dict(name="cavity256_ra1e6_fp32", n=(256, 256, 256), Ra=1e6, Pr=0.71, noise=1e-4, seed=0, steps=5000)
 
 
+# configuration 4: a batch of independent cavities advanced together
+CFG4 = dict(name="batch64_fp32", ncav=64, nmin=24, nmax=96, ra_log10=(3.0, 6.0), Pr=0.71, noise=1e-3, steps=1000)
+
+_MASK64 = (1 << 64) - 1
+
+
+def _splitmix64(x: int) -> int:
+    """splitmix64 output for state x (Steele, Lea & Flood 2014), as an input draw."""
+    z = (x + 0x9E3779B97F4A7C15) & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def batch_cavities(ncav: int = CFG4["ncav"], nmin: int = CFG4["nmin"], nmax: int = CFG4["nmax"],
+                   ra_log10=CFG4["ra_log10"]):
+    """Cavity b of the batch: n_d = nmin + draw mod (nmax - nmin + 1) for d = x, y, z, and
+    log10 Ra uniform on ra_log10 from the next draw; the seed of its initial noise is b."""
+    out = []
+    span = nmax - nmin + 1
+    for b in range(ncav):
+        key = (b << 40) + (1 << 39)
+        n = tuple(nmin + _splitmix64(key + d) % span for d in range(3))
+        u = (_splitmix64(key + 3) >> 11) * (1.0 / 9007199254740992.0)
+        ra = 10.0 ** (ra_log10[0] + (ra_log10[1] - ra_log10[0]) * u)
+        out.append(dict(n=n, Ra=ra, seed=b))
+    return out
+
+
 def wall_temperature(ny: int, nz: int, seed: int, base: float = 1.0, sigma: float = 0.01) -> np.ndarray:
     """Hot-wall temperature base + N(0, sigma^2) per wall node, (j-1) + ny (k-1) order."""
     rng = np.random.default_rng(seed)
