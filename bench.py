@@ -42,8 +42,9 @@ UNIT = "point-updates/s"
 # 166, update 11, residual sums 10, spectral radius of the new state 25
 FP64_FLOP_PER_POINT = 212
 # algorithmic HBM bytes per interior point-update of one fused pass: every
-# stored array read once and written once (FP64: 5 x 8 B; FP32-mixed: 6 x 4 B)
-BYTES_PER_POINT = {"fp64": 80, "fp32": 48}
+# stored array read once and written once (FP64: 5 x 8 B; FP32-mixed: 7 x 4 B,
+# u, v, w and the hi/lo pairs of p and T)
+BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129e6

@@ -54,7 +54,7 @@ extern "C" {
 
 /* arithmetic forms */
 #define CAVITY_FP64 0       /* every field and every operation in FP64 */
-#define CAVITY_FP32_MIXED 1 /* u, v, w, T in FP32; p as an FP32 hi/lo pair; FP64 reductions */
+#define CAVITY_FP32_MIXED 1 /* u, v, w in FP32; p and T as FP32 hi/lo pairs; FP64 reductions */
 
 /* field masks */
 #define CAVITY_FIELD_P 1
@@ -156,16 +156,22 @@ CAVITY_API int cavity_get_time(cavity_t *h, long long *step, double *t, double *
 /* Number of blocks (px*py*pz). */
 CAVITY_API int cavity_num_blocks(cavity_t *h);
 
-/* Whole array of one field of one block, walls and ghosts included, as
+/* Whole stored array `field` of one block, walls and ghosts included, as
  * stored (p before the pending centre shift), (k, j, i) order over local
- * nodes -1 .. n+2 of each axis: count = (nx_b+4)(ny_b+4)(nz_b+4).
+ * nodes -1 .. n+2 of each axis: count = (nx_b+4)(ny_b+4)(nz_b+4).  Array
+ * index: FP64 form p, u, v, w, T (0..4); FP32-mixed form p_hi, p_lo, u, v,
+ * w, T_hi, T_lo (0..6).  The FP32-mixed step forms p's wall and ghost values
+ * and the adiabatic T where it reads them, so those stored entries are only
+ * refreshed by state changes (creation, set_fields, parameters).
  * dims (optional) receives nx_b, ny_b, nz_b, ox, oy, oz (global node index
  * = o + local index).  For checks of the ghost exchange. */
 CAVITY_API int cavity_get_block_array(cavity_t *h, int block, int field, double *host, size_t count, int dims[6]);
 
 /* The last packed buffer of one cut face of one block (Section 4.5 layout:
  * p at depth 2 with depth fastest, then u, v, w, T at depth 1), widened to
- * FP64; count must equal 6*nb*nc.  CAVITY_ERR_INVALID_ARG if the face is a
+ * FP64; count must equal 6*nb*nc (FP64 form) or 9*nb*nc (FP32-mixed form:
+ * p_hi then p_lo at depth 2, then u, v, w, T_hi, T_lo at depth 1).
+ * CAVITY_ERR_INVALID_ARG if the face is a
  * wall. */
 CAVITY_API int cavity_get_face_buffer(cavity_t *h, int block, int face, double *host, size_t count);
 

@@ -97,10 +97,12 @@ __device__ __forceinline__ long long node_index(const BlockDev &B, int i, int j,
 }
 
 // Arrays of one buffer set.  FP64 form: p, u, v, w, T.  FP32-mixed form:
-// p_hi, p_lo, u, v, w, T (p = p_hi + p_lo, an unevaluated FP32 pair).
+// p_hi, p_lo, u, v, w, T_hi, T_lo (p = p_hi + p_lo and T = T_hi + T_lo,
+// unevaluated FP32 pairs: their time-step accumulation is compensated).
+// NP = arrays of p; the transported fields u, v, w, T start at array NP.
 template <class S> struct Store;
 template <> struct Store<double> { static constexpr int NA = 5, NP = 1; };
-template <> struct Store<float> { static constexpr int NA = 6, NP = 2; };
+template <> struct Store<float> { static constexpr int NA = 7, NP = 2; };
 
 template <class S>
 __device__ __forceinline__ double load_p(const S *base, long long fs, long long o);
@@ -119,6 +121,16 @@ __device__ __forceinline__ void store_p<float>(float *base, long long fs, long l
   const float hi = (float)v;
   base[o] = hi;
   base[fs + o] = (float)(v - (double)hi);
+}
+
+// temperature: array NP + 3 (FP64), or the pair NP + 3 (hi), NP + 4 (lo) (FP32-mixed)
+template <class S>
+__device__ __forceinline__ double load_T(const S *base, long long fs, long long o) {
+  return load_p<S>(base + (Store<S>::NP + 3) * fs, fs, o);
+}
+template <class S>
+__device__ __forceinline__ void store_T(S *base, long long fs, long long o, double v) {
+  store_p<S>(base + (Store<S>::NP + 3) * fs, fs, o, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,11 +343,10 @@ __device__ __forceinline__ void nusselt_node(const BlockDev &B, const CavConst &
   const int high = face & 1;
   const int w = high ? B.nx + 1 : 0, s = high ? -1 : 1;
   const long long W = node_index<S>(B, w, c1, c2);
-  const S *T = base + (Store<S>::NP + 3) * B.fstride;
   const int J = B.oy + c1, K = B.oz + c2;
   const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
   const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
-  const double T1 = (double)T[W + s], T2 = (double)T[W + 2 * s];
+  const double T1 = load_T<S>(base, B.fstride, W + s), T2 = load_T<S>(base, B.fstride, W + 2 * s);
   const double flux = (3.0 * tw - 4.0 * T1 + T2) * (0.5 * C.ih[0]) * C.inv_dT;
   if (high) nu_c += -flux; else nu_h += flux;
 }
@@ -360,7 +371,6 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
   const long long N1 = W + s * step, N2 = W + 2 * s * step, G = W - s * step;
   const long long fs = B.fstride;
   constexpr int NP = Store<S>::NP;
-  S *T = base + (NP + 3) * fs;
   if (other) {
     base[NP * fs + W] = S(0); base[(NP + 1) * fs + W] = S(0); base[(NP + 2) * fs + W] = S(0);
     other[NP * fs + W] = S(0); other[(NP + 1) * fs + W] = S(0); other[(NP + 2) * fs + W] = S(0);
@@ -369,20 +379,19 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
   const double pw = 2.0 * p1 - p2;
   store_p<S>(base, fs, W, pw);
   store_p<S>(base, fs, G, 2.0 * pw - p1);
+  const double T1 = load_T<S>(base, fs, N1), T2 = load_T<S>(base, fs, N2);
   if (axis == 0) {
     const int J = B.oy + iw[1], K = B.oz + iw[2];
     const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
     const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
     if (other) {
-      T[W] = (S)tw;
-      other[(NP + 3) * fs + W] = (S)tw;
+      store_T<S>(base, fs, W, tw);
+      store_T<S>(other, fs, W, tw);
     }
-    const double T1 = (double)T[N1], T2 = (double)T[N2];
     const double flux = (3.0 * tw - 4.0 * T1 + T2) * (0.5 * C.ih[0]) * C.inv_dT;
     if (high) nu_c += -flux; else nu_h += flux;
   } else {
-    const double T1 = (double)T[N1], T2 = (double)T[N2];
-    T[W] = (S)((4.0 * T1 - T2) / 3.0);
+    store_T<S>(base, fs, W, (4.0 * T1 - T2) / 3.0);
   }
 }
 
@@ -561,7 +570,7 @@ __global__ void __launch_bounds__(256) k_pack(ExchArgs a) {
     buf[2LL * pa * plane + 2LL * e] = pq[p_first];
     buf[2LL * pa * plane + 2LL * e + 1] = pq[p_first + dstep];
   }
-  for (int v = 0; v < 4; ++v)
+  for (int v = 0; v < Store<S>::NA - NP; ++v)  // u, v, w, T (FP32-mixed: T_hi, T_lo)
     buf[2LL * NP * plane + (long long)v * plane + e] = q[(long long)(NP + v) * B.fstride + v_node];
 }
 
@@ -584,7 +593,7 @@ __global__ void __launch_bounds__(256) k_unpack(ExchArgs a) {
     pq[p_first] = buf[2LL * pa * plane + 2LL * e];
     pq[p_first + dstep] = buf[2LL * pa * plane + 2LL * e + 1];
   }
-  for (int v = 0; v < 4; ++v)
+  for (int v = 0; v < Store<S>::NA - NP; ++v)
     q[(long long)(NP + v) * B.fstride + v_node] = buf[2LL * NP * plane + (long long)v * plane + e];
 }
 
@@ -625,18 +634,20 @@ __global__ void k_init(InitArgs a) {
   const double x = __dmul_rn((double)I, C.h[0]);
   const double lin = __dadd_rn(a.t_hot, __dmul_rn(__dsub_rn(a.t_cold, a.t_hot), x));
   const double pert = __dmul_rn(a.noise, __dsub_rn(__dmul_rn(2.0, U), 1.0));
-  S *T = (S *)B.base[a.parity] + (Store<S>::NP + 3) * B.fstride;
-  T[node_index<S>(B, i, j, k)] = (S)__dadd_rn(lin, pert);
+  store_T<S>((S *)B.base[a.parity], B.fstride, node_index<S>(B, i, j, k), __dadd_rn(lin, pert));
 }
 
 // field f (0 = p, 1..4 = u, v, w, T) of node offset o, widened to FP64
 template <class S>
 __device__ __forceinline__ double get_field(const S *q, long long fs, int f, long long o) {
-  return f == 0 ? load_p<S>(q, fs, o) : (double)q[(long long)(Store<S>::NP + f - 1) * fs + o];
+  if (f == 0) return load_p<S>(q, fs, o);
+  if (f == 4) return load_T<S>(q, fs, o);
+  return (double)q[(long long)(Store<S>::NP + f - 1) * fs + o];
 }
 template <class S>
 __device__ __forceinline__ void put_field(S *q, long long fs, int f, long long o, double v) {
   if (f == 0) store_p<S>(q, fs, o, v);
+  else if (f == 4) store_T<S>(q, fs, o, v);
   else q[(long long)(Store<S>::NP + f - 1) * fs + o] = (S)v;
 }
 

@@ -1,7 +1,8 @@
 // FP32-mixed form of the fused step (Eqs. 1-3, Section 3.1 stencils): u, v,
-// w, T stored and updated in FP32; p stored as an unevaluated FP32 pair
-// (p_hi + p_lo) and accumulated with an error-free transformation, so the
-// time-step accumulation of p keeps about 48 significant bits; every
+// w stored and updated in FP32; p and T stored as unevaluated FP32 pairs
+// (hi + lo) and accumulated with an error-free transformation, so their
+// time-step accumulation keeps about 48 significant bits (T's rounding would
+// otherwise reach w through the buoyancy coefficient Ra Pr); every
 // difference of the stencils is formed relative to the centre node (exact in
 // FP32 for neighbouring values), hi-minus-hi plus lo-minus-lo for p, so no
 // cancellation is lost.  Residual sums are FP32 within a thread's z-chunk and
@@ -18,8 +19,9 @@
 // two-node halo with TMA (cp.async.bulk.tensor.4d over x, y, z and the array
 // index: all six arrays in one copy) into a ring of R shared-memory slots,
 // each guarded by an mbarrier with a bounded wait; the z-neighbours live in
-// register queues (5 deep for p, 3 for u, v, w, T).  HBM sees each array
-// read once and written once per step: 48 bytes per interior point.
+// register queues (5 deep for p, 3 for u, v, w, T).  HBM sees each of the
+// seven arrays read once and written once per step: 56 bytes per interior
+// point.
 #pragma once
 
 #include <cuda.h>
@@ -30,7 +32,7 @@ namespace bdc {
 
 constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 64, kF32R = 8;  // default tile height, z chunk, ring depth
 constexpr int kF32BX = kF32TX + 8;  // x halo 4 on each side: the box starts on a 16-byte boundary
-constexpr int kF32NA = 6;           // p_hi, p_lo, u, v, w, T
+constexpr int kF32NA = 7;           // p_hi, p_lo, u, v, w, T_hi, T_lo
 __host__ __device__ constexpr int f32_box_y(int TY) { return TY + 4; }  // y halo 2 (pressure star)
 __host__ __device__ constexpr int f32_slot_floats(int TY) { return kF32NA * f32_box_y(TY) * kF32BX; }
 __host__ __device__ constexpr int f32_smem_bytes(int TY, int R) { return R * f32_slot_floats(TY) * 4 + R * 8; }
@@ -117,9 +119,20 @@ __device__ __forceinline__ void wall_pressure(float h1, float l1, float h2, floa
   extrapolate_pair(hw, lw, h1, l1, hg, lg);
 }
 
-// adiabatic wall temperature (4 T1 - T2) / 3 = T1 + (T1 - T2) / 3
-__device__ __forceinline__ float wall_temperature(float t1, float t2) {
-  return fmaf(t1 - t2, 1.f / 3.f, t1);
+// (h, l) + d for an FP32 pair: two-sum of the hi part, error carried into lo
+__device__ __forceinline__ void pair_add(float h, float l, float d, float &rh, float &rl) {
+  const float s = h + d;
+  const float bp = s - h;
+  const float e = (h - (s - bp)) + (d - bp);
+  const float lo = l + e;
+  rh = s + lo;
+  rl = lo - (rh - s);
+}
+
+// adiabatic wall temperature (4 T1 - T2) / 3 = T1 + (T1 - T2) / 3 of FP32 pairs
+__device__ __forceinline__ void wall_temperature(float h1, float l1, float h2, float l2, float &hw, float &lw) {
+  const float d = (h1 - h2) + (l1 - l2);
+  pair_add(h1, l1, d * (1.f / 3.f), hw, lw);
 }
 
 // Apply the x and y wall conditions to one freshly loaded plane slot.
@@ -131,14 +144,14 @@ template <int NT, int BY>
 __device__ __forceinline__ void fix_plane_walls(float *s, int tid, bool wxl, bool wxh, bool wyl, bool wyh,
                                                 int lxh, int lyh) {
   constexpr int BX = kF32BX, AS = BX * BY;
-  float *H = s, *L = s + AS, *T = s + 5 * AS;
+  float *H = s, *L = s + AS, *TH = s + 5 * AS, *TL = s + 6 * AS;
   static_assert(NT >= 2 * (BX + BY), "thread groups");
   if (wyl && tid < BX) {
     const int x = tid;
     float hw, lw, hg, lg;
     wall_pressure(H[2 * BX + x], L[2 * BX + x], H[3 * BX + x], L[3 * BX + x], hw, lw, hg, lg);
     H[BX + x] = hw; L[BX + x] = lw; H[x] = hg; L[x] = lg;
-    T[BX + x] = wall_temperature(T[2 * BX + x], T[3 * BX + x]);
+    wall_temperature(TH[2 * BX + x], TL[2 * BX + x], TH[3 * BX + x], TL[3 * BX + x], TH[BX + x], TL[BX + x]);
   } else if (wyh && tid >= BX && tid < 2 * BX) {
     const int x = tid - BX;
     const int r1 = lyh, r2 = lyh - 1;  // rows of nodes ny and ny - 1
@@ -146,7 +159,8 @@ __device__ __forceinline__ void fix_plane_walls(float *s, int tid, bool wxl, boo
     wall_pressure(H[r1 * BX + x], L[r1 * BX + x], H[r2 * BX + x], L[r2 * BX + x], hw, lw, hg, lg);
     H[(r1 + 1) * BX + x] = hw; L[(r1 + 1) * BX + x] = lw;
     if (r1 + 2 < BY) { H[(r1 + 2) * BX + x] = hg; L[(r1 + 2) * BX + x] = lg; }
-    T[(r1 + 1) * BX + x] = wall_temperature(T[r1 * BX + x], T[r2 * BX + x]);
+    wall_temperature(TH[r1 * BX + x], TL[r1 * BX + x], TH[r2 * BX + x], TL[r2 * BX + x], TH[(r1 + 1) * BX + x],
+                     TL[(r1 + 1) * BX + x]);
   } else if (wxl && tid >= 2 * BX && tid < 2 * BX + BY) {
     const int y = tid - 2 * BX;
     float hw, lw, hg, lg;
@@ -243,8 +257,8 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
 
   bool bad = false;
   // prologue: planes k0-2 .. k0+1 give the initial z queues
-  float ph[5], pq[5], uq[3], vq[3], wq[3], Tq[3];
-  float T2next = 0.f;  // T at plane k0+1 (z-wall temperature of the bottom chunk)
+  float ph[5], pq[5], uq[3], vq[3], wq[3], Tq[3], Tl[3];
+  float T2next = 0.f, T2next_lo = 0.f;  // T at plane k0+1 (z-wall temperature of the bottom chunk)
   for (int pl = 0; pl < 4; ++pl) {
     if (!bad && !wait_plane(pl)) bad = true;
     if (!bad) {
@@ -256,8 +270,9 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         vq[pl - 1] = s[3 * AS + col];
         wq[pl - 1] = s[4 * AS + col];
         Tq[pl - 1] = s[5 * AS + col];
+        Tl[pl - 1] = s[6 * AS + col];
       }
-      if (pl == 3) T2next = s[5 * AS + col];
+      if (pl == 3) { T2next = s[5 * AS + col]; T2next_lo = s[6 * AS + col]; }
       if (fix && pl >= 2) fix_plane_walls<NT, BY>(s, tid, wxl, wxh, wyl, wyh, lxh, lyh);
     }
   }
@@ -265,7 +280,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   // constant indices keep the queues in registers
   if (wzl && k0 == 1) {
     wall_pressure(ph[2], pq[2], ph[3], pq[3], ph[1], pq[1], ph[0], pq[0]);
-    Tq[0] = wall_temperature(Tq[1], T2next);
+    wall_temperature(Tq[1], Tl[1], T2next, T2next_lo, Tq[0], Tl[0]);
   } else if (wzl && k0 == 2) {
     float hg, lg;
     wall_pressure(ph[1], pq[1], ph[2], pq[2], ph[0], pq[0], hg, lg);
@@ -289,6 +304,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
       vq[2] = sk1[3 * AS + col];
       wq[2] = sk1[4 * AS + col];
       Tq[2] = sk1[5 * AS + col];
+      Tl[2] = sk1[6 * AS + col];
       if (wzh) {
         if (k + 2 == B.nz + 1) {
           float hg, lg;
@@ -296,7 +312,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         } else if (k + 2 == B.nz + 2) {
           extrapolate_pair(ph[3], pq[3], ph[2], pq[2], ph[4], pq[4]);  // ghost = 2 p_w - p_nz
         }
-        if (k + 1 == B.nz + 1) Tq[2] = wall_temperature(Tq[1], Tq[0]);
+        if (k + 1 == B.nz + 1) wall_temperature(Tq[1], Tl[1], Tq[0], Tl[0], Tq[2], Tl[2]);
       }
       if (fix) fix_plane_walls<NT, BY>(sk2, tid, wxl, wxh, wyl, wyh, lxh, lyh);
       if (active) {
@@ -313,7 +329,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         const float d4x = (axp2 + axm2) - 4.f * (axp1 + axm1);
         const float d4y = (ayp2 + aym2) - 4.f * (ayp1 + aym1);
         const float d4z = (azp2 + azm2) - 4.f * (azp1 + azm1);
-        const float u0 = uq[1], v0 = vq[1], w0 = wq[1], T0 = Tq[1];
+        const float u0 = uq[1], v0 = vq[1], w0 = wq[1], T0 = Tq[1], T0l = Tl[1];
         const float b2 = fmaxf(fmaf(u0, u0, fmaf(v0, v0, w0 * w0)), b2min);
         const float f4 = 4.f * b2;
         const float sx = fabsf(u0) + sqrt_pos(fmaf(u0, u0, f4));
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         const float ax = u0 * h2x, ay = v0 * h2y, az = w0 * h2z;
         const float mpx = nhx - ax, mmx = nhx + ax, mpy = nhy - ay, mmy = nhy + ay, mpz = nhz - az, mmz = nhz + az;
         const float tpx = ahx - ax, tmx = ahx + ax, tpy = ahy - ay, tmy = ahy + ay, tpz = ahz - az, tmz = ahz + az;
-        const float *Us = sk + 2 * AS, *Vs = sk + 3 * AS, *Ws = sk + 4 * AS, *Ts = sk + 5 * AS;
+        const float *Us = sk + 2 * AS, *Vs = sk + 3 * AS, *Ws = sk + 4 * AS, *Ts = sk + 5 * AS, *Tls = sk + 6 * AS;
 #define BDC_F32_DIFFS(S, q0, zp, zm, dxp, dxm, dyp, dym, dzp, dzm) \
   const float dxp = S[col + 1] - q0, dxm = S[col - 1] - q0;        \
   const float dyp = S[col + BX] - q0, dym = S[col - BX] - q0;      \
@@ -333,33 +349,34 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         BDC_F32_DIFFS(Us, u0, uq[2], uq[0], uxp, uxm, uyp, uym, uzp, uzm)
         BDC_F32_DIFFS(Vs, v0, vq[2], vq[0], vxp, vxm, vyp, vym, vzp, vzm)
         BDC_F32_DIFFS(Ws, w0, wq[2], wq[0], wxp, wxm, wyp, wym, wzp, wzm)
-        BDC_F32_DIFFS(Ts, T0, Tq[2], Tq[0], txp, txm, typ, tym, tzp, tzm)
 #undef BDC_F32_DIFFS
+        // temperature differences of the pair (hi and lo separately)
+        const float txp = pdiff(Ts[col + 1], Tls[col + 1], T0, T0l), txm = pdiff(Ts[col - 1], Tls[col - 1], T0, T0l);
+        const float typ = pdiff(Ts[col + BX], Tls[col + BX], T0, T0l);
+        const float tym = pdiff(Ts[col - BX], Tls[col - BX], T0, T0l);
+        const float tzp = pdiff(Tq[2], Tl[2], T0, T0l), tzm = pdiff(Tq[0], Tl[0], T0, T0l);
         const float tru = fmaf(mpx, uxp, fmaf(mmx, uxm, fmaf(mpy, uyp, fmaf(mmy, uym, fmaf(mpz, uzp, mmz * uzm)))));
         const float trv = fmaf(mpx, vxp, fmaf(mmx, vxm, fmaf(mpy, vyp, fmaf(mmy, vym, fmaf(mpz, vzp, mmz * vzm)))));
         const float trw = fmaf(mpx, wxp, fmaf(mmx, wxm, fmaf(mpy, wyp, fmaf(mmy, wym, fmaf(mpz, wzp, mmz * wzm)))));
         const float rT = fmaf(tpx, txp, fmaf(tmx, txm, fmaf(tpy, typ, fmaf(tmy, tym, fmaf(tpz, tzp, tmz * tzm)))));
         const float divV = fmaf(uxp - uxm, h2x, fmaf(vyp - vym, h2y, (wzp - wzm) * h2z));
         const float rp = fmaf(-b2, divV, -diss);
-        const float buoy = gs * (T0 - tinf);
+        const float buoy = gs * ((T0 - tinf) + T0l);
         const float ru = fmaf(-(axp1 - axm1), h2x, tru);
         const float rv = fmaf(-(ayp1 - aym1), h2y, fmaf(gy_on, buoy, trv));
         const float rw = fmaf(-(azp1 - azm1), h2z, fmaf(gz_on, buoy, trw));
-        // explicit update; p through an error-free two-sum on the pair
-        const float un = fmaf(dt, ru, u0), vn = fmaf(dt, rv, v0), wn = fmaf(dt, rw, w0), Tn = fmaf(dt, rT, T0);
-        const float del = fmaf(dt, rp, -cshift);
-        const float sum = p0h + del;
-        const float bp = sum - p0h;
-        const float err = (p0h - (sum - bp)) + (del - bp);
-        const float lo1 = p0l + err;
-        const float hin = sum + lo1;
-        const float lon = lo1 - (hin - sum);
+        // explicit update; p and T through an error-free two-sum on their pairs
+        const float un = fmaf(dt, ru, u0), vn = fmaf(dt, rv, v0), wn = fmaf(dt, rw, w0);
+        float hin, lon, Tnh, Tnl;
+        pair_add(p0h, p0l, fmaf(dt, rp, -cshift), hin, lon);
+        pair_add(T0, T0l, dt * rT, Tnh, Tnl);
         out[0] = hin;
         out[fs] = lon;
         out[2 * fs] = un;
         out[3 * fs] = vn;
         out[4 * fs] = wn;
-        out[5 * fs] = Tn;
+        out[5 * fs] = Tnh;
+        out[6 * fs] = Tnl;
         s0 = fmaf(rp, rp, s0); s1 = fmaf(ru, ru, s1); s2 = fmaf(rv, rv, s2); s3 = fmaf(rw, rw, s3);
         s4 = fmaf(rT, rT, s4);
         // spectral radius of the new state: lambda_d <= |V_d| + beta gives a
@@ -381,7 +398,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
       ph[0] = ph[1]; ph[1] = ph[2]; ph[2] = ph[3]; ph[3] = ph[4];
       pq[0] = pq[1]; pq[1] = pq[2]; pq[2] = pq[3]; pq[3] = pq[4];
       uq[0] = uq[1]; uq[1] = uq[2]; vq[0] = vq[1]; vq[1] = vq[2];
-      wq[0] = wq[1]; wq[1] = wq[2]; Tq[0] = Tq[1]; Tq[1] = Tq[2];
+      wq[0] = wq[1]; wq[1] = wq[2]; Tq[0] = Tq[1]; Tq[1] = Tq[2]; Tl[0] = Tl[1]; Tl[1] = Tl[2];
     }
     bad = __syncthreads_or(bad);
     if (!bad && tid == 0 && issued < nplanes) {

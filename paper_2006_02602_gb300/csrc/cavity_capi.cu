@@ -301,7 +301,7 @@ int build_layout(cavity *h) {
       } else {
         h->hcut.push_back(CutFace{id, f, B.nbr[f], n1, n2, cut, xoff});
         cut += ceil_div((long long)n1 * n2, 256);
-        xoff += (long long)(2 * h->np + 4) * n1 * n2;
+        xoff += (long long)(h->na + h->np) * n1 * n2;
       }
     }
   }
@@ -956,7 +956,7 @@ int cavity_get_face_buffer(cavity_t *h, int block, int face, double *host, size_
   if (!h || !host || block < 0 || block >= h->nblocks || face < 0 || face > 5) return CAVITY_ERR_INVALID_ARG;
   for (const CutFace &c : h->hcut) {
     if (c.src != block || c.face != face) continue;
-    const size_t n = (size_t)(2 * h->np + 4) * c.nb * c.nc;
+    const size_t n = (size_t)(h->na + h->np) * c.nb * c.nc;
     if (count != n) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
     DeviceGuard g(h->dev);
     if (h->f32) {

@@ -274,7 +274,8 @@ def test_fp32_initial_state(m):
     o = oracle.OracleCavity(*n, dict(Ra=1e4), noise=1e-3, seed=5)
     with m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=5, noise_amp=1e-3, Ra=1e4) as c:
         g, ref = c.fields(), o.fields()
-        assert np.array_equal(g[4], ref[4].astype(np.float32).astype(np.float64))
+        # T is stored as an FP32 pair: the initial values survive to ~2^-48
+        assert np.max(np.abs(g[4] - ref[4])) <= 1e-14
         assert np.all(g[:4] == 0)
 
 
@@ -321,7 +322,7 @@ def test_fp32_ghosts_and_buffers_bit_exact(m):
     with m.Cavity(48, 40, 44, **kw) as ref, m.Cavity(48, 40, 44, blocks=blocks, **kw) as c:
         ref.step(30)
         c.step(30)
-        NA = 6  # p_hi, p_lo, u, v, w, T
+        NA = 7  # p_hi, p_lo, u, v, w, T_hi, T_lo
         G = [m.cavity_get_block_array(ref.h, 0, f)[0] for f in range(NA)]
         for b in range(8):
             arrs = [m.cavity_get_block_array(c.h, b, f)[0] for f in range(NA)]
@@ -341,16 +342,16 @@ def test_fp32_ghosts_and_buffers_bit_exact(m):
                 bax, cax = [d for d in range(3) if d != a]
                 nb, nc = n[bax], n[cax]
                 buf = m.load_library()
-                out = np.empty(8 * nb * nc)
+                out = np.empty(9 * nb * nc)
                 rc = buf.cavity_get_face_buffer(c.h, b, face, out.ctypes.data_as(m._dp), out.size)
                 assert rc == 0
-                exp = np.empty(8 * nb * nc)
+                exp = np.empty(9 * nb * nc)
                 for pa in range(2):
                     for d in range(2):
                         idx = [slice(2, 2 + n[0]), slice(2, 2 + n[1]), slice(2, 2 + n[2])]
                         idx[a] = (n[a] - 1 + d if hi else 1 + d) + 1
                         exp[2 * pa * nb * nc + d:2 * (pa + 1) * nb * nc:2] = arrs[pa][idx[2], idx[1], idx[0]].reshape(-1)
-                for v in range(4):
+                for v in range(5):  # u, v, w, T_hi, T_lo
                     idx = [slice(2, 2 + n[0]), slice(2, 2 + n[1]), slice(2, 2 + n[2])]
                     idx[a] = (n[a] if hi else 1) + 1
                     exp[4 * nb * nc + v * nb * nc:4 * nb * nc + (v + 1) * nb * nc] = \
@@ -369,7 +370,8 @@ def test_fp32_set_fields_wall_field_and_nonfinite(m):
         c.set_fields(q)
         g = c.fields()
         assert np.max(np.abs(g[0] - q[0])) <= 1e-12 * np.max(np.abs(q[0]))  # the hi/lo pair keeps p
-        assert np.array_equal(g[1:], q[1:].astype(np.float32).astype(np.float64))
+        assert np.array_equal(g[1:4], q[1:4].astype(np.float32).astype(np.float64))
+        assert np.max(np.abs(g[4] - q[4])) <= 1e-14 * np.max(np.abs(q[4]))  # and the T pair keeps T
         o.step(30)
         c.step(30)
         assert_fields_close(c.fields(), o.fields(), FP32_TOL, "fp32 set_fields")
