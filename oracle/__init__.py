@@ -92,6 +92,11 @@ def lib():
             L.orc_face_len.restype = ctypes.c_size_t
             L.orc_pack.argtypes = [B, _dp, ctypes.c_int, _dp]
             L.orc_unpack.argtypes = [B, _dp, ctypes.c_int, _dp]
+            L.orc_rates_vjp.argtypes = [P, B, _dp, _dp, _dp, _dp]
+            L.orc_spectral_argmax.argtypes = [P, B, _dp, ctypes.POINTER(ctypes.c_int)]
+            L.orc_spectral_argmax.restype = ctypes.c_double
+            L.orc_spectral_vjp.argtypes = [P, B, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           _dp, _dp]
             _lib = L
     return _lib
 
@@ -325,3 +330,114 @@ class OracleCavity:
         """Single-block only: the whole array including walls and pressure ghosts."""
         assert len(self.blocks) == 1
         return self.blocks[0].q
+
+
+# ---------------------------------------------------------------------------
+# Discrete adjoint of the explicit step (single block).  Objective: the
+# hot-wall Nusselt number averaged over steps 1..N,
+#     J = (1/N) sum_n Nu_hot(Q^n),
+# controls: the hot-wall temperature field theta (ny*nz) and Ra.  One step
+# Q^{n+1} = G(Q^n) is: dt = cfl / max_m sr(Q^n_m); Q~ = Q^n + dt R(Q^n);
+# p = p~ - mean_centre(p~); walls from the new interior and theta.  Its
+# adjoint, in reverse order: gauge, update (identity + dt R^T via the C
+# reverse of the rates), dt through the argmax node of the spectral bound,
+# then the wall values folded back onto the interior nodes they were formed
+# from (and onto theta for the hot-wall temperature).
+
+def _fold_walls(cav: "OracleCavity", qbar: np.ndarray, thetabar: np.ndarray) -> None:
+    """Adjoint of the wall conditions: move wall/ghost adjoints of qbar
+    (full array) onto interior nodes 1, 2 and, for the hot wall's T, onto theta."""
+    c = cav.blocks[0].c
+    n = (c.nx, c.ny, c.nz)
+    for face in range(6):
+        a, hi = face // 2, face % 2
+        w = n[a] + 1 if hi else 0
+        s = -1 if hi else 1
+
+        def sl(node):  # [f, k, j, i] slices of one layer along axis a over the face interior
+            idx = [slice(2, 2 + n[0]), slice(2, 2 + n[1]), slice(2, 2 + n[2])]
+            idx[a] = node + 1
+            return (idx[2], idx[1], idx[0])
+
+        W, N1, N2, G = sl(w), sl(w + s), sl(w + 2 * s), sl(w - s)
+        P = qbar[0]
+        pw, pg = P[W].copy(), P[G].copy()
+        P[N1] += 2.0 * pw + 3.0 * pg      # p_w = 2 p1 - p2, p_g = 2 p_w - p1 = 3 p1 - 2 p2
+        P[N2] += -pw - 2.0 * pg
+        P[W] = 0.0
+        P[G] = 0.0
+        T = qbar[4]
+        tw = T[W].copy()
+        if a == 0:
+            if not hi:  # hot wall: T_w = theta(j, k), theta index (j-1) + ny (k-1)
+                thetabar += tw.reshape(-1)
+        else:
+            T[N1] += (4.0 / 3.0) * tw        # T_w = (4 T1 - T2) / 3
+            T[N2] += (-1.0 / 3.0) * tw
+        T[W] = 0.0
+        for f in (1, 2, 3):
+            qbar[f][W] = 0.0
+
+
+def nusselt_gradient(nx, ny, nz, params: dict, steps: int, seed: int = 0, noise: float = 0.0,
+                     t_hot_wall=None):
+    """J = mean over steps 1..N of Nu_hot, and dJ/dtheta (ny*nz), dJ/dRa by the
+    discrete adjoint.  params may leave u_ref unset so that it follows Ra."""
+    L = lib()
+    floor_follows_ra = params.get("u_ref") is None  # u_ref = max(1, sqrt(Ra Pr))
+    cav = OracleCavity(nx, ny, nz, params, noise=noise, seed=seed, t_hot_wall=t_hot_wall)
+    blk = cav.blocks[0]
+    cp = ctypes.byref(cav.cp)
+    cb = ctypes.byref(blk.c)
+    N = int(steps)
+    traj, dts, argm, smaxes = [], [], [], []
+    J = 0.0
+    for _ in range(N):
+        q = blk.q.copy()
+        idx = (ctypes.c_int * 3)()
+        smax = L.orc_spectral_argmax(cp, cb, _ptr(q), idx)
+        traj.append(q)
+        argm.append((idx[0], idx[1], idx[2]))
+        smaxes.append(smax)
+        cav.step(1)
+        dts.append(cav.dt)
+        J += cav.nusselt[0]
+    J /= N
+    p = cav.p
+    hx = 1.0 / (nx + 1)
+    coef = 1.0 / (N * ny * nz * 2.0 * hx * (p["t_hot"] - p["t_cold"]))
+    xbar = np.zeros((NF, nz, ny, nx))
+    thetabar = np.zeros(ny * nz)
+    rabar = 0.0
+    centre = centre_nodes((nx, ny, nz))
+    # beta^2 floor kappa u_ref^2 = kappa max(1, Ra Pr) when u_ref follows Ra
+    dfloor_dra = p["kappa"] * p["Pr"] if (floor_follows_ra and p["Ra"] * p["Pr"] > 1.0) else 0.0
+    for n in range(N, 0, -1):
+        # objective term of Q^n: (3 theta - 4 T_1 + T_2) / (2 h_x dT), averaged
+        xbar[4][:, :, 0] += -4.0 * coef
+        xbar[4][:, :, 1] += coef
+        thetabar += 3.0 * coef
+        q = traj[n - 1]
+        # gauge: p = p~ - mean_centre(p~)
+        ytil = xbar.copy()
+        ssum = ytil[0].sum()
+        for (I, J_, K) in centre:
+            ytil[0][K - 1, J_ - 1, I - 1] -= ssum / len(centre)
+        # update: X~ = X + dt R(Q)
+        dt = dts[n - 1]
+        R = rates(p, q)
+        dtbar = float(np.sum(ytil * R))
+        rbar = np.ascontiguousarray(dt * ytil)
+        qbar = np.zeros_like(q)
+        qbar[:, 2:-2, 2:-2, 2:-2] = ytil
+        pbar = np.zeros(2)
+        L.orc_rates_vjp(cp, cb, _ptr(q), _ptr(rbar), _ptr(qbar), _ptr(pbar))
+        # dt = cfl / S, S = spectral bound at the argmax node
+        S = smaxes[n - 1]
+        sbar = -p["cfl"] * dtbar / (S * S)
+        i, j, k = argm[n - 1]
+        L.orc_spectral_vjp(cp, cb, _ptr(q), i, j, k, sbar, _ptr(qbar), _ptr(pbar))
+        _fold_walls(cav, qbar, thetabar)
+        xbar = qbar[:, 2:-2, 2:-2, 2:-2].copy()
+        rabar += p["Pr"] * pbar[0] + dfloor_dra * pbar[1]
+    return J, thetabar, rabar

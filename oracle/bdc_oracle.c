@@ -24,7 +24,7 @@
  * Section 4.5, Listings 1-2 and "Optimized V3": ghost faces are packed into
  * contiguous buffers, p at depth 2, u, v, w, T at depth 1, on every cut face.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - thermal scaling: rho = 1, alpha = 1, nu = Pr, g*sigma = Ra*Pr, unit cube;
  *  - the dissipation acts with the damping sign (Eq. 1 read as
  *    dp/dt = -beta^2 (rho div V + sum_d eps_d delta_d^4 p / h_d^4));
@@ -423,4 +423,172 @@ void orc_unpack(const orc_block *b, double *q, int face, const double *buf) {
       for (int v = 0; v < 4; ++v)
         q[at(b, FU + v, idx[0], idx[1], idx[2])] = buf[2 * plane + (size_t)v * plane + (size_t)ic * nb + ib];
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Discrete adjoint of the rates (reverse of orc_rates, node by node).
+ * Given rbar[f][k-1][j-1][i-1] (adjoint of dq/dt at every interior node),
+ * accumulate into qbar (same layout as q, walls and ghosts included) the
+ * transposed Jacobian product, and into pbar[0] the adjoint of g*sigma
+ * (= Ra Pr), into pbar[1] the adjoint of the beta^2 floor kappa u_ref^2.
+ * Subgradients at the kinks: |x|' = sign(x) with sign(0) = 0; the max in
+ * beta^2 follows the branch taken.  Sequential: the scatter to the stencil
+ * inputs has no write conflicts. */
+void orc_rates_vjp(const orc_params *P, const orc_block *b, const double *q, const double *rbar, double *qbar,
+                   double *pbar) {
+  double h[3];
+  spacings(b, h);
+  const double nu = P->Pr, alpha = 1.0;
+  const double beta2_floor = P->kappa * P->u_ref * P->u_ref;
+  const size_t nint = (size_t)b->nx * b->ny * b->nz;
+  const int di[3] = {1, 0, 0}, dj[3] = {0, 1, 0}, dk[3] = {0, 0, 1};
+  double gsbar = 0.0, floorbar = 0.0;
+  for (int k = 1; k <= b->nz; ++k)
+    for (int j = 1; j <= b->ny; ++j)
+      for (int i = 1; i <= b->nx; ++i) {
+        const size_t o = (size_t)(i - 1) + (size_t)b->nx * ((size_t)(j - 1) + (size_t)b->ny * (size_t)(k - 1));
+        const double rp = rbar[FP * nint + o], rT = rbar[FT * nint + o];
+        const double rV[3] = {rbar[FU * nint + o], rbar[FV * nint + o], rbar[FW * nint + o]};
+        double V[3];
+        for (int d = 0; d < 3; ++d) V[d] = q[at(b, FU + d, i, j, k)];
+        const double p0 = q[at(b, FP, i, j, k)];
+        const double T0 = q[at(b, FT, i, j, k)];
+        double Vbar[3] = {0.0, 0.0, 0.0};
+        /* forward intermediates */
+        double beta2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+        const int floored = beta2 < beta2_floor;
+        if (floored) beta2 = beta2_floor;
+        double divV = 0.0, dissip = 0.0, delta4[3], lambda[3], sq[3], eps[3];
+        for (int d = 0; d < 3; ++d) {
+          const double Vp = q[at(b, FU + d, i + di[d], j + dj[d], k + dk[d])];
+          const double Vm = q[at(b, FU + d, i - di[d], j - dj[d], k - dk[d])];
+          divV += (Vp - Vm) / (2.0 * h[d]);
+          const double pp2 = q[at(b, FP, i + 2 * di[d], j + 2 * dj[d], k + 2 * dk[d])];
+          const double pp1 = q[at(b, FP, i + di[d], j + dj[d], k + dk[d])];
+          const double pm1 = q[at(b, FP, i - di[d], j - dj[d], k - dk[d])];
+          const double pm2 = q[at(b, FP, i - 2 * di[d], j - 2 * dj[d], k - 2 * dk[d])];
+          delta4[d] = pp2 - 4.0 * pp1 + 6.0 * p0 - 4.0 * pm1 + pm2;
+          sq[d] = sqrt(V[d] * V[d] + 4.0 * beta2);
+          lambda[d] = 0.5 * (fabs(V[d]) + sq[d]);
+          eps[d] = P->c4 * lambda[d] * h[d] * h[d] * h[d] / beta2;
+          dissip += eps[d] * delta4[d] / (h[d] * h[d] * h[d] * h[d]);
+        }
+        const double Rp = divV + dissip;
+        double beta2bar = 0.0;
+
+        /* energy: dT/dt = -sum V_d dT/dx_d + alpha lap T */
+        for (int d = 0; d < 3; ++d) {
+          const double Tp = q[at(b, FT, i + di[d], j + dj[d], k + dk[d])];
+          const double Tm = q[at(b, FT, i - di[d], j - dj[d], k - dk[d])];
+          const double cbar = -rT, lbar = alpha * rT;
+          qbar[at(b, FT, i + di[d], j + dj[d], k + dk[d])] += cbar * V[d] / (2.0 * h[d]) + lbar / (h[d] * h[d]);
+          qbar[at(b, FT, i - di[d], j - dj[d], k - dk[d])] += -cbar * V[d] / (2.0 * h[d]) + lbar / (h[d] * h[d]);
+          qbar[at(b, FT, i, j, k)] += -2.0 * lbar / (h[d] * h[d]);
+          Vbar[d] += cbar * (Tp - Tm) / (2.0 * h[d]);
+        }
+        /* momentum component c */
+        for (int c = 0; c < 3; ++c) {
+          const double cbar = -rV[c], lbar = nu * rV[c];
+          for (int d = 0; d < 3; ++d) {
+            const double qp = q[at(b, FU + c, i + di[d], j + dj[d], k + dk[d])];
+            const double qm = q[at(b, FU + c, i - di[d], j - dj[d], k - dk[d])];
+            qbar[at(b, FU + c, i + di[d], j + dj[d], k + dk[d])] += cbar * V[d] / (2.0 * h[d]) + lbar / (h[d] * h[d]);
+            qbar[at(b, FU + c, i - di[d], j - dj[d], k - dk[d])] += -cbar * V[d] / (2.0 * h[d]) + lbar / (h[d] * h[d]);
+            Vbar[c] += -2.0 * lbar / (h[d] * h[d]);
+            Vbar[d] += cbar * (qp - qm) / (2.0 * h[d]);
+          }
+          qbar[at(b, FP, i + di[c], j + dj[c], k + dk[c])] += -rV[c] / (2.0 * h[c]);
+          qbar[at(b, FP, i - di[c], j - dj[c], k - dk[c])] += rV[c] / (2.0 * h[c]);
+          if (c == P->gravity_axis) {
+            qbar[at(b, FT, i, j, k)] += P->Ra * P->Pr * rV[c];
+            gsbar += (T0 - P->t_inf) * rV[c];
+          }
+        }
+        /* continuity: dp/dt = -beta^2 (divV + sum_d eps_d delta4_d / h_d^4) */
+        beta2bar += -Rp * rp;
+        const double Rpbar = -beta2 * rp;
+        for (int d = 0; d < 3; ++d) {
+          qbar[at(b, FU + d, i + di[d], j + dj[d], k + dk[d])] += Rpbar / (2.0 * h[d]);
+          qbar[at(b, FU + d, i - di[d], j - dj[d], k - dk[d])] += -Rpbar / (2.0 * h[d]);
+          const double h4 = h[d] * h[d] * h[d] * h[d];
+          const double epsbar = Rpbar * delta4[d] / h4;
+          const double d4bar = Rpbar * eps[d] / h4;
+          qbar[at(b, FP, i + 2 * di[d], j + 2 * dj[d], k + 2 * dk[d])] += d4bar;
+          qbar[at(b, FP, i + di[d], j + dj[d], k + dk[d])] += -4.0 * d4bar;
+          qbar[at(b, FP, i, j, k)] += 6.0 * d4bar;
+          qbar[at(b, FP, i - di[d], j - dj[d], k - dk[d])] += -4.0 * d4bar;
+          qbar[at(b, FP, i - 2 * di[d], j - 2 * dj[d], k - 2 * dk[d])] += d4bar;
+          const double h3 = h[d] * h[d] * h[d];
+          const double lambdabar = epsbar * P->c4 * h3 / beta2;
+          beta2bar += -epsbar * P->c4 * lambda[d] * h3 / (beta2 * beta2);
+          const double sgn = V[d] > 0.0 ? 1.0 : (V[d] < 0.0 ? -1.0 : 0.0);
+          Vbar[d] += lambdabar * 0.5 * (sgn + V[d] / sq[d]);
+          beta2bar += lambdabar * 0.5 * (2.0 / sq[d]);
+        }
+        if (floored) {
+          floorbar += beta2bar;
+        } else {
+          for (int d = 0; d < 3; ++d) Vbar[d] += beta2bar * 2.0 * V[d];
+        }
+        for (int d = 0; d < 3; ++d) qbar[at(b, FU + d, i, j, k)] += Vbar[d];
+      }
+  pbar[0] += gsbar;
+  pbar[1] += floorbar;
+}
+
+/* Node (1-based interior i, j, k) where the spectral-radius bound is largest
+ * (first in k, j, i order among equal values); returns the maximum. */
+double orc_spectral_argmax(const orc_params *P, const orc_block *b, const double *q, int *idx) {
+  double h[3];
+  spacings(b, h);
+  const double nu = P->Pr, alpha = 1.0;
+  const double beta2_floor = P->kappa * P->u_ref * P->u_ref;
+  const double dmax = nu > alpha ? nu : alpha;
+  const double diff = 2.0 * dmax * (1.0 / (h[0] * h[0]) + 1.0 / (h[1] * h[1]) + 1.0 / (h[2] * h[2]));
+  double smax = -1.0;
+  for (int k = 1; k <= b->nz; ++k)
+    for (int j = 1; j <= b->ny; ++j)
+      for (int i = 1; i <= b->nx; ++i) {
+        double V[3];
+        V[0] = q[at(b, FU, i, j, k)];
+        V[1] = q[at(b, FV, i, j, k)];
+        V[2] = q[at(b, FW, i, j, k)];
+        double beta2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+        if (beta2 < beta2_floor) beta2 = beta2_floor;
+        double s = 0.0;
+        for (int d = 0; d < 3; ++d) s += 0.5 * (fabs(V[d]) + sqrt(V[d] * V[d] + 4.0 * beta2)) / h[d];
+        s += diff;
+        if (s > smax) {
+          smax = s;
+          idx[0] = i; idx[1] = j; idx[2] = k;
+        }
+      }
+  return smax;
+}
+
+/* Adjoint of the spectral-radius bound at node (i, j, k): qbar of u, v, w
+ * there += sbar * d(bound)/dV, pbar[1] (beta^2 floor) += sbar * d/dfloor. */
+void orc_spectral_vjp(const orc_params *P, const orc_block *b, const double *q, int i, int j, int k, double sbar,
+                      double *qbar, double *pbar) {
+  double h[3];
+  spacings(b, h);
+  const double beta2_floor = P->kappa * P->u_ref * P->u_ref;
+  double V[3];
+  for (int d = 0; d < 3; ++d) V[d] = q[at(b, FU + d, i, j, k)];
+  double beta2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+  const int floored = beta2 < beta2_floor;
+  if (floored) beta2 = beta2_floor;
+  double beta2bar = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double sq = sqrt(V[d] * V[d] + 4.0 * beta2);
+    const double lambdabar = sbar / h[d];
+    const double sgn = V[d] > 0.0 ? 1.0 : (V[d] < 0.0 ? -1.0 : 0.0);
+    qbar[at(b, FU + d, i, j, k)] += lambdabar * 0.5 * (sgn + V[d] / sq);
+    beta2bar += lambdabar * 0.5 * (2.0 / sq);
+  }
+  if (floored) {
+    pbar[1] += beta2bar;
+  } else {
+    for (int d = 0; d < 3; ++d) qbar[at(b, FU + d, i, j, k)] += beta2bar * 2.0 * V[d];
+  }
 }
