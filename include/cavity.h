@@ -210,6 +210,25 @@ CAVITY_API int cavity_batch_get_fields(cavity_t *h, int cav, int field_mask, dou
  * single shape: CAVITY_ERR_UNSUPPORTED. */
 CAVITY_API int cavity_autotune(cavity_t *h, int steps, double out[4]);
 
+/* Discrete adjoint, part 1: from the current state run nsteps steps and
+ * return J = (1/nsteps) sum over steps 1..nsteps of the hot-wall Nusselt
+ * number.  The state every ckpt steps is kept on the device (checkpoints)
+ * for cavity_adjoint_backward.  Single-block, single-cavity handles only
+ * (CAVITY_ERR_UNSUPPORTED otherwise).  The state afterwards is the state
+ * after the nsteps steps. */
+CAVITY_API int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J);
+
+/* Discrete adjoint, part 2: gradient of the J of the last
+ * cavity_adjoint_forward with respect to the hot-wall temperature field
+ * (grad_wall: ny*nz host values, (j-1) + ny (k-1) order; n must equal
+ * ny*nz; may be NULL) and to Ra (grad_ra, may be NULL).  Reverse sweep of
+ * the step (Section 2 scheme; dt, beta^2 and |V| differentiated along the
+ * forward branch) in FP64, each ckpt-step segment recomputed from its
+ * checkpoint.  When u_ref was left to its default it follows Ra
+ * (u_ref^2 = Ra Pr) in the derivative.  The state is restored to the one
+ * after the forward run. */
+CAVITY_API int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *grad_ra);
+
 /* Measurement: run nsteps steps as plain launches (no graph replay) with CUDA
  * events around every kernel on the handle's stream.  ms[0..3] receive the
  * mean duration per launch of the fused step kernel, the wall/finalise

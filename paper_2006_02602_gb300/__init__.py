@@ -41,7 +41,7 @@ EXPORTED = (
     "cavity_get_time", "cavity_num_blocks", "cavity_get_block_array", "cavity_get_face_buffer",
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
     "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
-    "cavity_batch_get_fields", "cavity_autotune",
+    "cavity_batch_get_fields", "cavity_autotune", "cavity_adjoint_forward", "cavity_adjoint_backward",
 )
 
 
@@ -102,6 +102,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_batch_state": ([_H, ctypes.c_int, _dp], ctypes.c_int),
         "cavity_batch_get_fields": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
         "cavity_autotune": ([_H, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_adjoint_forward": ([_H, ctypes.c_int, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_adjoint_backward": ([_H, _dp, ctypes.c_size_t, _dp], ctypes.c_int),
         "cavity_step_block_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(cavity_params), ctypes.c_double, ctypes.c_double,
                                        ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
@@ -141,11 +143,12 @@ def cavity_default_params(**overrides) -> cavity_params:
     _check(load_library().cavity_default_params(ctypes.byref(p)))
     for k, v in overrides.items():
         setattr(p, k, v)
-    if "Ra" in overrides or "Pr" in overrides:
-        if "u_ref" not in overrides:
-            p.u_ref = max(1.0, math.sqrt(p.Ra * p.Pr))
-    if ("t_hot" in overrides or "t_cold" in overrides) and "t_inf" not in overrides:
-        p.t_inf = 0.5 * (p.t_hot + p.t_cold)
+    # defaults left to the library: u_ref = max(1, sqrt(Ra Pr)) (and it then
+    # follows Ra in derivatives), t_inf = (t_hot + t_cold) / 2
+    if "u_ref" not in overrides:
+        p.u_ref = -1.0
+    if "t_inf" not in overrides:
+        p.t_inf = math.nan
     return p
 
 
@@ -306,6 +309,21 @@ def cavity_autotune(h, steps: int = 20) -> dict:
     out = np.zeros(4)
     _check(load_library().cavity_autotune(h, int(steps), out.ctypes.data_as(_dp)), h)
     return {"tile_y": int(out[0]), "kc": int(out[1]), "ring": int(out[2]), "us_per_step": out[3]}
+
+
+def cavity_adjoint_forward(h, nsteps: int, ckpt: int) -> float:
+    """J = mean Nu_hot over the next nsteps steps; checkpoints every ckpt steps."""
+    J = ctypes.c_double()
+    _check(load_library().cavity_adjoint_forward(h, int(nsteps), int(ckpt), ctypes.byref(J)), h)
+    return J.value
+
+
+def cavity_adjoint_backward(h, ny: int, nz: int) -> tuple[np.ndarray, float]:
+    """(dJ/d hot-wall temperature [ny*nz], dJ/dRa) of the last adjoint forward run."""
+    g = np.zeros(ny * nz)
+    gra = ctypes.c_double()
+    _check(load_library().cavity_adjoint_backward(h, g.ctypes.data_as(_dp), g.size, ctypes.byref(gra)), h)
+    return g, gra.value
 
 
 def cavity_strerror(code: int) -> str:

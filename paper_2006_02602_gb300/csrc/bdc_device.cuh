@@ -333,7 +333,8 @@ struct BcArgs {
   int parity;                 // buffer set holding the new state
   int mode;                   // 0 after a step, 1 after init / set_fields,
                               // 2 after a step whose kernel applied the walls itself:
-                              //   Nusselt sums over the x-wall faces only
+                              //   Nusselt sums over the x-wall faces only,
+                              // 3 walls only, no reductions
 };
 
 // Nusselt sums of one x-wall node (no writes)
@@ -485,6 +486,7 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
                       nu_h, nu_c, a.mode == 1 ? (S *)B.base[a.parity ^ 1] : nullptr);
     }
   }
+  if (a.mode == 3) return;  // walls only (a stored state's walls made explicit), no reductions
   nu_h = warp_sum(nu_h);
   nu_c = warp_sum(nu_c);
   if ((tid & 31) == 0) { sh[(tid >> 5) * 2] = nu_h; sh[(tid >> 5) * 2 + 1] = nu_c; }

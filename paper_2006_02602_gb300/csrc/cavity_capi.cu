@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/cavity.h"
+#include "bdc_adjoint.cuh"
 #include "bdc_device.cuh"
 #include "bdc_step_f32.cuh"
 
@@ -59,8 +60,28 @@ bool f32_variant_ok(int ty, int kc, int r) {
 
 }  // namespace
 
+// checkpoints and work arrays of the discrete adjoint (single-block cavity)
+struct AdjointStore {
+  int nsteps = 0, ckpt = 0, ncp = 0, nparts = 0;
+  size_t set_bytes = 0;        // one buffer set of the block
+  char *ckpt_mem = nullptr;    // ncp buffer sets: the state at steps 0, ckpt, 2 ckpt, ...
+  CavState *ckpt_cs = nullptr;  // their scalars (device)
+  char *seg_mem = nullptr;     // ckpt buffer sets: one recomputed segment
+  char *final_mem = nullptr;   // the state after the forward run
+  CavState final_cs{};
+  int final_parity = 0;
+  long long final_steps = 0;
+  double *X = nullptr, *Yt = nullptr, *Q = nullptr, *thetabar = nullptr, *scal = nullptr, *argpart = nullptr;
+  double *dts = nullptr;       // dt of every step (device)
+  BlockDev *block = nullptr;   // descriptor of a segment slot (wall pass of FP32 states)
+  bool have_forward = false;
+  double J = 0.0;
+};
+
 struct cavity {
   int dev = 0;
+  bool u_ref_auto = true;  // u_ref follows Ra (default)
+  AdjointStore adj;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int ncav = 1;
@@ -668,6 +689,11 @@ void release(cavity *h) {
                   h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps, h->d_nus};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  AdjointStore &A = h->adj;
+  void *aptrs[] = {A.ckpt_mem, A.ckpt_cs, A.seg_mem, A.final_mem, A.X, A.Yt, A.Q, A.thetabar, A.scal,
+                   A.argpart, A.dts, A.block};
+  for (void *p : aptrs)
+    if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -772,10 +798,12 @@ int cavity_batch_size(cavity_t *h) { return h ? h->ncav : CAVITY_ERR_INVALID_ARG
 int cavity_set_params(cavity_t *h, const cavity_params *p) {
   if (!h || !p) return CAVITY_ERR_INVALID_ARG;
   cavity_params q = *p;
+  const bool auto_uref = !(q.u_ref >= 0.0);
   resolve_defaults(&q);
   if (check_params(q) != CAVITY_OK) return fail(h, CAVITY_ERR_INVALID_ARG, "invalid parameters");
   DeviceGuard g(h->dev);
   CK(cudaStreamSynchronize(h->stream));
+  h->u_ref_auto = auto_uref;
   for (auto &pc : h->prms) pc = q;
   int rc = upload_consts(h);
   if (rc != CAVITY_OK) return rc;
@@ -1039,6 +1067,161 @@ int cavity_autotune(cavity_t *h, int steps, double out[4]) {
     out[2] = best.r;
     out[3] = best_us;
   }
+  return rc;
+}
+
+int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
+  if (!h || nsteps < 1 || ckpt < 1) return CAVITY_ERR_INVALID_ARG;
+  if (h->ncav != 1 || h->nblocks != 1) return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: single-block cavity only");
+  DeviceGuard g(h->dev);
+  AdjointStore &A = h->adj;
+  const BlockDev &B = h->hb[0];
+  const cavity_desc &d = h->descs[0];
+  const size_t set_bytes = (size_t)h->na * (size_t)B.fstride * h->esize;
+  const int ncp = (nsteps + ckpt - 1) / ckpt;
+  const long long fs = (long long)(d.nx + 4) * (d.ny + 4) * (d.nz + 4);
+  const int nparts = 2 * 152;
+  CK(cudaStreamSynchronize(h->stream));
+  if (A.set_bytes != set_bytes || A.ncp < ncp || A.ckpt < ckpt || A.nsteps < nsteps) {
+    void *aptrs[] = {A.ckpt_mem, A.ckpt_cs, A.seg_mem, A.final_mem, A.X, A.Yt, A.Q, A.thetabar, A.scal,
+                     A.argpart, A.dts, A.block};
+    for (void *p : aptrs)
+      if (p) cudaFree(p);
+    A = AdjointStore{};
+    CK(cudaMalloc(&A.ckpt_mem, set_bytes * ncp));
+    CK(cudaMalloc(&A.ckpt_cs, sizeof(CavState) * ncp));
+    CK(cudaMalloc(&A.seg_mem, set_bytes * ckpt));
+    CK(cudaMalloc(&A.final_mem, set_bytes));
+    CK(cudaMalloc(&A.X, sizeof(double) * 5 * fs));
+    CK(cudaMalloc(&A.Yt, sizeof(double) * 5 * fs));
+    CK(cudaMalloc(&A.Q, sizeof(double) * 5 * fs));
+    CK(cudaMalloc(&A.thetabar, sizeof(double) * d.ny * d.nz));
+    CK(cudaMalloc(&A.scal, sizeof(double) * kScCount));
+    CK(cudaMalloc(&A.argpart, sizeof(double) * 2 * nparts));
+    CK(cudaMalloc(&A.dts, sizeof(double) * nsteps));
+    CK(cudaMalloc(&A.block, sizeof(BlockDev)));
+    A.set_bytes = set_bytes;
+  }
+  A.nsteps = nsteps;
+  A.ckpt = ckpt;
+  A.ncp = ncp;
+  A.nparts = nparts;
+  CK(cudaMemsetAsync(A.scal, 0, sizeof(double) * kScCount, h->stream));
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % ckpt == 0) {
+      const int c = n / ckpt;
+      CK(cudaMemcpyAsync(A.ckpt_mem + (size_t)c * set_bytes, h->hb[0].base[h->parity], set_bytes,
+                         cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(A.ckpt_cs + c, h->d_cs, sizeof(CavState), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CK(cudaGraphLaunch(h->graph[h->parity], h->stream));
+    h->parity ^= 1;
+    h->steps_taken += 1;
+    k_adj_acc_nusselt<<<1, 1, 0, h->stream>>>(h->d_cs, A.scal);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(A.final_mem, h->hb[0].base[h->parity], set_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(&A.final_cs, h->d_cs, sizeof(CavState), cudaMemcpyDeviceToHost, h->stream));
+  double acc = 0.0;
+  CK(cudaMemcpyAsync(&acc, A.scal + kScJ, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  A.final_parity = h->parity;
+  A.final_steps = h->steps_taken;
+  A.J = acc / nsteps;
+  A.have_forward = true;
+  if (J) *J = A.J;
+  return state_status(A.final_cs);
+}
+
+int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *grad_ra) {
+  if (!h) return CAVITY_ERR_INVALID_ARG;
+  AdjointStore &A = h->adj;
+  if (!A.have_forward) return fail(h, CAVITY_ERR_INVALID_ARG, "adjoint: no forward run recorded");
+  const cavity_desc &d = h->descs[0];
+  if (grad_wall && n != (size_t)d.ny * d.nz) return fail(h, CAVITY_ERR_INVALID_ARG, "grad_wall count must be ny*nz");
+  DeviceGuard g(h->dev);
+  const BlockDev B0 = h->hb[0];
+  const cavity_params &p = h->prms[0];
+  AdjArgs a{};
+  a.C = h->hcc[0];
+  a.g = AdjGeom{d.nx, d.ny, d.nz, (long long)d.nx + 4, (long long)d.ny + 4,
+                (long long)(d.nx + 4) * (d.ny + 4) * (d.nz + 4)};
+  a.Yt = A.Yt;
+  a.scal = A.scal;
+  a.thetabar = A.thetabar;
+  a.argpart = A.argpart;
+  a.coef = 1.0 / ((double)A.nsteps * d.ny * d.nz * 2.0 * a.C.h[0] * (p.t_hot - p.t_cold));
+  a.dfloor = (h->u_ref_auto && p.Ra * p.Pr > 1.0) ? p.kappa * p.Pr : 0.0;
+  double *X = A.X, *Q = A.Q;
+  CK(cudaMemsetAsync(X, 0, sizeof(double) * 5 * a.g.fs, h->stream));
+  CK(cudaMemsetAsync(A.thetabar, 0, sizeof(double) * d.ny * d.nz, h->stream));
+  CK(cudaMemsetAsync(A.scal, 0, sizeof(double) * kScCount, h->stream));
+  const long long nint = (long long)d.nx * d.ny * d.nz;
+  const long long nfold = 2LL * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
+  std::vector<double> dts(A.ckpt);
+  int rc = CAVITY_OK;
+  for (int c = A.ncp - 1; c >= 0 && rc == CAVITY_OK; --c) {
+    const int s0 = c * A.ckpt, s1 = std::min(s0 + A.ckpt, A.nsteps);
+    // recompute the segment from its checkpoint, keeping every state
+    CK(cudaMemcpyAsync(B0.base[0], A.ckpt_mem + (size_t)c * A.set_bytes, A.set_bytes, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(h->d_cs, A.ckpt_cs + c, sizeof(CavState), cudaMemcpyDeviceToDevice, h->stream));
+    h->parity = 0;
+    for (int s = s0; s < s1; ++s) {
+      CK(cudaMemcpyAsync(A.seg_mem + (size_t)(s - s0) * A.set_bytes, B0.base[h->parity], A.set_bytes,
+                         cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(A.dts + s, &h->d_cs->dt, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      if (s < s1 - 1) {
+        CK(cudaGraphLaunch(h->graph[h->parity], h->stream));
+        h->parity ^= 1;
+      }
+    }
+    CK(cudaMemcpyAsync(dts.data(), A.dts + s0, sizeof(double) * (s1 - s0), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // reverse sweep over the segment
+    for (int s = s1 - 1; s >= s0; --s) {
+      a.B = B0;
+      a.B.base[0] = A.seg_mem + (size_t)(s - s0) * A.set_bytes;
+      a.dt = dts[s - s0];
+      a.X = X;
+      a.Q = Q;
+      if (h->f32) {
+        // the FP32-mixed step forms p and T wall values on the fly: write them into the stored state
+        CK(cudaMemcpyAsync(A.block, &a.B, sizeof(BlockDev), cudaMemcpyHostToDevice, h->stream));
+        BcArgs ba = bc_args(h, 0, 3);
+        ba.blocks = A.block;
+        k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(ba);
+        CK(cudaGetLastError());
+      }
+      k_adj_objective<<<ceil_div((long long)d.ny * d.nz, 256), 256, 0, h->stream>>>(a);
+      k_adj_sum_p<<<A.nparts, 256, 0, h->stream>>>(a);
+      k_adj_prepare<<<ceil_div(5 * a.g.fs, 256), 256, 0, h->stream>>>(a);
+      if (h->f32) {
+        k_adj_rates<float><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
+        k_adj_argmax<float><<<A.nparts, 256, 0, h->stream>>>(a);
+        k_adj_dt<float><<<1, 1, 0, h->stream>>>(a, A.nparts);
+      } else {
+        k_adj_rates<double><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
+        k_adj_argmax<double><<<A.nparts, 256, 0, h->stream>>>(a);
+        k_adj_dt<double><<<1, 1, 0, h->stream>>>(a, A.nparts);
+      }
+      k_adj_fold<<<ceil_div(nfold, 256), 256, 0, h->stream>>>(a);
+      k_adj_finish<<<1, 1, 0, h->stream>>>(a);
+      if (cudaGetLastError() != cudaSuccess) { rc = fail(h, CAVITY_ERR_CUDA, "adjoint kernel launch failed"); break; }
+      std::swap(X, Q);
+    }
+  }
+  // back to the state after the forward run
+  CK(cudaMemcpyAsync(h->hb[0].base[A.final_parity], A.final_mem, A.set_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_cs, &A.final_cs, sizeof(CavState), cudaMemcpyHostToDevice, h->stream));
+  h->parity = A.final_parity;
+  h->steps_taken = A.final_steps;
+  double ra = 0.0;
+  CK(cudaMemcpyAsync(&ra, A.scal + kScRa, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (grad_wall)
+    CK(cudaMemcpyAsync(grad_wall, A.thetabar, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (grad_ra) *grad_ra = ra;
   return rc;
 }
 
