@@ -30,7 +30,7 @@
 
 namespace bdc {
 
-constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 64, kF32R = 8;  // default tile height, z chunk, ring depth
+constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 64, kF32R = 8, kF32P = 1;  // default shape: tile height, z chunk, ring depth, nodes per thread
 constexpr int kF32BX = kF32TX + 8;  // x halo 4 on each side: the box starts on a 16-byte boundary
 constexpr int kF32NA = 7;           // p_hi, p_lo, u, v, w, T_hi, T_lo
 __host__ __device__ constexpr int f32_box_y(int TY) { return TY + 4; }  // y halo 2 (pressure star)
@@ -88,12 +88,72 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
-// hi/lo difference (a - c) of two FP32 pairs
-__device__ __forceinline__ float pdiff(float ah, float al, float ch, float cl) { return (ah - ch) + (al - cl); }
+// FP32 arithmetic with the rounding of every operation fixed (no contraction
+// left to the compiler), on one node (float) or on two nodes packed in one
+// register pair (float2: one f32x2 instruction per operation).  Both forms of
+// the step kernel evaluate the same expression trees, so they give identical
+// fields.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 
-// square root of a positive FP32 value as x * rsqrt(x) (two instructions,
-// within a few ulp); the FP32 form uses it for the wave speeds only
-__device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+// f32x2 operations as PTX with an explicit rounding modifier.  The code
+// generator still fuses a packed product into a packed sum that consumes
+// it, so the expression trees below never add to a packed product: they use
+// explicit FMAs instead, and rmul (a rounded product, per component) where
+// the rounded value itself is needed (the increment of a two-sum).
+#define BDC_F32X2_BINOP(NAME, OP)                                                                  \
+  __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                                     \
+    float2 r;                                                                                      \
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" OP \
+        " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                              \
+        : "=f"(r.x), "=f"(r.y)                                                                     \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                 \
+    return r;                                                                                      \
+  }
+BDC_F32X2_BINOP(vadd, "add.rn.f32x2")
+BDC_F32X2_BINOP(vsub, "sub.rn.f32x2")
+BDC_F32X2_BINOP(vmul, "mul.rn.f32x2")
+#undef BDC_F32X2_BINOP
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+__device__ __forceinline__ float2 vabs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float2 vmax(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 rmul(float2 a, float2 b) {
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float vrsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ float2 vrsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+
+template <class V> __device__ __forceinline__ V splat(float s);
+template <> __device__ __forceinline__ float splat<float>(float s) { return s; }
+template <> __device__ __forceinline__ float2 splat<float2>(float s) { return make_float2(s, s); }
+
+// hi/lo difference (a - c) of two FP32 pairs
+template <class V>
+__device__ __forceinline__ V pdiff(V ah, V al, V ch, V cl) { return vadd(vsub(ah, ch), vsub(al, cl)); }
+
+// (h, l) + d for an FP32 pair: two-sum of the hi part, error carried into lo
+template <class V>
+__device__ __forceinline__ void pair_add(V h, V l, V d, V &rh, V &rl) {
+  const V s = vadd(h, d);
+  const V bp = vsub(s, h);
+  const V e = vadd(vsub(h, vsub(s, bp)), vsub(d, bp));
+  const V lo = vadd(l, e);
+  rh = vadd(s, lo);
+  rl = vsub(lo, vsub(rh, s));
+}
 
 __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
   hi = (float)v;
@@ -103,12 +163,12 @@ __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
 // a + (a - b) for FP32 pairs: the linear extrapolation 2a - b with the hi
 // parts' rounding error carried into lo (two-sum), so about 48 bits survive
 __device__ __forceinline__ void extrapolate_pair(float ah, float al, float bh, float bl, float &rh, float &rl) {
-  const float d = ah - bh;  // exact for neighbouring values
-  const float s = ah + d;
-  const float bp = s - ah;
-  const float e = (ah - (s - bp)) + (d - bp);
+  const float d = vsub(ah, bh);  // exact for neighbouring values
+  const float s = vadd(ah, d);
+  const float bp = vsub(s, ah);
+  const float e = vadd(vsub(ah, vsub(s, bp)), vsub(d, bp));
   rh = s;
-  rl = e + (al + (al - bl));
+  rl = vadd(e, vadd(al, vsub(al, bl)));
 }
 
 // wall and ghost pressure from the two layers next to a wall (p1 nearest):
@@ -119,20 +179,10 @@ __device__ __forceinline__ void wall_pressure(float h1, float l1, float h2, floa
   extrapolate_pair(hw, lw, h1, l1, hg, lg);
 }
 
-// (h, l) + d for an FP32 pair: two-sum of the hi part, error carried into lo
-__device__ __forceinline__ void pair_add(float h, float l, float d, float &rh, float &rl) {
-  const float s = h + d;
-  const float bp = s - h;
-  const float e = (h - (s - bp)) + (d - bp);
-  const float lo = l + e;
-  rh = s + lo;
-  rl = lo - (rh - s);
-}
-
 // adiabatic wall temperature (4 T1 - T2) / 3 = T1 + (T1 - T2) / 3 of FP32 pairs
 __device__ __forceinline__ void wall_temperature(float h1, float l1, float h2, float l2, float &hw, float &lw) {
-  const float d = (h1 - h2) + (l1 - l2);
-  pair_add(h1, l1, d * (1.f / 3.f), hw, lw);
+  const float d = vadd(vsub(h1, h2), vsub(l1, l2));
+  pair_add(h1, l1, vmul(d, 1.f / 3.f), hw, lw);
 }
 
 // Apply the x and y wall conditions to one freshly loaded plane slot.
@@ -174,6 +224,9 @@ __device__ __forceinline__ void fix_plane_walls(float *s, int tid, bool wxl, boo
     H[y * BX + c1 + 1] = hw; L[y * BX + c1 + 1] = lw;
     if (c1 + 2 < BX) { H[y * BX + c1 + 2] = hg; L[y * BX + c1 + 2] = lg; }
   }
+  // the slot is refilled by TMA later: order these generic-proxy writes
+  // before the async proxy's
+  if (tid < 2 * (BX + BY)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -187,6 +240,172 @@ __device__ __forceinline__ float warp_max_f(float v) {
   return v;
 }
 
+// Constants of the FP32 update, broadcast to the value type.
+template <class V>
+struct F32K {
+  V ihx, ihy, ihz, h2x, h2y, h2z, mh2x, mh2y, mh2z, nhx, nhy, nhz, ahx, ahy, ahz, c4h, gs, tinf, b2min, dt, mdt, mcs, gy,
+      gz, diffsr;
+};
+
+template <class V>
+__device__ __forceinline__ F32K<V> f32_consts(const CavConst &C, const CavState &S) {
+  F32K<V> K;
+  K.ihx = splat<V>((float)C.ih[0]); K.ihy = splat<V>((float)C.ih[1]); K.ihz = splat<V>((float)C.ih[2]);
+  K.h2x = splat<V>((float)C.ih2[0]); K.h2y = splat<V>((float)C.ih2[1]); K.h2z = splat<V>((float)C.ih2[2]);
+  K.mh2x = splat<V>(-(float)C.ih2[0]); K.mh2y = splat<V>(-(float)C.ih2[1]); K.mh2z = splat<V>(-(float)C.ih2[2]);
+  K.nhx = splat<V>((float)(C.nu * C.ihh[0])); K.nhy = splat<V>((float)(C.nu * C.ihh[1]));
+  K.nhz = splat<V>((float)(C.nu * C.ihh[2]));
+  K.ahx = splat<V>((float)(C.alpha * C.ihh[0])); K.ahy = splat<V>((float)(C.alpha * C.ihh[1]));
+  K.ahz = splat<V>((float)(C.alpha * C.ihh[2]));
+  K.c4h = splat<V>((float)(0.5 * C.c4)); K.gs = splat<V>((float)C.gs); K.tinf = splat<V>((float)C.t_inf);
+  K.b2min = splat<V>((float)C.b2min);
+  const float dt = (float)S.dt;
+  K.dt = splat<V>(dt); K.mdt = splat<V>(-dt); K.mcs = splat<V>(-(float)S.c);
+  K.gy = splat<V>(C.gaxis == 1 ? 1.f : 0.f); K.gz = splat<V>(C.gaxis == 2 ? 1.f : 0.f);
+  K.diffsr = splat<V>((float)C.diffsr);
+  return K;
+}
+
+// The stencil of one node (or two): centre values and neighbour-minus-centre
+// differences (hi/lo pair differences for p and T).
+template <class V>
+struct F32Nb {
+  V ph, pl;                                                                  // centre p pair
+  V pxp1, pxm1, pxp2, pxm2, pyp1, pym1, pyp2, pym2, pzp1, pzm1, pzp2, pzm2;  // p differences
+  V u, v, w, th, tl;                                                         // centre u, v, w, T pair
+  V uxp, uxm, uyp, uym, uzp, uzm, vxp, vxm, vyp, vym, vzp, vzm, wxp, wxm, wyp, wym, wzp, wzm;
+  V txp, txm, typ, tym, tzp, tzm;
+};
+
+template <class V>
+struct F32Out {
+  V ph, pl, u, v, w, th, tl;  // new state
+  V rp, ru, rv, rw, rt;       // rates (rp with the sign flipped; only its square is summed)
+};
+
+// Rates of Eqs. 1-3 at the node(s) and the explicit update; p and T through
+// an error-free two-sum on their pairs.
+template <class V>
+__device__ __forceinline__ void f32_update(const F32K<V> &K, const F32Nb<V> &n, F32Out<V> &o) {
+  const V m4 = splat<V>(-4.f), four = splat<V>(4.f);
+  const V d4x = vfma(m4, vadd(n.pxp1, n.pxm1), vadd(n.pxp2, n.pxm2));
+  const V d4y = vfma(m4, vadd(n.pyp1, n.pym1), vadd(n.pyp2, n.pym2));
+  const V d4z = vfma(m4, vadd(n.pzp1, n.pzm1), vadd(n.pzp2, n.pzm2));
+  const V b2 = vmax(vfma(n.u, n.u, vfma(n.v, n.v, vmul(n.w, n.w))), K.b2min);
+  const V f4 = vmul(four, b2);
+  // 2 lambda_d = |V_d| + sqrt(V_d^2 + 4 beta^2), the root as x * rsqrt(x) fused
+  const V qx = vfma(n.u, n.u, f4), qy = vfma(n.v, n.v, f4), qz = vfma(n.w, n.w, f4);
+  const V sx = vfma(qx, vrsqrt(qx), vabs(n.u));
+  const V sy = vfma(qy, vrsqrt(qy), vabs(n.v));
+  const V sz = vfma(qz, vrsqrt(qz), vabs(n.w));
+  const V diss = vmul(K.c4h, vfma(vmul(sx, K.ihx), d4x, vfma(vmul(sy, K.ihy), d4y, vmul(vmul(sz, K.ihz), d4z))));
+  // transport: along each axis -V_d (q+ - q-)/(2h) + D (q+ - 2 q0 + q-)/h^2
+  // = cp * (q+ - q0) + cm * (q- - q0), cp = D/h^2 - V_d/(2h), cm = D/h^2 + V_d/(2h)
+  const V mpx = vfma(n.u, K.mh2x, K.nhx), mmx = vfma(n.u, K.h2x, K.nhx);
+  const V mpy = vfma(n.v, K.mh2y, K.nhy), mmy = vfma(n.v, K.h2y, K.nhy);
+  const V mpz = vfma(n.w, K.mh2z, K.nhz), mmz = vfma(n.w, K.h2z, K.nhz);
+  const V tpx = vfma(n.u, K.mh2x, K.ahx), tmx = vfma(n.u, K.h2x, K.ahx);
+  const V tpy = vfma(n.v, K.mh2y, K.ahy), tmy = vfma(n.v, K.h2y, K.ahy);
+  const V tpz = vfma(n.w, K.mh2z, K.ahz), tmz = vfma(n.w, K.h2z, K.ahz);
+  const V tru = vfma(mpx, n.uxp, vfma(mmx, n.uxm, vfma(mpy, n.uyp, vfma(mmy, n.uym, vfma(mpz, n.uzp, vmul(mmz, n.uzm))))));
+  const V trv = vfma(mpx, n.vxp, vfma(mmx, n.vxm, vfma(mpy, n.vyp, vfma(mmy, n.vym, vfma(mpz, n.vzp, vmul(mmz, n.vzm))))));
+  const V trw = vfma(mpx, n.wxp, vfma(mmx, n.wxm, vfma(mpy, n.wyp, vfma(mmy, n.wym, vfma(mpz, n.wzp, vmul(mmz, n.wzm))))));
+  o.rt = vfma(tpx, n.txp, vfma(tmx, n.txm, vfma(tpy, n.typ, vfma(tmy, n.tym, vfma(tpz, n.tzp, vmul(tmz, n.tzm))))));
+  const V divV = vfma(vsub(n.uxp, n.uxm), K.h2x, vfma(vsub(n.vyp, n.vym), K.h2y, vmul(vsub(n.wzp, n.wzm), K.h2z)));
+  o.rp = vfma(b2, divV, diss);  // = -dp/dt
+  const V buoy = vmul(K.gs, vadd(vsub(n.th, K.tinf), n.tl));
+  o.ru = vfma(vsub(n.pxm1, n.pxp1), K.h2x, tru);
+  o.rv = vfma(vsub(n.pym1, n.pyp1), K.h2y, vfma(K.gy, buoy, trv));
+  o.rw = vfma(vsub(n.pzm1, n.pzp1), K.h2z, vfma(K.gz, buoy, trw));
+  o.u = vfma(K.dt, o.ru, n.u);
+  o.v = vfma(K.dt, o.rv, n.v);
+  o.w = vfma(K.dt, o.rw, n.w);
+  pair_add(n.ph, n.pl, vfma(K.mdt, o.rp, K.mcs), o.ph, o.pl);  // p - dt (-dp/dt) - pending centre shift
+  pair_add(n.th, n.tl, rmul(K.dt, o.rt), o.th, o.tl);
+}
+
+// Spectral radius of the new state: lambda_d <= |V_d| + beta gives a cheap
+// bound; the exact value is needed only where the bound could raise the
+// thread's running maximum, so the maximum is unchanged.
+template <class V>
+__device__ __forceinline__ V f32_spectral_bound(const F32K<V> &K, V un, V vn, V wn) {
+  const V b2n = vmax(vfma(un, un, vfma(vn, vn, vmul(wn, wn))), K.b2min);
+  const V rb = vrsqrt(b2n);  // beta = b2n * rsqrt(b2n), fused into each |V_d| + beta
+  return vfma(vfma(b2n, rb, vabs(un)), K.ihx, vfma(vfma(b2n, rb, vabs(vn)), K.ihy, vfma(vfma(b2n, rb, vabs(wn)), K.ihz, K.diffsr)));
+}
+
+__device__ __forceinline__ float f32_spectral_exact(const F32K<float> &K, float un, float vn, float wn) {
+  const float b2n = vmax(vfma(un, un, vfma(vn, vn, vmul(wn, wn))), K.b2min);
+  const float f4n = vmul(4.f, b2n);
+  const float qx = vfma(un, un, f4n), qy = vfma(vn, vn, f4n), qz = vfma(wn, wn, f4n);
+  const float sx = vfma(qx, rsqrtf(qx), vabs(un));
+  const float sy = vfma(qy, rsqrtf(qy), vabs(vn));
+  const float sz = vfma(qz, rsqrtf(qz), vabs(wn));
+  return vfma(0.5f, vfma(sx, K.ihx, vfma(sy, K.ihy, vmul(sz, K.ihz))), K.diffsr);
+}
+
+__device__ __forceinline__ void f32_spectral_max(const F32K<float> &K, float bound, float un, float vn, float wn,
+                                                 float &smax) {
+  if (vmul(bound, 1.00001f) > smax) smax = fmaxf(smax, f32_spectral_exact(K, un, vn, wn));
+}
+
+// CTA partials: FP32 per thread and per warp tree, FP64 across warps (fixed order)
+template <int NT>
+__device__ __forceinline__ void f32_partials(double *partials, int cta, int tid, float s0, float s1, float s2,
+                                             float s3, float s4, float smax) {
+  __shared__ double red[NT / 32][6];
+  const int lane = tid & 31, wid = tid >> 5;
+  const float w0s = warp_sum_f(s0), w1s = warp_sum_f(s1), w2s = warp_sum_f(s2), w3s = warp_sum_f(s3);
+  const float w4s = warp_sum_f(s4), wms = warp_max_f(smax);
+  if (lane == 0) {
+    red[wid][0] = w0s; red[wid][1] = w1s; red[wid][2] = w2s; red[wid][3] = w3s; red[wid][4] = w4s;
+    red[wid][5] = wms;
+  }
+  __syncthreads();
+  if (tid < 6) {
+    double acc = red[0][tid];
+    for (int q = 1; q < NT / 32; ++q) acc = (tid == 5) ? fmax(acc, red[q][tid]) : acc + red[q][tid];
+    partials[(long long)cta * kPartStride + tid] = acc;
+  }
+}
+
+// Tile of one CTA and the walls that fall inside its boxes.
+struct F32Tile {
+  int b, i0, j0, k0, k1, tx, ty, nplanes, x0, y0, zbase, lxh, lyh;
+  bool wxl, wxh, wyl, wyh, wzl, wzh, fix;
+};
+
+template <int TY, int KC>
+__device__ __forceinline__ F32Tile f32_tile(const StepF32Args &a, int cta) {
+  F32Tile T;
+  T.b = find_block(a.blocks, a.nblocks, cta);
+  const BlockDev &B = a.blocks[T.b];
+  const int t = cta - B.tile_begin;
+  T.tx = t % B.tiles_x;
+  T.ty = (t / B.tiles_x) % B.tiles_y;
+  const int tz = t / (B.tiles_x * B.tiles_y);
+  T.i0 = T.tx * kF32TX + 1;
+  T.j0 = T.ty * TY + 1;
+  T.k0 = tz * KC + 1;
+  T.k1 = min(T.k0 + KC - 1, B.nz);
+  T.nplanes = (T.k1 - T.k0 + 1) + 4;  // z = k0-2 .. k1+2
+  T.x0 = XO<float>::v - 1 + T.i0 - 4;
+  T.y0 = (T.j0 - 2) + 1;
+  T.zbase = (T.k0 - 2) + 1;
+  T.wxl = B.wall[0] && T.tx == 0;
+  T.wxh = B.wall[1] && B.nx + 1 <= T.i0 + kF32TX + 3;
+  T.wyl = B.wall[2] && T.ty == 0;
+  T.wyh = B.wall[3] && B.ny + 1 <= T.j0 + TY + 1;
+  T.wzl = B.wall[4];
+  T.wzh = B.wall[5];
+  T.fix = T.wxl || T.wxh || T.wyl || T.wyh;
+  T.lxh = B.nx - T.i0 + 4;
+  T.lyh = B.ny - T.j0 + 2;
+  return T;
+}
+
+// One node per thread: a 32 x TY tile of threads; the z neighbours of the
+// thread's column live in register queues (5 deep for p, 3 for u, v, w, T).
 template <int TY, int KC, int R>
 __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(StepF32Args a) {
   static_assert(R >= 4 && (R & (R - 1)) == 0, "ring depth: a power of two >= 4");
@@ -198,27 +417,14 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
 
   const int cta = blockIdx.x;
-  const int b = find_block(a.blocks, a.nblocks, cta);
-  const BlockDev &B = a.blocks[b];
+  const F32Tile T = f32_tile<TY, KC>(a, cta);
+  const BlockDev &B = a.blocks[T.b];
   const CavConst &C = a.cc[B.cav];
-  const int t = cta - B.tile_begin;
-  const int tx = t % B.tiles_x, ty = (t / B.tiles_x) % B.tiles_y, tz = t / (B.tiles_x * B.tiles_y);
-  const int i0 = tx * TX + 1, j0 = ty * TY + 1, k0 = tz * KC + 1;
-  const int k1 = min(k0 + KC - 1, B.nz);
+  const int k0 = T.k0, k1 = T.k1;
   const int li = threadIdx.x, lj = threadIdx.y, tid = lj * TX + li;
-  const int i = i0 + li, j = j0 + lj;
+  const int i = T.i0 + li, j = T.j0 + lj;
   const bool active = (i <= B.nx) && (j <= B.ny);
-  const CUtensorMap *map = a.maps + 2 * b + a.parity;
-  const int nplanes = (k1 - k0 + 1) + 4;  // z = k0-2 .. k1+2
-  const int x0 = XO<float>::v - 1 + i0 - 4, y0 = (j0 - 2) + 1, zbase = (k0 - 2) + 1;
-  // walls whose wall/ghost nodes fall inside this tile's boxes
-  const bool wxl = B.wall[0] && tx == 0;
-  const bool wxh = B.wall[1] && B.nx + 1 <= i0 + TX + 3;
-  const bool wyl = B.wall[2] && ty == 0;
-  const bool wyh = B.wall[3] && B.ny + 1 <= j0 + TY + 1;
-  const bool wzl = B.wall[4], wzh = B.wall[5];
-  const bool fix = wxl || wxh || wyl || wyh;
-  const int lxh = B.nx - i0 + 4, lyh = B.ny - j0 + 2;
+  const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
 
   if (tid == 0) {
     for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
@@ -230,27 +436,16 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   auto issue = [&](int pl) {
     const int s = pl & (R - 1);
     mbar_expect_tx(&bars[s], SB);
-    tma_load_4d(ring + s * SF, map, &bars[s], x0, y0, zbase + pl, 0);
+    tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
   };
   if (tid == 0) {
-    for (; issued < min(R, nplanes); ++issued) issue(issued);
+    for (; issued < min(R, T.nplanes); ++issued) issue(issued);
   }
   auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1)); };
   auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
   const int col = (lj + 2) * BX + (li + 4);  // own column inside a slot
 
-  // constants in FP32
-  const float ihx = (float)C.ih[0], ihy = (float)C.ih[1], ihz = (float)C.ih[2];
-  const float h2x = (float)C.ih2[0], h2y = (float)C.ih2[1], h2z = (float)C.ih2[2];
-  const float nu = (float)C.nu, gs = (float)C.gs, tinf = (float)C.t_inf, b2min = (float)C.b2min;
-  const float nhx = (float)(C.nu * C.ihh[0]), nhy = (float)(C.nu * C.ihh[1]), nhz = (float)(C.nu * C.ihh[2]);
-  const float ahx = (float)(C.alpha * C.ihh[0]), ahy = (float)(C.alpha * C.ihh[1]), ahz = (float)(C.alpha * C.ihh[2]);
-  const float c4h = (float)(0.5 * C.c4), diffsr = (float)C.diffsr;
-  const float gy_on = C.gaxis == 1 ? 1.f : 0.f, gz_on = C.gaxis == 2 ? 1.f : 0.f;
-  const float dt = (float)a.cs[B.cav].dt;
-  const float cshift = (float)a.cs[B.cav].c;
-  (void)nu;
-
+  const F32K<float> K = f32_consts<float>(C, a.cs[B.cav]);
   const long long fs = B.fstride;
   // output pointer of this thread's node at plane k0 (advanced one plane per k)
   float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
@@ -273,15 +468,15 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         Tl[pl - 1] = s[6 * AS + col];
       }
       if (pl == 3) { T2next = s[5 * AS + col]; T2next_lo = s[6 * AS + col]; }
-      if (fix && pl >= 2) fix_plane_walls<NT, BY>(s, tid, wxl, wxh, wyl, wyh, lxh, lyh);
+      if (T.fix && pl >= 2) fix_plane_walls<NT, BY>(s, tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
     }
   }
   // bottom z wall inside the queue (queue slot q holds plane k0 - 2 + q);
   // constant indices keep the queues in registers
-  if (wzl && k0 == 1) {
+  if (T.wzl && k0 == 1) {
     wall_pressure(ph[2], pq[2], ph[3], pq[3], ph[1], pq[1], ph[0], pq[0]);
     wall_temperature(Tq[1], Tl[1], T2next, T2next_lo, Tq[0], Tl[0]);
-  } else if (wzl && k0 == 2) {
+  } else if (T.wzl && k0 == 2) {
     float hg, lg;
     wall_pressure(ph[1], pq[1], ph[2], pq[2], ph[0], pq[0], hg, lg);
   }
@@ -289,7 +484,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   bad = __syncthreads_or(bad);
   if (!bad && tid == 0) {
     // slots of planes 0 and 1 are free again
-    for (; issued < min(R + 2, nplanes); ++issued) issue(issued);
+    for (; issued < min(R + 2, T.nplanes); ++issued) issue(issued);
   }
 
   for (int k = k0; k <= k1 && !bad; ++k) {
@@ -305,7 +500,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
       wq[2] = sk1[4 * AS + col];
       Tq[2] = sk1[5 * AS + col];
       Tl[2] = sk1[6 * AS + col];
-      if (wzh) {
+      if (T.wzh) {
         if (k + 2 == B.nz + 1) {
           float hg, lg;
           wall_pressure(ph[3], pq[3], ph[2], pq[2], ph[4], pq[4], hg, lg);
@@ -314,85 +509,53 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         }
         if (k + 1 == B.nz + 1) wall_temperature(Tq[1], Tl[1], Tq[0], Tl[0], Tq[2], Tl[2]);
       }
-      if (fix) fix_plane_walls<NT, BY>(sk2, tid, wxl, wxh, wyl, wyh, lxh, lyh);
+      if (T.fix) fix_plane_walls<NT, BY>(sk2, tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
       if (active) {
-        const float p0h = ph[2], p0l = pq[2];
+        F32Nb<float> n;
+        n.ph = ph[2];
+        n.pl = pq[2];
         const float *H = sk, *L = sk + AS;
-        // pressure differences relative to the centre (hi/lo)
-        const float axp1 = pdiff(H[col + 1], L[col + 1], p0h, p0l), axm1 = pdiff(H[col - 1], L[col - 1], p0h, p0l);
-        const float axp2 = pdiff(H[col + 2], L[col + 2], p0h, p0l), axm2 = pdiff(H[col - 2], L[col - 2], p0h, p0l);
-        const float ayp1 = pdiff(H[col + BX], L[col + BX], p0h, p0l), aym1 = pdiff(H[col - BX], L[col - BX], p0h, p0l);
-        const float ayp2 = pdiff(H[col + 2 * BX], L[col + 2 * BX], p0h, p0l);
-        const float aym2 = pdiff(H[col - 2 * BX], L[col - 2 * BX], p0h, p0l);
-        const float azp1 = pdiff(ph[3], pq[3], p0h, p0l), azm1 = pdiff(ph[1], pq[1], p0h, p0l);
-        const float azp2 = pdiff(ph[4], pq[4], p0h, p0l), azm2 = pdiff(ph[0], pq[0], p0h, p0l);
-        const float d4x = (axp2 + axm2) - 4.f * (axp1 + axm1);
-        const float d4y = (ayp2 + aym2) - 4.f * (ayp1 + aym1);
-        const float d4z = (azp2 + azm2) - 4.f * (azp1 + azm1);
-        const float u0 = uq[1], v0 = vq[1], w0 = wq[1], T0 = Tq[1], T0l = Tl[1];
-        const float b2 = fmaxf(fmaf(u0, u0, fmaf(v0, v0, w0 * w0)), b2min);
-        const float f4 = 4.f * b2;
-        const float sx = fabsf(u0) + sqrt_pos(fmaf(u0, u0, f4));
-        const float sy = fabsf(v0) + sqrt_pos(fmaf(v0, v0, f4));
-        const float sz = fabsf(w0) + sqrt_pos(fmaf(w0, w0, f4));
-        const float diss = c4h * fmaf(sx * ihx, d4x, fmaf(sy * ihy, d4y, sz * ihz * d4z));
-        // transport: along each axis -V_d (q+ - q-)/(2h) + D (q+ - 2 q0 + q-)/h^2
-        // = cp * (q+ - q0) + cm * (q- - q0), cp = D/h^2 - V_d/(2h), cm = D/h^2 + V_d/(2h)
-        const float ax = u0 * h2x, ay = v0 * h2y, az = w0 * h2z;
-        const float mpx = nhx - ax, mmx = nhx + ax, mpy = nhy - ay, mmy = nhy + ay, mpz = nhz - az, mmz = nhz + az;
-        const float tpx = ahx - ax, tmx = ahx + ax, tpy = ahy - ay, tmy = ahy + ay, tpz = ahz - az, tmz = ahz + az;
+        n.pxp1 = pdiff(H[col + 1], L[col + 1], n.ph, n.pl);
+        n.pxm1 = pdiff(H[col - 1], L[col - 1], n.ph, n.pl);
+        n.pxp2 = pdiff(H[col + 2], L[col + 2], n.ph, n.pl);
+        n.pxm2 = pdiff(H[col - 2], L[col - 2], n.ph, n.pl);
+        n.pyp1 = pdiff(H[col + BX], L[col + BX], n.ph, n.pl);
+        n.pym1 = pdiff(H[col - BX], L[col - BX], n.ph, n.pl);
+        n.pyp2 = pdiff(H[col + 2 * BX], L[col + 2 * BX], n.ph, n.pl);
+        n.pym2 = pdiff(H[col - 2 * BX], L[col - 2 * BX], n.ph, n.pl);
+        n.pzp1 = pdiff(ph[3], pq[3], n.ph, n.pl);
+        n.pzm1 = pdiff(ph[1], pq[1], n.ph, n.pl);
+        n.pzp2 = pdiff(ph[4], pq[4], n.ph, n.pl);
+        n.pzm2 = pdiff(ph[0], pq[0], n.ph, n.pl);
+        n.u = uq[1]; n.v = vq[1]; n.w = wq[1]; n.th = Tq[1]; n.tl = Tl[1];
         const float *Us = sk + 2 * AS, *Vs = sk + 3 * AS, *Ws = sk + 4 * AS, *Ts = sk + 5 * AS, *Tls = sk + 6 * AS;
-#define BDC_F32_DIFFS(S, q0, zp, zm, dxp, dxm, dyp, dym, dzp, dzm) \
-  const float dxp = S[col + 1] - q0, dxm = S[col - 1] - q0;        \
-  const float dyp = S[col + BX] - q0, dym = S[col - BX] - q0;      \
-  const float dzp = zp - q0, dzm = zm - q0;
-        BDC_F32_DIFFS(Us, u0, uq[2], uq[0], uxp, uxm, uyp, uym, uzp, uzm)
-        BDC_F32_DIFFS(Vs, v0, vq[2], vq[0], vxp, vxm, vyp, vym, vzp, vzm)
-        BDC_F32_DIFFS(Ws, w0, wq[2], wq[0], wxp, wxm, wyp, wym, wzp, wzm)
-#undef BDC_F32_DIFFS
-        // temperature differences of the pair (hi and lo separately)
-        const float txp = pdiff(Ts[col + 1], Tls[col + 1], T0, T0l), txm = pdiff(Ts[col - 1], Tls[col - 1], T0, T0l);
-        const float typ = pdiff(Ts[col + BX], Tls[col + BX], T0, T0l);
-        const float tym = pdiff(Ts[col - BX], Tls[col - BX], T0, T0l);
-        const float tzp = pdiff(Tq[2], Tl[2], T0, T0l), tzm = pdiff(Tq[0], Tl[0], T0, T0l);
-        const float tru = fmaf(mpx, uxp, fmaf(mmx, uxm, fmaf(mpy, uyp, fmaf(mmy, uym, fmaf(mpz, uzp, mmz * uzm)))));
-        const float trv = fmaf(mpx, vxp, fmaf(mmx, vxm, fmaf(mpy, vyp, fmaf(mmy, vym, fmaf(mpz, vzp, mmz * vzm)))));
-        const float trw = fmaf(mpx, wxp, fmaf(mmx, wxm, fmaf(mpy, wyp, fmaf(mmy, wym, fmaf(mpz, wzp, mmz * wzm)))));
-        const float rT = fmaf(tpx, txp, fmaf(tmx, txm, fmaf(tpy, typ, fmaf(tmy, tym, fmaf(tpz, tzp, tmz * tzm)))));
-        const float divV = fmaf(uxp - uxm, h2x, fmaf(vyp - vym, h2y, (wzp - wzm) * h2z));
-        const float rp = fmaf(-b2, divV, -diss);
-        const float buoy = gs * ((T0 - tinf) + T0l);
-        const float ru = fmaf(-(axp1 - axm1), h2x, tru);
-        const float rv = fmaf(-(ayp1 - aym1), h2y, fmaf(gy_on, buoy, trv));
-        const float rw = fmaf(-(azp1 - azm1), h2z, fmaf(gz_on, buoy, trw));
-        // explicit update; p and T through an error-free two-sum on their pairs
-        const float un = fmaf(dt, ru, u0), vn = fmaf(dt, rv, v0), wn = fmaf(dt, rw, w0);
-        float hin, lon, Tnh, Tnl;
-        pair_add(p0h, p0l, fmaf(dt, rp, -cshift), hin, lon);
-        pair_add(T0, T0l, dt * rT, Tnh, Tnl);
-        out[0] = hin;
-        out[fs] = lon;
-        out[2 * fs] = un;
-        out[3 * fs] = vn;
-        out[4 * fs] = wn;
-        out[5 * fs] = Tnh;
-        out[6 * fs] = Tnl;
-        s0 = fmaf(rp, rp, s0); s1 = fmaf(ru, ru, s1); s2 = fmaf(rv, rv, s2); s3 = fmaf(rw, rw, s3);
-        s4 = fmaf(rT, rT, s4);
-        // spectral radius of the new state: lambda_d <= |V_d| + beta gives a
-        // cheap bound; the exact value is needed only where the bound could
-        // raise this thread's running maximum, so the maximum is unchanged
-        const float b2n = fmaxf(fmaf(un, un, fmaf(vn, vn, wn * wn)), b2min);
-        const float bn = sqrt_pos(b2n);
-        const float bound = fmaf(fabsf(un) + bn, ihx, fmaf(fabsf(vn) + bn, ihy, fmaf(fabsf(wn) + bn, ihz, diffsr)));
-        if (bound * 1.00001f > smax) {
-          const float f4n = 4.f * b2n;
-          const float srn = fmaf(0.5f, fmaf(fabsf(un) + sqrt_pos(fmaf(un, un, f4n)), ihx,
-                                            fmaf(fabsf(vn) + sqrt_pos(fmaf(vn, vn, f4n)), ihy,
-                                                 (fabsf(wn) + sqrt_pos(fmaf(wn, wn, f4n))) * ihz)),
-                                 diffsr);
-          smax = fmaxf(smax, srn);
-        }
+        n.uxp = vsub(Us[col + 1], n.u); n.uxm = vsub(Us[col - 1], n.u);
+        n.uyp = vsub(Us[col + BX], n.u); n.uym = vsub(Us[col - BX], n.u);
+        n.uzp = vsub(uq[2], n.u); n.uzm = vsub(uq[0], n.u);
+        n.vxp = vsub(Vs[col + 1], n.v); n.vxm = vsub(Vs[col - 1], n.v);
+        n.vyp = vsub(Vs[col + BX], n.v); n.vym = vsub(Vs[col - BX], n.v);
+        n.vzp = vsub(vq[2], n.v); n.vzm = vsub(vq[0], n.v);
+        n.wxp = vsub(Ws[col + 1], n.w); n.wxm = vsub(Ws[col - 1], n.w);
+        n.wyp = vsub(Ws[col + BX], n.w); n.wym = vsub(Ws[col - BX], n.w);
+        n.wzp = vsub(wq[2], n.w); n.wzm = vsub(wq[0], n.w);
+        n.txp = pdiff(Ts[col + 1], Tls[col + 1], n.th, n.tl);
+        n.txm = pdiff(Ts[col - 1], Tls[col - 1], n.th, n.tl);
+        n.typ = pdiff(Ts[col + BX], Tls[col + BX], n.th, n.tl);
+        n.tym = pdiff(Ts[col - BX], Tls[col - BX], n.th, n.tl);
+        n.tzp = pdiff(Tq[2], Tl[2], n.th, n.tl);
+        n.tzm = pdiff(Tq[0], Tl[0], n.th, n.tl);
+        F32Out<float> o;
+        f32_update(K, n, o);
+        out[0] = o.ph;
+        out[fs] = o.pl;
+        out[2 * fs] = o.u;
+        out[3 * fs] = o.v;
+        out[4 * fs] = o.w;
+        out[5 * fs] = o.th;
+        out[6 * fs] = o.tl;
+        s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
+        s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
+        f32_spectral_max(K, f32_spectral_bound(K, o.u, o.v, o.w), o.u, o.v, o.w, smax);
       }
       out += B.plane;
       ph[0] = ph[1]; ph[1] = ph[2]; ph[2] = ph[3]; ph[3] = ph[4];
@@ -401,7 +564,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
       wq[0] = wq[1]; wq[1] = wq[2]; Tq[0] = Tq[1]; Tq[1] = Tq[2]; Tl[0] = Tl[1]; Tl[1] = Tl[2];
     }
     bad = __syncthreads_or(bad);
-    if (!bad && tid == 0 && issued < nplanes) {
+    if (!bad && tid == 0 && issued < T.nplanes) {
       // the slot of plane pk is free: refill it with the next plane
       issue(issued);
       ++issued;
@@ -416,21 +579,203 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
     }
     __syncthreads();
   }
-  // CTA partials: FP32 per thread and per warp tree, FP64 across warps (fixed order)
-  __shared__ double red[NT / 32][6];
-  const int lane = tid & 31, wid = tid >> 5;
-  const float w0s = warp_sum_f(s0), w1s = warp_sum_f(s1), w2s = warp_sum_f(s2), w3s = warp_sum_f(s3);
-  const float w4s = warp_sum_f(s4), wms = warp_max_f(smax);
-  if (lane == 0) {
-    red[wid][0] = w0s; red[wid][1] = w1s; red[wid][2] = w2s; red[wid][3] = w3s; red[wid][4] = w4s;
-    red[wid][5] = wms;
+  f32_partials<NT>(a.partials, cta, tid, s0, s1, s2, s3, s4, smax);
+}
+
+__device__ __forceinline__ float2 ld2(const float *s, int idx) { return *reinterpret_cast<const float2 *>(s + idx); }
+__device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+
+// Two nodes per thread: a 16 x TY tile of threads covers the same 32 x TY
+// nodes, thread (li, lj) the nodes i = i0 + 2 li and i + 1 of row j, packed
+// in register pairs (f32x2 arithmetic, 64-bit shared loads and global
+// stores).  The z neighbours are read from the ring (planes k-2 .. k+2 stay
+// resident while plane k is computed), so no register queues rotate; walls
+// in z are formed from the loaded interior layers where they are read.
+template <int TY, int KC, int R>
+__global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_step_f32p(StepF32Args a) {
+  static_assert(R >= 8 && (R & (R - 1)) == 0, "ring depth: a power of two >= 8 (five planes resident)");
+  constexpr int NTX = kF32TX / 2, NT = NTX * TY;
+  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;
+  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float *ring = reinterpret_cast<float *>(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
+
+  const int cta = blockIdx.x;
+  const F32Tile T = f32_tile<TY, KC>(a, cta);
+  const BlockDev &B = a.blocks[T.b];
+  const CavConst &C = a.cc[B.cav];
+  const int k0 = T.k0, k1 = T.k1;
+  const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
+  const int i = T.i0 + 2 * li, j = T.j0 + lj;
+  const bool act0 = (i <= B.nx) && (j <= B.ny), act1 = (i + 1 <= B.nx) && (j <= B.ny);
+  const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
+
+  if (tid == 0) {
+    for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
   }
   __syncthreads();
-  if (tid < 6) {
-    double acc = red[0][tid];
-    for (int q = 1; q < NT / 32; ++q) acc = (tid == 5) ? fmax(acc, red[q][tid]) : acc + red[q][tid];
-    a.partials[(long long)cta * kPartStride + tid] = acc;
+  int issued = 0;
+  auto issue = [&](int pl) {
+    const int s = pl & (R - 1);
+    mbar_expect_tx(&bars[s], SB);
+    tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
+  };
+  if (tid == 0) {
+    for (; issued < min(R, T.nplanes); ++issued) issue(issued);
   }
+  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1)); };
+  auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
+  const int col = (lj + 2) * BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
+
+  const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
+  const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
+  const long long fs = B.fstride;
+  // i is odd, so the pair starts on an 8-byte boundary of the row
+  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
+
+  bool bad = false;
+  // prologue: planes k0-2 .. k0+1; the x and y walls of the interior planes
+  for (int pl = 0; pl < 4; ++pl) {
+    if (!bad && !wait_plane(pl)) bad = true;
+    if (!bad && T.fix && pl >= 2) fix_plane_walls<NT, BY>(slot(pl), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+  }
+  float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
+  float smax = 0.f;
+  bad = __syncthreads_or(bad);
+
+  for (int k = k0; k <= k1 && !bad; ++k) {
+    const int pk = k - k0 + 2;  // plane index of k
+    if (!wait_plane(pk + 2)) bad = true;
+    if (!bad) {
+      if (T.fix) fix_plane_walls<NT, BY>(slot(pk + 2), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+      if (act0) {
+        const float *S0 = slot(pk), *Sm1 = slot(pk - 1), *Sm2 = slot(pk - 2), *Sp1 = slot(pk + 1),
+                    *Sp2 = slot(pk + 2);
+        F32Nb<float2> n;
+        // pressure: centre pair and its z neighbours (walls formed in place)
+        n.ph = ld2(S0, col);
+        n.pl = ld2(S0 + AS, col);
+        float2 zm2h = ld2(Sm2, col), zm2l = ld2(Sm2 + AS, col), zm1h = ld2(Sm1, col), zm1l = ld2(Sm1 + AS, col);
+        float2 zp1h = ld2(Sp1, col), zp1l = ld2(Sp1 + AS, col), zp2h = ld2(Sp2, col), zp2l = ld2(Sp2 + AS, col);
+        float2 th = ld2(S0 + 5 * AS, col), tl = ld2(S0 + 6 * AS, col);
+        float2 tzmh = ld2(Sm1 + 5 * AS, col), tzml = ld2(Sm1 + 6 * AS, col);
+        float2 tzph = ld2(Sp1 + 5 * AS, col), tzpl = ld2(Sp1 + 6 * AS, col);
+        if (T.wzl && k <= 2) {
+          float hg, lg;
+          if (k == 1) {  // z = 0 wall and z = -1 ghost from the layers z = 1, 2
+            wall_pressure(n.ph.x, n.pl.x, zp1h.x, zp1l.x, zm1h.x, zm1l.x, zm2h.x, zm2l.x);
+            wall_pressure(n.ph.y, n.pl.y, zp1h.y, zp1l.y, zm1h.y, zm1l.y, zm2h.y, zm2l.y);
+            wall_temperature(th.x, tl.x, tzph.x, tzpl.x, tzmh.x, tzml.x);
+            wall_temperature(th.y, tl.y, tzph.y, tzpl.y, tzmh.y, tzml.y);
+          } else {  // k == 2: z = 0 wall from z = 1, 2
+            wall_pressure(zm1h.x, zm1l.x, n.ph.x, n.pl.x, zm2h.x, zm2l.x, hg, lg);
+            wall_pressure(zm1h.y, zm1l.y, n.ph.y, n.pl.y, zm2h.y, zm2l.y, hg, lg);
+          }
+        }
+        if (T.wzh && k >= B.nz - 1) {
+          float hg, lg;
+          if (k == B.nz) {  // z = nz+1 wall and nz+2 ghost from the layers nz, nz-1
+            wall_pressure(n.ph.x, n.pl.x, zm1h.x, zm1l.x, zp1h.x, zp1l.x, zp2h.x, zp2l.x);
+            wall_pressure(n.ph.y, n.pl.y, zm1h.y, zm1l.y, zp1h.y, zp1l.y, zp2h.y, zp2l.y);
+            wall_temperature(th.x, tl.x, tzmh.x, tzml.x, tzph.x, tzpl.x);
+            wall_temperature(th.y, tl.y, tzmh.y, tzml.y, tzph.y, tzpl.y);
+          } else {  // k == nz-1: z = nz+1 wall from nz, nz-1
+            wall_pressure(zp1h.x, zp1l.x, n.ph.x, n.pl.x, zp2h.x, zp2l.x, hg, lg);
+            wall_pressure(zp1h.y, zp1l.y, n.ph.y, n.pl.y, zp2h.y, zp2l.y, hg, lg);
+          }
+        }
+        n.pzp1 = pdiff(zp1h, zp1l, n.ph, n.pl);
+        n.pzm1 = pdiff(zm1h, zm1l, n.ph, n.pl);
+        n.pzp2 = pdiff(zp2h, zp2l, n.ph, n.pl);
+        n.pzm2 = pdiff(zm2h, zm2l, n.ph, n.pl);
+        {
+          const float *H = S0, *L = S0 + AS;
+          const float2 ah = ld2(H, col - 2), al = ld2(L, col - 2), dh = ld2(H, col + 2), dl = ld2(L, col + 2);
+          n.pxp1 = make_float2(pdiff(n.ph.y, n.pl.y, n.ph.x, n.pl.x), pdiff(dh.x, dl.x, n.ph.y, n.pl.y));
+          n.pxm1 = make_float2(pdiff(ah.y, al.y, n.ph.x, n.pl.x), pdiff(n.ph.x, n.pl.x, n.ph.y, n.pl.y));
+          n.pxp2 = pdiff(dh, dl, n.ph, n.pl);
+          n.pxm2 = pdiff(ah, al, n.ph, n.pl);
+          n.pyp1 = pdiff(ld2(H, col + BX), ld2(L, col + BX), n.ph, n.pl);
+          n.pym1 = pdiff(ld2(H, col - BX), ld2(L, col - BX), n.ph, n.pl);
+          n.pyp2 = pdiff(ld2(H, col + 2 * BX), ld2(L, col + 2 * BX), n.ph, n.pl);
+          n.pym2 = pdiff(ld2(H, col - 2 * BX), ld2(L, col - 2 * BX), n.ph, n.pl);
+        }
+        // velocity: x differences per node, y and z packed
+#define BDC_F32P_VEL(F, c0, xp, xm, yp, ym, zp, zm)                                                  \
+  {                                                                                                \
+    const float *Q = S0 + F * AS;                                                                  \
+    c0 = ld2(Q, col);                                                                              \
+    const float qm = Q[col - 1], qp = Q[col + 2];                                                  \
+    xp = make_float2(vsub(c0.y, c0.x), vsub(qp, c0.y));                                            \
+    xm = make_float2(vsub(qm, c0.x), vsub(c0.x, c0.y));                                            \
+    yp = vsub(ld2(Q, col + BX), c0);                                                               \
+    ym = vsub(ld2(Q, col - BX), c0);                                                               \
+    zp = vsub(ld2(Sp1 + F * AS, col), c0);                                                         \
+    zm = vsub(ld2(Sm1 + F * AS, col), c0);                                                         \
+  }
+        BDC_F32P_VEL(2, n.u, n.uxp, n.uxm, n.uyp, n.uym, n.uzp, n.uzm)
+        BDC_F32P_VEL(3, n.v, n.vxp, n.vxm, n.vyp, n.vym, n.vzp, n.vzm)
+        BDC_F32P_VEL(4, n.w, n.wxp, n.wxm, n.wyp, n.wym, n.wzp, n.wzm)
+#undef BDC_F32P_VEL
+        // temperature pair
+        n.th = th;
+        n.tl = tl;
+        {
+          const float *TH = S0 + 5 * AS, *TL = S0 + 6 * AS;
+          n.txp = make_float2(pdiff(th.y, tl.y, th.x, tl.x), pdiff(TH[col + 2], TL[col + 2], th.y, tl.y));
+          n.txm = make_float2(pdiff(TH[col - 1], TL[col - 1], th.x, tl.x), pdiff(th.x, tl.x, th.y, tl.y));
+          n.typ = pdiff(ld2(TH, col + BX), ld2(TL, col + BX), th, tl);
+          n.tym = pdiff(ld2(TH, col - BX), ld2(TL, col - BX), th, tl);
+          n.tzp = pdiff(tzph, tzpl, th, tl);
+          n.tzm = pdiff(tzmh, tzml, th, tl);
+        }
+        F32Out<float2> o;
+        f32_update(K, n, o);
+        const float2 bound = f32_spectral_bound(K, o.u, o.v, o.w);
+        f32_spectral_max(K1, bound.x, o.u.x, o.v.x, o.w.x, smax);
+        if (act1) {
+          st2(out, o.ph);
+          st2(out + fs, o.pl);
+          st2(out + 2 * fs, o.u);
+          st2(out + 3 * fs, o.v);
+          st2(out + 4 * fs, o.w);
+          st2(out + 5 * fs, o.th);
+          st2(out + 6 * fs, o.tl);
+          f32_spectral_max(K1, bound.y, o.u.y, o.v.y, o.w.y, smax);
+        } else {  // the x extent is odd: the pair's second node is a wall or beyond
+          out[0] = o.ph.x;
+          out[fs] = o.pl.x;
+          out[2 * fs] = o.u.x;
+          out[3 * fs] = o.v.x;
+          out[4 * fs] = o.w.x;
+          out[5 * fs] = o.th.x;
+          out[6 * fs] = o.tl.x;
+          o.rp.y = o.ru.y = o.rv.y = o.rw.y = o.rt.y = 0.f;
+        }
+        s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
+        s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
+      }
+      out += B.plane;
+    }
+    bad = __syncthreads_or(bad);
+    if (!bad && tid == 0 && issued < T.nplanes) {
+      // the slot of plane pk - 2 is free: refill it with the next plane
+      issue(issued);
+      ++issued;
+    }
+  }
+  if (bad) {
+    if (tid == 0) {
+      atomicOr(&a.cs[B.cav].flags, 2);
+      for (int pl = max(0, issued - R); pl < issued; ++pl) (void)wait_plane(pl);
+    }
+    __syncthreads();
+  }
+  f32_partials<NT>(a.partials, cta, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
+                   vadd(s4.x, s4.y), smax);
 }
 
 // Spectral-radius partials of the current state (no update), with the step

@@ -41,20 +41,23 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// FP32 step-kernel tile shapes compiled in: (tile height TY, z chunk KC, ring depth R)
-#define BDC_F32_VARIANTS(X) X(8, 16, 8) X(8, 32, 8) X(8, 64, 8) X(4, 32, 8) X(4, 64, 8)
+// FP32 step-kernel shapes compiled in: (nodes per thread along x P, tile
+// height TY, z chunk KC, ring depth R); P = 1 is k_step_f32, P = 2 k_step_f32p
+#define BDC_F32_VARIANTS(X)                                                                       \
+  X(1, 8, 16, 8) X(1, 8, 32, 8) X(1, 8, 64, 8) X(1, 4, 32, 8) X(1, 4, 64, 8) X(2, 8, 32, 8) X(2, 8, 64, 8) \
+      X(2, 16, 32, 8) X(2, 16, 64, 8)
 struct F32Shape {
-  int ty, kc, r;
+  int p, ty, kc, r;
 };
 const F32Shape kF32Shapes[] = {
-#define BDC_SHAPE(TY, KC, R) {TY, KC, R},
+#define BDC_SHAPE(P, TY, KC, R) {P, TY, KC, R},
     BDC_F32_VARIANTS(BDC_SHAPE)
 #undef BDC_SHAPE
 };
 
-bool f32_variant_ok(int ty, int kc, int r) {
+bool f32_variant_ok(int p, int ty, int kc, int r) {
   for (const F32Shape &s : kF32Shapes)
-    if (s.ty == ty && s.kc == kc && s.r == r) return true;
+    if (s.p == p && s.ty == ty && s.kc == kc && s.r == r) return true;
   return false;
 }
 
@@ -96,6 +99,7 @@ struct cavity {
   int np = 1;                     // pressure arrays
   int tx = kTX, ty = kTY, kc = kKC;
   int f32_r = 0;                  // ring depth of the FP32 step kernel
+  int f32_p = 1;                  // nodes per thread along x of the FP32 step kernel
   int nblocks = 0;
   std::vector<BlockDev> hb;
   std::vector<WallFace> hwall;
@@ -361,10 +365,16 @@ int encode_maps(cavity *h) {
   return CAVITY_OK;
 }
 
-cudaError_t f32_set_smem(int ty, int kc, int r) {
-#define BDC_ATTR(TY, KC, R)                                                                              \
-  if (ty == TY && kc == KC && r == R)                                                                    \
-    return cudaFuncSetAttribute(k_step_f32<TY, KC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+template <int P, int TY, int KC, int R>
+auto f32_kernel() {
+  if constexpr (P == 1) return k_step_f32<TY, KC, R>;
+  else return k_step_f32p<TY, KC, R>;
+}
+
+cudaError_t f32_set_smem(int p, int ty, int kc, int r) {
+#define BDC_ATTR(P, TY, KC, R)                                                                                   \
+  if (p == P && ty == TY && kc == KC && r == R)                                                                  \
+    return cudaFuncSetAttribute(f32_kernel<P, TY, KC, R>(), cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                 f32_smem_bytes(TY, R));
   BDC_F32_VARIANTS(BDC_ATTR)
 #undef BDC_ATTR
@@ -421,7 +431,7 @@ int alloc_device(cavity *h) {
   if (h->f32) {
     rc = encode_maps(h);
     if (rc != CAVITY_OK) return rc;
-    CK(f32_set_smem(h->ty, h->kc, h->f32_r));
+    CK(f32_set_smem(h->f32_p, h->ty, h->kc, h->f32_r));
   }
   return CAVITY_OK;
 }
@@ -478,9 +488,9 @@ ExchArgs exch_args(cavity *h, int parity) {
 
 void launch_step_kernel(cavity *h, int parity) {
   if (h->f32) {
-#define BDC_LAUNCH(TY, KC, R)                                                                          \
-  if (h->ty == TY && h->kc == KC && h->f32_r == R)                                                     \
-    k_step_f32<TY, KC, R><<<h->n_step, dim3(kF32TX, TY), f32_smem_bytes(TY, R), h->stream>>>(          \
+#define BDC_LAUNCH(P, TY, KC, R)                                                                           \
+  if (h->f32_p == P && h->ty == TY && h->kc == KC && h->f32_r == R)                                        \
+    f32_kernel<P, TY, KC, R>()<<<h->n_step, dim3(kF32TX / P, TY), f32_smem_bytes(TY, R), h->stream>>>(     \
         step_f32_args(h, parity));
     BDC_F32_VARIANTS(BDC_LAUNCH)
 #undef BDC_LAUNCH
@@ -492,8 +502,8 @@ void launch_step_kernel(cavity *h, int parity) {
 void launch_spectral(cavity *h) {
   const StepArgs sa = step_args(h, h->parity, 1);
   if (h->f32) {
-#define BDC_SPEC(TY, KC, R)                                                                                      \
-  if (h->ty == TY && h->kc == KC && h->f32_r == R)                                                               \
+#define BDC_SPEC(P, TY, KC, R)                                                                                   \
+  if (h->f32_p == P && h->ty == TY && h->kc == KC && h->f32_r == R)                                              \
     k_spectral<float, kF32TX, TY, KC><<<h->n_step, dim3(kF32TX, TY), 0, h->stream>>>(sa);
     BDC_F32_VARIANTS(BDC_SPEC)
 #undef BDC_SPEC
@@ -572,8 +582,9 @@ int build_graphs(cavity *h) {
 }
 
 // change the FP32 step kernel's tile shape: work lists, maps, graphs
-int retile(cavity *h, int ty, int kc, int r) {
+int retile(cavity *h, int p, int ty, int kc, int r) {
   CK(cudaStreamSynchronize(h->stream));
+  h->f32_p = p;
   h->ty = ty;
   h->kc = kc;
   h->f32_r = r;
@@ -582,7 +593,7 @@ int retile(cavity *h, int ty, int kc, int r) {
   if (rc == CAVITY_OK) rc = upload_tables(h);
   if (rc == CAVITY_OK) rc = encode_maps(h);
   if (rc != CAVITY_OK) return rc;
-  CK(f32_set_smem(ty, kc, r));
+  CK(f32_set_smem(p, ty, kc, r));
   return build_graphs(h);
 }
 
@@ -739,13 +750,16 @@ int create_common(const cavity_desc *descs, const cavity_params *params, int n, 
     h->ty = kF32TY;
     h->kc = kF32KC;
     h->f32_r = kF32R;
-    // tile override for tuning sweeps: BDC_F32_TILE="TY,KC,R" (a compiled shape)
+    h->f32_p = kF32P;
+    // shape override for tuning sweeps: BDC_F32_TILE="TY,KC,R[,P]" (a compiled shape)
     if (const char *env = std::getenv("BDC_F32_TILE")) {
-      int ty = 0, kc = 0, r = 0;
-      if (std::sscanf(env, "%d,%d,%d", &ty, &kc, &r) == 3 && f32_variant_ok(ty, kc, r)) {
+      int ty = 0, kc = 0, r = 0, p = 1;
+      const int got = std::sscanf(env, "%d,%d,%d,%d", &ty, &kc, &r, &p);
+      if (got >= 3 && f32_variant_ok(p, ty, kc, r)) {
         h->ty = ty;
         h->kc = kc;
         h->f32_r = r;
+        h->f32_p = p;
       }
     }
   }
@@ -1009,7 +1023,7 @@ int cavity_exchange(cavity_t *h) {
   return launch_exchange(h, h->parity);
 }
 
-int cavity_autotune(cavity_t *h, int steps, double out[4]) {
+int cavity_autotune(cavity_t *h, int steps, double out[5]) {
   if (!h || steps < 1) return CAVITY_ERR_INVALID_ARG;
   if (!h->f32) return fail(h, CAVITY_ERR_UNSUPPORTED, "the FP64 form has one tile shape");
   DeviceGuard g(h->dev);
@@ -1035,10 +1049,10 @@ int cavity_autotune(cavity_t *h, int steps, double out[4]) {
   if (rc == CAVITY_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     rc = fail(h, CAVITY_ERR_CUDA, "event creation failed");
   double best_us = 1e300;
-  F32Shape best = {h->ty, h->kc, h->f32_r};
+  F32Shape best = {h->f32_p, h->ty, h->kc, h->f32_r};
   for (const F32Shape &s : kF32Shapes) {
     if (rc != CAVITY_OK) break;
-    rc = retile(h, s.ty, s.kc, s.r);
+    rc = retile(h, s.p, s.ty, s.kc, s.r);
     if (rc != CAVITY_OK) break;
     rc = cavity_step(h, 2);  // warm-up
     if (rc != CAVITY_OK) break;
@@ -1056,7 +1070,7 @@ int cavity_autotune(cavity_t *h, int steps, double out[4]) {
     }
     rc = restore();
   }
-  if (rc == CAVITY_OK) rc = retile(h, best.ty, best.kc, best.r);
+  if (rc == CAVITY_OK) rc = retile(h, best.p, best.ty, best.kc, best.r);
   if (rc == CAVITY_OK) rc = restore();
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -1065,7 +1079,8 @@ int cavity_autotune(cavity_t *h, int steps, double out[4]) {
     out[0] = best.ty;
     out[1] = best.kc;
     out[2] = best.r;
-    out[3] = best_us;
+    out[3] = best.p;
+    out[4] = best_us;
   }
   return rc;
 }

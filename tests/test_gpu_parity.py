@@ -316,6 +316,29 @@ def test_fp32_blocks_bit_identical(m, blocks):
         assert c.time == ref.time
 
 
+@pytest.mark.parametrize("shape", ["8,32,8,2", "16,64,8,2"])
+def test_fp32_two_node_kernel(m, monkeypatch, shape):
+    """The kernel with two nodes per thread: ragged sizes against the oracle
+    (odd nx leaves a lone node in the last pair), and a decomposition with odd
+    per-block x extents bit-equal to one block."""
+    monkeypatch.setenv("BDC_F32_TILE", shape)
+    for n in [(37, 21, 18), (2, 2, 2), (65, 9, 40)]:
+        o, c = run_pair32(m, n, 3e4, 25, noise=1e-3, seed=11)
+        with c:
+            g, ref = c.fields(), o.fields()
+            speed = max(np.max(np.abs(ref[f])) for f in (1, 2, 3))
+            for f, name in enumerate(oracle.FIELDS):
+                scale = speed if f in (1, 2, 3) else np.max(np.abs(ref[f]))
+                e = np.max(np.abs(g[f] - ref[f])) / scale
+                assert e <= FP32_TOL, f"fp32 {shape} n={n} field {name}: {e:.3e}"
+    kw = dict(precision=m.CAVITY_FP32_MIXED, seed=9, noise_amp=1e-3, Ra=1e5)
+    with m.Cavity(47, 40, 44, **kw) as ref, m.Cavity(47, 40, 44, blocks=(3, 2, 2), **kw) as c:
+        ref.step(60)
+        c.step(60)
+        assert np.array_equal(c.fields(), ref.fields())
+        assert c.time == ref.time
+
+
 def test_fp32_ghosts_and_buffers_bit_exact(m):
     blocks = (2, 2, 2)
     kw = dict(precision=m.CAVITY_FP32_MIXED, seed=9, noise_amp=1e-3, Ra=1e5)
