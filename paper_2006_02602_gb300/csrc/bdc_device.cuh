@@ -55,7 +55,6 @@ struct CavConst {
   long long centre_off[kMaxCentre];  // element offset of the node in its field array
   int tile_begin, tile_end;          // k_step CTAs of this cavity
   int bc_begin, bc_end;              // k_bc CTAs of this cavity (all wall faces)
-  int nus_begin, nus_end;            // k_bc CTAs of this cavity in the Nusselt-only mode (x walls)
   long long wall_off;                // offset of this cavity's wall temperatures
 };
 
@@ -332,25 +331,10 @@ struct BcArgs {
   const double *t_wall;       // hot walls then cold walls, per cavity at wall_off
   int parity;                 // buffer set holding the new state
   int mode;                   // 0 after a step, 1 after init / set_fields,
-                              // 2 after a step whose kernel applied the walls itself:
-                              //   Nusselt sums over the x-wall faces only,
-                              // 3 walls only, no reductions
+                              // 3 walls only, no reductions,
+                              // 4 finalise only (after an FP32 step): Nusselt
+                              //   sums in the step partials
 };
-
-// Nusselt sums of one x-wall node (no writes)
-template <class S>
-__device__ __forceinline__ void nusselt_node(const BlockDev &B, const CavConst &C, const S *base, int face, int c1,
-                                             int c2, const double *t_wall, double &nu_h, double &nu_c) {
-  const int high = face & 1;
-  const int w = high ? B.nx + 1 : 0, s = high ? -1 : 1;
-  const long long W = node_index<S>(B, w, c1, c2);
-  const int J = B.oy + c1, K = B.oz + c2;
-  const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
-  const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
-  const double T1 = load_T<S>(base, B.fstride, W + s), T2 = load_T<S>(base, B.fstride, W + 2 * s);
-  const double flux = (3.0 * tw - 4.0 * T1 + T2) * (0.5 * C.ih[0]) * C.inv_dT;
-  if (high) nu_c += -flux; else nu_h += flux;
-}
 
 // Walls of one face node.  u = v = w = 0 and the isothermal T never change
 // between steps: they are written (into both buffer sets) only when `other`
@@ -396,29 +380,44 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
   }
 }
 
-template <class S>
-__device__ void finalize_cavity(const BcArgs &a, int cv, double *sh) {
+// One cavity's per-CTA partials reduced in a fixed order by a CTA of NT
+// threads (tid = its linear thread index; sh holds NT / 32 * 8 doubles), and
+// its state advanced.  Nusselt sums: per wall-kernel CTA (modes 0-2), or in
+// the step partials' slots 6 and 7 as sums of 3 T_w - 4 T_1 + T_2 (mode 4).
+template <class S, int NT>
+__device__ void finalize_cavity(const BcArgs &a, int cv, double *sh, int tid) {
   const CavConst &C = a.cc[cv];
   CavState &st = a.cs[cv];
-  const int tid = threadIdx.x;
   // residual sums and spectral max over this cavity's k_step CTAs, fixed order
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int q = C.tile_begin + tid; q < C.tile_end; q += kBcThreads) {
+  double nh = 0, nc = 0;
+#pragma unroll 4
+  for (int q = C.tile_begin + tid; q < C.tile_end; q += NT) {
     const double *pp = a.step_partials + (long long)q * kPartStride;
     for (int f = 0; f < 5; ++f) acc[f] += pp[f];
     acc[5] = fmax(acc[5], pp[5]);
+    if (a.mode == 4) {
+      nh += pp[6];
+      nc += pp[7];
+    }
   }
-  double nh = 0, nc = 0;
-  const int qb = a.mode == 2 ? C.nus_begin : C.bc_begin, qe = a.mode == 2 ? C.nus_end : C.bc_end;
-  for (int q = qb + tid; q < qe; q += kBcThreads) {
-    nh += a.bc_partials[2LL * q];
-    nc += a.bc_partials[2LL * q + 1];
+  if (a.mode != 4) {
+    for (int q = C.bc_begin + tid; q < C.bc_end; q += NT) {
+      nh += a.bc_partials[2LL * q];
+      nc += a.bc_partials[2LL * q + 1];
+    }
   }
   const int lane = tid & 31, wid = tid >> 5;
   for (int f = 0; f < 5; ++f) acc[f] = warp_sum(acc[f]);
   acc[5] = warp_max(acc[5]);
   nh = warp_sum(nh);
   nc = warp_sum(nc);
+  // centre pressure of the new state: the (at most 8) nodes loaded in parallel
+  __shared__ double shc[8];
+  if (a.mode != 1 && tid < C.ncentre) {
+    const BlockDev &B = a.blocks[C.centre_blk[tid]];
+    shc[tid] = load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[tid]);
+  }
   __syncthreads();
   if (lane == 0) {
     for (int f = 0; f < 6; ++f) sh[wid * 8 + f] = acc[f];
@@ -429,8 +428,12 @@ __device__ void finalize_cavity(const BcArgs &a, int cv, double *sh) {
   if (tid == 0) {
     double tot[8];
     for (int f = 0; f < 8; ++f) tot[f] = sh[f];
-    for (int q = 1; q < kBcThreads / 32; ++q)
+    for (int q = 1; q < NT / 32; ++q)
       for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], sh[q * 8 + f]) : tot[f] + sh[q * 8 + f];
+    if (a.mode == 4) {  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
+      tot[6] *= 0.5 * C.ih[0] * C.inv_dT;
+      tot[7] *= -0.5 * C.ih[0] * C.inv_dT;
+    }
     bool bad = !isfinite(tot[5]);
     if (a.mode != 1) {
       for (int f = 0; f < 5; ++f) {
@@ -441,10 +444,7 @@ __device__ void finalize_cavity(const BcArgs &a, int cv, double *sh) {
       st.step += 1;
       // centre pressure of the new state, lexicographic (k, j, i) order
       double csum = 0.0;
-      for (int m = 0; m < C.ncentre; ++m) {
-        const BlockDev &B = a.blocks[C.centre_blk[m]];
-        csum += load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[m]);
-      }
+      for (int m = 0; m < C.ncentre; ++m) csum += shc[m];
       st.c = csum / (double)C.ncentre;
     }
     st.dt = C.cfl / tot[5];
@@ -478,11 +478,7 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
     const int e = (cta - F.cta_begin) * kBcThreads + tid;
     if (e < F.n1 * F.n2) {
       const BlockDev &B = a.blocks[F.block];
-      if (a.mode == 2)
-        nusselt_node<S>(B, a.cc[F.cav], (const S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
-                        nu_h, nu_c);
-      else
-        apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
+      apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
                       nu_h, nu_c, a.mode == 1 ? (S *)B.base[a.parity ^ 1] : nullptr);
     }
   }
@@ -500,14 +496,14 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
     // counter per cavity, so the cavities of a batch finalise in parallel)
     __threadfence();
     const CavConst &C = a.cc[cav];
-    const unsigned int nct = (unsigned int)(a.mode == 2 ? C.nus_end - C.nus_begin : C.bc_end - C.bc_begin);
+    const unsigned int nct = (unsigned int)(C.bc_end - C.bc_begin);
     const unsigned int prev = atomicAdd(a.counter + cav, 1u);
     am_last = (prev == nct - 1);
   }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  finalize_cavity<S>(a, cav, sh);
+  finalize_cavity<S, kBcThreads>(a, cav, sh, tid);
   if (tid == 0) a.counter[cav] = 0u;
 }
 

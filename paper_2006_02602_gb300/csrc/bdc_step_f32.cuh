@@ -30,7 +30,7 @@
 
 namespace bdc {
 
-constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 64, kF32R = 8, kF32P = 1;  // default shape: tile height, z chunk, ring depth, nodes per thread
+constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 32, kF32R = 8, kF32P = 2;  // default shape: tile height, z chunk, ring depth, nodes per thread
 constexpr int kF32BX = kF32TX + 8;  // x halo 4 on each side: the box starts on a 16-byte boundary
 constexpr int kF32NA = 7;           // p_hi, p_lo, u, v, w, T_hi, T_lo
 __host__ __device__ constexpr int f32_box_y(int TY) { return TY + 4; }  // y halo 2 (pressure star)
@@ -44,7 +44,7 @@ struct StepF32Args {
   const CavConst *cc;
   CavState *cs;               // dt and c read; flags bit 1 set on a timed-out wait
   const CUtensorMap *maps;    // [2 * block + parity], in global memory
-  double *partials;           // [cta][kPartStride]
+  double *partials;           // [cta][kPartStride]: 5 rate sums, spectral max, 2 Nusselt sums
   int parity;
 };
 
@@ -133,8 +133,14 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ float2 rmul(float2 a, float2 b) {
   return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
 }
-__device__ __forceinline__ float vrsqrt(float a) { return rsqrtf(a); }
-__device__ __forceinline__ float2 vrsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+// reciprocal square root as the one hardware approximation (relative error
+// about 2^-22); its arguments here are >= kappa u_ref^2 > 0, never subnormal
+__device__ __forceinline__ float vrsqrt(float a) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ float2 vrsqrt(float2 a) { return make_float2(vrsqrt(a.x), vrsqrt(a.y)); }
 
 template <class V> __device__ __forceinline__ V splat(float s);
 template <> __device__ __forceinline__ float splat<float>(float s) { return s; }
@@ -338,9 +344,9 @@ __device__ __forceinline__ float f32_spectral_exact(const F32K<float> &K, float 
   const float b2n = vmax(vfma(un, un, vfma(vn, vn, vmul(wn, wn))), K.b2min);
   const float f4n = vmul(4.f, b2n);
   const float qx = vfma(un, un, f4n), qy = vfma(vn, vn, f4n), qz = vfma(wn, wn, f4n);
-  const float sx = vfma(qx, rsqrtf(qx), vabs(un));
-  const float sy = vfma(qy, rsqrtf(qy), vabs(vn));
-  const float sz = vfma(qz, rsqrtf(qz), vabs(wn));
+  const float sx = vfma(qx, vrsqrt(qx), vabs(un));
+  const float sy = vfma(qy, vrsqrt(qy), vabs(vn));
+  const float sz = vfma(qz, vrsqrt(qz), vabs(wn));
   return vfma(0.5f, vfma(sx, K.ihx, vfma(sy, K.ihy, vmul(sz, K.ihz))), K.diffsr);
 }
 
@@ -349,24 +355,44 @@ __device__ __forceinline__ void f32_spectral_max(const F32K<float> &K, float bou
   if (vmul(bound, 1.00001f) > smax) smax = fmaxf(smax, f32_spectral_exact(K, un, vn, wn));
 }
 
-// CTA partials: FP32 per thread and per warp tree, FP64 across warps (fixed order)
+// CTA partials: rate sums FP32 per thread and per warp tree, FP64 across
+// warps (fixed order); Nusselt sums FP64 from the column sums on.  Slots:
+// 5 rate sums, spectral max, hot and cold sums of 3 T_w - 4 T_1 + T_2; the
+// per-cavity reduction (k_finalize) reads them in a fixed order.
 template <int NT>
 __device__ __forceinline__ void f32_partials(double *partials, int cta, int tid, float s0, float s1, float s2,
-                                             float s3, float s4, float smax) {
-  __shared__ double red[NT / 32][6];
+                                             float s3, float s4, float smax, double nuh, double nuc) {
+  __shared__ double red[NT / 32][8];
   const int lane = tid & 31, wid = tid >> 5;
   const float w0s = warp_sum_f(s0), w1s = warp_sum_f(s1), w2s = warp_sum_f(s2), w3s = warp_sum_f(s3);
   const float w4s = warp_sum_f(s4), wms = warp_max_f(smax);
+  const double wnh = warp_sum(nuh), wnc = warp_sum(nuc);
   if (lane == 0) {
     red[wid][0] = w0s; red[wid][1] = w1s; red[wid][2] = w2s; red[wid][3] = w3s; red[wid][4] = w4s;
-    red[wid][5] = wms;
+    red[wid][5] = wms; red[wid][6] = wnh; red[wid][7] = wnc;
   }
   __syncthreads();
-  if (tid < 6) {
+  if (tid < 8) {
     double acc = red[0][tid];
     for (int q = 1; q < NT / 32; ++q) acc = (tid == 5) ? fmax(acc, red[q][tid]) : acc + red[q][tid];
     partials[(long long)cta * kPartStride + tid] = acc;
   }
+}
+
+__device__ __forceinline__ double pair_value(float h, float l) { return (double)h + (double)l; }
+
+// (sh, sl) += (h, l): compensated FP32 sum (two-sum of the hi parts).  The
+// Nusselt sums use it for the columns next to an isothermal x wall: the sum
+// over a column's chunk of the new T (and of the stored wall T beside it)
+// keeps about 48 bits, and 3 T_w - 4 T_1 + T_2 is formed from those sums in
+// FP64 after the sweep, so no FP64 work runs per node.
+template <class V>
+__device__ __forceinline__ void acc_pair(V &sh, V &sl, V h, V l) {
+  const V s = vadd(sh, h);
+  const V bp = vsub(s, sh);
+  const V e = vadd(vsub(sh, vsub(s, bp)), vsub(h, bp));
+  sl = vadd(sl, vadd(e, l));
+  sh = s;
 }
 
 // Tile of one CTA and the walls that fall inside its boxes.
@@ -424,6 +450,15 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   const int li = threadIdx.x, lj = threadIdx.y, tid = lj * TX + li;
   const int i = T.i0 + li, j = T.j0 + lj;
   const bool active = (i <= B.nx) && (j <= B.ny);
+  // Nusselt sums of the new state: weights of this column in 3 T_w - 4 T_1 + T_2
+  const bool xw0 = B.wall[0], xw1 = B.wall[1];
+  const double wh = xw0 ? (i == 1 ? -4.0 : (i == 2 ? 1.0 : 0.0)) : 0.0;
+  const double wc = xw1 ? (i == B.nx ? -4.0 : (i == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
+  const bool nus = active && (wh != 0.0 || wc != 0.0);
+  const bool hot_next = xw0 && i == 1, cold_next = xw1 && i == B.nx;  // the column beside the wall
+  const int wofs = hot_next ? -1 : 1;
+  const bool nus_warp = __any_sync(0xffffffffu, nus);
+  float ch = 0.f, cl = 0.f, wsh = 0.f, wsl = 0.f;  // column sums of T and of the wall T beside it
   const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
 
   if (tid == 0) {
@@ -446,7 +481,8 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   const int col = (lj + 2) * BX + (li + 4);  // own column inside a slot
 
   const F32K<float> K = f32_consts<float>(C, a.cs[B.cav]);
-  const long long fs = B.fstride;
+  const long long fs = B.fstride, plane = B.plane;
+  const int nz = B.nz;
   // output pointer of this thread's node at plane k0 (advanced one plane per k)
   float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
 
@@ -487,6 +523,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
     for (; issued < min(R + 2, T.nplanes); ++issued) issue(issued);
   }
 
+#pragma unroll 2
   for (int k = k0; k <= k1 && !bad; ++k) {
     const int pk = k - k0 + 2;  // plane index of k
     if (!wait_plane(pk + 2)) bad = true;
@@ -501,13 +538,13 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
       Tq[2] = sk1[5 * AS + col];
       Tl[2] = sk1[6 * AS + col];
       if (T.wzh) {
-        if (k + 2 == B.nz + 1) {
+        if (k + 2 == nz + 1) {
           float hg, lg;
           wall_pressure(ph[3], pq[3], ph[2], pq[2], ph[4], pq[4], hg, lg);
-        } else if (k + 2 == B.nz + 2) {
+        } else if (k + 2 == nz + 2) {
           extrapolate_pair(ph[3], pq[3], ph[2], pq[2], ph[4], pq[4]);  // ghost = 2 p_w - p_nz
         }
-        if (k + 1 == B.nz + 1) wall_temperature(Tq[1], Tl[1], Tq[0], Tl[0], Tq[2], Tl[2]);
+        if (k + 1 == nz + 1) wall_temperature(Tq[1], Tl[1], Tq[0], Tl[0], Tq[2], Tl[2]);
       }
       if (T.fix) fix_plane_walls<NT, BY>(sk2, tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
       if (active) {
@@ -556,8 +593,12 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
         s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
         f32_spectral_max(K, f32_spectral_bound(K, o.u, o.v, o.w), o.u, o.v, o.w, smax);
+        if (nus_warp) {
+          acc_pair(ch, cl, o.th, o.tl);
+          acc_pair(wsh, wsl, Ts[col + wofs], Tls[col + wofs]);
+        }
       }
-      out += B.plane;
+      out += plane;
       ph[0] = ph[1]; ph[1] = ph[2]; ph[2] = ph[3]; ph[3] = ph[4];
       pq[0] = pq[1]; pq[1] = pq[2]; pq[2] = pq[3]; pq[3] = pq[4];
       uq[0] = uq[1]; uq[1] = uq[2]; vq[0] = vq[1]; vq[1] = vq[2];
@@ -579,7 +620,13 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
     }
     __syncthreads();
   }
-  f32_partials<NT>(a.partials, cta, tid, s0, s1, s2, s3, s4, smax);
+  double nuh = 0.0, nuc = 0.0;
+  if (nus) {
+    const double col_t = pair_value(ch, cl), wall_t = 3.0 * pair_value(wsh, wsl);
+    nuh = wh * col_t + (hot_next ? wall_t : 0.0);
+    nuc = wc * col_t + (cold_next ? wall_t : 0.0);
+  }
+  f32_partials<NT>(a.partials, cta, tid, s0, s1, s2, s3, s4, smax, nuh, nuc);
 }
 
 __device__ __forceinline__ float2 ld2(const float *s, int idx) { return *reinterpret_cast<const float2 *>(s + idx); }
@@ -609,6 +656,20 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
   const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
   const int i = T.i0 + 2 * li, j = T.j0 + lj;
   const bool act0 = (i <= B.nx) && (j <= B.ny), act1 = (i + 1 <= B.nx) && (j <= B.ny);
+  // Nusselt sums of the new state: weights of the two columns in 3 T_w - 4 T_1 + T_2
+  const bool xw0 = B.wall[0], xw1 = B.wall[1];
+  const double wh0 = (xw0 && act0) ? (i == 1 ? -4.0 : (i == 2 ? 1.0 : 0.0)) : 0.0;
+  const double wh1 = (xw0 && act1) ? (i + 1 == 2 ? 1.0 : 0.0) : 0.0;
+  const double wc0 = (xw1 && act0) ? (i == B.nx ? -4.0 : (i == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
+  const double wc1 = (xw1 && act1) ? (i + 1 == B.nx ? -4.0 : (i + 1 == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
+  const bool nus = wh0 != 0.0 || wh1 != 0.0 || wc0 != 0.0 || wc1 != 0.0;
+  // the column beside a wall: node i next to x = 0 or x = nx + 1, or node i + 1 next to x = nx + 1
+  const bool hot_next = xw0 && act0 && i == 1, cold_next0 = xw1 && act0 && i == B.nx;
+  const bool cold_next1 = xw1 && act1 && i + 1 == B.nx;
+  const int wofs = hot_next ? -1 : (cold_next0 ? 1 : 2);
+  const bool nus_warp = __any_sync(0xffffffffu, nus);
+  float2 ch = make_float2(0.f, 0.f), cl = ch;
+  float wsh = 0.f, wsl = 0.f;
   const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
 
   if (tid == 0) {
@@ -632,7 +693,8 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
 
   const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
   const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
-  const long long fs = B.fstride;
+  const long long fs = B.fstride, plane = B.plane;
+  const int nz = B.nz;
   // i is odd, so the pair starts on an 8-byte boundary of the row
   float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
 
@@ -675,9 +737,9 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
             wall_pressure(zm1h.y, zm1l.y, n.ph.y, n.pl.y, zm2h.y, zm2l.y, hg, lg);
           }
         }
-        if (T.wzh && k >= B.nz - 1) {
+        if (T.wzh && k >= nz - 1) {
           float hg, lg;
-          if (k == B.nz) {  // z = nz+1 wall and nz+2 ghost from the layers nz, nz-1
+          if (k == nz) {  // z = nz+1 wall and nz+2 ghost from the layers nz, nz-1
             wall_pressure(n.ph.x, n.pl.x, zm1h.x, zm1l.x, zp1h.x, zp1l.x, zp2h.x, zp2l.x);
             wall_pressure(n.ph.y, n.pl.y, zm1h.y, zm1l.y, zp1h.y, zp1l.y, zp2h.y, zp2l.y);
             wall_temperature(th.x, tl.x, tzmh.x, tzml.x, tzph.x, tzpl.x);
@@ -757,8 +819,12 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
         }
         s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
         s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
+        if (nus_warp) {
+          acc_pair(ch, cl, o.th, o.tl);
+          acc_pair(wsh, wsl, S0[5 * AS + col + wofs], S0[6 * AS + col + wofs]);
+        }
       }
-      out += B.plane;
+      out += plane;
     }
     bad = __syncthreads_or(bad);
     if (!bad && tid == 0 && issued < T.nplanes) {
@@ -774,8 +840,23 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
     }
     __syncthreads();
   }
+  double nuh = 0.0, nuc = 0.0;
+  if (nus) {
+    const double t0 = pair_value(ch.x, cl.x), t1 = act1 ? pair_value(ch.y, cl.y) : 0.0;
+    const double wall_t = 3.0 * pair_value(wsh, wsl);
+    nuh = wh0 * t0 + wh1 * t1 + (hot_next ? wall_t : 0.0);
+    nuc = wc0 * t0 + wc1 * t1 + (cold_next0 || cold_next1 ? wall_t : 0.0);
+  }
   f32_partials<NT>(a.partials, cta, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
-                   vadd(s4.x, s4.y), smax);
+                   vadd(s4.x, s4.y), smax, nuh, nuc);
+}
+
+// Per-cavity reduction after the FP32 step: one CTA per cavity reads the
+// cavity's step partials in a fixed order and advances its state.
+constexpr int kFinThreads = 512;
+__global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a) {
+  __shared__ double sh[kFinThreads / 32 * 8];
+  finalize_cavity<float, kFinThreads>(a, blockIdx.x, sh, threadIdx.x);
 }
 
 // Spectral-radius partials of the current state (no update), with the step

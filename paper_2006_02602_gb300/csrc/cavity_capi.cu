@@ -103,16 +103,15 @@ struct cavity {
   int nblocks = 0;
   std::vector<BlockDev> hb;
   std::vector<WallFace> hwall;
-  std::vector<WallFace> hnus;  // x-wall faces (Nusselt-only wall pass)
   std::vector<CutFace> hcut;
   long long xbuf_elems = 0;
-  int n_step = 0, n_bc = 0, n_cut = 0, n_nus = 0;
+  int n_step = 0, n_bc = 0, n_cut = 0;
   int part_cap = 0;  // step partials allocated (CTAs)
 
   BlockDev *d_blocks = nullptr;
   CavConst *d_cc = nullptr;
   CavState *d_cs = nullptr;
-  WallFace *d_wall = nullptr, *d_nus = nullptr;
+  WallFace *d_wall = nullptr;
   CutFace *d_cut = nullptr;
   CUtensorMap *d_maps = nullptr;
   double *d_step_part = nullptr, *d_bc_part = nullptr, *d_twall = nullptr, *d_stage = nullptr;
@@ -297,13 +296,12 @@ int build_layout(cavity *h) {
   h->twall.assign((size_t)wall_off, 0.0);
   assign_tiles(h);
   // wall faces (all, and the x walls alone), cut faces; contiguous per cavity
-  int bc = 0, cut = 0, nus = 0;
+  int bc = 0, cut = 0;
   long long xoff = 0;
   h->hwall.clear();
   h->hcut.clear();
-  h->hnus.clear();
   for (int c = 0; c < h->ncav; ++c) {
-    h->hcc[c].bc_begin = h->hcc[c].nus_begin = -1;
+    h->hcc[c].bc_begin = -1;
   }
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
@@ -317,12 +315,6 @@ int build_layout(cavity *h) {
         if (C.bc_begin < 0) C.bc_begin = bc;
         bc += ceil_div((long long)n1 * n2, kBcThreads);
         C.bc_end = bc;
-        if (a == 0) {
-          h->hnus.push_back(WallFace{id, f, n1, n2, nus, B.cav});
-          if (C.nus_begin < 0) C.nus_begin = nus;
-          nus += ceil_div((long long)n1 * n2, kBcThreads);
-          C.nus_end = nus;
-        }
       } else {
         h->hcut.push_back(CutFace{id, f, B.nbr[f], n1, n2, cut, xoff});
         cut += ceil_div((long long)n1 * n2, 256);
@@ -332,7 +324,6 @@ int build_layout(cavity *h) {
   }
   h->n_bc = bc;
   h->n_cut = cut;
-  h->n_nus = nus;
   h->xbuf_elems = xoff;
   return CAVITY_OK;
 }
@@ -413,7 +404,6 @@ int alloc_device(cavity *h) {
   CK(cudaMalloc(&h->d_cs, sizeof(CavState) * h->ncav));
   CK(cudaMemsetAsync(h->d_cs, 0, sizeof(CavState) * h->ncav, h->stream));
   CK(cudaMalloc(&h->d_wall, sizeof(WallFace) * std::max<size_t>(1, h->hwall.size())));
-  CK(cudaMalloc(&h->d_nus, sizeof(WallFace) * std::max<size_t>(1, h->hnus.size())));
   CK(cudaMalloc(&h->d_cut, sizeof(CutFace) * std::max<size_t>(1, h->hcut.size())));
   int rc = ensure_partials(h);
   if (rc != CAVITY_OK) return rc;
@@ -424,8 +414,6 @@ int alloc_device(cavity *h) {
   if (h->xbuf_elems > 0) CK(cudaMalloc(&h->d_xbuf, h->esize * (size_t)h->xbuf_elems));
   if (!h->hwall.empty())
     CK(cudaMemcpyAsync(h->d_wall, h->hwall.data(), sizeof(WallFace) * h->hwall.size(), cudaMemcpyHostToDevice, h->stream));
-  if (!h->hnus.empty())
-    CK(cudaMemcpyAsync(h->d_nus, h->hnus.data(), sizeof(WallFace) * h->hnus.size(), cudaMemcpyHostToDevice, h->stream));
   if (!h->hcut.empty())
     CK(cudaMemcpyAsync(h->d_cut, h->hcut.data(), sizeof(CutFace) * h->hcut.size(), cudaMemcpyHostToDevice, h->stream));
   if (h->f32) {
@@ -471,8 +459,8 @@ StepF32Args step_f32_args(cavity *h, int parity) {
 BcArgs bc_args(cavity *h, int parity, int mode) {
   BcArgs a;
   a.blocks = h->d_blocks;
-  a.faces = mode == 2 ? h->d_nus : h->d_wall;
-  a.nfaces = (int)(mode == 2 ? h->hnus.size() : h->hwall.size());
+  a.faces = h->d_wall;
+  a.nfaces = (int)h->hwall.size();
   a.cc = h->d_cc; a.cs = h->d_cs; a.ncav = h->ncav;
   a.step_partials = h->d_step_part; a.bc_partials = h->d_bc_part; a.counter = h->d_counter;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
@@ -513,10 +501,11 @@ void launch_spectral(cavity *h) {
 }
 
 // mode 0: after a step; mode 1: state refresh.  The FP32 step kernel applies
-// the walls itself, so after its steps only the Nusselt sums remain (mode 2).
+// the walls where it reads them and leaves the Nusselt sums in its partials,
+// so after its steps only the per-cavity reduction remains (k_finalize).
 void launch_bc_kernel(cavity *h, int parity, int mode) {
   if (h->f32) {
-    if (mode == 0) k_bc<float><<<h->n_nus, kBcThreads, 0, h->stream>>>(bc_args(h, parity, 2));
+    if (mode == 0) k_finalize<<<h->ncav, kFinThreads, 0, h->stream>>>(bc_args(h, parity, 4));
     else k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
   } else {
     k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
@@ -697,7 +686,7 @@ void release(cavity *h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   void *ptrs[] = {h->d_fields, h->d_blocks, h->d_cc, h->d_cs, h->d_wall, h->d_cut, h->d_step_part,
-                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps, h->d_nus};
+                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   AdjointStore &A = h->adj;
