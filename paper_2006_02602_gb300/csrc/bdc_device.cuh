@@ -198,6 +198,25 @@ __device__ __forceinline__ double spectral_f64(const CavConst &C, double u, doub
   return 0.5 * (sx * C.ih[0] + sy * C.ih[1] + sz * C.ih[2]) + C.diffsr;
 }
 
+// FP32 estimate of spectral_f64 (the same formula: relative error below
+// 1e-6).  A node whose estimate, raised by 1e-5, stays at or below a value
+// the exact FP64 maximum already reached cannot raise that maximum, so only
+// the few candidates are evaluated in FP64 (GB300's FP64 pipe is narrow) and
+// the maximum -- hence dt -- is exactly the FP64 one.
+__device__ __forceinline__ float spectral_est_f32(const CavConst &C, double u, double v, double w) {
+  const float uf = (float)u, vf = (float)v, wf = (float)w;
+  const float b2 = fmaxf(__fmaf_rn(uf, uf, __fmaf_rn(vf, vf, __fmul_rn(wf, wf))), (float)C.b2min);
+  const float f4 = __fmul_rn(4.f, b2);
+  const float qx = __fmaf_rn(uf, uf, f4), qy = __fmaf_rn(vf, vf, f4), qz = __fmaf_rn(wf, wf, f4);
+  float rx, ry, rz;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(qx));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(qy));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rz) : "f"(qz));
+  const float sx = __fmaf_rn(qx, rx, fabsf(uf)), sy = __fmaf_rn(qy, ry, fabsf(vf)), sz = __fmaf_rn(qz, rz, fabsf(wf));
+  return __fmaf_rn(0.5f, __fmaf_rn(sx, (float)C.ih[0], __fmaf_rn(sy, (float)C.ih[1], __fmul_rn(sz, (float)C.ih[2]))),
+                   (float)C.diffsr);
+}
+
 // ---------------------------------------------------------------------------
 // k_step, FP64: one thread per (i, j) column of a TX x TY tile, sweeping a
 // chunk of KC planes in k.  The z-neighbours live in register queues
@@ -208,9 +227,12 @@ struct StepArgs {
   int nblocks;
   const CavConst *cc;
   const CavState *cs;
-  double *partials;  // [cta][kPartStride]
+  double *partials;  // [tile][kPartStride]
   int parity;        // read base[parity], write base[parity ^ 1]
   int mode;          // 0 = step, 1 = spectral radius of the current state only
+  unsigned int *tile_counter;  // persistent CTAs fetch tiles from it (reset by the next k_bc);
+                               // null: one CTA per tile
+  int ntiles;
 };
 
 __device__ __forceinline__ int find_block(const BlockDev *blocks, int nblocks, int cta) {
@@ -222,10 +244,11 @@ __device__ __forceinline__ int find_block(const BlockDev *blocks, int nblocks, i
   return lo;
 }
 
+// wfloor: a warp-uniform FP32 value at or below an exact spectral value some
+// lane of the warp has already recorded (carried across the warp's tiles)
 template <int TX, int TY, int KC>
-__global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
+__device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float &wfloor) {
   constexpr int NT = TX * TY;
-  const int cta = blockIdx.x;
   const int b = find_block(a.blocks, a.nblocks, cta);
   const BlockDev &B = a.blocks[b];
   const CavConst &C = a.cc[B.cav];
@@ -290,7 +313,15 @@ __global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
         dst[o + 3 * fs] = wn;
         dst[o + 4 * fs] = Tn;
         s0 += r[0] * r[0]; s1 += r[1] * r[1]; s2 += r[2] * r[2]; s3 += r[3] * r[3]; s4 += r[4] * r[4];
-        smax = fmax(smax, spectral_f64(C, un, vn, wn));
+        float best = 0.f;
+        if (__fmul_rn(spectral_est_f32(C, un, vn, wn), 1.00001f) > wfloor) {
+          const double e = spectral_f64(C, un, vn, wn);
+          smax = fmax(smax, e);
+          best = __double2float_rd(e);
+        }
+        // share over the lanes sweeping this tile (all active lanes run the same k range):
+        // non-negative floats order like their bit patterns
+        wfloor = fmaxf(wfloor, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(best))));
       } else {
         smax = fmax(smax, spectral_f64(C, uq1, vq1, wq1));
       }
@@ -315,6 +346,29 @@ __global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
   }
 }
 
+// Persistent form: as many CTAs as fit on the GPU at once take tiles in
+// order from a counter, so the last round is short (one CTA per tile left a
+// partial wave of up to a third of the step on 152 SMs).  Partials stay
+// indexed by tile: the reductions do not depend on which CTA took a tile.
+template <int TX, int TY, int KC>
+__global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
+  float wfloor = 0.f;
+  if (!a.tile_counter) {
+    step_tile_f64<TX, TY, KC>(a, blockIdx.x, wfloor);
+    return;
+  }
+  __shared__ int s_tile;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_tile = (int)atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= a.ntiles) break;
+    step_tile_f64<TX, TY, KC>(a, tile, wfloor);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // k_bc: wall conditions + Nusselt partials; the last CTA finalises.
 
@@ -329,6 +383,7 @@ struct BcArgs {
   double *bc_partials;        // [cta][2]
   unsigned int *counter;
   const double *t_wall;       // hot walls then cold walls, per cavity at wall_off
+  unsigned int *tile_counter; // the persistent step kernel's tile counter: reset here
   int parity;                 // buffer set holding the new state
   int mode;                   // 0 after a step, 1 after init / set_fields,
                               // 3 walls only, no reductions,
@@ -469,6 +524,7 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
   __shared__ double sh[(kBcThreads / 32) * 8];
   __shared__ bool am_last;
   const int cta = blockIdx.x, tid = threadIdx.x;
+  if (cta == 0 && tid == 0 && a.tile_counter) *a.tile_counter = 0u;  // the step kernel has finished
   double nu_h = 0.0, nu_c = 0.0;
   int cav = 0;
   if (a.nfaces > 0) {

@@ -27,7 +27,7 @@ using namespace bdc;
 
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kKC = 16;  // k_step tile of the FP64 form
+constexpr int kTX = 32, kTY = 8, kKC = 8;  // k_step tile of the FP64 form
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -115,7 +115,8 @@ struct cavity {
   CutFace *d_cut = nullptr;
   CUtensorMap *d_maps = nullptr;
   double *d_step_part = nullptr, *d_bc_part = nullptr, *d_twall = nullptr, *d_stage = nullptr;
-  unsigned int *d_counter = nullptr;
+  unsigned int *d_counter = nullptr;  // [ncav] k_bc CTAs done per cavity, then the FP64 step's tile counter
+  int persist_ctas = 0;               // CTAs of the persistent FP64 step kernel that fit on the GPU
   void *d_fields = nullptr, *d_xbuf = nullptr;
   size_t field_bytes = 0;
   size_t stage_elems = 0;
@@ -408,8 +409,14 @@ int alloc_device(cavity *h) {
   int rc = ensure_partials(h);
   if (rc != CAVITY_OK) return rc;
   CK(cudaMalloc(&h->d_bc_part, sizeof(double) * 2 * std::max(1, h->n_bc)));
-  CK(cudaMalloc(&h->d_counter, sizeof(unsigned int) * h->ncav));
-  CK(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int) * h->ncav, h->stream));
+  CK(cudaMalloc(&h->d_counter, sizeof(unsigned int) * (h->ncav + 1)));
+  CK(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int) * (h->ncav + 1), h->stream));
+  {
+    int nsm = 0, per_sm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_f64<kTX, kTY, kKC>, kTX * kTY, 0));
+    h->persist_ctas = std::max(1, nsm * per_sm);
+  }
   CK(cudaMalloc(&h->d_twall, sizeof(double) * std::max<size_t>(1, h->twall.size())));
   if (h->xbuf_elems > 0) CK(cudaMalloc(&h->d_xbuf, h->esize * (size_t)h->xbuf_elems));
   if (!h->hwall.empty())
@@ -446,6 +453,7 @@ StepArgs step_args(cavity *h, int parity, int mode) {
   StepArgs a;
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.partials = h->d_step_part; a.parity = parity; a.mode = mode;
+  a.tile_counter = h->d_counter + h->ncav; a.ntiles = h->n_step;
   return a;
 }
 
@@ -463,6 +471,7 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.nfaces = (int)h->hwall.size();
   a.cc = h->d_cc; a.cs = h->d_cs; a.ncav = h->ncav;
   a.step_partials = h->d_step_part; a.bc_partials = h->d_bc_part; a.counter = h->d_counter;
+  a.tile_counter = h->d_counter + h->ncav;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
   return a;
 }
@@ -483,7 +492,8 @@ void launch_step_kernel(cavity *h, int parity) {
     BDC_F32_VARIANTS(BDC_LAUNCH)
 #undef BDC_LAUNCH
   } else {
-    k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(step_args(h, parity, 0));
+    k_step_f64<kTX, kTY, kKC><<<std::min(h->n_step, h->persist_ctas), dim3(kTX, kTY), 0, h->stream>>>(
+        step_args(h, parity, 0));
   }
 }
 
@@ -496,7 +506,7 @@ void launch_spectral(cavity *h) {
     BDC_F32_VARIANTS(BDC_SPEC)
 #undef BDC_SPEC
   } else {
-    k_step_f64<kTX, kTY, kKC><<<h->n_step, dim3(kTX, kTY), 0, h->stream>>>(sa);
+    k_step_f64<kTX, kTY, kKC><<<std::min(h->n_step, h->persist_ctas), dim3(kTX, kTY), 0, h->stream>>>(sa);
   }
 }
 

@@ -161,9 +161,9 @@ extern "C" CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *
       cudaMemcpyAsync(d_cc, &C, sizeof(C), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(d_cs, &S, sizeof(S), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return CAVITY_ERR_CUDA;
-  StepArgs a;
+  StepArgs a{};  // tile_counter null: one CTA per tile
   a.blocks = d_block; a.nblocks = 1; a.cc = d_cc; a.cs = d_cs;
-  a.partials = d_part; a.parity = 0; a.mode = 0;
+  a.partials = d_part; a.parity = 0; a.mode = 0; a.ntiles = (int)ntiles;
   k_step_f64<kTX, kTY, kKC><<<(int)ntiles, dim3(kTX, kTY), 0, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return CAVITY_ERR_CUDA;
   k_noalloc_reduce<<<1, 256, 0, st>>>(d_part, (int)ntiles, d_cc, out6);
