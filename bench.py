@@ -199,8 +199,8 @@ def roofline_for(precision, pts, step_ms, hbm):
     hbm_obj = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if hbm else None,
                "bytes_per_point": bpp, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if precision == "fp32":
-        return dict(kernel="k_step_f32 (TMA-staged fused residual + update + reductions)", traffic=None,
-                    kernel_ms=step_ms, **hbm_obj)
+        return dict(kernel="k_step_f32p (TMA-staged fused residual + update + partials; two nodes per thread, "
+                           "f32x2)", traffic=None, kernel_ms=step_ms, **hbm_obj)
     tf = FP64_FLOP_PER_POINT * pts / step_s / 1e12
     return {"kernel": "k_step_f64 (fused residual + update + reductions)", "bound": "alu", "achieved": tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
@@ -217,7 +217,8 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
     c = m.Cavity(*n, blocks=blocks, precision=prec, seed=cfg["seed"] + rank, noise_amp=cfg["noise"],
                  device=local, stream=stream.cuda_stream, Ra=cfg["Ra"], Pr=cfg["Pr"])
     nb = blocks[0] * blocks[1] * blocks[2]
-    launches_per_step = 2 + (2 if nb > 1 else 0)
+    # FP64: step, walls, finalise; FP32-mixed: step, finalise; + pack, unpack when split
+    launches_per_step = (3 if precision == "fp64" else 2) + (2 if nb > 1 else 0)
     both_buffers = pts * BYTES_PER_POINT[precision]  # the two buffer sets of the state
     flush = both_buffers < 1.2 * L2_BYTES
     scratch = torch.empty(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=f"cuda:{local}") if flush else None
@@ -333,6 +334,47 @@ def measure_batch(m, torch, steps, warmup, rank, world, local, stream):
             "dtype": "f32 (p as f32 hi/lo pair, f64 reductions)"}
 
 
+def measure_adjoint(m, torch, rank, world, local, stream):
+    """Configuration 5: gradient of the mean hot-wall Nusselt number over 500
+    FP32-mixed steps of a 128^3 cavity w.r.t. the 128x128 hot-wall temperature
+    field and Ra, checkpoints every 50 steps.  Wall time of the checkpointed
+    forward run and of the reverse sweep (segment recomputation + FP64
+    adjoint kernels), through the public API."""
+    cfg = workloads.CFG5
+    n = cfg["n"]
+    pts = n[0] * n[1] * n[2]
+    theta = workloads.wall_temperature(n[1], n[2], seed=cfg["theta_seed"], sigma=cfg["theta_sigma"])
+    c = m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=cfg["seed"] + rank, noise_amp=cfg["noise"], device=local,
+                 stream=stream.cuda_stream, Ra=cfg["Ra"], Pr=cfg["Pr"])
+    m.cavity_set_wall_temperature(c.h, 0, theta)
+    m.cavity_adjoint_forward(c.h, 20, 10)  # warm-up (allocations, graphs)
+    m.cavity_adjoint_backward(c.h, n[1], n[2])
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        J = m.cavity_adjoint_forward(c.h, cfg["steps"], cfg["ckpt"])
+        t1 = time.perf_counter()
+        g, gra = m.cavity_adjoint_backward(c.h, n[1], n[2])
+        t2 = time.perf_counter()
+    rc = c.sync()
+    c.close()
+    fwd, bwd = t1 - t0, t2 - t1
+    if world > 1:
+        t = torch.tensor([fwd, bwd], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        fwd, bwd = float(t[0]), float(t[1])
+    steps = cfg["steps"]
+    return {"metric": "gradient point-steps/s (forward + reverse sweep)", "value": pts * steps * world / (fwd + bwd),
+            "unit": "point-steps/s", "steps": steps, "checkpoint_every": cfg["ckpt"],
+            "forward_ms_per_step": 1e3 * fwd / steps, "backward_ms_per_step": 1e3 * bwd / steps,
+            "J": J, "dJ_dRa": gra, "grad_wall_norm": float(np.linalg.norm(g)), "clocks": clk.summary(), "status": rc,
+            "config": {"workload": f"adjoint of {steps} steps, cavity {n[0]}^3 Ra {cfg['Ra']:g}, FP32-mixed forward, "
+                                   f"FP64 reverse sweep, checkpoints every {cfg['ckpt']}"},
+            "dtype": "f32 forward (p, T as f32 pairs), f64 adjoint"}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -371,6 +413,7 @@ def run_ours(args):
             variants[name] = v
         variants["batch64_fp32"] = measure_batch(m, torch, min(args.steps, 500), args.warmup, rank, world, local,
                                                  stream)
+        variants["adjoint_cfg5"] = measure_adjoint(m, torch, rank, world, local, stream)
         line["variants"] = variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, blocks)

@@ -370,7 +370,8 @@ __global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// k_bc: wall conditions + Nusselt partials; the last CTA finalises.
+// k_bc (wall conditions + Nusselt partials) and k_finalize (reduction of the
+// partials, state advance).
 
 struct BcArgs {
   const BlockDev *blocks;
@@ -380,14 +381,14 @@ struct BcArgs {
   CavState *cs;
   int ncav;
   const double *step_partials;
-  double *bc_partials;        // [cta][2]
-  unsigned int *counter;
+  double *bc_partials;        // [k_bc cta][2]
+  unsigned int *counter;      // per cavity: k_finalize slices done
   const double *t_wall;       // hot walls then cold walls, per cavity at wall_off
   unsigned int *tile_counter; // the persistent step kernel's tile counter: reset here
   int parity;                 // buffer set holding the new state
   int mode;                   // 0 after a step, 1 after init / set_fields,
-                              // 3 walls only, no reductions,
-                              // 4 finalise only (after an FP32 step): Nusselt
+                              // 3 walls only (k_bc), no reductions,
+                              // 4 after an FP32 step (k_finalize only): Nusselt
                               //   sums in the step partials
 };
 
@@ -435,79 +436,104 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
   }
 }
 
-// One cavity's per-CTA partials reduced in a fixed order by a CTA of NT
-// threads (tid = its linear thread index; sh holds NT / 32 * 8 doubles), and
-// its state advanced.  Nusselt sums: per wall-kernel CTA (modes 0-2), or in
-// the step partials' slots 6 and 7 as sums of 3 T_w - 4 T_1 + T_2 (mode 4).
-template <class S, int NT>
-__device__ void finalize_cavity(const BcArgs &a, int cv, double *sh, int tid) {
-  const CavConst &C = a.cc[cv];
-  CavState &st = a.cs[cv];
-  // residual sums and spectral max over this cavity's k_step CTAs, fixed order
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  double nh = 0, nc = 0;
-#pragma unroll 4
-  for (int q = C.tile_begin + tid; q < C.tile_end; q += NT) {
-    const double *pp = a.step_partials + (long long)q * kPartStride;
+// ---------------------------------------------------------------------------
+// Finalise: one cavity's per-CTA partials reduced in a fixed order and its
+// state advanced (residual RMS, spectral maximum -> next dt, Nusselt numbers,
+// time, step count, centre pressure).  GB300's FP64 pipe does about two
+// lanes per clock per SM, so the FP64 sums are spread over kFinSlices CTAs
+// per cavity (contiguous slices of the partials), and the last of them
+// combines the slices in order.  Nusselt sums: the wall kernel's partials
+// (modes 0, 1) or the step partials' slots 6 and 7, sums of
+// 3 T_w - 4 T_1 + T_2 (mode 4, FP32 step).
+constexpr int kFinThreads = 128, kFinSlices = 16;
+
+template <int NT>
+__device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long long b0, long long b1,
+                             double tot[8], double *sh, int tid) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long q = q0 + tid; q < q1; q += NT) {
+    const double *pp = a.step_partials + q * kPartStride;
     for (int f = 0; f < 5; ++f) acc[f] += pp[f];
     acc[5] = fmax(acc[5], pp[5]);
     if (a.mode == 4) {
-      nh += pp[6];
-      nc += pp[7];
+      acc[6] += pp[6];
+      acc[7] += pp[7];
     }
   }
-  if (a.mode != 4) {
-    for (int q = C.bc_begin + tid; q < C.bc_end; q += NT) {
-      nh += a.bc_partials[2LL * q];
-      nc += a.bc_partials[2LL * q + 1];
-    }
+  for (long long q = b0 + tid; q < b1; q += NT) {
+    acc[6] += a.bc_partials[2 * q];
+    acc[7] += a.bc_partials[2 * q + 1];
   }
   const int lane = tid & 31, wid = tid >> 5;
-  for (int f = 0; f < 5; ++f) acc[f] = warp_sum(acc[f]);
-  acc[5] = warp_max(acc[5]);
-  nh = warp_sum(nh);
-  nc = warp_sum(nc);
-  // centre pressure of the new state: the (at most 8) nodes loaded in parallel
+  for (int f = 0; f < 8; ++f) acc[f] = (f == 5) ? warp_max(acc[f]) : warp_sum(acc[f]);
+  if (lane == 0)
+    for (int f = 0; f < 8; ++f) sh[wid * 8 + f] = acc[f];
+  __syncthreads();
+  if (tid == 0) {
+    for (int f = 0; f < 8; ++f) tot[f] = sh[f];
+    for (int q = 1; q < NT / 32; ++q)
+      for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], sh[q * 8 + f]) : tot[f] + sh[q * 8 + f];
+  }
+}
+
+// mid: [ncav][kFinSlices][8] slice totals; a.counter: per cavity, zero between launches
+template <class S>
+__global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid) {
+  __shared__ double sh[kFinThreads / 32 * 8];
+  __shared__ double shm[kFinSlices * 8];
   __shared__ double shc[8];
+  __shared__ bool am_last;
+  static_assert(kFinSlices * 8 <= kFinThreads, "one slice total per thread");
+  const int cav = blockIdx.x / kFinSlices, g = blockIdx.x % kFinSlices, tid = threadIdx.x;
+  const CavConst &C = a.cc[cav];
+  const long long nt = C.tile_end - C.tile_begin, nb = a.mode == 4 ? 0 : C.bc_end - C.bc_begin;
+  double tot[8];
+  reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / kFinSlices, C.tile_begin + nt * (g + 1) / kFinSlices,
+                            C.bc_begin + nb * g / kFinSlices, C.bc_begin + nb * (g + 1) / kFinSlices, tot, sh, tid);
+  double *my = mid + ((long long)cav * kFinSlices + g) * 8;
+  if (tid == 0) {
+    for (int f = 0; f < 8; ++f) my[f] = tot[f];
+    __threadfence();
+    am_last = atomicAdd(a.counter + cav, 1u) == (unsigned int)kFinSlices - 1u;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // the slice totals and the centre pressure of the new state (at most 8
+  // nodes) loaded in parallel, then folded in order by one thread
+  if (tid < kFinSlices * 8) shm[tid] = mid[(long long)cav * kFinSlices * 8 + tid];
   if (a.mode != 1 && tid < C.ncentre) {
     const BlockDev &B = a.blocks[C.centre_blk[tid]];
     shc[tid] = load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[tid]);
   }
   __syncthreads();
-  if (lane == 0) {
-    for (int f = 0; f < 6; ++f) sh[wid * 8 + f] = acc[f];
-    sh[wid * 8 + 6] = nh;
-    sh[wid * 8 + 7] = nc;
+  if (tid != 0) return;
+  for (int f = 0; f < 8; ++f) tot[f] = shm[f];
+  for (int q = 1; q < kFinSlices; ++q)
+    for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], shm[q * 8 + f]) : tot[f] + shm[q * 8 + f];
+  if (a.mode == 4) {  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
+    tot[6] *= 0.5 * C.ih[0] * C.inv_dT;
+    tot[7] *= -0.5 * C.ih[0] * C.inv_dT;
   }
-  __syncthreads();
-  if (tid == 0) {
-    double tot[8];
-    for (int f = 0; f < 8; ++f) tot[f] = sh[f];
-    for (int q = 1; q < NT / 32; ++q)
-      for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], sh[q * 8 + f]) : tot[f] + sh[q * 8 + f];
-    if (a.mode == 4) {  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
-      tot[6] *= 0.5 * C.ih[0] * C.inv_dT;
-      tot[7] *= -0.5 * C.ih[0] * C.inv_dT;
+  CavState &st = a.cs[cav];
+  bool bad = !isfinite(tot[5]);
+  if (a.mode != 1) {
+    for (int f = 0; f < 5; ++f) {
+      st.res[f] = sqrt(tot[f] * C.inv_nint);
+      bad = bad || !isfinite(tot[f]);
     }
-    bool bad = !isfinite(tot[5]);
-    if (a.mode != 1) {
-      for (int f = 0; f < 5; ++f) {
-        st.res[f] = sqrt(tot[f] * C.inv_nint);
-        bad = bad || !isfinite(tot[f]);
-      }
-      st.t += st.dt;
-      st.step += 1;
-      // centre pressure of the new state, lexicographic (k, j, i) order
-      double csum = 0.0;
-      for (int m = 0; m < C.ncentre; ++m) csum += shc[m];
-      st.c = csum / (double)C.ncentre;
-    }
-    st.dt = C.cfl / tot[5];
-    st.nu_hot = tot[6] * C.inv_nwall;
-    st.nu_cold = tot[7] * C.inv_nwall;
-    if (bad) st.flags |= 1;
+    st.t += st.dt;
+    st.step += 1;
+    // centre pressure of the new state, lexicographic (k, j, i) order
+    double csum = 0.0;
+    for (int m = 0; m < C.ncentre; ++m) csum += shc[m];
+    st.c = csum / (double)C.ncentre;
   }
-  __syncthreads();
+  st.dt = C.cfl / tot[5];
+  st.nu_hot = tot[6] * C.inv_nwall;
+  st.nu_cold = tot[7] * C.inv_nwall;
+  if (bad) st.flags |= 1;
+  a.counter[cav] = 0u;
 }
 
 __device__ __forceinline__ int find_face(const WallFace *faces, int nfaces, int cta) {
@@ -519,18 +545,17 @@ __device__ __forceinline__ int find_face(const WallFace *faces, int nfaces, int 
   return lo;
 }
 
+// k_bc: wall conditions of every wall face node and the Nusselt partials of
+// the x walls, one partial pair per CTA (reduced by k_finalize).
 template <class S>
 __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
-  __shared__ double sh[(kBcThreads / 32) * 8];
-  __shared__ bool am_last;
+  __shared__ double sh[(kBcThreads / 32) * 2];
   const int cta = blockIdx.x, tid = threadIdx.x;
   if (cta == 0 && tid == 0 && a.tile_counter) *a.tile_counter = 0u;  // the step kernel has finished
   double nu_h = 0.0, nu_c = 0.0;
-  int cav = 0;
   if (a.nfaces > 0) {
     const int fi = find_face(a.faces, a.nfaces, cta);
     const WallFace &F = a.faces[fi];
-    cav = F.cav;
     const int e = (cta - F.cta_begin) * kBcThreads + tid;
     if (e < F.n1 * F.n2) {
       const BlockDev &B = a.blocks[F.block];
@@ -548,19 +573,7 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
     for (int q = 0; q < kBcThreads / 32; ++q) { h += sh[2 * q]; c += sh[2 * q + 1]; }
     a.bc_partials[2LL * cta] = h;
     a.bc_partials[2LL * cta + 1] = c;
-    // the last of this cavity's CTAs to finish reduces the cavity (one
-    // counter per cavity, so the cavities of a batch finalise in parallel)
-    __threadfence();
-    const CavConst &C = a.cc[cav];
-    const unsigned int nct = (unsigned int)(C.bc_end - C.bc_begin);
-    const unsigned int prev = atomicAdd(a.counter + cav, 1u);
-    am_last = (prev == nct - 1);
   }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  finalize_cavity<S, kBcThreads>(a, cav, sh, tid);
-  if (tid == 0) a.counter[cav] = 0u;
 }
 
 // ---------------------------------------------------------------------------

@@ -851,14 +851,6 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
                    vadd(s4.x, s4.y), smax, nuh, nuc);
 }
 
-// Per-cavity reduction after the FP32 step: one CTA per cavity reads the
-// cavity's step partials in a fixed order and advances its state.
-constexpr int kFinThreads = 512;
-__global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a) {
-  __shared__ double sh[kFinThreads / 32 * 8];
-  finalize_cavity<float, kFinThreads>(a, blockIdx.x, sh, threadIdx.x);
-}
-
 // Spectral-radius partials of the current state (no update), with the step
 // kernel's tiling so that the finalise reduction reads the same layout.
 template <class S, int TX, int TY, int KC>

@@ -115,6 +115,7 @@ struct cavity {
   CutFace *d_cut = nullptr;
   CUtensorMap *d_maps = nullptr;
   double *d_step_part = nullptr, *d_bc_part = nullptr, *d_twall = nullptr, *d_stage = nullptr;
+  double *d_fin = nullptr;  // k_finalize slice totals [ncav][kFinSlices][8]
   unsigned int *d_counter = nullptr;  // [ncav] k_bc CTAs done per cavity, then the FP64 step's tile counter
   int persist_ctas = 0;               // CTAs of the persistent FP64 step kernel that fit on the GPU
   void *d_fields = nullptr, *d_xbuf = nullptr;
@@ -409,6 +410,7 @@ int alloc_device(cavity *h) {
   int rc = ensure_partials(h);
   if (rc != CAVITY_OK) return rc;
   CK(cudaMalloc(&h->d_bc_part, sizeof(double) * 2 * std::max(1, h->n_bc)));
+  CK(cudaMalloc(&h->d_fin, sizeof(double) * 8 * kFinSlices * h->ncav));
   CK(cudaMalloc(&h->d_counter, sizeof(unsigned int) * (h->ncav + 1)));
   CK(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int) * (h->ncav + 1), h->stream));
   {
@@ -510,15 +512,23 @@ void launch_spectral(cavity *h) {
   }
 }
 
-// mode 0: after a step; mode 1: state refresh.  The FP32 step kernel applies
-// the walls where it reads them and leaves the Nusselt sums in its partials,
-// so after its steps only the per-cavity reduction remains (k_finalize).
+// mode 0: after a step; mode 1: state refresh; 3: walls only.  The walls
+// kernel (k_bc) writes the walls and the Nusselt partials, k_finalize reduces
+// the partials and advances the state.  The FP32 step kernel applies the
+// walls where it reads them and leaves the Nusselt sums in its own partials,
+// so after its steps only k_finalize runs.
 void launch_bc_kernel(cavity *h, int parity, int mode) {
+  const int nfin = h->ncav * kFinSlices;
   if (h->f32) {
-    if (mode == 0) k_finalize<<<h->ncav, kFinThreads, 0, h->stream>>>(bc_args(h, parity, 4));
-    else k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
+    if (mode == 0) {
+      k_finalize<float><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity, 4), h->d_fin);
+      return;
+    }
+    k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
+    if (mode != 3) k_finalize<float><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity, mode), h->d_fin);
   } else {
     k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
+    if (mode != 3) k_finalize<double><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity, mode), h->d_fin);
   }
 }
 
@@ -696,7 +706,7 @@ void release(cavity *h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   void *ptrs[] = {h->d_fields, h->d_blocks, h->d_cc, h->d_cs, h->d_wall, h->d_cut, h->d_step_part,
-                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps};
+                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps, h->d_fin};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   AdjointStore &A = h->adj;

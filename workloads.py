@@ -24,6 +24,12 @@ CFG2 = dict(name="cavity128_ra1e5", n=(128, 128, 128), Ra=1e5, Pr=0.71, noise=1e
 CFG3 = dict(name="cavity256_ra1e6_fp32", n=(256, 256, 256), Ra=1e6, Pr=0.71, noise=1e-4, seed=0, steps=5000)
 
 
+# configuration 5: the discrete adjoint (gradient of the mean hot-wall Nusselt
+# number w.r.t. the hot-wall temperature field and Ra), FP32-mixed forward
+CFG5 = dict(name="adjoint128_fp32", n=(128, 128, 128), Ra=1e5, Pr=0.71, noise=1e-3, seed=0, steps=500, ckpt=50,
+            theta_seed=11, theta_sigma=0.01)
+
+
 # configuration 4: a batch of independent cavities advanced together
 CFG4 = dict(name="batch64_fp32", ncav=64, nmin=24, nmax=96, ra_log10=(3.0, 6.0), Pr=0.71, noise=1e-3, steps=1000)
 
