@@ -45,6 +45,12 @@ FP64_FLOP_PER_POINT = 212
 # stored array read once and written once (FP64: 5 x 8 B; FP32-mixed: 7 x 4 B,
 # u, v, w and the hi/lo pairs of p and T)
 BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the same workload (profiles/k_step_f64_cavity128_2x2x2.md,
+# profiles/k_step_f32p_cavity256.md); None where no capture of the current
+# kernel exists
+TRAFFIC = {("fp64", "cfg2", (2, 2, 2)): 112.886016e6 + 54.552832e6,
+           ("fp32", "cfg3", (1, 1, 1)): 550.061824e6 + 435.558656e6}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129e6
@@ -192,7 +198,7 @@ def run_reference(args):
     return 0
 
 
-def roofline_for(precision, pts, step_ms, hbm):
+def roofline_for(precision, pts, step_ms, hbm, traffic=None):
     step_s = step_ms / 1e3
     bpp = BYTES_PER_POINT[precision]
     gbs = bpp * pts / step_s / 1e9
@@ -200,10 +206,10 @@ def roofline_for(precision, pts, step_ms, hbm):
                "bytes_per_point": bpp, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if precision == "fp32":
         return dict(kernel="k_step_f32p (TMA-staged fused residual + update + partials; two nodes per thread, "
-                           "f32x2)", traffic=None, kernel_ms=step_ms, **hbm_obj)
+                           "f32x2)", traffic=traffic, kernel_ms=step_ms, **hbm_obj)
     tf = FP64_FLOP_PER_POINT * pts / step_s / 1e12
     return {"kernel": "k_step_f64 (fused residual + update + reductions)", "bound": "alu", "achieved": tf,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
             "peak_source": "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure measured)",
             "kernel_ms": step_ms, "flop_per_point": FP64_FLOP_PER_POINT, "hbm_view": hbm_obj}
 
@@ -263,7 +269,8 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
            "gpu_launches": launches_per_step * steps, "clocks": clk.summary(), "status": rc,
            "l2": ("L2 flushed (2 x L2 buffer written) before every timed step: the state fits in L2" if flush else
                   f"no flush: the two state buffers ({both_buffers / 1e6:.0f} MB) exceed the 129 MB L2"),
-           "roofline": roofline_for(precision, pts, kms[0], measured_peaks().get("hbm_gbs"))}
+           "roofline": roofline_for(precision, pts, kms[0], measured_peaks().get("hbm_gbs"),
+                                    TRAFFIC.get((precision, workload, tuple(blocks))))}
     if e2e:
         # end to end through the public API with host buffers: initial state
         # from host, every step followed by the residual + Nusselt read, final
