@@ -85,6 +85,7 @@ def lib():
             L.orc_spectral_max.argtypes = [P, B, _dp]
             L.orc_spectral_max.restype = ctypes.c_double
             L.orc_update.argtypes = [B, _dp, _dp, ctypes.c_double, _dp]
+            L.orc_update_local.argtypes = [ctypes.POINTER(_Params), B, _dp, _dp, _dp]
             L.orc_shift_pressure.argtypes = [B, _dp, ctypes.c_double]
             L.orc_bc.argtypes = [B, _dp, _dp, _dp]
             L.orc_nusselt_sums.argtypes = [P, B, _dp, _dp, _dp]
@@ -174,8 +175,9 @@ class OracleCavity:
     """One cavity, optionally split into px*py*pz blocks exchanging ghost faces."""
 
     def __init__(self, nx, ny, nz, params: dict | None = None, blocks=(1, 1, 1), seed: int = 0,
-                 noise: float = 0.0, t_hot_wall=None, t_cold_wall=None):
+                 noise: float = 0.0, t_hot_wall=None, t_cold_wall=None, local_dt: bool = False):
         self.L = lib()
+        self.local_dt = bool(local_dt)  # local time stepping: each node at dt_n = cfl / S_n
         self.p = default_params(**(params or {}))
         self.cp = _cparams(self.p)
         self.gn = (int(nx), int(ny), int(nz))
@@ -295,7 +297,10 @@ class OracleCavity:
             tot = np.zeros(NF)
             for blk in self.blocks:                                             # a3
                 s = np.zeros(NF)
-                self.L.orc_update(ctypes.byref(blk.c), _ptr(blk.q), _ptr(blk.dq), self.dt, _ptr(s))
+                if self.local_dt:  # each node at its own stable step (pseudo time)
+                    self.L.orc_update_local(cp, ctypes.byref(blk.c), _ptr(blk.q), _ptr(blk.dq), _ptr(s))
+                else:
+                    self.L.orc_update(ctypes.byref(blk.c), _ptr(blk.q), _ptr(blk.dq), self.dt, _ptr(s))
                 tot += s
             self.residual = np.sqrt(tot / self.nint)
             c = self.centre_value()                                             # a5

@@ -211,34 +211,42 @@ void orc_rates(const orc_params *P, const orc_block *b, const double *q, double 
       }
 }
 
+/* Spectral-radius bound of the explicit step at node (i, j, k): the sum over
+ * axes of the acoustic wave speeds lambda_d / h_d plus the diffusive term
+ * 2 max(nu, alpha) sum 1/h_d^2 (Section 2, the stable dt). */
+static double node_spectral(const orc_params *P, const orc_block *b, const double *q, const double h[3], int i, int j,
+                            int k) {
+  const double nu = P->Pr, alpha = 1.0;
+  const double beta2_floor = P->kappa * P->u_ref * P->u_ref;
+  const double dmax = nu > alpha ? nu : alpha;
+  const double diff = 2.0 * dmax * (1.0 / (h[0] * h[0]) + 1.0 / (h[1] * h[1]) + 1.0 / (h[2] * h[2]));
+  double V[3];
+  V[0] = q[at(b, FU, i, j, k)];
+  V[1] = q[at(b, FV, i, j, k)];
+  V[2] = q[at(b, FW, i, j, k)];
+  double beta2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+  if (beta2 < beta2_floor) beta2 = beta2_floor;
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double lambda = 0.5 * (fabs(V[d]) + sqrt(V[d] * V[d] + 4.0 * beta2));
+    s += lambda / h[d];
+  }
+  return s + diff;
+}
+
 /* Largest spectral-radius bound over the block interior (the denominator of
  * the stable explicit dt); max is exact, so the result does not depend on
  * the loop order. */
 double orc_spectral_max(const orc_params *P, const orc_block *b, const double *q) {
   double h[3];
   spacings(b, h);
-  const double nu = P->Pr, alpha = 1.0;
-  const double beta2_floor = P->kappa * P->u_ref * P->u_ref;
-  const double dmax = nu > alpha ? nu : alpha;
-  const double diff = 2.0 * dmax * (1.0 / (h[0] * h[0]) + 1.0 / (h[1] * h[1]) + 1.0 / (h[2] * h[2]));
   double smax = 0.0;
   const int nx = b->nx, ny = b->ny, nz = b->nz;
 #pragma omp parallel for schedule(static) reduction(max : smax)
   for (int k = 1; k <= nz; ++k)
     for (int j = 1; j <= ny; ++j)
       for (int i = 1; i <= nx; ++i) {
-        double V[3];
-        V[0] = q[at(b, FU, i, j, k)];
-        V[1] = q[at(b, FV, i, j, k)];
-        V[2] = q[at(b, FW, i, j, k)];
-        double beta2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
-        if (beta2 < beta2_floor) beta2 = beta2_floor;
-        double s = 0.0;
-        for (int d = 0; d < 3; ++d) {
-          const double lambda = 0.5 * (fabs(V[d]) + sqrt(V[d] * V[d] + 4.0 * beta2));
-          s += lambda / h[d];
-        }
-        s += diff;
+        const double s = node_spectral(P, b, q, h, i, j, k);
         if (s > smax) smax = s;
       }
   return smax;
@@ -271,6 +279,46 @@ void orc_update(const orc_block *b, double *q, const double *dqdt, double dt, do
     sumsq[f] = s;
   }
   free(plane);
+}
+
+/* Local time stepping (the iteration in pseudo time of Section 3.1, each node
+ * at its own stable step): q <- q + dt_n dq/dt with dt_n = cfl / S_n, S_n the
+ * spectral bound of node n in the state before the update (all dt_n are
+ * taken before any node changes).  sumsq as in orc_update. */
+void orc_update_local(const orc_params *P, const orc_block *b, double *q, const double *dqdt, double *sumsq) {
+  const int nx = b->nx, ny = b->ny, nz = b->nz;
+  const size_t nint = (size_t)nx * ny * nz;
+  double h[3];
+  spacings(b, h);
+  double *dtl = (double *)malloc(nint * sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int k = 1; k <= nz; ++k)
+    for (int j = 1; j <= ny; ++j)
+      for (int i = 1; i <= nx; ++i) {
+        const size_t o = (size_t)(i - 1) + (size_t)nx * ((size_t)(j - 1) + (size_t)ny * (size_t)(k - 1));
+        dtl[o] = P->cfl / node_spectral(P, b, q, h, i, j, k);
+      }
+  double *plane = (double *)calloc((size_t)nz * NF, sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int k = 1; k <= nz; ++k)
+    for (int f = 0; f < NF; ++f) {
+      double s = 0.0;
+      for (int j = 1; j <= ny; ++j)
+        for (int i = 1; i <= nx; ++i) {
+          const size_t o = (size_t)(i - 1) + (size_t)nx * ((size_t)(j - 1) + (size_t)ny * (size_t)(k - 1));
+          const double r = dqdt[(size_t)f * nint + o];
+          q[at(b, f, i, j, k)] = q[at(b, f, i, j, k)] + dtl[o] * r;
+          s += r * r;
+        }
+      plane[(size_t)(k - 1) * NF + f] = s;
+    }
+  for (int f = 0; f < NF; ++f) {
+    double s = 0.0;
+    for (int k = 0; k < nz; ++k) s += plane[(size_t)k * NF + f];
+    sumsq[f] = s;
+  }
+  free(plane);
+  free(dtl);
 }
 
 /* Section 2: pressure rescaled at the centre -- subtract c from interior p. */
