@@ -214,9 +214,9 @@ CAVITY_API int cavity_autotune(cavity_t *h, int steps, double out[5]);
 /* Discrete adjoint, part 1: from the current state run nsteps steps and
  * return J = (1/nsteps) sum over steps 1..nsteps of the hot-wall Nusselt
  * number.  The state every ckpt steps is kept on the device (checkpoints)
- * for cavity_adjoint_backward.  Single-block, single-cavity handles only
- * (CAVITY_ERR_UNSUPPORTED otherwise).  The state afterwards is the state
- * after the nsteps steps. */
+ * for cavity_adjoint_backward.  Single-block, single-cavity handles with
+ * global time stepping only (CAVITY_ERR_UNSUPPORTED otherwise).  The state
+ * afterwards is the state after the nsteps steps. */
 CAVITY_API int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J);
 
 /* Discrete adjoint, part 2: gradient of the J of the last
@@ -229,6 +229,17 @@ CAVITY_API int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double 
  * (u_ref^2 = Ra Pr) in the derivative.  The state is restored to the one
  * after the forward run. */
 CAVITY_API int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *grad_ra);
+
+/* Time stepping.  CAVITY_DT_GLOBAL (default): every node advances by the one
+ * stable step dt = cfl / max_n S_n (time accurate, Section 2).  CAVITY_DT_LOCAL:
+ * node n advances by its own dt_n = cfl / S_n, S_n its spectral bound in the
+ * state before the step -- the iteration in pseudo time towards a steady
+ * state (Section 3.1); residuals, Nusselt numbers and the centre rescale are
+ * unchanged, and the time t keeps summing the global dt.  Both precisions and
+ * batch handles; CAVITY_ERR_INVALID_ARG for another mode. */
+#define CAVITY_DT_GLOBAL 0
+#define CAVITY_DT_LOCAL 1
+CAVITY_API int cavity_set_time_stepping(cavity_t *h, int mode);
 
 /* Measurement: run nsteps steps as plain launches (no graph replay) with CUDA
  * events around every kernel on the handle's stream.  ms[0..3] receive the

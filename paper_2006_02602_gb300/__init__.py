@@ -31,6 +31,9 @@ CAVITY_ERR_UNSUPPORTED = -6
 CAVITY_FP64 = 0
 CAVITY_FP32_MIXED = 1
 
+CAVITY_DT_GLOBAL = 0
+CAVITY_DT_LOCAL = 1
+
 CAVITY_FIELD_P, CAVITY_FIELD_U, CAVITY_FIELD_V, CAVITY_FIELD_W, CAVITY_FIELD_T = 1, 2, 4, 8, 16
 CAVITY_FIELD_ALL = 31
 
@@ -42,6 +45,7 @@ EXPORTED = (
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
     "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
     "cavity_batch_get_fields", "cavity_autotune", "cavity_adjoint_forward", "cavity_adjoint_backward",
+    "cavity_set_time_stepping",
 )
 
 
@@ -96,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_get_face_buffer": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
         "cavity_exchange": ([_H], ctypes.c_int),
         "cavity_time_kernels": ([_H, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_set_time_stepping": ([_H, ctypes.c_int], ctypes.c_int),
         "cavity_create_batch": ([ctypes.POINTER(cavity_desc), ctypes.POINTER(cavity_params), ctypes.c_int,
                                  ctypes.POINTER(_H)], ctypes.c_int),
         "cavity_batch_size": ([_H], ctypes.c_int),
@@ -242,6 +247,10 @@ def cavity_get_face_buffer(h, block: int, face: int, nb: int, nc: int) -> np.nda
 
 def cavity_exchange(h) -> None:
     _check(load_library().cavity_exchange(h), h)
+
+
+def cavity_set_time_stepping(h, mode: int) -> None:
+    _check(load_library().cavity_set_time_stepping(h, int(mode)), h)
 
 
 def cavity_time_kernels(h, nsteps: int) -> np.ndarray:

@@ -233,6 +233,7 @@ struct StepArgs {
   unsigned int *tile_counter;  // persistent CTAs fetch tiles from it (reset by the next k_bc);
                                // null: one CTA per tile
   int ntiles;
+  int local_dt;                // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
 };
 
 __device__ __forceinline__ int find_block(const BlockDev *blocks, int nblocks, int cta) {
@@ -302,11 +303,12 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
 #undef BDC_LOAD7
         double r[5];
         rates_f64(C, n, r);
-        const double pn = (pq2 - cshift) + dt * r[0];
-        const double un = uq1 + dt * r[1];
-        const double vn = vq1 + dt * r[2];
-        const double wn = wq1 + dt * r[3];
-        const double Tn = Tq1 + dt * r[4];
+        const double dtn = a.local_dt ? C.cfl / spectral_f64(C, uq1, vq1, wq1) : dt;
+        const double pn = (pq2 - cshift) + dtn * r[0];
+        const double un = uq1 + dtn * r[1];
+        const double vn = vq1 + dtn * r[2];
+        const double wn = wq1 + dtn * r[3];
+        const double Tn = Tq1 + dtn * r[4];
         dst[o] = pn;
         dst[o + fs] = un;
         dst[o + 2 * fs] = vn;

@@ -46,6 +46,7 @@ struct StepF32Args {
   const CUtensorMap *maps;    // [2 * block + parity], in global memory
   double *partials;           // [cta][kPartStride]: 5 rate sums, spectral max, 2 Nusselt sums
   int parity;
+  int local_dt;               // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -250,7 +251,7 @@ __device__ __forceinline__ float warp_max_f(float v) {
 template <class V>
 struct F32K {
   V ihx, ihy, ihz, h2x, h2y, h2z, mh2x, mh2y, mh2z, nhx, nhy, nhz, ahx, ahy, ahz, c4h, gs, tinf, b2min, dt, mdt, mcs, gy,
-      gz, diffsr;
+      gz, diffsr, cfl;
 };
 
 template <class V>
@@ -269,6 +270,7 @@ __device__ __forceinline__ F32K<V> f32_consts(const CavConst &C, const CavState 
   K.dt = splat<V>(dt); K.mdt = splat<V>(-dt); K.mcs = splat<V>(-(float)S.c);
   K.gy = splat<V>(C.gaxis == 1 ? 1.f : 0.f); K.gz = splat<V>(C.gaxis == 2 ? 1.f : 0.f);
   K.diffsr = splat<V>((float)C.diffsr);
+  K.cfl = splat<V>((float)C.cfl);
   return K;
 }
 
@@ -289,10 +291,10 @@ struct F32Out {
   V rp, ru, rv, rw, rt;       // rates (rp with the sign flipped; only its square is summed)
 };
 
-// Rates of Eqs. 1-3 at the node(s) and the explicit update; p and T through
-// an error-free two-sum on their pairs.
+// Rates of Eqs. 1-3 at the node(s) and the explicit update with step dt
+// (mdt = -dt); p and T through an error-free two-sum on their pairs.
 template <class V>
-__device__ __forceinline__ void f32_update(const F32K<V> &K, const F32Nb<V> &n, F32Out<V> &o) {
+__device__ __forceinline__ void f32_update(const F32K<V> &K, const F32Nb<V> &n, V dt, V mdt, F32Out<V> &o) {
   const V m4 = splat<V>(-4.f), four = splat<V>(4.f);
   const V d4x = vfma(m4, vadd(n.pxp1, n.pxm1), vadd(n.pxp2, n.pxm2));
   const V d4y = vfma(m4, vadd(n.pyp1, n.pym1), vadd(n.pyp2, n.pym2));
@@ -323,11 +325,11 @@ __device__ __forceinline__ void f32_update(const F32K<V> &K, const F32Nb<V> &n, 
   o.ru = vfma(vsub(n.pxm1, n.pxp1), K.h2x, tru);
   o.rv = vfma(vsub(n.pym1, n.pyp1), K.h2y, vfma(K.gy, buoy, trv));
   o.rw = vfma(vsub(n.pzm1, n.pzp1), K.h2z, vfma(K.gz, buoy, trw));
-  o.u = vfma(K.dt, o.ru, n.u);
-  o.v = vfma(K.dt, o.rv, n.v);
-  o.w = vfma(K.dt, o.rw, n.w);
-  pair_add(n.ph, n.pl, vfma(K.mdt, o.rp, K.mcs), o.ph, o.pl);  // p - dt (-dp/dt) - pending centre shift
-  pair_add(n.th, n.tl, rmul(K.dt, o.rt), o.th, o.tl);
+  o.u = vfma(dt, o.ru, n.u);
+  o.v = vfma(dt, o.rv, n.v);
+  o.w = vfma(dt, o.rw, n.w);
+  pair_add(n.ph, n.pl, vfma(mdt, o.rp, K.mcs), o.ph, o.pl);  // p - dt (-dp/dt) - pending centre shift
+  pair_add(n.th, n.tl, rmul(dt, o.rt), o.th, o.tl);
 }
 
 // Spectral radius of the new state: lambda_d <= |V_d| + beta gives a cheap
@@ -582,7 +584,12 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
         n.tzp = pdiff(Tq[2], Tl[2], n.th, n.tl);
         n.tzm = pdiff(Tq[0], Tl[0], n.th, n.tl);
         F32Out<float> o;
-        f32_update(K, n, o);
+        float dtn = K.dt, mdtn = K.mdt;
+        if (a.local_dt) {  // this node's own stable step
+          dtn = __fdiv_rn(K.cfl, f32_spectral_exact(K, n.u, n.v, n.w));
+          mdtn = -dtn;
+        }
+        f32_update(K, n, dtn, mdtn, o);
         out[0] = o.ph;
         out[fs] = o.pl;
         out[2 * fs] = o.u;
@@ -795,7 +802,13 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
           n.tzm = pdiff(tzmh, tzml, th, tl);
         }
         F32Out<float2> o;
-        f32_update(K, n, o);
+        float2 dtn = K.dt, mdtn = K.mdt;
+        if (a.local_dt) {  // each node's own stable step
+          dtn = make_float2(__fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.x, n.v.x, n.w.x)),
+                            __fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.y, n.v.y, n.w.y)));
+          mdtn = make_float2(-dtn.x, -dtn.y);
+        }
+        f32_update(K, n, dtn, mdtn, o);
         const float2 bound = f32_spectral_bound(K, o.u, o.v, o.w);
         f32_spectral_max(K1, bound.x, o.u.x, o.v.x, o.w.x, smax);
         if (act1) {

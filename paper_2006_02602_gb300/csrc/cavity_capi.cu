@@ -100,6 +100,7 @@ struct cavity {
   int tx = kTX, ty = kTY, kc = kKC;
   int f32_r = 0;                  // ring depth of the FP32 step kernel
   int f32_p = 1;                  // nodes per thread along x of the FP32 step kernel
+  int local_dt = 0;               // CAVITY_DT_LOCAL: each node at its own stable step
   int nblocks = 0;
   std::vector<BlockDev> hb;
   std::vector<WallFace> hwall;
@@ -455,14 +456,14 @@ StepArgs step_args(cavity *h, int parity, int mode) {
   StepArgs a;
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.partials = h->d_step_part; a.parity = parity; a.mode = mode;
-  a.tile_counter = h->d_counter + h->ncav; a.ntiles = h->n_step;
+  a.tile_counter = h->d_counter + h->ncav; a.ntiles = h->n_step; a.local_dt = h->local_dt;
   return a;
 }
 
 StepF32Args step_f32_args(cavity *h, int parity) {
   StepF32Args a;
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
-  a.maps = h->d_maps; a.partials = h->d_step_part; a.parity = parity;
+  a.maps = h->d_maps; a.partials = h->d_step_part; a.parity = parity; a.local_dt = h->local_dt;
   return a;
 }
 
@@ -1096,6 +1097,7 @@ int cavity_autotune(cavity_t *h, int steps, double out[5]) {
 
 int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
   if (!h || nsteps < 1 || ckpt < 1) return CAVITY_ERR_INVALID_ARG;
+  if (h->local_dt) return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: global time stepping only");
   if (h->ncav != 1 || h->nblocks != 1) return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: single-block cavity only");
   DeviceGuard g(h->dev);
   AdjointStore &A = h->adj;
@@ -1247,6 +1249,14 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
   CK(cudaStreamSynchronize(h->stream));
   if (grad_ra) *grad_ra = ra;
   return rc;
+}
+
+int cavity_set_time_stepping(cavity_t *h, int mode) {
+  if (!h || (mode != CAVITY_DT_GLOBAL && mode != CAVITY_DT_LOCAL)) return CAVITY_ERR_INVALID_ARG;
+  DeviceGuard g(h->dev);
+  CK(cudaStreamSynchronize(h->stream));
+  h->local_dt = mode == CAVITY_DT_LOCAL;
+  return build_graphs(h);  // the kernels' arguments are part of the captured graphs
 }
 
 int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
