@@ -230,6 +230,16 @@ CAVITY_API int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double 
  * after the forward run. */
 CAVITY_API int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *grad_ra);
 
+/* Interior/shell split with overlap (Section 4.7): when on, each step first
+ * computes the nodes within two layers of a cut face, then exchanges the new
+ * ghost layers (pack + unpack) on a second stream while the remaining nodes
+ * are stepped, and applies the walls and the reductions after both.  Fields
+ * are bit-identical to the plain schedule; the residual sums are reduced in
+ * another order.  FP64 single-cavity handles (CAVITY_ERR_UNSUPPORTED
+ * otherwise); without cut faces there is nothing to overlap and the call
+ * changes nothing.  on = 0 returns to the plain schedule. */
+CAVITY_API int cavity_set_overlap(cavity_t *h, int on);
+
 /* Time stepping.  CAVITY_DT_GLOBAL (default): every node advances by the one
  * stable step dt = cfl / max_n S_n (time accurate, Section 2).  CAVITY_DT_LOCAL:
  * node n advances by its own dt_n = cfl / S_n, S_n its spectral bound in the

@@ -45,7 +45,7 @@ EXPORTED = (
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
     "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
     "cavity_batch_get_fields", "cavity_autotune", "cavity_adjoint_forward", "cavity_adjoint_backward",
-    "cavity_set_time_stepping",
+    "cavity_set_time_stepping", "cavity_set_overlap",
 )
 
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_exchange": ([_H], ctypes.c_int),
         "cavity_time_kernels": ([_H, ctypes.c_int, _dp], ctypes.c_int),
         "cavity_set_time_stepping": ([_H, ctypes.c_int], ctypes.c_int),
+        "cavity_set_overlap": ([_H, ctypes.c_int], ctypes.c_int),
         "cavity_create_batch": ([ctypes.POINTER(cavity_desc), ctypes.POINTER(cavity_params), ctypes.c_int,
                                  ctypes.POINTER(_H)], ctypes.c_int),
         "cavity_batch_size": ([_H], ctypes.c_int),
@@ -247,6 +248,10 @@ def cavity_get_face_buffer(h, block: int, face: int, nb: int, nc: int) -> np.nda
 
 def cavity_exchange(h) -> None:
     _check(load_library().cavity_exchange(h), h)
+
+
+def cavity_set_overlap(h, on: bool) -> None:
+    _check(load_library().cavity_set_overlap(h, int(bool(on))), h)
 
 
 def cavity_set_time_stepping(h, mode: int) -> None:

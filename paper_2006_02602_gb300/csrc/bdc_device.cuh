@@ -76,6 +76,12 @@ struct WallFace {     // one wall face of one block, processed by k_bc
   int cav;
 };
 
+struct ShellFace {    // the two layers next to one cut face, processed by k_shell_f64
+  int block, face;
+  int n1, n2;         // face interior extents (faster, slower face axis)
+  int cta_begin;
+};
+
 struct CutFace {      // one cut face of one block, processed by k_pack / k_unpack
   int src, face, dst;
   int nb, nc;         // face extents (faster, slower face axis)
@@ -198,6 +204,20 @@ __device__ __forceinline__ double spectral_f64(const CavConst &C, double u, doub
   return 0.5 * (sx * C.ih[0] + sy * C.ih[1] + sz * C.ih[2]) + C.diffsr;
 }
 
+// Rates and explicit update of one node: the new p, u, v, w, T in q (p with
+// the pending centre shift taken off), the rates in r.  One function for
+// k_step_f64 and k_shell_f64, so a node gives the same bits in either.
+__device__ __forceinline__ void update_node_f64(const CavConst &C, const NodeF64 &n, double dt, double cshift,
+                                                int local_dt, double q[5], double r[5]) {
+  rates_f64(C, n, r);
+  const double dtn = local_dt ? C.cfl / spectral_f64(C, n.u[0], n.v[0], n.w[0]) : dt;
+  q[0] = (n.p[0] - cshift) + dtn * r[0];
+  q[1] = n.u[0] + dtn * r[1];
+  q[2] = n.v[0] + dtn * r[2];
+  q[3] = n.w[0] + dtn * r[3];
+  q[4] = n.T[0] + dtn * r[4];
+}
+
 // FP32 estimate of spectral_f64 (the same formula: relative error below
 // 1e-6).  A node whose estimate, raised by 1e-5, stays at or below a value
 // the exact FP64 maximum already reached cannot raise that maximum, so only
@@ -234,7 +254,20 @@ struct StepArgs {
                                // null: one CTA per tile
   int ntiles;
   int local_dt;                // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
+  int skip_shell;              // 1: leave the nodes within two layers of a cut face to k_shell_f64
 };
+
+// whether local node (i, j, k) of B lies within two layers of one of B's cut
+// faces with index below `faces` (all six: faces = 6)
+__device__ __forceinline__ bool in_shell(const BlockDev &B, int i, int j, int k, int faces) {
+  const int x[3] = {i, j, k}, n[3] = {B.nx, B.ny, B.nz};
+  for (int f = 0; f < faces; ++f) {
+    if (B.wall[f]) continue;
+    const int a = f >> 1;
+    if ((f & 1) ? x[a] >= n[a] - 1 : x[a] <= 2) return true;
+  }
+  return false;
+}
 
 __device__ __forceinline__ int find_block(const BlockDev *blocks, int nblocks, int cta) {
   int lo = 0, hi = nblocks - 1;
@@ -286,7 +319,9 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
       NodeF64 n;
       const double pq4 = __ldg(P + o + 2 * pl);
       const double uq2 = __ldg(U + o + pl), vq2 = __ldg(V + o + pl), wq2 = __ldg(W + o + pl), Tq2 = __ldg(TT + o + pl);
-      if (a.mode == 0) {
+      if (a.mode == 0 && a.skip_shell && in_shell(B, i, j, k, 6)) {
+        // computed by k_shell_f64 (interior/shell split)
+      } else if (a.mode == 0) {
         n.p[0] = pq2; n.p[5] = pq1; n.p[6] = pq3; n.p[11] = pq0; n.p[12] = pq4;
         n.p[1] = __ldg(P + o - 1); n.p[2] = __ldg(P + o + 1);
         n.p[7] = __ldg(P + o - 2); n.p[8] = __ldg(P + o + 2);
@@ -301,19 +336,10 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
         BDC_LOAD7(n.w, W, wq0, wq1, wq2)
         BDC_LOAD7(n.T, TT, Tq0, Tq1, Tq2)
 #undef BDC_LOAD7
-        double r[5];
-        rates_f64(C, n, r);
-        const double dtn = a.local_dt ? C.cfl / spectral_f64(C, uq1, vq1, wq1) : dt;
-        const double pn = (pq2 - cshift) + dtn * r[0];
-        const double un = uq1 + dtn * r[1];
-        const double vn = vq1 + dtn * r[2];
-        const double wn = wq1 + dtn * r[3];
-        const double Tn = Tq1 + dtn * r[4];
-        dst[o] = pn;
-        dst[o + fs] = un;
-        dst[o + 2 * fs] = vn;
-        dst[o + 3 * fs] = wn;
-        dst[o + 4 * fs] = Tn;
+        double r[5], qn[5];
+        update_node_f64(C, n, dt, cshift, a.local_dt, qn, r);
+        const double un = qn[1], vn = qn[2], wn = qn[3];
+        for (int f = 0; f < 5; ++f) dst[o + f * fs] = qn[f];
         s0 += r[0] * r[0]; s1 += r[1] * r[1]; s2 += r[2] * r[2]; s3 += r[3] * r[3]; s4 += r[4] * r[4];
         float best = 0.f;
         if (__fmul_rn(spectral_est_f32(C, un, vn, wn), 1.00001f) > wfloor) {
@@ -372,6 +398,90 @@ __global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// k_shell_f64: the nodes within two layers of a cut face (the interior/shell
+// split of Section 4.7).  They are stepped first, so that the exchange of the
+// new ghost layers can run on a second stream while k_step_f64 (skip_shell)
+// steps the rest.  One thread per (layer, face position) of each cut face;
+// a node near an edge belongs to the first cut face (in face order) within
+// two layers of it.  Partials: one slot per CTA after the tiles' slots.
+
+struct ShellArgs {
+  const BlockDev *blocks;
+  const ShellFace *faces;
+  int nfaces;
+  const CavConst *cc;
+  const CavState *cs;
+  double *partials;       // slot part_off + cta
+  long long part_off;
+  int parity;
+  int local_dt;
+};
+
+constexpr int kShellThreads = 256;
+
+static __global__ void __launch_bounds__(kShellThreads) k_shell_f64(ShellArgs a) {
+  const int cta = blockIdx.x, tid = threadIdx.x;
+  int lo = 0, hi = a.nfaces - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.faces[mid].cta_begin <= cta) lo = mid; else hi = mid - 1;
+  }
+  const ShellFace &F = a.faces[lo];
+  const BlockDev &B = a.blocks[F.block];
+  const CavConst &C = a.cc[B.cav];
+  double s[5] = {0, 0, 0, 0, 0}, smax = 0.0;
+  const long long per_layer = (long long)F.n1 * F.n2;
+  const long long e = (long long)(cta - F.cta_begin) * kShellThreads + tid;
+  if (e < 2 * per_layer) {
+    const int d = (int)(e / per_layer) + 1;
+    const long long r2 = e % per_layer;
+    const int ax = F.face >> 1, hi_face = F.face & 1;
+    const int n[3] = {B.nx, B.ny, B.nz};
+    int x[3];
+    x[ax] = hi_face ? n[ax] + 1 - d : d;
+    x[ax == 0 ? 1 : 0] = (int)(r2 % F.n1) + 1;
+    x[ax == 2 ? 1 : 2] = (int)(r2 / F.n1) + 1;
+    if (!in_shell(B, x[0], x[1], x[2], F.face)) {  // not claimed by an earlier cut face
+      const double *src = (const double *)B.base[a.parity];
+      double *dst = (double *)B.base[a.parity ^ 1];
+      const long long fs = B.fstride, pt = B.pitch, pl = B.plane;
+      const long long o = node_index<double>(B, x[0], x[1], x[2]);
+      NodeF64 nd;
+      const long long po[13] = {0, -1, 1, -pt, pt, -pl, pl, -2, 2, -2 * pt, 2 * pt, -2 * pl, 2 * pl};
+      for (int q = 0; q < 13; ++q) nd.p[q] = __ldg(src + o + po[q]);
+      for (int q = 0; q < 7; ++q) {
+        nd.u[q] = __ldg(src + fs + o + po[q]);
+        nd.v[q] = __ldg(src + 2 * fs + o + po[q]);
+        nd.w[q] = __ldg(src + 3 * fs + o + po[q]);
+        nd.T[q] = __ldg(src + 4 * fs + o + po[q]);
+      }
+      const CavState &st = a.cs[B.cav];
+      double r[5], qn[5];
+      update_node_f64(C, nd, st.dt, st.c, a.local_dt, qn, r);
+      for (int f = 0; f < 5; ++f) {
+        dst[o + f * fs] = qn[f];
+        s[f] = r[f] * r[f];
+      }
+      smax = spectral_f64(C, qn[1], qn[2], qn[3]);
+    }
+  }
+  __shared__ double red[kShellThreads / 32][6];
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int f = 0; f < 5; ++f) s[f] = warp_sum(s[f]);
+  smax = warp_max(smax);
+  if (lane == 0) {
+    for (int f = 0; f < 5; ++f) red[wid][f] = s[f];
+    red[wid][5] = smax;
+  }
+  __syncthreads();
+  if (tid < 6) {
+    double acc = red[0][tid];
+    for (int q = 1; q < kShellThreads / 32; ++q) acc = (tid == 5) ? fmax(acc, red[q][tid]) : acc + red[q][tid];
+    a.partials[(a.part_off + cta) * kPartStride + tid] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // k_bc (wall conditions + Nusselt partials) and k_finalize (reduction of the
 // partials, state advance).
 
@@ -387,6 +497,7 @@ struct BcArgs {
   unsigned int *counter;      // per cavity: k_finalize slices done
   const double *t_wall;       // hot walls then cold walls, per cavity at wall_off
   unsigned int *tile_counter; // the persistent step kernel's tile counter: reset here
+  long long shell_begin, shell_end;  // k_shell_f64 partial slots of this step (single cavity; empty if equal)
   int parity;                 // buffer set holding the new state
   int mode;                   // 0 after a step, 1 after init / set_fields,
                               // 3 walls only (k_bc), no reductions,
@@ -451,7 +562,7 @@ constexpr int kFinThreads = 128, kFinSlices = 16;
 
 template <int NT>
 __device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long long b0, long long b1,
-                             double tot[8], double *sh, int tid) {
+                             long long s0, long long s1, double tot[8], double *sh, int tid) {
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (long long q = q0 + tid; q < q1; q += NT) {
     const double *pp = a.step_partials + q * kPartStride;
@@ -461,6 +572,11 @@ __device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long l
       acc[6] += pp[6];
       acc[7] += pp[7];
     }
+  }
+  for (long long q = s0 + tid; q < s1; q += NT) {  // shell-kernel partials
+    const double *pp = a.step_partials + q * kPartStride;
+    for (int f = 0; f < 5; ++f) acc[f] += pp[f];
+    acc[5] = fmax(acc[5], pp[5]);
   }
   for (long long q = b0 + tid; q < b1; q += NT) {
     acc[6] += a.bc_partials[2 * q];
@@ -489,9 +605,12 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   const int cav = blockIdx.x / kFinSlices, g = blockIdx.x % kFinSlices, tid = threadIdx.x;
   const CavConst &C = a.cc[cav];
   const long long nt = C.tile_end - C.tile_begin, nb = a.mode == 4 ? 0 : C.bc_end - C.bc_begin;
+  const long long ns = a.shell_end - a.shell_begin;
   double tot[8];
   reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / kFinSlices, C.tile_begin + nt * (g + 1) / kFinSlices,
-                            C.bc_begin + nb * g / kFinSlices, C.bc_begin + nb * (g + 1) / kFinSlices, tot, sh, tid);
+                            C.bc_begin + nb * g / kFinSlices, C.bc_begin + nb * (g + 1) / kFinSlices,
+                            a.shell_begin + ns * g / kFinSlices, a.shell_begin + ns * (g + 1) / kFinSlices, tot, sh,
+                            tid);
   double *my = mid + ((long long)cav * kFinSlices + g) * 8;
   if (tid == 0) {
     for (int f = 0; f < 8; ++f) my[f] = tot[f];

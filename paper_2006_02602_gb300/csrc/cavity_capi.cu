@@ -101,6 +101,13 @@ struct cavity {
   int f32_r = 0;                  // ring depth of the FP32 step kernel
   int f32_p = 1;                  // nodes per thread along x of the FP32 step kernel
   int local_dt = 0;               // CAVITY_DT_LOCAL: each node at its own stable step
+  // interior/shell split with overlapped exchange (FP64, single cavity, cut faces)
+  bool overlap = false;
+  std::vector<ShellFace> hshell;
+  ShellFace *d_shell = nullptr;
+  int n_shell = 0;                // k_shell_f64 CTAs
+  cudaStream_t side = nullptr;    // the exchange's stream while the interior is stepped
+  cudaEvent_t ev_shell = nullptr, ev_exch = nullptr;
   int nblocks = 0;
   std::vector<BlockDev> hb;
   std::vector<WallFace> hwall;
@@ -383,12 +390,13 @@ int upload_tables(cavity *h) {
 }
 
 int ensure_partials(cavity *h) {
-  if (h->part_cap >= h->n_step) return CAVITY_OK;
+  const int need = h->n_step + (h->overlap ? h->n_shell : 0);
+  if (h->part_cap >= need) return CAVITY_OK;
   CK(cudaStreamSynchronize(h->stream));
   if (h->d_step_part) cudaFree(h->d_step_part);
   h->d_step_part = nullptr;
-  CK(cudaMalloc(&h->d_step_part, sizeof(double) * kPartStride * std::max(1, h->n_step)));
-  h->part_cap = h->n_step;
+  CK(cudaMalloc(&h->d_step_part, sizeof(double) * kPartStride * std::max(1, need)));
+  h->part_cap = need;
   return CAVITY_OK;
 }
 
@@ -457,6 +465,7 @@ StepArgs step_args(cavity *h, int parity, int mode) {
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.partials = h->d_step_part; a.parity = parity; a.mode = mode;
   a.tile_counter = h->d_counter + h->ncav; a.ntiles = h->n_step; a.local_dt = h->local_dt;
+  a.skip_shell = 0;
   return a;
 }
 
@@ -476,6 +485,7 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.step_partials = h->d_step_part; a.bc_partials = h->d_bc_part; a.counter = h->d_counter;
   a.tile_counter = h->d_counter + h->ncav;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
+  a.shell_begin = a.shell_end = 0;
   return a;
 }
 
@@ -533,14 +543,16 @@ void launch_bc_kernel(cavity *h, int parity, int mode) {
   }
 }
 
-void launch_pack(cavity *h, int parity) {
-  if (h->f32) k_pack<float><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
-  else k_pack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+void launch_pack(cavity *h, int parity, cudaStream_t s = nullptr) {
+  if (!s) s = h->stream;
+  if (h->f32) k_pack<float><<<h->n_cut, 256, 0, s>>>(exch_args(h, parity));
+  else k_pack<double><<<h->n_cut, 256, 0, s>>>(exch_args(h, parity));
 }
 
-void launch_unpack(cavity *h, int parity) {
-  if (h->f32) k_unpack<float><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
-  else k_unpack<double><<<h->n_cut, 256, 0, h->stream>>>(exch_args(h, parity));
+void launch_unpack(cavity *h, int parity, cudaStream_t s = nullptr) {
+  if (!s) s = h->stream;
+  if (h->f32) k_unpack<float><<<h->n_cut, 256, 0, s>>>(exch_args(h, parity));
+  else k_unpack<double><<<h->n_cut, 256, 0, s>>>(exch_args(h, parity));
 }
 
 int launch_exchange(cavity *h, int parity) {
@@ -552,8 +564,37 @@ int launch_exchange(cavity *h, int parity) {
   return CAVITY_OK;
 }
 
+// The overlapped step (FP64, cut faces): shell nodes first, then the
+// exchange of the new ghost layers on the side stream while the persistent
+// kernel steps the remaining nodes; walls and the finalise after both.
+int launch_step_overlapped(cavity *h, int parity) {
+  const ShellArgs sa{h->d_blocks, h->d_shell, (int)h->hshell.size(), h->d_cc, h->d_cs, h->d_step_part,
+                     (long long)h->n_step, parity, h->local_dt};
+  k_shell_f64<<<h->n_shell, kShellThreads, 0, h->stream>>>(sa);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev_shell, h->stream));
+  CK(cudaStreamWaitEvent(h->side, h->ev_shell, 0));
+  launch_pack(h, parity ^ 1, h->side);
+  launch_unpack(h, parity ^ 1, h->side);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev_exch, h->side));
+  StepArgs st = step_args(h, parity, 0);
+  st.skip_shell = 1;
+  k_step_f64<kTX, kTY, kKC><<<std::min(h->n_step, h->persist_ctas), dim3(kTX, kTY), 0, h->stream>>>(st);
+  CK(cudaGetLastError());
+  CK(cudaStreamWaitEvent(h->stream, h->ev_exch, 0));
+  BcArgs ba = bc_args(h, parity ^ 1, 0);
+  k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(ba);
+  ba.shell_begin = h->n_step;
+  ba.shell_end = (long long)h->n_step + h->n_shell;
+  k_finalize<double><<<h->ncav * kFinSlices, kFinThreads, 0, h->stream>>>(ba, h->d_fin);
+  CK(cudaGetLastError());
+  return CAVITY_OK;
+}
+
 // one explicit step reading buffer set `parity`, leaving the new state in parity ^ 1
 int launch_step(cavity *h, int parity) {
+  if (h->overlap) return launch_step_overlapped(h, parity);
   launch_step_kernel(h, parity);
   CK(cudaGetLastError());
   launch_bc_kernel(h, parity ^ 1, 0);
@@ -707,7 +748,7 @@ void release(cavity *h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   void *ptrs[] = {h->d_fields, h->d_blocks, h->d_cc, h->d_cs, h->d_wall, h->d_cut, h->d_step_part,
-                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps, h->d_fin};
+                  h->d_bc_part, h->d_counter, h->d_twall, h->d_xbuf, h->d_stage, h->d_maps, h->d_fin, h->d_shell};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   AdjointStore &A = h->adj;
@@ -716,6 +757,9 @@ void release(cavity *h) {
   for (void *p : aptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_shell) cudaEventDestroy(h->ev_shell);
+  if (h->ev_exch) cudaEventDestroy(h->ev_exch);
 }
 
 int create_common(const cavity_desc *descs, const cavity_params *params, int n, cavity_t **out) {
@@ -1249,6 +1293,38 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
   CK(cudaStreamSynchronize(h->stream));
   if (grad_ra) *grad_ra = ra;
   return rc;
+}
+
+int cavity_set_overlap(cavity_t *h, int on) {
+  if (!h) return CAVITY_ERR_INVALID_ARG;
+  if (on && (h->f32 || h->ncav != 1))
+    return fail(h, CAVITY_ERR_UNSUPPORTED, "overlap: FP64 single-cavity handles only");
+  DeviceGuard g(h->dev);
+  CK(cudaStreamSynchronize(h->stream));
+  h->overlap = on && h->n_cut > 0;  // nothing to overlap without cut faces
+  if (h->overlap && h->hshell.empty()) {
+    int cta = 0;
+    for (int id = 0; id < h->nblocks; ++id) {
+      const BlockDev &B = h->hb[id];
+      const int n[3] = {B.nx, B.ny, B.nz};
+      for (int f = 0; f < 6; ++f) {
+        if (B.wall[f]) continue;
+        const int a = f / 2;
+        const int n1 = n[a == 0 ? 1 : 0], n2 = n[a == 2 ? 1 : 2];
+        h->hshell.push_back(ShellFace{id, f, n1, n2, cta});
+        cta += ceil_div(2LL * n1 * n2, kShellThreads);
+      }
+    }
+    h->n_shell = cta;
+    CK(cudaMalloc(&h->d_shell, sizeof(ShellFace) * h->hshell.size()));
+    CK(cudaMemcpy(h->d_shell, h->hshell.data(), sizeof(ShellFace) * h->hshell.size(), cudaMemcpyHostToDevice));
+    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_shell, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_exch, cudaEventDisableTiming));
+  }
+  const int rc = ensure_partials(h);
+  if (rc != CAVITY_OK) return rc;
+  return build_graphs(h);
 }
 
 int cavity_set_time_stepping(cavity_t *h, int mode) {
