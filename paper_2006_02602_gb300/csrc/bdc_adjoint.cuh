@@ -1,4 +1,4 @@
-// Discrete adjoint of the explicit step (single-block cavity), FP64.
+// Discrete adjoint of the explicit step (single-block cavity).
 //
 // Objective J = (1/N) sum_{n=1..N} Nu_hot(Q^n); controls: the hot-wall
 // temperature field theta and Ra.  A step Q^{n+1} = G(Q^n) is: dt = cfl / S,
@@ -11,7 +11,7 @@
 //   k_adj_prepare    Yt = Xbar minus that sum shared over the centre nodes;
 //                    Q = Yt on the interior, 0 on walls and ghosts
 //   k_adj_rates      at every interior node the reverse of the rates
-//                    applied to dt Yt, added with FP64 atomics into Q at the
+//                    applied to dt Yt, added with atomics into Q at the
 //                    stencil's inputs; sums of Yt R (for dt), of the
 //                    buoyancy and beta^2-floor adjoints
 //   k_adj_argmax + k_adj_dt  dt's dependence: -cfl dtbar / S^2 times the
@@ -22,15 +22,24 @@
 //   k_adj_finish     Ra adjoint from the buoyancy (g sigma = Ra Pr) and floor
 //                    (kappa u_ref^2 = kappa Ra Pr) sums; reset the scalars
 // Subgradients at kinks follow the forward branch (|x| with sign(0) = 0, the
-// beta^2 floor, the argmax node).  The state Q^n is read through the storage
-// helpers, so the forward may be FP64 or FP32-mixed; the adjoint is FP64.
+// beta^2 floor, the argmax node).
+//
+// Precision: the adjoint arrays X, Yt, Q hold A (the reverse sweep's type):
+// FP64 after an FP64 forward, FP32 after an FP32-mixed forward, whose
+// trajectory carries FP32 precision anyway.  The rates' reverse works on
+// neighbour-minus-centre differences; for the FP32-mixed state the p and T
+// differences are formed from their hi/lo pairs (as the forward step does),
+// so FP32 arithmetic loses no cancellation.  The sums over nodes (dt, g sigma,
+// beta^2 floor, the p adjoint) and the wall gradient stay FP64.
 #pragma once
+
+#include <type_traits>
 
 #include "bdc_device.cuh"
 
 namespace bdc {
 
-struct AdjGeom {  // dense FP64 adjoint arrays over local nodes -1 .. n+2, 5 fields
+struct AdjGeom {  // dense adjoint arrays over local nodes -1 .. n+2, 5 fields
   int nx, ny, nz;
   long long ex, ey, fs;  // row length, rows, elements per field
 };
@@ -45,9 +54,9 @@ struct AdjArgs {
   BlockDev B;        // the state Q^n being read (buffer set base[0])
   CavConst C;
   AdjGeom g;
-  double *X;         // adjoint of the interior state after the step
-  double *Yt;        // X after the centre-shift transpose
-  double *Q;         // scatter target: adjoint of Q^n (interior, walls, ghosts)
+  void *X;           // adjoint of the interior state after the step (type A)
+  void *Yt;          // X after the centre-shift transpose (type A)
+  void *Q;           // scatter target: adjoint of Q^n, interior, walls, ghosts (type A)
   double *scal;      // kSc* scalars
   double *thetabar;  // ny*nz, (j-1) + ny (k-1)
   double *argpart;   // per-CTA (max, index) pairs of k_adj_argmax
@@ -56,32 +65,50 @@ struct AdjArgs {
   double dfloor;     // d(beta^2 floor)/dRa
 };
 
+template <class A> __device__ __forceinline__ A *arr(void *p) { return static_cast<A *>(p); }
+
+// interior node (i, j, k), 1-based, of linear interior index e (x fastest);
+// 32-bit division: the adjoint's block has fewer than 2^31 interior nodes
+__device__ __forceinline__ void unflat(const AdjGeom &g, unsigned e, int &i, int &j, int &k) {
+  const unsigned nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+  const unsigned r = e / nx;
+  i = (int)(e - r * nx) + 1;
+  j = (int)(r % ny) + 1;
+  k = (int)(r / ny) + 1;
+}
+
 // state value of field f (0 = p, 1..4 = u, v, w, T) at local node (i, j, k)
 template <class S>
 __device__ __forceinline__ double st(const AdjArgs &a, int f, int i, int j, int k) {
   return get_field<S>((const S *)a.B.base[0], a.B.fstride, f, node_index<S>(a.B, i, j, k));
 }
 
+template <class A>
 __global__ void k_adj_objective(AdjArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.g.ny * a.g.nz) return;
   const int j = e % a.g.ny + 1, k = e / a.g.ny + 1;
-  a.X[aidx(a.g, 4, 1, j, k)] += -4.0 * a.coef;
-  a.X[aidx(a.g, 4, 2, j, k)] += a.coef;
+  A *X = arr<A>(a.X);
+  X[aidx(a.g, 4, 1, j, k)] += (A)(-4.0 * a.coef);
+  X[aidx(a.g, 4, 2, j, k)] += (A)a.coef;
   a.thetabar[e] += 3.0 * a.coef;
 }
 
+template <class A>
 __global__ void k_adj_sum_p(AdjArgs a) {
   const long long n = (long long)a.g.nx * a.g.ny * a.g.nz;
+  const A *X = arr<A>(a.X);
   double s = 0.0;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % a.g.nx) + 1, j = (int)((e / a.g.nx) % a.g.ny) + 1, k = (int)(e / ((long long)a.g.nx * a.g.ny)) + 1;
-    s += a.X[aidx(a.g, 0, i, j, k)];
+    int i, j, k;
+    unflat(a.g, (unsigned)e, i, j, k);
+    s += (double)X[aidx(a.g, 0, i, j, k)];
   }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) atomicAdd(&a.scal[kScSumP], s);
 }
 
+template <class A>
 __global__ void k_adj_prepare(AdjArgs a) {
   const long long n = a.g.fs * 5;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,123 +116,182 @@ __global__ void k_adj_prepare(AdjArgs a) {
   const int f = (int)(e / a.g.fs);
   const long long r = e % a.g.fs;
   const int i = (int)(r % a.g.ex) - 1, j = (int)((r / a.g.ex) % a.g.ey) - 1, k = (int)(r / (a.g.ex * a.g.ey)) - 1;
-  double v = 0.0;
+  A v = 0;
   if (i >= 1 && i <= a.g.nx && j >= 1 && j <= a.g.ny && k >= 1 && k <= a.g.nz) {
-    v = a.X[e];
+    v = arr<A>(a.X)[e];
     if (f == 0) {
       const int *gn = a.C.gn;
       const bool ci = (gn[0] % 2) ? i == (gn[0] + 1) / 2 : (i == gn[0] / 2 || i == gn[0] / 2 + 1);
       const bool cj = (gn[1] % 2) ? j == (gn[1] + 1) / 2 : (j == gn[1] / 2 || j == gn[1] / 2 + 1);
       const bool ck = (gn[2] % 2) ? k == (gn[2] + 1) / 2 : (k == gn[2] / 2 || k == gn[2] / 2 + 1);
-      if (ci && cj && ck) v -= a.scal[kScSumP] / (double)a.C.ncentre;
+      if (ci && cj && ck) v = (A)((double)v - a.scal[kScSumP] / (double)a.C.ncentre);
     }
   }
-  a.Yt[e] = v;
-  a.Q[e] = v;
+  arr<A>(a.Yt)[e] = v;
+  arr<A>(a.Q)[e] = v;
 }
 
-// reverse of the rates at one interior node, scattered with atomics
-template <class S>
+// The node's stencil as the reverse of the rates needs it: the velocities,
+// neighbour-minus-centre differences dp[f][d] (node + e_d) and dm[f][d]
+// (node - e_d) of the five fields, p's at +-2 e_d, and tb = T - T_inf.
+template <class R>
+struct AdjStencil {
+  R V[3], dp[5][3], dm[5][3], d2p[3], d2m[3], tb;
+};
+
+template <class S, class R>
+__device__ __forceinline__ void load_stencil(const AdjArgs &a, int i, int j, int k, AdjStencil<R> &s) {
+  const int o3[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
+    // FP32-mixed state: p and T as hi/lo pairs, differences formed per part
+    const float *q = (const float *)a.B.base[0];
+    const long long fs = a.B.fstride, o = node_index<float>(a.B, i, j, k);
+    const long long step[3] = {1, a.B.pitch, a.B.plane};
+    const float ph = q[o], pl = q[fs + o], th = q[5 * fs + o], tl = q[6 * fs + o];
+    const float c[3] = {q[2 * fs + o], q[3 * fs + o], q[4 * fs + o]};
+    auto pdf = [&](long long off) { return (q[o + off] - ph) + (q[fs + o + off] - pl); };
+    auto tdf = [&](long long off) { return (q[5 * fs + o + off] - th) + (q[6 * fs + o + off] - tl); };
+    for (int d = 0; d < 3; ++d) {
+      const long long st_ = step[d];
+      s.V[d] = c[d];
+      s.dp[0][d] = pdf(st_);
+      s.dm[0][d] = pdf(-st_);
+      s.d2p[d] = pdf(2 * st_);
+      s.d2m[d] = pdf(-2 * st_);
+      for (int f = 1; f <= 3; ++f) {
+        s.dp[f][d] = q[(1 + f) * fs + o + st_] - c[f - 1];
+        s.dm[f][d] = q[(1 + f) * fs + o - st_] - c[f - 1];
+      }
+      s.dp[4][d] = tdf(st_);
+      s.dm[4][d] = tdf(-st_);
+    }
+    s.tb = (th - (float)a.C.t_inf) + tl;
+  } else {
+    double c0[5];
+    for (int f = 0; f < 5; ++f) c0[f] = st<S>(a, f, i, j, k);
+    for (int d = 0; d < 3; ++d) {
+      s.V[d] = (R)c0[1 + d];
+      for (int f = 0; f < 5; ++f) {
+        s.dp[f][d] = (R)(st<S>(a, f, i + o3[d][0], j + o3[d][1], k + o3[d][2]) - c0[f]);
+        s.dm[f][d] = (R)(st<S>(a, f, i - o3[d][0], j - o3[d][1], k - o3[d][2]) - c0[f]);
+      }
+      s.d2p[d] = (R)(st<S>(a, 0, i + 2 * o3[d][0], j + 2 * o3[d][1], k + 2 * o3[d][2]) - c0[0]);
+      s.d2m[d] = (R)(st<S>(a, 0, i - 2 * o3[d][0], j - 2 * o3[d][1], k - 2 * o3[d][2]) - c0[0]);
+    }
+    s.tb = (R)(c0[4] - a.C.t_inf);
+  }
+}
+
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+
+// Reverse of the rates at one interior node in type R, scattered with atomics
+// into Q (type R).  The forward rates are formed from the same differences,
+// since 4th differences and gradients need only neighbour-minus-centre values.
+template <class S, class R>
 __global__ void __launch_bounds__(256) k_adj_rates(AdjArgs a) {
   const long long n = (long long)a.g.nx * a.g.ny * a.g.nz;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double dtbar = 0.0, gsbar = 0.0, floorbar = 0.0;
   if (e < n) {
-    const int i = (int)(e % a.g.nx) + 1, j = (int)((e / a.g.nx) % a.g.ny) + 1, k = (int)(e / ((long long)a.g.nx * a.g.ny)) + 1;
+    int i, j, k;
+    unflat(a.g, (unsigned)e, i, j, k);
     const CavConst &C = a.C;
     const int o3[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    // stencil values: centre, then +d / -d per axis, and p at +-2d
-    double c0[5], qp[5][3], qm[5][3], p2p[3], p2m[3];
-    for (int f = 0; f < 5; ++f) c0[f] = st<S>(a, f, i, j, k);
+    R *Q = arr<R>(a.Q);
+    AdjStencil<R> s;
+    load_stencil<S, R>(a, i, j, k, s);
+    const R *V = s.V;
+    const R ih[3] = {(R)C.ih[0], (R)C.ih[1], (R)C.ih[2]}, ih2[3] = {(R)C.ih2[0], (R)C.ih2[1], (R)C.ih2[2]};
+    const R ihh[3] = {(R)C.ihh[0], (R)C.ihh[1], (R)C.ihh[2]};
+    const R c4 = (R)C.c4, nu = (R)C.nu, alpha = (R)C.alpha, gs = (R)C.gs;
+    R b2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const bool floored = b2 < (R)C.b2min;
+    if (floored) b2 = (R)C.b2min;
+    // sq = sqrt(V_d^2 + 4 b2) and isq = 1/sq from one reciprocal square root
+    // (the reverse needs V_d / sq and 1 / sq: no divisions)
+    R sq[3], isq[3], lam[3], d4[3], ad[3], divV = 0, diss = 0;
     for (int d = 0; d < 3; ++d) {
-      for (int f = 0; f < 5; ++f) {
-        qp[f][d] = st<S>(a, f, i + o3[d][0], j + o3[d][1], k + o3[d][2]);
-        qm[f][d] = st<S>(a, f, i - o3[d][0], j - o3[d][1], k - o3[d][2]);
-      }
-      p2p[d] = st<S>(a, 0, i + 2 * o3[d][0], j + 2 * o3[d][1], k + 2 * o3[d][2]);
-      p2m[d] = st<S>(a, 0, i - 2 * o3[d][0], j - 2 * o3[d][1], k - 2 * o3[d][2]);
-    }
-    const double V[3] = {c0[1], c0[2], c0[3]};
-    double b2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
-    const bool floored = b2 < C.b2min;
-    if (floored) b2 = C.b2min;
-    double sq[3], lam[3], d4[3], a_[3], divV = 0.0, diss = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      sq[d] = sqrt(V[d] * V[d] + 4.0 * b2);
-      lam[d] = 0.5 * (fabs(V[d]) + sq[d]);
-      d4[d] = (p2p[d] + p2m[d]) - 4.0 * (qp[0][d] + qm[0][d]) + 6.0 * c0[0];
-      a_[d] = V[d] * C.ih2[d];
-      divV += (qp[1 + d][d] - qm[1 + d][d]) * C.ih2[d];
-      diss += C.c4 * lam[d] * C.ih[d] * d4[d];
+      const R qd = V[d] * V[d] + (R)4 * b2;
+      isq[d] = rsqrt_r(qd);
+      sq[d] = qd * isq[d];
+      lam[d] = (R)0.5 * ((V[d] < 0 ? -V[d] : V[d]) + sq[d]);
+      d4[d] = (s.d2p[d] + s.d2m[d]) - (R)4 * (s.dp[0][d] + s.dm[0][d]);
+      ad[d] = V[d] * ih2[d];
+      divV += (s.dp[1 + d][d] - s.dm[1 + d][d]) * ih2[d];
+      diss += c4 * lam[d] * ih[d] * d4[d];
     }
     // forward rates (for dt's adjoint: dtbar = sum Yt R)
-    double R[5];
-    R[0] = -b2 * divV - diss;
+    R Rf[5];
+    Rf[0] = -b2 * divV - diss;
     for (int q = 1; q <= 4; ++q) {
-      const double D = q == 4 ? C.alpha : C.nu;
-      double r = 0.0;
-      for (int d = 0; d < 3; ++d)
-        r += (D * C.ihh[d] - a_[d]) * (qp[q][d] - c0[q]) + (D * C.ihh[d] + a_[d]) * (qm[q][d] - c0[q]);
+      const R D = q == 4 ? alpha : nu;
+      R r = 0;
+      for (int d = 0; d < 3; ++d) r += (D * ihh[d] - ad[d]) * s.dp[q][d] + (D * ihh[d] + ad[d]) * s.dm[q][d];
       if (q <= 3) {
         const int cc = q - 1;
-        r += -(qp[0][cc] - qm[0][cc]) * C.ih2[cc];
-        if (cc == C.gaxis) r += C.gs * (c0[4] - C.t_inf);
+        r += -(s.dp[0][cc] - s.dm[0][cc]) * ih2[cc];
+        if (cc == C.gaxis) r += gs * s.tb;
       }
-      R[q] = r;
+      Rf[q] = r;
     }
-    double yt[5];
+    const R *Yt = arr<R>(a.Yt);
+    R yt[5], dtb = 0;
     for (int f = 0; f < 5; ++f) {
-      yt[f] = a.Yt[aidx(a.g, f, i, j, k)];
-      dtbar += yt[f] * R[f];
+      yt[f] = Yt[aidx(a.g, f, i, j, k)];
+      dtb += yt[f] * Rf[f];
     }
-    double rb[5];
-    for (int f = 0; f < 5; ++f) rb[f] = a.dt * yt[f];
+    dtbar = (double)dtb;
+    R rb[5];
+    for (int f = 0; f < 5; ++f) rb[f] = (R)a.dt * yt[f];
     // adjoints of the centre values (accumulated here, one atomic each at the end)
-    double cbar[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    double abar[3] = {0.0, 0.0, 0.0};
+    R cbar[5] = {0, 0, 0, 0, 0};
+    R abar[3] = {0, 0, 0};
+    R gsb = 0;
     // transported fields
     for (int q = 1; q <= 4; ++q) {
-      const double D = q == 4 ? C.alpha : C.nu;
+      const R D = q == 4 ? alpha : nu;
       for (int d = 0; d < 3; ++d) {
-        atomicAdd(&a.Q[aidx(a.g, q, i + o3[d][0], j + o3[d][1], k + o3[d][2])], rb[q] * (D * C.ihh[d] - a_[d]));
-        atomicAdd(&a.Q[aidx(a.g, q, i - o3[d][0], j - o3[d][1], k - o3[d][2])], rb[q] * (D * C.ihh[d] + a_[d]));
-        cbar[q] += -2.0 * rb[q] * D * C.ihh[d];
-        abar[d] += -rb[q] * (qp[q][d] - qm[q][d]);
+        atomicAdd(&Q[aidx(a.g, q, i + o3[d][0], j + o3[d][1], k + o3[d][2])], rb[q] * (D * ihh[d] - ad[d]));
+        atomicAdd(&Q[aidx(a.g, q, i - o3[d][0], j - o3[d][1], k - o3[d][2])], rb[q] * (D * ihh[d] + ad[d]));
+        cbar[q] += (R)(-2) * rb[q] * D * ihh[d];
+        abar[d] += -rb[q] * (s.dp[q][d] - s.dm[q][d]);
       }
       if (q <= 3) {
         const int cc = q - 1;
-        atomicAdd(&a.Q[aidx(a.g, 0, i + o3[cc][0], j + o3[cc][1], k + o3[cc][2])], -rb[q] * C.ih2[cc]);
-        atomicAdd(&a.Q[aidx(a.g, 0, i - o3[cc][0], j - o3[cc][1], k - o3[cc][2])], rb[q] * C.ih2[cc]);
+        atomicAdd(&Q[aidx(a.g, 0, i + o3[cc][0], j + o3[cc][1], k + o3[cc][2])], -rb[q] * ih2[cc]);
+        atomicAdd(&Q[aidx(a.g, 0, i - o3[cc][0], j - o3[cc][1], k - o3[cc][2])], rb[q] * ih2[cc]);
         if (cc == C.gaxis) {
-          cbar[4] += C.gs * rb[q];
-          gsbar += (c0[4] - C.t_inf) * rb[q];
+          cbar[4] += gs * rb[q];
+          gsb += s.tb * rb[q];
         }
       }
     }
-    for (int d = 0; d < 3; ++d) cbar[1 + d] += abar[d] * C.ih2[d];
+    gsbar = (double)gsb;
+    for (int d = 0; d < 3; ++d) cbar[1 + d] += abar[d] * ih2[d];
     // continuity: R_p = -b2 divV - diss
-    double b2bar = -divV * rb[0];
-    const double divbar = -b2 * rb[0], dissbar = -rb[0];
+    R b2bar = -divV * rb[0];
+    const R divbar = -b2 * rb[0], dissbar = -rb[0];
     for (int d = 0; d < 3; ++d) {
-      atomicAdd(&a.Q[aidx(a.g, 1 + d, i + o3[d][0], j + o3[d][1], k + o3[d][2])], divbar * C.ih2[d]);
-      atomicAdd(&a.Q[aidx(a.g, 1 + d, i - o3[d][0], j - o3[d][1], k - o3[d][2])], -divbar * C.ih2[d]);
-      const double lambar = dissbar * C.c4 * C.ih[d] * d4[d];
-      const double d4bar = dissbar * C.c4 * lam[d] * C.ih[d];
-      atomicAdd(&a.Q[aidx(a.g, 0, i + 2 * o3[d][0], j + 2 * o3[d][1], k + 2 * o3[d][2])], d4bar);
-      atomicAdd(&a.Q[aidx(a.g, 0, i - 2 * o3[d][0], j - 2 * o3[d][1], k - 2 * o3[d][2])], d4bar);
-      atomicAdd(&a.Q[aidx(a.g, 0, i + o3[d][0], j + o3[d][1], k + o3[d][2])], -4.0 * d4bar);
-      atomicAdd(&a.Q[aidx(a.g, 0, i - o3[d][0], j - o3[d][1], k - o3[d][2])], -4.0 * d4bar);
-      cbar[0] += 6.0 * d4bar;
-      const double sgn = V[d] > 0.0 ? 1.0 : (V[d] < 0.0 ? -1.0 : 0.0);
-      cbar[1 + d] += lambar * 0.5 * (sgn + V[d] / sq[d]);
-      b2bar += lambar / sq[d];
+      atomicAdd(&Q[aidx(a.g, 1 + d, i + o3[d][0], j + o3[d][1], k + o3[d][2])], divbar * ih2[d]);
+      atomicAdd(&Q[aidx(a.g, 1 + d, i - o3[d][0], j - o3[d][1], k - o3[d][2])], -divbar * ih2[d]);
+      const R lambar = dissbar * c4 * ih[d] * d4[d];
+      const R d4bar = dissbar * c4 * lam[d] * ih[d];
+      atomicAdd(&Q[aidx(a.g, 0, i + 2 * o3[d][0], j + 2 * o3[d][1], k + 2 * o3[d][2])], d4bar);
+      atomicAdd(&Q[aidx(a.g, 0, i - 2 * o3[d][0], j - 2 * o3[d][1], k - 2 * o3[d][2])], d4bar);
+      atomicAdd(&Q[aidx(a.g, 0, i + o3[d][0], j + o3[d][1], k + o3[d][2])], (R)(-4) * d4bar);
+      atomicAdd(&Q[aidx(a.g, 0, i - o3[d][0], j - o3[d][1], k - o3[d][2])], (R)(-4) * d4bar);
+      cbar[0] += (R)6 * d4bar;
+      const R sgn = V[d] > 0 ? (R)1 : (V[d] < 0 ? (R)(-1) : (R)0);
+      cbar[1 + d] += lambar * (R)0.5 * (sgn + V[d] * isq[d]);
+      b2bar += lambar * isq[d];
     }
     if (floored) {
-      floorbar += b2bar;
+      floorbar = (double)b2bar;
     } else {
-      for (int d = 0; d < 3; ++d) cbar[1 + d] += 2.0 * V[d] * b2bar;
+      for (int d = 0; d < 3; ++d) cbar[1 + d] += (R)2 * V[d] * b2bar;
     }
-    for (int f = 0; f < 5; ++f) atomicAdd(&a.Q[aidx(a.g, f, i, j, k)], cbar[f]);
+    for (int f = 0; f < 5; ++f) atomicAdd(&Q[aidx(a.g, f, i, j, k)], cbar[f]);
   }
   dtbar = warp_sum(dtbar);
   gsbar = warp_sum(gsbar);
@@ -217,15 +303,34 @@ __global__ void __launch_bounds__(256) k_adj_rates(AdjArgs a) {
   }
 }
 
-// largest spectral bound of Q^n and its node (smallest linear index among equal values)
+// largest spectral bound of Q^n and its node (smallest linear index among
+// equal values: each thread visits its nodes in increasing index)
 template <class S>
 __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
   const long long n = (long long)a.g.nx * a.g.ny * a.g.nz;
   double best = -1.0, bidx = 0.0;
+  float wfloor = 0.f;  // at or below an exact bound a lane of this warp reached
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % a.g.nx) + 1, j = (int)((e / a.g.nx) % a.g.ny) + 1, k = (int)(e / ((long long)a.g.nx * a.g.ny)) + 1;
-    const double s = spectral_f64(a.C, st<S>(a, 1, i, j, k), st<S>(a, 2, i, j, k), st<S>(a, 3, i, j, k));
-    if (s > best) { best = s; bidx = (double)e; }
+    int i, j, k;
+    unflat(a.g, (unsigned)e, i, j, k);
+    const S *q = (const S *)a.B.base[0];
+    const long long o = node_index<S>(a.B, i, j, k), fs = a.B.fstride;
+    constexpr int NP = Store<S>::NP;  // u, v, w follow the p array(s)
+    const S u = q[NP * fs + o], v = q[(NP + 1) * fs + o], w = q[(NP + 2) * fs + o];
+    // exact FP64 bound only where an FP32 estimate (relative error < 1e-6)
+    // raised by 1e-5 could reach the running maximum: the argmax is unchanged
+    if (__fmul_rn(spectral_est_f32(a.C, u, v, w), 1.00001f) >= wfloor) {
+      const double s = spectral_f64(a.C, u, v, w);
+      if (s > best) {
+        best = s;
+        bidx = (double)e;
+      }
+    }
+    // a warp-shared floor (a value some lane's node attained exactly), so that
+    // the FP64 path runs only when a node of the warp could reach it:
+    // non-negative floats order like their bit patterns
+    const float bf = best > 0.0 ? __double2float_rd(best) : 0.f;
+    wfloor = fmaxf(wfloor, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(bf))));
   }
   for (int o = 16; o > 0; o >>= 1) {
     const double ob = __shfl_xor_sync(0xffffffffu, best, o), oi = __shfl_xor_sync(0xffffffffu, bidx, o);
@@ -243,17 +348,37 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
   }
 }
 
-// dt = cfl / S: add (-cfl dtbar / S^2) d(bound)/dV at the argmax node (one thread)
-template <class S>
-__global__ void k_adj_dt(AdjArgs a, int nparts) {
+// dt = cfl / S: add (-cfl dtbar / S^2) d(bound)/dV at the argmax node.  One
+// CTA of kAdjDtThreads: the per-CTA (max, index) pairs of k_adj_argmax are
+// reduced in parallel (largest value, smallest index among equals), then one
+// thread differentiates the bound at that node (FP64).
+constexpr int kAdjDtThreads = 256;
+template <class S, class A>
+__global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts) {
+  __shared__ double sb[kAdjDtThreads], si[kAdjDtThreads];
+  const int tid = threadIdx.x;
   double best = -1.0, bidx = 0.0;
-  for (int q = 0; q < nparts; ++q)
+  for (int q = tid; q < nparts; q += kAdjDtThreads)
     if (a.argpart[2 * q] > best || (a.argpart[2 * q] == best && a.argpart[2 * q + 1] < bidx)) {
       best = a.argpart[2 * q];
       bidx = a.argpart[2 * q + 1];
     }
+  sb[tid] = best;
+  si[tid] = bidx;
+  __syncthreads();
+  for (int o = kAdjDtThreads / 2; o > 0; o >>= 1) {
+    if (tid < o && (sb[tid + o] > sb[tid] || (sb[tid + o] == sb[tid] && si[tid + o] < si[tid]))) {
+      sb[tid] = sb[tid + o];
+      si[tid] = si[tid + o];
+    }
+    __syncthreads();
+  }
+  if (tid != 0) return;
+  best = sb[0];
+  bidx = si[0];
   const long long e = (long long)bidx;
-  const int i = (int)(e % a.g.nx) + 1, j = (int)((e / a.g.nx) % a.g.ny) + 1, k = (int)(e / ((long long)a.g.nx * a.g.ny)) + 1;
+  int i, j, k;
+    unflat(a.g, (unsigned)e, i, j, k);
   const double sbar = -a.C.cfl * a.scal[kScDtbar] / (best * best);
   const double V[3] = {st<S>(a, 1, i, j, k), st<S>(a, 2, i, j, k), st<S>(a, 3, i, j, k)};
   double b2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
@@ -267,10 +392,13 @@ __global__ void k_adj_dt(AdjArgs a, int nparts) {
     b2bar += sbar * a.C.ih[d] / sq;
   }
   if (floored) a.scal[kScFloor] += b2bar;
-  for (int d = 0; d < 3; ++d) a.Q[aidx(a.g, 1 + d, i, j, k)] += vbar[d] + (floored ? 0.0 : 2.0 * V[d] * b2bar);
+  A *Q = arr<A>(a.Q);
+  for (int d = 0; d < 3; ++d)
+    Q[aidx(a.g, 1 + d, i, j, k)] += (A)(vbar[d] + (floored ? 0.0 : 2.0 * V[d] * b2bar));
 }
 
 // wall and ghost adjoints onto the interior nodes they are formed from
+template <class A>
 __global__ void k_adj_fold(AdjArgs a) {
   const int n[3] = {a.g.nx, a.g.ny, a.g.nz};
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -282,6 +410,7 @@ __global__ void k_adj_fold(AdjArgs a) {
     e -= cnt;
   }
   if (face >= 6) return;
+  A *Q = arr<A>(a.Q);
   const int ax = face >> 1, high = face & 1;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int c1 = (int)(e % n[a1]) + 1, c2 = (int)(e / n[a1]) + 1;
@@ -290,15 +419,15 @@ __global__ void k_adj_fold(AdjArgs a) {
   iw[ax] = w; i1[ax] = w + s; i2[ax] = w + 2 * s; ig[ax] = w - s;
   iw[a1] = i1[a1] = i2[a1] = ig[a1] = c1;
   iw[a2] = i1[a2] = i2[a2] = ig[a2] = c2;
-  const double pw = a.Q[aidx(a.g, 0, iw[0], iw[1], iw[2])], pg = a.Q[aidx(a.g, 0, ig[0], ig[1], ig[2])];
-  atomicAdd(&a.Q[aidx(a.g, 0, i1[0], i1[1], i1[2])], 2.0 * pw + 3.0 * pg);
-  atomicAdd(&a.Q[aidx(a.g, 0, i2[0], i2[1], i2[2])], -pw - 2.0 * pg);
-  const double tw = a.Q[aidx(a.g, 4, iw[0], iw[1], iw[2])];
+  const A pw = Q[aidx(a.g, 0, iw[0], iw[1], iw[2])], pg = Q[aidx(a.g, 0, ig[0], ig[1], ig[2])];
+  atomicAdd(&Q[aidx(a.g, 0, i1[0], i1[1], i1[2])], (A)2 * pw + (A)3 * pg);
+  atomicAdd(&Q[aidx(a.g, 0, i2[0], i2[1], i2[2])], -pw - (A)2 * pg);
+  const A tw = Q[aidx(a.g, 4, iw[0], iw[1], iw[2])];
   if (ax == 0) {
-    if (!high) a.thetabar[(c1 - 1) + (long long)n[1] * (c2 - 1)] += tw;
+    if (!high) a.thetabar[(c1 - 1) + (long long)n[1] * (c2 - 1)] += (double)tw;
   } else {
-    atomicAdd(&a.Q[aidx(a.g, 4, i1[0], i1[1], i1[2])], (4.0 / 3.0) * tw);
-    atomicAdd(&a.Q[aidx(a.g, 4, i2[0], i2[1], i2[2])], (-1.0 / 3.0) * tw);
+    atomicAdd(&Q[aidx(a.g, 4, i1[0], i1[1], i1[2])], (A)(4.0 / 3.0) * tw);
+    atomicAdd(&Q[aidx(a.g, 4, i2[0], i2[1], i2[2])], (A)(-1.0 / 3.0) * tw);
   }
 }
 

@@ -223,8 +223,7 @@ __device__ __forceinline__ void update_node_f64(const CavConst &C, const NodeF64
 // the exact FP64 maximum already reached cannot raise that maximum, so only
 // the few candidates are evaluated in FP64 (GB300's FP64 pipe is narrow) and
 // the maximum -- hence dt -- is exactly the FP64 one.
-__device__ __forceinline__ float spectral_est_f32(const CavConst &C, double u, double v, double w) {
-  const float uf = (float)u, vf = (float)v, wf = (float)w;
+__device__ __forceinline__ float spectral_est_f32(const CavConst &C, float uf, float vf, float wf) {
   const float b2 = fmaxf(__fmaf_rn(uf, uf, __fmaf_rn(vf, vf, __fmul_rn(wf, wf))), (float)C.b2min);
   const float f4 = __fmul_rn(4.f, b2);
   const float qx = __fmaf_rn(uf, uf, f4), qy = __fmaf_rn(vf, vf, f4), qz = __fmaf_rn(wf, wf, f4);
@@ -235,6 +234,9 @@ __device__ __forceinline__ float spectral_est_f32(const CavConst &C, double u, d
   const float sx = __fmaf_rn(qx, rx, fabsf(uf)), sy = __fmaf_rn(qy, ry, fabsf(vf)), sz = __fmaf_rn(qz, rz, fabsf(wf));
   return __fmaf_rn(0.5f, __fmaf_rn(sx, (float)C.ih[0], __fmaf_rn(sy, (float)C.ih[1], __fmul_rn(sz, (float)C.ih[2]))),
                    (float)C.diffsr);
+}
+__device__ __forceinline__ float spectral_est_f32(const CavConst &C, double u, double v, double w) {
+  return spectral_est_f32(C, (float)u, (float)v, (float)w);
 }
 
 // ---------------------------------------------------------------------------

@@ -74,7 +74,8 @@ struct AdjointStore {
   CavState final_cs{};
   int final_parity = 0;
   long long final_steps = 0;
-  double *X = nullptr, *Yt = nullptr, *Q = nullptr, *thetabar = nullptr, *scal = nullptr, *argpart = nullptr;
+  void *X = nullptr, *Yt = nullptr, *Q = nullptr;  // adjoint arrays: FP64 (FP64 forward) or FP32 (FP32-mixed)
+  double *thetabar = nullptr, *scal = nullptr, *argpart = nullptr;
   double *dts = nullptr;       // dt of every step (device)
   BlockDev *block = nullptr;   // descriptor of a segment slot (wall pass of FP32 states)
   bool have_forward = false;
@@ -845,6 +846,19 @@ int create_common(const cavity_desc *descs, const cavity_params *params, int n, 
 }  // namespace
 
 // ===========================================================================
+// the reverse of one step: state storage S, adjoint arrays and arithmetic Ad
+template <class S, class Ad>
+void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint, long long nfold) {
+  k_adj_objective<Ad><<<ceil_div((long long)a.g.ny * a.g.nz, 256), 256, 0, h->stream>>>(a);
+  k_adj_sum_p<Ad><<<nparts, 256, 0, h->stream>>>(a);
+  k_adj_prepare<Ad><<<ceil_div(5 * a.g.fs, 256), 256, 0, h->stream>>>(a);
+  k_adj_rates<S, Ad><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
+  k_adj_argmax<S><<<nparts, 256, 0, h->stream>>>(a);
+  k_adj_dt<S, Ad><<<1, kAdjDtThreads, 0, h->stream>>>(a, nparts);
+  k_adj_fold<Ad><<<ceil_div(nfold, 256), 256, 0, h->stream>>>(a);
+  k_adj_finish<<<1, 1, 0, h->stream>>>(a);
+}
+
 extern "C" {
 
 int cavity_default_params(cavity_params *p) {
@@ -1142,6 +1156,8 @@ int cavity_autotune(cavity_t *h, int steps, double out[5]) {
 int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
   if (!h || nsteps < 1 || ckpt < 1) return CAVITY_ERR_INVALID_ARG;
   if (h->local_dt) return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: global time stepping only");
+  if ((long long)h->descs[0].nx * h->descs[0].ny * h->descs[0].nz >= (1LL << 31))
+    return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: fewer than 2^31 interior nodes");
   if (h->ncav != 1 || h->nblocks != 1) return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: single-block cavity only");
   DeviceGuard g(h->dev);
   AdjointStore &A = h->adj;
@@ -1162,9 +1178,10 @@ int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
     CK(cudaMalloc(&A.ckpt_cs, sizeof(CavState) * ncp));
     CK(cudaMalloc(&A.seg_mem, set_bytes * ckpt));
     CK(cudaMalloc(&A.final_mem, set_bytes));
-    CK(cudaMalloc(&A.X, sizeof(double) * 5 * fs));
-    CK(cudaMalloc(&A.Yt, sizeof(double) * 5 * fs));
-    CK(cudaMalloc(&A.Q, sizeof(double) * 5 * fs));
+    const size_t abytes = (h->f32 ? sizeof(float) : sizeof(double)) * 5 * fs;
+    CK(cudaMalloc(&A.X, abytes));
+    CK(cudaMalloc(&A.Yt, abytes));
+    CK(cudaMalloc(&A.Q, abytes));
     CK(cudaMalloc(&A.thetabar, sizeof(double) * d.ny * d.nz));
     CK(cudaMalloc(&A.scal, sizeof(double) * kScCount));
     CK(cudaMalloc(&A.argpart, sizeof(double) * 2 * nparts));
@@ -1222,8 +1239,8 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
   a.argpart = A.argpart;
   a.coef = 1.0 / ((double)A.nsteps * d.ny * d.nz * 2.0 * a.C.h[0] * (p.t_hot - p.t_cold));
   a.dfloor = (h->u_ref_auto && p.Ra * p.Pr > 1.0) ? p.kappa * p.Pr : 0.0;
-  double *X = A.X, *Q = A.Q;
-  CK(cudaMemsetAsync(X, 0, sizeof(double) * 5 * a.g.fs, h->stream));
+  void *X = A.X, *Q = A.Q;
+  CK(cudaMemsetAsync(X, 0, (h->f32 ? sizeof(float) : sizeof(double)) * 5 * a.g.fs, h->stream));
   CK(cudaMemsetAsync(A.thetabar, 0, sizeof(double) * d.ny * d.nz, h->stream));
   CK(cudaMemsetAsync(A.scal, 0, sizeof(double) * kScCount, h->stream));
   const long long nint = (long long)d.nx * d.ny * d.nz;
@@ -1263,20 +1280,8 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
         k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(ba);
         CK(cudaGetLastError());
       }
-      k_adj_objective<<<ceil_div((long long)d.ny * d.nz, 256), 256, 0, h->stream>>>(a);
-      k_adj_sum_p<<<A.nparts, 256, 0, h->stream>>>(a);
-      k_adj_prepare<<<ceil_div(5 * a.g.fs, 256), 256, 0, h->stream>>>(a);
-      if (h->f32) {
-        k_adj_rates<float><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
-        k_adj_argmax<float><<<A.nparts, 256, 0, h->stream>>>(a);
-        k_adj_dt<float><<<1, 1, 0, h->stream>>>(a, A.nparts);
-      } else {
-        k_adj_rates<double><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
-        k_adj_argmax<double><<<A.nparts, 256, 0, h->stream>>>(a);
-        k_adj_dt<double><<<1, 1, 0, h->stream>>>(a, A.nparts);
-      }
-      k_adj_fold<<<ceil_div(nfold, 256), 256, 0, h->stream>>>(a);
-      k_adj_finish<<<1, 1, 0, h->stream>>>(a);
+      if (h->f32) launch_adjoint_step<float, float>(h, a, A.nparts, nint, nfold);
+      else launch_adjoint_step<double, double>(h, a, A.nparts, nint, nfold);
       if (cudaGetLastError() != cudaSuccess) { rc = fail(h, CAVITY_ERR_CUDA, "adjoint kernel launch failed"); break; }
       std::swap(X, Q);
     }
