@@ -303,6 +303,158 @@ __global__ void __launch_bounds__(256) k_adj_rates(AdjArgs a) {
   }
 }
 
+// Gather form of k_adj_rates for the FP32 sweep (FP32-mixed state): one
+// thread per node m of the padded arrays (walls and ghosts included) sums
+// what the interior nodes of its stencil would have scattered into it --
+// recomputing their coefficients from their velocities and Yt -- adds its
+// own centre terms when m is interior, and writes Q(m) once: no atomics.
+// Q(m) = Yt(m) + sum of incoming contributions (Yt is zero off the interior).
+__global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double dtbar = 0.0, gsbar = 0.0, floorbar = 0.0;
+  if (e < a.g.fs) {
+    const int i = (int)(e % a.g.ex) - 1, j = (int)((e / a.g.ex) % a.g.ey) - 1, k = (int)(e / (a.g.ex * a.g.ey)) - 1;
+    const CavConst &C = a.C;
+    const float *q = (const float *)a.B.base[0];
+    const long long fs = a.B.fstride;
+    const float *Yt = arr<float>(a.Yt);
+    const float dt = (float)a.dt;
+    const float ih[3] = {(float)C.ih[0], (float)C.ih[1], (float)C.ih[2]};
+    const float ih2[3] = {(float)C.ih2[0], (float)C.ih2[1], (float)C.ih2[2]};
+    const float ihh[3] = {(float)C.ihh[0], (float)C.ihh[1], (float)C.ihh[2]};
+    const float c4 = (float)C.c4, b2min = (float)C.b2min, Dq[5] = {0.f, (float)C.nu, (float)C.nu, (float)C.nu,
+                                                                      (float)C.alpha};
+    const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
+    auto interior = [&](int x, int y, int z) { return x >= 1 && x <= nn[0] && y >= 1 && y <= nn[1] && z >= 1 && z <= nn[2]; };
+    float out[5];
+    const bool inner = interior(i, j, k);
+    for (int f = 0; f < 5; ++f) out[f] = inner ? Yt[aidx(a.g, f, i, j, k)] : 0.f;
+    auto lambda = [&](float Vd, float b2) {
+      const float qd = Vd * Vd + 4.f * b2;
+      return 0.5f * (fabsf(Vd) + qd * rsqrtf(qd));
+    };
+    // Sources n = m + s e_d and m + 2 s e_d.  Every load is unconditional
+    // (at n when n is interior, else at m, which is always in range), so the
+    // loads issue together; a select drops the contributions of non-interior n.
+    const long long astr[3] = {1, a.g.ex, a.g.ex * a.g.ey};
+    const long long sstr[3] = {1, a.B.pitch, a.B.plane};
+    const long long om = node_index<float>(a.B, i, j, k);
+    const int xm[3] = {i, j, k};
+    for (int d = 0; d < 3; ++d) {
+      for (int s = -1; s <= 1; s += 2) {
+        // first neighbour: transport, pressure gradient, divergence, dissipation (-4 d4bar at n +- e_d)
+        {
+          const int c = xm[d] + s;
+          int x3[3] = {i, j, k};
+          x3[d] = c;
+          const bool in = interior(x3[0], x3[1], x3[2]);
+          const long long ea = in ? e + s * astr[d] : e, es = in ? om + s * sstr[d] : om;
+          const float V[3] = {q[2 * fs + es], q[3 * fs + es], q[4 * fs + es]};
+          const float b2 = fmaxf(V[0] * V[0] + V[1] * V[1] + V[2] * V[2], b2min);
+          float rb[5];
+          for (int f = 0; f < 5; ++f) rb[f] = dt * Yt[ea + f * a.g.fs];
+          const float ad = V[d] * ih2[d];
+          for (int f = 1; f <= 4; ++f) {
+            const float cf = rb[f] * (Dq[f] * ihh[d] + (float)s * ad);
+            out[f] += in ? cf : 0.f;
+          }
+          float c0 = (float)s * rb[1 + d] * ih2[d] + 4.f * rb[0] * c4 * lambda(V[d], b2) * ih[d];
+          float c1 = (float)s * b2 * rb[0] * ih2[d];  // -s divbar ih2, divbar = -b2 rb0
+          out[0] += in ? c0 : 0.f;
+          out[1 + d] += in ? c1 : 0.f;
+        }
+        // second neighbour: dissipation (d4bar at n +- 2 e_d), d4bar = -rb0 c4 lambda ih
+        {
+          int x3[3] = {i, j, k};
+          x3[d] = xm[d] + 2 * s;
+          const bool in = interior(x3[0], x3[1], x3[2]);
+          const long long ea = in ? e + 2 * s * astr[d] : e, es = in ? om + 2 * s * sstr[d] : om;
+          const float V[3] = {q[2 * fs + es], q[3 * fs + es], q[4 * fs + es]};
+          const float b2 = fmaxf(V[0] * V[0] + V[1] * V[1] + V[2] * V[2], b2min);
+          const float c0 = -dt * Yt[ea] * c4 * lambda(V[d], b2) * ih[d];
+          out[0] += in ? c0 : 0.f;
+        }
+      }
+    }
+    if (inner) {
+      // centre terms of m itself (the diagonal of the node's own reverse) and
+      // the node sums, as in k_adj_rates
+      AdjStencil<float> st_;
+      load_stencil<float, float>(a, i, j, k, st_);
+      const float *V = st_.V;
+      float b2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+      const bool floored = b2 < b2min;
+      if (floored) b2 = b2min;
+      float sq[3], isq[3], lam[3], d4[3], ad[3], divV = 0.f, diss = 0.f;
+      for (int d = 0; d < 3; ++d) {
+        const float qd = V[d] * V[d] + 4.f * b2;
+        isq[d] = rsqrtf(qd);
+        sq[d] = qd * isq[d];
+        lam[d] = 0.5f * (fabsf(V[d]) + sq[d]);
+        d4[d] = (st_.d2p[d] + st_.d2m[d]) - 4.f * (st_.dp[0][d] + st_.dm[0][d]);
+        ad[d] = V[d] * ih2[d];
+        divV += (st_.dp[1 + d][d] - st_.dm[1 + d][d]) * ih2[d];
+        diss += c4 * lam[d] * ih[d] * d4[d];
+      }
+      float Rf[5];
+      Rf[0] = -b2 * divV - diss;
+      for (int f = 1; f <= 4; ++f) {
+        float r = 0.f;
+        for (int d = 0; d < 3; ++d) r += (Dq[f] * ihh[d] - ad[d]) * st_.dp[f][d] + (Dq[f] * ihh[d] + ad[d]) * st_.dm[f][d];
+        if (f <= 3) {
+          const int cc = f - 1;
+          r += -(st_.dp[0][cc] - st_.dm[0][cc]) * ih2[cc];
+          if (cc == C.gaxis) r += (float)C.gs * st_.tb;
+        }
+        Rf[f] = r;
+      }
+      float yt[5], rb[5], dtb = 0.f;
+      for (int f = 0; f < 5; ++f) {
+        yt[f] = Yt[aidx(a.g, f, i, j, k)];
+        dtb += yt[f] * Rf[f];
+        rb[f] = dt * yt[f];
+      }
+      dtbar = (double)dtb;
+      float abar[3] = {0.f, 0.f, 0.f}, gsb = 0.f;
+      for (int f = 1; f <= 4; ++f) {
+        for (int d = 0; d < 3; ++d) {
+          out[f] += -2.f * rb[f] * Dq[f] * ihh[d];
+          abar[d] += -rb[f] * (st_.dp[f][d] - st_.dm[f][d]);
+        }
+        if (f <= 3 && f - 1 == C.gaxis) {
+          out[4] += (float)C.gs * rb[f];
+          gsb += st_.tb * rb[f];
+        }
+      }
+      gsbar = (double)gsb;
+      for (int d = 0; d < 3; ++d) out[1 + d] += abar[d] * ih2[d];
+      float b2bar = -divV * rb[0];
+      for (int d = 0; d < 3; ++d) {
+        const float lambar = -rb[0] * c4 * ih[d] * d4[d];
+        out[0] += 6.f * (-rb[0] * c4 * lam[d] * ih[d]);
+        const float sgn = V[d] > 0.f ? 1.f : (V[d] < 0.f ? -1.f : 0.f);
+        out[1 + d] += lambar * 0.5f * (sgn + V[d] * isq[d]);
+        b2bar += lambar * isq[d];
+      }
+      if (floored) {
+        floorbar = (double)b2bar;
+      } else {
+        for (int d = 0; d < 3; ++d) out[1 + d] += 2.f * V[d] * b2bar;
+      }
+    }
+    float *Q = arr<float>(a.Q);
+    for (int f = 0; f < 5; ++f) Q[aidx(a.g, f, i, j, k)] = out[f];
+  }
+  dtbar = warp_sum(dtbar);
+  gsbar = warp_sum(gsbar);
+  floorbar = warp_sum(floorbar);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&a.scal[kScDtbar], dtbar);
+    atomicAdd(&a.scal[kScGs], gsbar);
+    atomicAdd(&a.scal[kScFloor], floorbar);
+  }
+}
+
 // largest spectral bound of Q^n and its node (smallest linear index among
 // equal values: each thread visits its nodes in increasing index)
 template <class S>

@@ -852,7 +852,10 @@ void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint
   k_adj_objective<Ad><<<ceil_div((long long)a.g.ny * a.g.nz, 256), 256, 0, h->stream>>>(a);
   k_adj_sum_p<Ad><<<nparts, 256, 0, h->stream>>>(a);
   k_adj_prepare<Ad><<<ceil_div(5 * a.g.fs, 256), 256, 0, h->stream>>>(a);
-  k_adj_rates<S, Ad><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
+  if constexpr (std::is_same<Ad, float>::value)  // FP32 sweep: gather, no atomics
+    k_adj_gather<<<ceil_div(a.g.fs, 256), 256, 0, h->stream>>>(a);
+  else
+    k_adj_rates<S, Ad><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
   k_adj_argmax<S><<<nparts, 256, 0, h->stream>>>(a);
   k_adj_dt<S, Ad><<<1, kAdjDtThreads, 0, h->stream>>>(a, nparts);
   k_adj_fold<Ad><<<ceil_div(nfold, 256), 256, 0, h->stream>>>(a);
