@@ -57,7 +57,7 @@ L2_BYTES = 129e6
 WORKLOADS = {"cfg2": workloads.CFG2, "cfg3": workloads.CFG3}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--blocks", default=None, help="px,py,pz (default 2,2,2 for cfg2, 1,1,1 for cfg3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def measured_peaks():
@@ -139,6 +139,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(values, world: int, device: str) -> list[float]:
+    """Each of `values` maximised over the ranks: the slowest rank sets the
+    job's time (all ranks call this; 1 rank: unchanged)."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the (max) time."""
+    return units_per_rank * world / seconds
 
 
 def default_blocks(workload: str, blocks: str | None):
@@ -264,11 +281,8 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
             ms = sum(a.elapsed_time(b) for a, b in ev)
     barrier()
     rc = c.sync()
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    out = {"value": pts * steps * world / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+    ms, = max_over_ranks([ms], world, f"cuda:{local}")
+    out = {"value": job_value(pts * steps, world, ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
            "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
            "gpu_launches": launches_per_step * steps, "clocks": clk.summary(), "status": rc,
            "l2": ("L2 flushed (2 x L2 buffer written) before every timed step: the state fits in L2" if flush else
@@ -293,11 +307,8 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
         t1 = time.perf_counter()
         barrier()
         e2e_s = t1 - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=f"cuda:{local}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        out["e2e"] = {"value": pts * e2e_steps * world / e2e_s, "unit": UNIT, "steps": e2e_steps,
+        e2e_s, = max_over_ranks([e2e_s], world, f"cuda:{local}")
+        out["e2e"] = {"value": job_value(pts * e2e_steps, world, e2e_s), "unit": UNIT, "steps": e2e_steps,
                       "h2d_bytes_per_step": host0.nbytes / e2e_steps,
                       "d2h_bytes_per_step": res.nbytes / e2e_steps + 7 * 8}
     c.close()
@@ -329,12 +340,9 @@ def measure_batch(m, torch, steps, warmup, rank, world, local, stream):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     rc = m.cavity_sync(h)
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, = max_over_ranks([ms], world, f"cuda:{local}")
     m.cavity_destroy(h)
-    return {"value": pts * steps * world / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+    return {"value": job_value(pts * steps, world, ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
             "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
             "gpu_launches": 2 * steps, "clocks": clk.summary(), "status": rc, "autotune": tuned,
             "roofline": roofline_for("fp32", pts, kms[0], measured_peaks().get("hbm_gbs")),
@@ -372,12 +380,9 @@ def measure_adjoint(m, torch, rank, world, local, stream):
     rc = c.sync()
     c.close()
     fwd, bwd = t1 - t0, t2 - t1
-    if world > 1:
-        t = torch.tensor([fwd, bwd], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        fwd, bwd = float(t[0]), float(t[1])
+    fwd, bwd = max_over_ranks([fwd, bwd], world, f"cuda:{local}")
     steps = cfg["steps"]
-    return {"metric": "gradient point-steps/s (forward + reverse sweep)", "value": pts * steps * world / (fwd + bwd),
+    return {"metric": "gradient point-steps/s (forward + reverse sweep)", "value": job_value(pts * steps, world, fwd + bwd),
             "unit": "point-steps/s", "steps": steps, "checkpoint_every": cfg["ckpt"],
             "forward_ms_per_step": 1e3 * fwd / steps, "backward_ms_per_step": 1e3 * bwd / steps,
             "J": J, "dJ_dRa": gra, "grad_wall_norm": float(np.linalg.norm(g)), "clocks": clk.summary(), "status": rc,
