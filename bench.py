@@ -49,8 +49,7 @@ BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
 # capture of the same workload (profiles/k_step_f64_cavity128_2x2x2.md,
 # profiles/k_step_f32p_cavity256.md); None where no capture of the current
 # kernel exists
-TRAFFIC = {("fp64", "cfg2", (2, 2, 2)): 112.886016e6 + 54.552832e6,
-           ("fp32", "cfg3", (1, 1, 1)): 550.061824e6 + 435.558656e6}
+TRAFFIC = {("fp64", "cfg2", (2, 2, 2)): 112.886016e6 + 54.552832e6}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129e6
@@ -222,8 +221,9 @@ def roofline_for(precision, pts, step_ms, hbm, traffic=None):
     hbm_obj = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if hbm else None,
                "bytes_per_point": bpp, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if precision == "fp32":
-        return dict(kernel="k_step_f32p (TMA-staged fused residual + update + partials; two nodes per thread, "
-                           "f32x2)", traffic=traffic, kernel_ms=step_ms, **hbm_obj)
+        return dict(kernel="k_step_f32q (TMA-staged fused residual + update + partials; two nodes per thread, "
+                           "f32x2, z neighbours below the plane in registers)", traffic=traffic, kernel_ms=step_ms,
+                    **hbm_obj)
     tf = FP64_FLOP_PER_POINT * pts / step_s / 1e12
     return {"kernel": "k_step_f64 (fused residual + update + reductions)", "bound": "alu", "achieved": tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,

@@ -206,9 +206,11 @@ CAVITY_API int cavity_batch_get_fields(cavity_t *h, int cav, int field_mask, dou
  * steps on this handle's own cavities and keeps the fastest.  The state is
  * saved before the trials and restored after them (the step counter and the
  * fields are as before the call).  out (optional) receives the chosen tile
- * height, z-chunk, ring depth, nodes per thread along x (1 or 2) and
- * microseconds per step.  Every shape gives the same fields.  FP64 handles
- * have a single shape: CAVITY_ERR_UNSUPPORTED. */
+ * height, z-chunk, ring depth, kernel form (1: one node per thread; 2: two
+ * nodes, z neighbours from the shared-memory ring; 3: two nodes, the z
+ * neighbours below the plane in registers) and microseconds per step.  Every
+ * shape gives the same fields.  FP64 handles have a single shape:
+ * CAVITY_ERR_UNSUPPORTED. */
 CAVITY_API int cavity_autotune(cavity_t *h, int steps, double out[5]);
 
 /* Discrete adjoint, part 1: from the current state run nsteps steps and

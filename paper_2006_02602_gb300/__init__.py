@@ -322,7 +322,7 @@ def cavity_batch_get_fields(h, cav: int, shape, mask: int = CAVITY_FIELD_ALL) ->
 def cavity_autotune(h, steps: int = 20) -> dict:
     out = np.zeros(5)
     _check(load_library().cavity_autotune(h, int(steps), out.ctypes.data_as(_dp)), h)
-    return {"tile_y": int(out[0]), "kc": int(out[1]), "ring": int(out[2]), "nodes_per_thread": int(out[3]),
+    return {"tile_y": int(out[0]), "kc": int(out[1]), "ring": int(out[2]), "kernel_form": int(out[3]),
             "us_per_step": out[4]}
 
 

@@ -30,7 +30,7 @@
 
 namespace bdc {
 
-constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 32, kF32R = 8, kF32P = 2;  // default shape: tile height, z chunk, ring depth, nodes per thread
+constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 32, kF32R = 5, kF32P = 3;  // default shape: tile height, z chunk, ring depth, nodes per thread
 constexpr int kF32BX = kF32TX + 8;  // x halo 4 on each side: the box starts on a 16-byte boundary
 constexpr int kF32NA = 7;           // p_hi, p_lo, u, v, w, T_hi, T_lo
 __host__ __device__ constexpr int f32_box_y(int TY) { return TY + 4; }  // y halo 2 (pressure star)
@@ -842,6 +842,246 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
     bad = __syncthreads_or(bad);
     if (!bad && tid == 0 && issued < T.nplanes) {
       // the slot of plane pk - 2 is free: refill it with the next plane
+      issue(issued);
+      ++issued;
+    }
+  }
+  if (bad) {
+    if (tid == 0) {
+      atomicOr(&a.cs[B.cav].flags, 2);
+      for (int pl = max(0, issued - R); pl < issued; ++pl) (void)wait_plane(pl);
+    }
+    __syncthreads();
+  }
+  double nuh = 0.0, nuc = 0.0;
+  if (nus) {
+    const double t0 = pair_value(ch.x, cl.x), t1 = act1 ? pair_value(ch.y, cl.y) : 0.0;
+    const double wall_t = 3.0 * pair_value(wsh, wsl);
+    nuh = wh0 * t0 + wh1 * t1 + (hot_next ? wall_t : 0.0);
+    nuc = wc0 * t0 + wc1 * t1 + (cold_next0 || cold_next1 ? wall_t : 0.0);
+  }
+  f32_partials<NT>(a.partials, cta, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
+                   vadd(s4.x, s4.y), smax, nuh, nuc);
+}
+
+// Two nodes per thread as k_step_f32p, with the pair's z - 1 values (all
+// seven arrays) and p's z - 2 values carried in registers from the previous
+// planes: only planes k .. k+2 stay resident, so a ring of R = 5 slots keeps
+// two planes in flight in 67 KB and three CTAs share an SM (12 warps instead
+// of 8).  Slots are indexed modulo R.
+template <int TY, int KC, int R>
+__global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_step_f32q(StepF32Args a) {
+  static_assert(R >= 4, "ring depth: three planes resident and at least one in flight");
+  constexpr int NTX = kF32TX / 2, NT = NTX * TY;
+  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;
+  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float *ring = reinterpret_cast<float *>(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
+
+  const int cta = blockIdx.x;
+  const F32Tile T = f32_tile<TY, KC>(a, cta);
+  const BlockDev &B = a.blocks[T.b];
+  const CavConst &C = a.cc[B.cav];
+  const int k0 = T.k0, k1 = T.k1;
+  const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
+  const int i = T.i0 + 2 * li, j = T.j0 + lj;
+  const bool act0 = (i <= B.nx) && (j <= B.ny), act1 = (i + 1 <= B.nx) && (j <= B.ny);
+  // Nusselt sums of the new state: weights of the two columns in 3 T_w - 4 T_1 + T_2
+  const bool xw0 = B.wall[0], xw1 = B.wall[1];
+  const double wh0 = (xw0 && act0) ? (i == 1 ? -4.0 : (i == 2 ? 1.0 : 0.0)) : 0.0;
+  const double wh1 = (xw0 && act1) ? (i + 1 == 2 ? 1.0 : 0.0) : 0.0;
+  const double wc0 = (xw1 && act0) ? (i == B.nx ? -4.0 : (i == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
+  const double wc1 = (xw1 && act1) ? (i + 1 == B.nx ? -4.0 : (i + 1 == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
+  const bool nus = wh0 != 0.0 || wh1 != 0.0 || wc0 != 0.0 || wc1 != 0.0;
+  // the column beside a wall: node i next to x = 0 or x = nx + 1, or node i + 1 next to x = nx + 1
+  const bool hot_next = xw0 && act0 && i == 1, cold_next0 = xw1 && act0 && i == B.nx;
+  const bool cold_next1 = xw1 && act1 && i + 1 == B.nx;
+  const int wofs = hot_next ? -1 : (cold_next0 ? 1 : 2);
+  const bool nus_warp = __any_sync(0xffffffffu, nus);
+  float2 ch = make_float2(0.f, 0.f), cl = ch;
+  float wsh = 0.f, wsl = 0.f;
+  const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
+
+  if (tid == 0) {
+    for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+  }
+  __syncthreads();
+  int issued = 0;
+  auto issue = [&](int pl) {
+    const int s = pl % R;
+    mbar_expect_tx(&bars[s], SB);
+    tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
+  };
+  if (tid == 0) {
+    for (; issued < min(R, T.nplanes); ++issued) issue(issued);
+  }
+  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl % R], (uint32_t)((pl / R) & 1)); };
+  auto slot = [&](int pl) { return ring + (pl % R) * SF; };
+  const int col = (lj + 2) * BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
+
+  const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
+  const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
+  const long long fs = B.fstride, plane = B.plane;
+  const int nz = B.nz;
+  // i is odd, so the pair starts on an 8-byte boundary of the row
+  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
+
+  bool bad = false;
+  // prologue: planes k0-2 .. k0+1; the x and y walls of the interior planes;
+  // the register queues (z - 1: seven arrays of plane k0-1; z - 2: p of plane k0-2)
+  float2 qm1[7], qm2h = make_float2(0.f, 0.f), qm2l = qm2h;
+  for (int q = 0; q < 7; ++q) qm1[q] = qm2h;
+  for (int pl = 0; pl < 4; ++pl) {
+    if (!bad && !wait_plane(pl)) bad = true;
+    if (!bad && T.fix && pl >= 2) fix_plane_walls<NT, BY>(slot(pl), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+    if (!bad && act0 && pl == 0) {
+      qm2h = ld2(slot(0), col);
+      qm2l = ld2(slot(0) + AS, col);
+    }
+    if (!bad && act0 && pl == 1)
+      for (int q = 0; q < 7; ++q) qm1[q] = ld2(slot(1) + q * AS, col);
+  }
+  float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
+  float smax = 0.f;
+  bad = __syncthreads_or(bad);
+  if (!bad && tid == 0) {
+    // the slots of planes 0 and 1 are free again
+    for (; issued < min(R + 2, T.nplanes); ++issued) issue(issued);
+  }
+
+  for (int k = k0; k <= k1 && !bad; ++k) {
+    const int pk = k - k0 + 2;  // plane index of k
+    if (!wait_plane(pk + 2)) bad = true;
+    if (!bad) {
+      if (T.fix) fix_plane_walls<NT, BY>(slot(pk + 2), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+      if (act0) {
+        const float *S0 = slot(pk), *Sp1 = slot(pk + 1), *Sp2 = slot(pk + 2);
+        F32Nb<float2> n;
+        // pressure: centre pair and its z neighbours (walls formed in place)
+        n.ph = ld2(S0, col);
+        n.pl = ld2(S0 + AS, col);
+        float2 zm2h = qm2h, zm2l = qm2l, zm1h = qm1[0], zm1l = qm1[1];
+        float2 zp1h = ld2(Sp1, col), zp1l = ld2(Sp1 + AS, col), zp2h = ld2(Sp2, col), zp2l = ld2(Sp2 + AS, col);
+        float2 th = ld2(S0 + 5 * AS, col), tl = ld2(S0 + 6 * AS, col);
+        float2 tzmh = qm1[5], tzml = qm1[6];
+        float2 tzph = ld2(Sp1 + 5 * AS, col), tzpl = ld2(Sp1 + 6 * AS, col);
+        if (T.wzl && k <= 2) {
+          float hg, lg;
+          if (k == 1) {  // z = 0 wall and z = -1 ghost from the layers z = 1, 2
+            wall_pressure(n.ph.x, n.pl.x, zp1h.x, zp1l.x, zm1h.x, zm1l.x, zm2h.x, zm2l.x);
+            wall_pressure(n.ph.y, n.pl.y, zp1h.y, zp1l.y, zm1h.y, zm1l.y, zm2h.y, zm2l.y);
+            wall_temperature(th.x, tl.x, tzph.x, tzpl.x, tzmh.x, tzml.x);
+            wall_temperature(th.y, tl.y, tzph.y, tzpl.y, tzmh.y, tzml.y);
+          } else {  // k == 2: z = 0 wall from z = 1, 2
+            wall_pressure(zm1h.x, zm1l.x, n.ph.x, n.pl.x, zm2h.x, zm2l.x, hg, lg);
+            wall_pressure(zm1h.y, zm1l.y, n.ph.y, n.pl.y, zm2h.y, zm2l.y, hg, lg);
+          }
+        }
+        if (T.wzh && k >= nz - 1) {
+          float hg, lg;
+          if (k == nz) {  // z = nz+1 wall and nz+2 ghost from the layers nz, nz-1
+            wall_pressure(n.ph.x, n.pl.x, zm1h.x, zm1l.x, zp1h.x, zp1l.x, zp2h.x, zp2l.x);
+            wall_pressure(n.ph.y, n.pl.y, zm1h.y, zm1l.y, zp1h.y, zp1l.y, zp2h.y, zp2l.y);
+            wall_temperature(th.x, tl.x, tzmh.x, tzml.x, tzph.x, tzpl.x);
+            wall_temperature(th.y, tl.y, tzmh.y, tzml.y, tzph.y, tzpl.y);
+          } else {  // k == nz-1: z = nz+1 wall from nz, nz-1
+            wall_pressure(zp1h.x, zp1l.x, n.ph.x, n.pl.x, zp2h.x, zp2l.x, hg, lg);
+            wall_pressure(zp1h.y, zp1l.y, n.ph.y, n.pl.y, zp2h.y, zp2l.y, hg, lg);
+          }
+        }
+        n.pzp1 = pdiff(zp1h, zp1l, n.ph, n.pl);
+        n.pzm1 = pdiff(zm1h, zm1l, n.ph, n.pl);
+        n.pzp2 = pdiff(zp2h, zp2l, n.ph, n.pl);
+        n.pzm2 = pdiff(zm2h, zm2l, n.ph, n.pl);
+        {
+          const float *H = S0, *L = S0 + AS;
+          const float2 ah = ld2(H, col - 2), al = ld2(L, col - 2), dh = ld2(H, col + 2), dl = ld2(L, col + 2);
+          n.pxp1 = make_float2(pdiff(n.ph.y, n.pl.y, n.ph.x, n.pl.x), pdiff(dh.x, dl.x, n.ph.y, n.pl.y));
+          n.pxm1 = make_float2(pdiff(ah.y, al.y, n.ph.x, n.pl.x), pdiff(n.ph.x, n.pl.x, n.ph.y, n.pl.y));
+          n.pxp2 = pdiff(dh, dl, n.ph, n.pl);
+          n.pxm2 = pdiff(ah, al, n.ph, n.pl);
+          n.pyp1 = pdiff(ld2(H, col + BX), ld2(L, col + BX), n.ph, n.pl);
+          n.pym1 = pdiff(ld2(H, col - BX), ld2(L, col - BX), n.ph, n.pl);
+          n.pyp2 = pdiff(ld2(H, col + 2 * BX), ld2(L, col + 2 * BX), n.ph, n.pl);
+          n.pym2 = pdiff(ld2(H, col - 2 * BX), ld2(L, col - 2 * BX), n.ph, n.pl);
+        }
+        // velocity: x differences per node, y and z packed
+#define BDC_F32Q_VEL(F, c0, xp, xm, yp, ym, zp, zm)                                                  \
+  {                                                                                                \
+    const float *Q = S0 + F * AS;                                                                  \
+    c0 = ld2(Q, col);                                                                              \
+    const float qm = Q[col - 1], qp = Q[col + 2];                                                  \
+    xp = make_float2(vsub(c0.y, c0.x), vsub(qp, c0.y));                                            \
+    xm = make_float2(vsub(qm, c0.x), vsub(c0.x, c0.y));                                            \
+    yp = vsub(ld2(Q, col + BX), c0);                                                               \
+    ym = vsub(ld2(Q, col - BX), c0);                                                               \
+    zp = vsub(ld2(Sp1 + F * AS, col), c0);                                                         \
+    zm = vsub(qm1[F], c0);                                                         \
+  }
+        BDC_F32Q_VEL(2, n.u, n.uxp, n.uxm, n.uyp, n.uym, n.uzp, n.uzm)
+        BDC_F32Q_VEL(3, n.v, n.vxp, n.vxm, n.vyp, n.vym, n.vzp, n.vzm)
+        BDC_F32Q_VEL(4, n.w, n.wxp, n.wxm, n.wyp, n.wym, n.wzp, n.wzm)
+#undef BDC_F32Q_VEL
+        // temperature pair
+        n.th = th;
+        n.tl = tl;
+        {
+          const float *TH = S0 + 5 * AS, *TL = S0 + 6 * AS;
+          n.txp = make_float2(pdiff(th.y, tl.y, th.x, tl.x), pdiff(TH[col + 2], TL[col + 2], th.y, tl.y));
+          n.txm = make_float2(pdiff(TH[col - 1], TL[col - 1], th.x, tl.x), pdiff(th.x, tl.x, th.y, tl.y));
+          n.typ = pdiff(ld2(TH, col + BX), ld2(TL, col + BX), th, tl);
+          n.tym = pdiff(ld2(TH, col - BX), ld2(TL, col - BX), th, tl);
+          n.tzp = pdiff(tzph, tzpl, th, tl);
+          n.tzm = pdiff(tzmh, tzml, th, tl);
+        }
+        F32Out<float2> o;
+        float2 dtn = K.dt, mdtn = K.mdt;
+        if (a.local_dt) {  // each node's own stable step
+          dtn = make_float2(__fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.x, n.v.x, n.w.x)),
+                            __fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.y, n.v.y, n.w.y)));
+          mdtn = make_float2(-dtn.x, -dtn.y);
+        }
+        f32_update(K, n, dtn, mdtn, o);
+        const float2 bound = f32_spectral_bound(K, o.u, o.v, o.w);
+        f32_spectral_max(K1, bound.x, o.u.x, o.v.x, o.w.x, smax);
+        if (act1) {
+          st2(out, o.ph);
+          st2(out + fs, o.pl);
+          st2(out + 2 * fs, o.u);
+          st2(out + 3 * fs, o.v);
+          st2(out + 4 * fs, o.w);
+          st2(out + 5 * fs, o.th);
+          st2(out + 6 * fs, o.tl);
+          f32_spectral_max(K1, bound.y, o.u.y, o.v.y, o.w.y, smax);
+        } else {  // the x extent is odd: the pair's second node is a wall or beyond
+          out[0] = o.ph.x;
+          out[fs] = o.pl.x;
+          out[2 * fs] = o.u.x;
+          out[3 * fs] = o.v.x;
+          out[4 * fs] = o.w.x;
+          out[5 * fs] = o.th.x;
+          out[6 * fs] = o.tl.x;
+          o.rp.y = o.ru.y = o.rv.y = o.rw.y = o.rt.y = 0.f;
+        }
+        s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
+        s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
+        if (nus_warp) {
+          acc_pair(ch, cl, o.th, o.tl);
+          acc_pair(wsh, wsl, S0[5 * AS + col + wofs], S0[6 * AS + col + wofs]);
+        }
+        // the register queues move one plane: z - 2 <- z - 1 (p), z - 1 <- this plane
+        qm2h = qm1[0];
+        qm2l = qm1[1];
+        qm1[0] = n.ph; qm1[1] = n.pl; qm1[2] = n.u; qm1[3] = n.v; qm1[4] = n.w; qm1[5] = th; qm1[6] = tl;
+      }
+      out += plane;
+    }
+    bad = __syncthreads_or(bad);
+    if (!bad && tid == 0 && issued < T.nplanes) {
+      // the slot of plane pk is free: refill it with the next plane
       issue(issued);
       ++issued;
     }

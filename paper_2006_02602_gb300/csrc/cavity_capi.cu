@@ -41,11 +41,13 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// FP32 step-kernel shapes compiled in: (nodes per thread along x P, tile
-// height TY, z chunk KC, ring depth R); P = 1 is k_step_f32, P = 2 k_step_f32p
+// FP32 step-kernel shapes compiled in: (kernel form P, tile height TY, z
+// chunk KC, ring depth R); P = 1 is k_step_f32 (one node per thread), P = 2
+// k_step_f32p (two, z neighbours from the ring), P = 3 k_step_f32q (two, z
+// neighbours below the plane in registers)
 #define BDC_F32_VARIANTS(X)                                                                       \
   X(1, 8, 16, 8) X(1, 8, 32, 8) X(1, 8, 64, 8) X(1, 4, 32, 8) X(1, 4, 64, 8) X(2, 8, 32, 8) X(2, 8, 64, 8) \
-      X(2, 16, 32, 8) X(2, 16, 64, 8)
+      X(2, 16, 32, 8) X(2, 16, 64, 8) X(3, 8, 16, 5) X(3, 8, 24, 5) X(3, 8, 32, 5) X(3, 8, 64, 5) X(3, 8, 32, 6)
 struct F32Shape {
   int p, ty, kc, r;
 };
@@ -370,7 +372,8 @@ int encode_maps(cavity *h) {
 template <int P, int TY, int KC, int R>
 auto f32_kernel() {
   if constexpr (P == 1) return k_step_f32<TY, KC, R>;
-  else return k_step_f32p<TY, KC, R>;
+  else if constexpr (P == 2) return k_step_f32p<TY, KC, R>;
+  else return k_step_f32q<TY, KC, R>;
 }
 
 cudaError_t f32_set_smem(int p, int ty, int kc, int r) {
@@ -501,7 +504,8 @@ void launch_step_kernel(cavity *h, int parity) {
   if (h->f32) {
 #define BDC_LAUNCH(P, TY, KC, R)                                                                           \
   if (h->f32_p == P && h->ty == TY && h->kc == KC && h->f32_r == R)                                        \
-    f32_kernel<P, TY, KC, R>()<<<h->n_step, dim3(kF32TX / P, TY), f32_smem_bytes(TY, R), h->stream>>>(     \
+    f32_kernel<P, TY, KC, R>()<<<h->n_step, dim3(P == 1 ? kF32TX : kF32TX / 2, TY), f32_smem_bytes(TY, R),    \
+                                 h->stream>>>(                                                              \
         step_f32_args(h, parity));
     BDC_F32_VARIANTS(BDC_LAUNCH)
 #undef BDC_LAUNCH

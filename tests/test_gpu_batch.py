@@ -103,8 +103,8 @@ def test_autotune_restores_state_and_keeps_fields(m):
         m.cavity_step(ref, 3)
         before = [m.cavity_batch_get_fields(h, b, s) for b, s in enumerate(sizes)]
         choice = m.cavity_autotune(h, 5)
-        assert choice["tile_y"] in (4, 8, 16) and choice["kc"] in (16, 32, 64) and choice["us_per_step"] > 0
-        assert choice["nodes_per_thread"] in (1, 2)
+        assert choice["tile_y"] in (4, 8, 16) and choice["kc"] in (16, 24, 32, 64) and choice["us_per_step"] > 0
+        assert choice["kernel_form"] in (1, 2, 3)
         for b, s in enumerate(sizes):
             assert np.array_equal(m.cavity_batch_get_fields(h, b, s), before[b])
             assert m.cavity_batch_state(h, b)["step"] == 3
@@ -123,7 +123,8 @@ def test_fp32_tile_shapes_give_identical_fields(m, monkeypatch):
     pair, and the z chunks put chunk edges next to both z walls."""
     n = (45, 38, 70)
     out = []
-    for shape in ("8,16,8", "8,64,8", "4,32,8", "8,32,8,2", "8,64,8,2", "16,32,8,2"):
+    for shape in ("8,16,8", "8,64,8", "4,32,8", "8,32,8,2", "8,64,8,2", "16,32,8,2", "8,32,5,3", "8,64,5,3",
+                  "8,32,6,3"):
         monkeypatch.setenv("BDC_F32_TILE", shape)
         with m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=4, noise_amp=1e-3, Ra=2e5) as c:
             c.step(40)
