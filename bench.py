@@ -254,6 +254,7 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
         if world > 1:
             torch.distributed.barrier()
 
+    tuned = m.cavity_autotune(c.h, 10) if precision == "fp32" else None  # FP32: the autotuner picks the shape
     c.step(warmup)
     c.sync()
     kms = m.cavity_time_kernels(c.h, 20)
@@ -284,7 +285,7 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
     ms, = max_over_ranks([ms], world, f"cuda:{local}")
     out = {"value": job_value(pts * steps, world, ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
            "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
-           "gpu_launches": launches_per_step * steps, "clocks": clk.summary(), "status": rc,
+           "gpu_launches": launches_per_step * steps, "clocks": clk.summary(), "status": rc, "autotune": tuned,
            "l2": ("L2 flushed (2 x L2 buffer written) before every timed step: the state fits in L2" if flush else
                   f"no flush: the two state buffers ({both_buffers / 1e6:.0f} MB) exceed the 129 MB L2"),
            "roofline": roofline_for(precision, pts, kms[0], measured_peaks().get("hbm_gbs"),
@@ -417,6 +418,8 @@ def run_ours(args):
         "kernel_ms": r["kernel_ms"], "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
         "roofline": r["roofline"], "clocks": r["clocks"], "status": r["status"],
     }
+    if r.get("autotune"):
+        line["autotune"] = r["autotune"]
     if not args.no_variants and args.workload == "cfg2" and args.precision == "fp64":
         variants = {}
         for name, prec, wl, blk, steps in (("fp32_mixed_cfg2", "fp32", "cfg2", (2, 2, 2), min(args.steps, 500)),
