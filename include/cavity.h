@@ -209,7 +209,9 @@ CAVITY_API int cavity_batch_get_fields(cavity_t *h, int cav, int field_mask, dou
  * height, z-chunk, ring depth, kernel form (1: one node per thread; 2: two
  * nodes, z neighbours from the shared-memory ring; 3: two nodes, the z
  * neighbours below the plane in registers) and microseconds per step.  Every
- * shape gives the same fields.  FP64 handles have a single shape:
+ * shape gives the same fields.  With the environment variable BDC_F32_TILE
+ * ("TY,KC,R,form", a compiled shape, read at creation) the shape is pinned and
+ * no trials run (out[4] = 0).  FP64 handles have a single shape:
  * CAVITY_ERR_UNSUPPORTED. */
 CAVITY_API int cavity_autotune(cavity_t *h, int steps, double out[5]);
 

@@ -1104,6 +1104,16 @@ int cavity_autotune(cavity_t *h, int steps, double out[5]) {
   if (!h->f32) return fail(h, CAVITY_ERR_UNSUPPORTED, "the FP64 form has one tile shape");
   DeviceGuard g(h->dev);
   CK(cudaStreamSynchronize(h->stream));
+  if (std::getenv("BDC_F32_TILE")) {  // a pinned shape (set at creation): no trials
+    if (out) {
+      out[0] = h->ty;
+      out[1] = h->kc;
+      out[2] = h->f32_r;
+      out[3] = h->f32_p;
+      out[4] = 0.0;
+    }
+    return CAVITY_OK;
+  }
   // save the state (fields, per-cavity scalars, ping-pong parity, step count)
   void *backup = nullptr;
   CK(cudaMalloc(&backup, h->field_bytes));
