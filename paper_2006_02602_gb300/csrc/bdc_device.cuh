@@ -604,6 +604,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   __shared__ double shc[8];
   __shared__ bool am_last;
   static_assert(kFinSlices * 8 <= kFinThreads, "one slice total per thread");
+  // the next step kernel (a programmatic dependent) may start its prologue now;
+  // it waits for this grid's completion before it reads the state advanced here
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int cav = blockIdx.x / kFinSlices, g = blockIdx.x % kFinSlices, tid = threadIdx.x;
   const CavConst &C = a.cc[cav];
   const long long nt = C.tile_end - C.tile_begin, nb = a.mode == 4 ? 0 : C.bc_end - C.bc_begin;

@@ -482,7 +482,6 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
   const int col = (lj + 2) * BX + (li + 4);  // own column inside a slot
 
-  const F32K<float> K = f32_consts<float>(C, a.cs[B.cav]);
   const long long fs = B.fstride, plane = B.plane;
   const int nz = B.nz;
   // output pointer of this thread's node at plane k0 (advanced one plane per k)
@@ -520,6 +519,11 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   }
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f, smax = 0.f;
   bad = __syncthreads_or(bad);
+  // a programmatic dependent of the previous step's finalise: only now are its
+  // dt, centre shift and reads of the partials complete (nothing global was
+  // read from the state it writes, nor written, before this point)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const F32K<float> K = f32_consts<float>(C, a.cs[B.cav]);
   if (!bad && tid == 0) {
     // slots of planes 0 and 1 are free again
     for (; issued < min(R + 2, T.nplanes); ++issued) issue(issued);
@@ -698,8 +702,6 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
   auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
   const int col = (lj + 2) * BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
 
-  const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
-  const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
   const long long fs = B.fstride, plane = B.plane;
   const int nz = B.nz;
   // i is odd, so the pair starts on an 8-byte boundary of the row
@@ -714,6 +716,12 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
   float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
   float smax = 0.f;
   bad = __syncthreads_or(bad);
+  // a programmatic dependent of the previous step's finalise: only now are its
+  // dt, centre shift and reads of the partials complete (nothing global was
+  // read from the state it writes, nor written, before this point)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
+  const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
 
   for (int k = k0; k <= k1 && !bad; ++k) {
     const int pk = k - k0 + 2;  // plane index of k
@@ -922,8 +930,6 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
   auto slot = [&](int pl) { return ring + (pl % R) * SF; };
   const int col = (lj + 2) * BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
 
-  const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
-  const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
   const long long fs = B.fstride, plane = B.plane;
   const int nz = B.nz;
   // i is odd, so the pair starts on an 8-byte boundary of the row
@@ -947,6 +953,12 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
   float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
   float smax = 0.f;
   bad = __syncthreads_or(bad);
+  // a programmatic dependent of the previous step's finalise: only now are its
+  // dt, centre shift and reads of the partials complete (nothing global was
+  // read from the state it writes, nor written, before this point)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
+  const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
   if (!bad && tid == 0) {
     // the slots of planes 0 and 1 are free again
     for (; issued < min(R + 2, T.nplanes); ++issued) issue(issued);

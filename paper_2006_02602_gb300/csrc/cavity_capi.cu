@@ -136,7 +136,8 @@ struct cavity {
 
   int parity = 0;
   long long steps_taken = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step from parity 0 / 1
+  cudaGraphExec_t graph2[2] = {nullptr, nullptr};  // two steps from parity 0 / 1 (programmatic edge between them)
   std::string err;
 };
 
@@ -501,13 +502,31 @@ ExchArgs exch_args(cavity *h, int parity) {
   return a;
 }
 
-void launch_step_kernel(cavity *h, int parity) {
+// `after_finalise`: the launch directly follows, in the same stream capture,
+// the finalise of the previous step (the second step of a two-step graph with
+// no cut faces).  The FP32 step kernel is then launched as a programmatic
+// dependent: its prologue (TMA loads of the state, which the previous step
+// kernel completed before that finalise started) overlaps the finalise, and it
+// waits for the finalise before reading dt and the centre shift.  Every other
+// predecessor (an unpack writing ghost layers, a state upload, a copy) gets a
+// plain launch.
+void launch_step_kernel(cavity *h, int parity, bool after_finalise = false) {
   if (h->f32) {
-#define BDC_LAUNCH(P, TY, KC, R)                                                                           \
-  if (h->f32_p == P && h->ty == TY && h->kc == KC && h->f32_r == R)                                        \
-    f32_kernel<P, TY, KC, R>()<<<h->n_step, dim3(P == 1 ? kF32TX : kF32TX / 2, TY), f32_smem_bytes(TY, R),    \
-                                 h->stream>>>(                                                              \
-        step_f32_args(h, parity));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->n_step);
+    cfg.stream = h->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_finalise && h->n_cut == 0 ? 1 : 0;
+    const StepF32Args sa = step_f32_args(h, parity);
+#define BDC_LAUNCH(P, TY, KC, R)                                                 \
+  if (h->f32_p == P && h->ty == TY && h->kc == KC && h->f32_r == R) {             \
+    cfg.blockDim = dim3(P == 1 ? kF32TX : kF32TX / 2, TY);                        \
+    cfg.dynamicSmemBytes = f32_smem_bytes(TY, R);                                 \
+    cudaLaunchKernelEx(&cfg, f32_kernel<P, TY, KC, R>(), sa);                     \
+  }
     BDC_F32_VARIANTS(BDC_LAUNCH)
 #undef BDC_LAUNCH
   } else {
@@ -599,9 +618,9 @@ int launch_step_overlapped(cavity *h, int parity) {
 }
 
 // one explicit step reading buffer set `parity`, leaving the new state in parity ^ 1
-int launch_step(cavity *h, int parity) {
+int launch_step(cavity *h, int parity, bool after_finalise = false) {
   if (h->overlap) return launch_step_overlapped(h, parity);
-  launch_step_kernel(h, parity);
+  launch_step_kernel(h, parity, after_finalise);
   CK(cudaGetLastError());
   launch_bc_kernel(h, parity ^ 1, 0);
   CK(cudaGetLastError());
@@ -620,6 +639,8 @@ int refresh_state(cavity *h) {
 void drop_graphs(cavity *h) {
   for (auto &g : h->graph)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  for (auto &g : h->graph2)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
 int build_graphs(cavity *h) {
@@ -632,6 +653,18 @@ int build_graphs(cavity *h) {
     if (rc != CAVITY_OK) { if (g) cudaGraphDestroy(g); return rc; }
     CK(e);
     const cudaError_t e2 = cudaGraphInstantiate(&h->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    CK(e2);
+  }
+  for (int par = 0; par < 2; ++par) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(h, par);
+    if (rc == CAVITY_OK) rc = launch_step(h, par ^ 1, true);
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc != CAVITY_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    CK(e);
+    const cudaError_t e2 = cudaGraphInstantiate(&h->graph2[par], g, 0);
     cudaGraphDestroy(g);
     CK(e2);
   }
@@ -919,7 +952,12 @@ int cavity_set_wall_temperature(cavity_t *h, int wall, const double *host, size_
 int cavity_step(cavity_t *h, int nsteps) {
   if (!h || nsteps < 0) return CAVITY_ERR_INVALID_ARG;
   DeviceGuard g(h->dev);
-  for (int s = 0; s < nsteps; ++s) {
+  int s = 0;
+  for (; s + 2 <= nsteps; s += 2) {  // two steps per graph: the parity comes back
+    CK(cudaGraphLaunch(h->graph2[h->parity], h->stream));
+    h->steps_taken += 2;
+  }
+  if (s < nsteps) {
     CK(cudaGraphLaunch(h->graph[h->parity], h->stream));
     h->parity ^= 1;
     h->steps_taken += 1;
