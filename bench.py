@@ -39,8 +39,11 @@ METRIC = "grid-point updates/s per step"
 UNIT = "point-updates/s"
 # FP64 operations per interior point of the fused FP64 step (adds, multiplies,
 # compares = 1, FMA = 2, sqrt = 1), counted on the kernel's formulation: rates
-# 166, update 11, residual sums 10, spectral radius of the new state 25
-FP64_FLOP_PER_POINT = 212
+# 144 (beta^2 7, dissipation weights 15, fourth differences 18, dissipation 5,
+# divergence 8, continuity 2, advection-diffusion weights 24, u 16, v 17, w 17,
+# T 13, buoyancy 2), update 11, residual sums 10, spectral radius of the new
+# state 25
+FP64_FLOP_PER_POINT = 190
 # algorithmic HBM bytes per interior point-update of one fused pass: every
 # stored array read once and written once (FP64: 5 x 8 B; FP32-mixed: 7 x 4 B,
 # u, v, w and the hi/lo pairs of p and T)
@@ -49,7 +52,7 @@ BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
 # capture of the same workload (profiles/k_step_f64_cavity128_2x2x2.md,
 # profiles/k_step_f32p_cavity256.md); None where no capture of the current
 # kernel exists
-TRAFFIC = {("fp64", "cfg2", (2, 2, 2)): 112.886016e6 + 54.552832e6}
+TRAFFIC = {}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129e6

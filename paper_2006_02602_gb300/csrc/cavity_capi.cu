@@ -174,31 +174,8 @@ long long host_node_index(const BlockDev &B, size_t esize, int i, int j, int k) 
 }
 
 void fill_consts(cavity *h, int c) {
-  CavConst &C = h->hcc[c];
-  const cavity_params &p = h->prms[c];
   const int gn[3] = {h->descs[c].nx, h->descs[c].ny, h->descs[c].nz};
-  double sih = 0.0;
-  for (int d = 0; d < 3; ++d) {
-    const double np1 = (double)gn[d] + 1.0;
-    C.gn[d] = gn[d];
-    C.h[d] = 1.0 / np1;
-    C.ih[d] = np1;
-    C.ih2[d] = 0.5 * np1;
-    C.ihh[d] = np1 * np1;
-    sih += C.ihh[d];
-  }
-  C.nu = p.Pr;
-  C.alpha = 1.0;
-  C.gs = p.Ra * p.Pr;
-  C.t_inf = p.t_inf;
-  C.b2min = p.kappa * p.u_ref * p.u_ref;
-  C.c4 = p.c4;
-  C.cfl = p.cfl;
-  C.diffsr = 2.0 * std::max(C.nu, C.alpha) * sih;
-  C.inv_dT = 1.0 / (p.t_hot - p.t_cold);
-  C.inv_nint = 1.0 / ((double)gn[0] * gn[1] * gn[2]);
-  C.inv_nwall = 1.0 / ((double)gn[1] * gn[2]);
-  C.gaxis = p.gravity_axis;
+  set_cav_physics(h->hcc[c], gn, h->prms[c]);
 }
 
 void resolve_defaults(cavity_params *p) {

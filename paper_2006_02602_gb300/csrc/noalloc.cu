@@ -131,26 +131,7 @@ extern "C" CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *
 
   CavConst C{};
   const int gn[3] = {nx, ny, nz};
-  double sih = 0.0;
-  for (int d = 0; d < 3; ++d) {
-    const double np1 = (double)gn[d] + 1.0;
-    C.gn[d] = gn[d];
-    C.h[d] = 1.0 / np1;
-    C.ih[d] = np1;
-    C.ih2[d] = 0.5 * np1;
-    C.ihh[d] = np1 * np1;
-    sih += C.ihh[d];
-  }
-  C.nu = q.Pr;
-  C.alpha = 1.0;
-  C.gs = q.Ra * q.Pr;
-  C.t_inf = q.t_inf;
-  C.b2min = q.kappa * q.u_ref * q.u_ref;
-  C.c4 = q.c4;
-  C.cfl = q.cfl;
-  C.diffsr = 2.0 * std::max(C.nu, C.alpha) * sih;
-  C.inv_nint = 1.0 / ((double)nx * ny * nz);
-  C.gaxis = q.gravity_axis;
+  set_cav_physics(C, gn, q);
 
   CavState S{};
   S.dt = dt;
