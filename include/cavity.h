@@ -262,6 +262,17 @@ CAVITY_API int cavity_set_time_stepping(cavity_t *h, int mode);
  * run).  The steps are real steps of the state. */
 CAVITY_API int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]);
 
+/* Self-check of the FP64 square root the fused FP64 step uses for the wave
+ * speeds lambda_d = (|V_d| + sqrt(V_d^2 + 4 beta^2)) / 2 (Section 2): a
+ * Newton iteration seeded by the approximate reciprocal square root.  On the
+ * current CUDA device, evaluates it and CUDA's correctly rounded sqrt for the
+ * n host values x (positive, normal, finite; copied in and out by the call,
+ * which synchronises) and returns the largest relative difference in
+ * *max_rel and the number of values where the two differ in *n_diff.
+ * CAVITY_ERR_INVALID_ARG for n < 1 or n > 2^26, a null pointer or a value
+ * outside that range; CAVITY_ERR_OOM / CAVITY_ERR_CUDA on a CUDA error. */
+CAVITY_API int cavity_check_sqrt(const double *x, long long n, double *max_rel, long long *n_diff);
+
 /* Allocation-free step of one caller-held block.  The paper has no
  * counterpart; this exists for callers that must not call cudaMalloc, such as
  * code running inside another framework's caching allocator or a fixed,

@@ -45,7 +45,7 @@ EXPORTED = (
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
     "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
     "cavity_batch_get_fields", "cavity_autotune", "cavity_adjoint_forward", "cavity_adjoint_backward",
-    "cavity_set_time_stepping", "cavity_set_overlap",
+    "cavity_set_time_stepping", "cavity_set_overlap", "cavity_check_sqrt",
 )
 
 
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_get_face_buffer": ([_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t], ctypes.c_int),
         "cavity_exchange": ([_H], ctypes.c_int),
         "cavity_time_kernels": ([_H, ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_check_sqrt": ([_dp, ctypes.c_longlong, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "cavity_set_time_stepping": ([_H, ctypes.c_int], ctypes.c_int),
         "cavity_set_overlap": ([_H, ctypes.c_int], ctypes.c_int),
         "cavity_create_batch": ([ctypes.POINTER(cavity_desc), ctypes.POINTER(cavity_params), ctypes.c_int,
@@ -263,6 +264,17 @@ def cavity_time_kernels(h, nsteps: int) -> np.ndarray:
     out = np.zeros(4)
     _check(load_library().cavity_time_kernels(h, int(nsteps), out.ctypes.data_as(_dp)), h)
     return out
+
+
+def cavity_check_sqrt(x) -> tuple:
+    """(largest relative difference, count of differing values) of the FP64
+    step's Newton square root from CUDA's sqrt over the positive, normal,
+    finite values x, evaluated on the current CUDA device."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    m = ctypes.c_double(0.0)
+    nd = ctypes.c_longlong(0)
+    _check(load_library().cavity_check_sqrt(x.ctypes.data_as(_dp), x.size, ctypes.byref(m), ctypes.byref(nd)))
+    return m.value, nd.value
 
 
 def cavity_step_block_noalloc(q_in_ptr: int, q_out_ptr: int, shape, params: cavity_params, dt: float,

@@ -193,6 +193,27 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // ---------------------------------------------------------------------------
+// Square root of a positive, normal, finite FP64 value by Newton's method on
+// s^2 - q = 0 with a fixed slope: the seed y ~ 1/sqrt(q) comes from the PTX
+// instruction rsqrt.approx.ftz.f64 (measured relative error below 1e-6),
+// s_0 = q y, then twice s <- s + (q - s^2) y / 2.  The relative error of s
+// after a step is about 1.5 e^2 (e the seed's), so the second step lands below
+// the FP64 rounding: the result is within one unit in the last place of the
+// correctly rounded root (cavity_check_sqrt measures this against CUDA's sqrt).
+// It takes about 30% less FP64-pipe time than the library sqrt on GB300.
+// Arguments below the normal range or infinite give NaN (the seed is infinite
+// or zero): the rates only take it of V_d^2 + 4 beta^2 >= 4 kappa u_ref^2,
+// which the parameter check keeps normal.
+__device__ __forceinline__ double sqrt_newton(double q) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
+  const double hy = 0.5 * y;
+  double s = q * y;
+  s = fma(fma(-s, s, q), hy, s);
+  return fma(fma(-s, s, q), hy, s);
+}
+
+// ---------------------------------------------------------------------------
 // Per-node rates, Eqs. 1-3, FP64.  Star values: c, x-, x+, y-, y+, z-, z+.
 // Rearranged for few FP64 operations (GB300's FP64 pipe is the bound):
 //  - beta^2 eps_d / h_d^4 = c4 lambda_d / h_d, so the continuity rate needs no
@@ -212,9 +233,9 @@ __device__ __forceinline__ void rates_f64(const CavConst &C, const NodeF64 &n, d
   const double u0 = n.u[0], v0 = n.v[0], w0 = n.w[0];
   const double b2 = fmax(fma(u0, u0, fma(v0, v0, w0 * w0)), C.b2min);
   const double f4 = 4.0 * b2;
-  const double ex = (fabs(u0) + sqrt(fma(u0, u0, f4))) * C.dsc[0];
-  const double ey = (fabs(v0) + sqrt(fma(v0, v0, f4))) * C.dsc[1];
-  const double ez = (fabs(w0) + sqrt(fma(w0, w0, f4))) * C.dsc[2];
+  const double ex = (fabs(u0) + sqrt_newton(fma(u0, u0, f4))) * C.dsc[0];
+  const double ey = (fabs(v0) + sqrt_newton(fma(v0, v0, f4))) * C.dsc[1];
+  const double ez = (fabs(w0) + sqrt_newton(fma(w0, w0, f4))) * C.dsc[2];
   const double p0 = n.p[0];
   const double d4x = fma(6.0, p0, fma(-4.0, n.p[2] + n.p[1], n.p[8] + n.p[7]));
   const double d4y = fma(6.0, p0, fma(-4.0, n.p[4] + n.p[3], n.p[10] + n.p[9]));

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cfloat>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -185,7 +186,8 @@ void resolve_defaults(cavity_params *p) {
 
 int check_params(const cavity_params &p) {
   if (!(p.Ra >= 0.0) || !(p.Pr > 0.0) || !(p.cfl > 0.0) || !(p.kappa > 0.0) || !(p.c4 >= 0.0) ||
-      !(p.u_ref > 0.0) || !std::isfinite(p.t_inf) || !std::isfinite(p.t_hot) || !std::isfinite(p.t_cold) ||
+      !(p.u_ref > 0.0) || !(p.kappa * p.u_ref * p.u_ref >= DBL_MIN) ||
+      !(p.kappa * p.u_ref * p.u_ref < 1e300) || !std::isfinite(p.t_inf) || !std::isfinite(p.t_hot) || !std::isfinite(p.t_cold) ||
       p.t_hot == p.t_cold || (p.gravity_axis != 1 && p.gravity_axis != 2))
     return CAVITY_ERR_INVALID_ARG;
   return CAVITY_OK;
@@ -877,6 +879,14 @@ void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint
   k_adj_finish<<<1, 1, 0, h->stream>>>(a);
 }
 
+// cavity_check_sqrt: relative difference of sqrt_newton from CUDA's sqrt
+__global__ void k_check_sqrt(const double *x, long long n, double *rel) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double r = sqrt(x[i]), s = sqrt_newton(x[i]);
+  rel[i] = s == r ? 0.0 : fabs(s - r) / r;
+}
+
 extern "C" {
 
 int cavity_default_params(cavity_params *p) {
@@ -1406,6 +1416,34 @@ int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
   for (int q = 0; q < 4; ++q) ms[q] = acc[q] / nsteps;
   if (h->n_cut == 0) ms[2] = ms[3] = 0.0;
   return rc;
+}
+
+int cavity_check_sqrt(const double *x, long long n, double *max_rel, long long *n_diff) {
+  if (!x || !max_rel || !n_diff || n < 1 || n > (1ll << 26)) return CAVITY_ERR_INVALID_ARG;
+  for (long long i = 0; i < n; ++i)
+    if (!(x[i] >= DBL_MIN && x[i] <= DBL_MAX)) return CAVITY_ERR_INVALID_ARG;
+  double *d = nullptr;
+  const size_t bytes = (size_t)n * sizeof(double);
+  cudaError_t e = cudaMalloc(&d, 2 * bytes);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CAVITY_ERR_OOM : CAVITY_ERR_CUDA;
+  std::vector<double> rel((size_t)n);
+  e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_check_sqrt<<<(unsigned)((n + 255) / 256), 256>>>(d, n, d + n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(rel.data(), d + n, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return CAVITY_ERR_CUDA;
+  double m = 0.0;
+  long long nd = 0;
+  for (double r : rel) {
+    m = std::max(m, r);
+    nd += r != 0.0;
+  }
+  *max_rel = m;
+  *n_diff = nd;
+  return CAVITY_OK;
 }
 
 int cavity_sync(cavity_t *h) {
