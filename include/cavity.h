@@ -94,7 +94,10 @@ typedef struct {
  *  beta^2 = max(|V|^2, kappa u_ref^2)                 (Section 2)
  *  eps_d  = c4 lambda_d h_d^3 / beta^2                 (Eq. 1 dissipation)
  *  dt     = cfl / max[sum_d lambda_d/h_d + 2 max(nu,alpha) sum_d 1/h_d^2]
- *  gravity_axis 1 (y) or 2 (z). */
+ *  gravity_axis 1 (y) or 2 (z).
+ * Ra >= 0, Pr, cfl, kappa, u_ref > 0, c4 >= 0, finite distinct wall
+ * temperatures, and kappa u_ref^2 in [2^-126, 1e300]; anything else gives
+ * CAVITY_ERR_INVALID_ARG where the parameters are set. */
 typedef struct {
   double Ra, Pr, cfl, kappa, c4, u_ref, t_inf, t_hot, t_cold;
   int gravity_axis;

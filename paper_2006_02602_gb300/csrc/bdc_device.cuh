@@ -288,7 +288,8 @@ __device__ __forceinline__ void update_node_f64(const CavConst &C, const NodeF64
 }
 
 // FP32 estimate of spectral_f64 (the same formula: relative error below
-// 1e-6).  A node whose estimate, raised by 1e-5, stays at or below a value
+// 1e-6; beta_min^2 = kappa u_ref^2 is at least FP32's smallest normal, so the
+// estimate is finite).  A node whose estimate, raised by 1e-5, stays at or below a value
 // the exact FP64 maximum already reached cannot raise that maximum, so only
 // the few candidates are evaluated in FP64 (GB300's FP64 pipe is narrow) and
 // the maximum -- hence dt -- is exactly the FP64 one.
@@ -304,8 +305,21 @@ __device__ __forceinline__ float spectral_est_f32(const CavConst &C, float uf, f
   return __fmaf_rn(0.5f, __fmaf_rn(sx, (float)C.ih[0], __fmaf_rn(sy, (float)C.ih[1], __fmul_rn(sz, (float)C.ih[2]))),
                    (float)C.diffsr);
 }
+// |x| as FP32, rounded toward zero, from the FP64 bit pattern by integer
+// operations (a conversion instruction would take slots of GB300's narrow
+// FP64 pipe): the exponent rebiased from 1023 to 127, the significand cut to
+// 23 bits.  Relative error below 2^-23 in FP32's normal range; exponents
+// below it give a value below 2^-125, above it (and inf/NaN) a finite value
+// of FP32's largest exponent.
+__device__ __forceinline__ float abs_f32_trunc(double x) {
+  const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m = __funnelshift_l(lo, hi, 3) & 0x7fffffu;  // significand bits 51..29
+  const int ec = min(max(e, 896), 1150);
+  return __uint_as_float(((unsigned)(ec - 896) << 23) | m);
+}
 __device__ __forceinline__ float spectral_est_f32(const CavConst &C, double u, double v, double w) {
-  return spectral_est_f32(C, (float)u, (float)v, (float)w);
+  return spectral_est_f32(C, abs_f32_trunc(u), abs_f32_trunc(v), abs_f32_trunc(w));
 }
 
 // ---------------------------------------------------------------------------

@@ -186,7 +186,7 @@ void resolve_defaults(cavity_params *p) {
 
 int check_params(const cavity_params &p) {
   if (!(p.Ra >= 0.0) || !(p.Pr > 0.0) || !(p.cfl > 0.0) || !(p.kappa > 0.0) || !(p.c4 >= 0.0) ||
-      !(p.u_ref > 0.0) || !(p.kappa * p.u_ref * p.u_ref >= DBL_MIN) ||
+      !(p.u_ref > 0.0) || !(p.kappa * p.u_ref * p.u_ref >= FLT_MIN) ||
       !(p.kappa * p.u_ref * p.u_ref < 1e300) || !std::isfinite(p.t_inf) || !std::isfinite(p.t_hot) || !std::isfinite(p.t_cold) ||
       p.t_hot == p.t_cold || (p.gravity_axis != 1 && p.gravity_axis != 2))
     return CAVITY_ERR_INVALID_ARG;

@@ -240,6 +240,10 @@ def test_invalid_arguments_and_nonfinite(m):
         bad = m.cavity_default_params(Ra=1e4, gravity_axis=0)
         with pytest.raises(m.CavityError):
             m.cavity_set_params(c.h, bad)
+        # beta_min^2 = kappa u_ref^2 below FP32's normal range
+        for kw in (dict(kappa=1e-40, u_ref=1.0), dict(kappa=1e-10, u_ref=1e-20)):
+            with pytest.raises(m.CavityError):
+                m.cavity_set_params(c.h, m.cavity_default_params(Ra=1e4, **kw))
         with pytest.raises(m.CavityError):
             m.cavity_step(c.h, -1)
         # host-side injection of a non-finite value: the step flags it
