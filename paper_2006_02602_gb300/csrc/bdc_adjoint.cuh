@@ -319,11 +319,11 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
     const long long fs = a.B.fstride;
     const float *Yt = arr<float>(a.Yt);
     const float dt = (float)a.dt;
-    const float ih[3] = {(float)C.ih[0], (float)C.ih[1], (float)C.ih[2]};
-    const float ih2[3] = {(float)C.ih2[0], (float)C.ih2[1], (float)C.ih2[2]};
-    const float ihh[3] = {(float)C.ihh[0], (float)C.ihh[1], (float)C.ihh[2]};
-    const float c4 = (float)C.c4, b2min = (float)C.b2min, Dq[5] = {0.f, (float)C.nu, (float)C.nu, (float)C.nu,
-                                                                      (float)C.alpha};
+    // FP32 constants rounded on the host (no per-thread conversions)
+    const float ih[3] = {C.fih[0], C.fih[1], C.fih[2]};
+    const float ih2[3] = {C.fh2[0], C.fh2[1], C.fh2[2]};
+    const float ihh[3] = {C.fihh[0], C.fihh[1], C.fihh[2]};
+    const float c4 = C.fc4, b2min = C.fb2min, Dq[5] = {0.f, C.fnu, C.fnu, C.fnu, C.falpha};
     const int nn[3] = {a.g.nx, a.g.ny, a.g.nz};
     auto interior = [&](int x, int y, int z) { return x >= 1 && x <= nn[0] && y >= 1 && y <= nn[1] && z >= 1 && z <= nn[2]; };
     float out[5];
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
         if (f <= 3) {
           const int cc = f - 1;
           r += -(st_.dp[0][cc] - st_.dm[0][cc]) * ih2[cc];
-          if (cc == C.gaxis) r += (float)C.gs * st_.tb;
+          if (cc == C.gaxis) r += C.fgs * st_.tb;
         }
         Rf[f] = r;
       }
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
           abar[d] += -rb[f] * (st_.dp[f][d] - st_.dm[f][d]);
         }
         if (f <= 3 && f - 1 == C.gaxis) {
-          out[4] += (float)C.gs * rb[f];
+          out[4] += C.fgs * rb[f];
           gsb += st_.tb * rb[f];
         }
       }

@@ -52,6 +52,13 @@ struct CavConst {
   // weight of |V_d| + sqrt(V_d^2 + 4 beta^2)), nu / h_d^2, alpha / h_d^2,
   // 2 nu sum 1/h_d^2, 2 alpha sum 1/h_d^2, gs T_inf
   double dsc[3], nuhh[3], alhh[3], nu2s, al2s, gst;
+  // FP32 copies (rounded to nearest, as a device conversion would) of the
+  // constants the FP32 kernels and estimates use, so that no kernel spends
+  // FP64-pipe conversions on them: 1/h, 1/(2h), nu/h^2, alpha/h^2, c4/2, gs,
+  // T_inf, beta_min^2, the diffusive spectral term, cfl; 1/h^2, c4, nu, alpha
+  float fih[3], fh2[3], fnh[3], fah[3];
+  float fc4h, fgs, ftinf, fb2min, fdiffsr, fcfl;
+  float fihh[3], fc4, fnu, falpha;
   int gaxis;
   int gn[3];
   int ncentre;
@@ -95,6 +102,22 @@ inline void set_cav_physics(CavConst &C, const int gn[3], const cavity_params &p
   C.nu2s = 2.0 * C.nu * sih;
   C.al2s = 2.0 * C.alpha * sih;
   C.gst = C.gs * C.t_inf;
+  for (int d = 0; d < 3; ++d) {
+    C.fih[d] = (float)C.ih[d];
+    C.fh2[d] = (float)C.ih2[d];
+    C.fnh[d] = (float)(C.nu * C.ihh[d]);
+    C.fah[d] = (float)(C.alpha * C.ihh[d]);
+    C.fihh[d] = (float)C.ihh[d];
+  }
+  C.fc4 = (float)C.c4;
+  C.fnu = (float)C.nu;
+  C.falpha = (float)C.alpha;
+  C.fc4h = (float)(0.5 * C.c4);
+  C.fgs = (float)C.gs;
+  C.ftinf = (float)C.t_inf;
+  C.fb2min = (float)C.b2min;
+  C.fdiffsr = (float)C.diffsr;
+  C.fcfl = (float)C.cfl;
   C.gaxis = p.gravity_axis;
 }
 
@@ -294,7 +317,7 @@ __device__ __forceinline__ void update_node_f64(const CavConst &C, const NodeF64
 // the few candidates are evaluated in FP64 (GB300's FP64 pipe is narrow) and
 // the maximum -- hence dt -- is exactly the FP64 one.
 __device__ __forceinline__ float spectral_est_f32(const CavConst &C, float uf, float vf, float wf) {
-  const float b2 = fmaxf(__fmaf_rn(uf, uf, __fmaf_rn(vf, vf, __fmul_rn(wf, wf))), (float)C.b2min);
+  const float b2 = fmaxf(__fmaf_rn(uf, uf, __fmaf_rn(vf, vf, __fmul_rn(wf, wf))), C.fb2min);
   const float f4 = __fmul_rn(4.f, b2);
   const float qx = __fmaf_rn(uf, uf, f4), qy = __fmaf_rn(vf, vf, f4), qz = __fmaf_rn(wf, wf, f4);
   float rx, ry, rz;
@@ -302,8 +325,7 @@ __device__ __forceinline__ float spectral_est_f32(const CavConst &C, float uf, f
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(qy));
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rz) : "f"(qz));
   const float sx = __fmaf_rn(qx, rx, fabsf(uf)), sy = __fmaf_rn(qy, ry, fabsf(vf)), sz = __fmaf_rn(qz, rz, fabsf(wf));
-  return __fmaf_rn(0.5f, __fmaf_rn(sx, (float)C.ih[0], __fmaf_rn(sy, (float)C.ih[1], __fmul_rn(sz, (float)C.ih[2]))),
-                   (float)C.diffsr);
+  return __fmaf_rn(0.5f, __fmaf_rn(sx, C.fih[0], __fmaf_rn(sy, C.fih[1], __fmul_rn(sz, C.fih[2]))), C.fdiffsr);
 }
 // |x| as FP32, rounded toward zero, from the FP64 bit pattern by integer
 // operations (a conversion instruction would take slots of GB300's narrow

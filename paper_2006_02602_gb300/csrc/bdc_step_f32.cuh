@@ -47,6 +47,7 @@ struct StepF32Args {
   double *partials;           // [cta][kPartStride]: 5 rate sums, spectral max, 2 Nusselt sums
   int parity;
   int local_dt;               // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
+  int ntiles;                 // tiles of the step (the persistent form's grid may be smaller)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -257,20 +258,20 @@ struct F32K {
 template <class V>
 __device__ __forceinline__ F32K<V> f32_consts(const CavConst &C, const CavState &S) {
   F32K<V> K;
-  K.ihx = splat<V>((float)C.ih[0]); K.ihy = splat<V>((float)C.ih[1]); K.ihz = splat<V>((float)C.ih[2]);
-  K.h2x = splat<V>((float)C.ih2[0]); K.h2y = splat<V>((float)C.ih2[1]); K.h2z = splat<V>((float)C.ih2[2]);
-  K.mh2x = splat<V>(-(float)C.ih2[0]); K.mh2y = splat<V>(-(float)C.ih2[1]); K.mh2z = splat<V>(-(float)C.ih2[2]);
-  K.nhx = splat<V>((float)(C.nu * C.ihh[0])); K.nhy = splat<V>((float)(C.nu * C.ihh[1]));
-  K.nhz = splat<V>((float)(C.nu * C.ihh[2]));
-  K.ahx = splat<V>((float)(C.alpha * C.ihh[0])); K.ahy = splat<V>((float)(C.alpha * C.ihh[1]));
-  K.ahz = splat<V>((float)(C.alpha * C.ihh[2]));
-  K.c4h = splat<V>((float)(0.5 * C.c4)); K.gs = splat<V>((float)C.gs); K.tinf = splat<V>((float)C.t_inf);
-  K.b2min = splat<V>((float)C.b2min);
+  // the static constants come rounded to FP32 from the host; only dt and the
+  // centre shift are converted here
+  K.ihx = splat<V>(C.fih[0]); K.ihy = splat<V>(C.fih[1]); K.ihz = splat<V>(C.fih[2]);
+  K.h2x = splat<V>(C.fh2[0]); K.h2y = splat<V>(C.fh2[1]); K.h2z = splat<V>(C.fh2[2]);
+  K.mh2x = splat<V>(-C.fh2[0]); K.mh2y = splat<V>(-C.fh2[1]); K.mh2z = splat<V>(-C.fh2[2]);
+  K.nhx = splat<V>(C.fnh[0]); K.nhy = splat<V>(C.fnh[1]); K.nhz = splat<V>(C.fnh[2]);
+  K.ahx = splat<V>(C.fah[0]); K.ahy = splat<V>(C.fah[1]); K.ahz = splat<V>(C.fah[2]);
+  K.c4h = splat<V>(C.fc4h); K.gs = splat<V>(C.fgs); K.tinf = splat<V>(C.ftinf);
+  K.b2min = splat<V>(C.fb2min);
   const float dt = (float)S.dt;
   K.dt = splat<V>(dt); K.mdt = splat<V>(-dt); K.mcs = splat<V>(-(float)S.c);
   K.gy = splat<V>(C.gaxis == 1 ? 1.f : 0.f); K.gz = splat<V>(C.gaxis == 2 ? 1.f : 0.f);
-  K.diffsr = splat<V>((float)C.diffsr);
-  K.cfl = splat<V>((float)C.cfl);
+  K.diffsr = splat<V>(C.fdiffsr);
+  K.cfl = splat<V>(C.fcfl);
   return K;
 }
 
@@ -361,14 +362,16 @@ __device__ __forceinline__ void f32_spectral_max(const F32K<float> &K, float bou
 // warps (fixed order); Nusselt sums FP64 from the column sums on.  Slots:
 // 5 rate sums, spectral max, hot and cold sums of 3 T_w - 4 T_1 + T_2; the
 // per-cavity reduction (k_finalize) reads them in a fixed order.
+// `xwall`: the tile touches an isothermal x wall (uniform over the CTA); only
+// then can a thread hold Nusselt sums, and the FP64 warp sums run.
 template <int NT>
 __device__ __forceinline__ void f32_partials(double *partials, int cta, int tid, float s0, float s1, float s2,
-                                             float s3, float s4, float smax, double nuh, double nuc) {
+                                             float s3, float s4, float smax, double nuh, double nuc, bool xwall) {
   __shared__ double red[NT / 32][8];
   const int lane = tid & 31, wid = tid >> 5;
   const float w0s = warp_sum_f(s0), w1s = warp_sum_f(s1), w2s = warp_sum_f(s2), w3s = warp_sum_f(s3);
   const float w4s = warp_sum_f(s4), wms = warp_max_f(smax);
-  const double wnh = warp_sum(nuh), wnc = warp_sum(nuc);
+  const double wnh = xwall ? warp_sum(nuh) : 0.0, wnc = xwall ? warp_sum(nuc) : 0.0;
   if (lane == 0) {
     red[wid][0] = w0s; red[wid][1] = w1s; red[wid][2] = w2s; red[wid][3] = w3s; red[wid][4] = w4s;
     red[wid][5] = wms; red[wid][6] = wnh; red[wid][7] = wnc;
@@ -637,7 +640,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
     nuh = wh * col_t + (hot_next ? wall_t : 0.0);
     nuc = wc * col_t + (cold_next ? wall_t : 0.0);
   }
-  f32_partials<NT>(a.partials, cta, tid, s0, s1, s2, s3, s4, smax, nuh, nuc);
+  f32_partials<NT>(a.partials, cta, tid, s0, s1, s2, s3, s4, smax, nuh, nuc, T.wxl || T.wxh);
 }
 
 __device__ __forceinline__ float2 ld2(const float *s, int idx) { return *reinterpret_cast<const float2 *>(s + idx); }
@@ -869,19 +872,241 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
     nuc = wc0 * t0 + wc1 * t1 + (cold_next0 || cold_next1 ? wall_t : 0.0);
   }
   f32_partials<NT>(a.partials, cta, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
-                   vadd(s4.x, s4.y), smax, nuh, nuc);
+                   vadd(s4.x, s4.y), smax, nuh, nuc, T.wxl || T.wxh);
+}
+
+// Per-thread state of the register-queue FP32 kernels (two nodes per thread):
+// the pair's z - 1 values of all seven arrays and p's z - 2 values, the
+// running residual sums and spectral maximum, and the Nusselt column sums.
+struct F32QAcc {
+  float2 qm1[7], qm2h, qm2l;
+  float2 s0, s1, s2, s3, s4;
+  float smax;
+  float2 ch, cl;
+  float wsh, wsl;
+};
+
+// One plane of one thread's node pair: rates and update of the pair at plane
+// k from the resident slots of planes k, k+1, k+2 (S0, Sp1, Sp2) and the
+// register queues; writes the new state at `out`, accumulates the sums and
+// moves the queues one plane up.  `col`: the pair's first node inside a slot;
+// `wofs`: offset of the wall value read for the Nusselt sum.
+template <int TY>
+__device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, const float *Sp2, const F32K<float2> &K,
+                                          const F32K<float> &K1, int k, int nz, bool wzl, bool wzh, int local_dt,
+                                          float *out, long long fs, int col, int wofs, bool act1, bool nus_warp,
+                                          F32QAcc &acc) {
+  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;
+  float2(&qm1)[7] = acc.qm1;
+  float2 &qm2h = acc.qm2h, &qm2l = acc.qm2l;
+  float2 &s0 = acc.s0, &s1 = acc.s1, &s2 = acc.s2, &s3 = acc.s3, &s4 = acc.s4;
+  float &smax = acc.smax;
+  float2 &ch = acc.ch, &cl = acc.cl;
+  float &wsh = acc.wsh, &wsl = acc.wsl;
+  F32Nb<float2> n;
+  // pressure: centre pair and its z neighbours (walls formed in place)
+  n.ph = ld2(S0, col);
+  n.pl = ld2(S0 + AS, col);
+  float2 zm2h = qm2h, zm2l = qm2l, zm1h = qm1[0], zm1l = qm1[1];
+  float2 zp1h = ld2(Sp1, col), zp1l = ld2(Sp1 + AS, col), zp2h = ld2(Sp2, col), zp2l = ld2(Sp2 + AS, col);
+  float2 th = ld2(S0 + 5 * AS, col), tl = ld2(S0 + 6 * AS, col);
+  float2 tzmh = qm1[5], tzml = qm1[6];
+  float2 tzph = ld2(Sp1 + 5 * AS, col), tzpl = ld2(Sp1 + 6 * AS, col);
+  if (wzl && k <= 2) {
+    float hg, lg;
+    if (k == 1) {  // z = 0 wall and z = -1 ghost from the layers z = 1, 2
+      wall_pressure(n.ph.x, n.pl.x, zp1h.x, zp1l.x, zm1h.x, zm1l.x, zm2h.x, zm2l.x);
+      wall_pressure(n.ph.y, n.pl.y, zp1h.y, zp1l.y, zm1h.y, zm1l.y, zm2h.y, zm2l.y);
+      wall_temperature(th.x, tl.x, tzph.x, tzpl.x, tzmh.x, tzml.x);
+      wall_temperature(th.y, tl.y, tzph.y, tzpl.y, tzmh.y, tzml.y);
+    } else {  // k == 2: z = 0 wall from z = 1, 2
+      wall_pressure(zm1h.x, zm1l.x, n.ph.x, n.pl.x, zm2h.x, zm2l.x, hg, lg);
+      wall_pressure(zm1h.y, zm1l.y, n.ph.y, n.pl.y, zm2h.y, zm2l.y, hg, lg);
+    }
+  }
+  if (wzh && k >= nz - 1) {
+    float hg, lg;
+    if (k == nz) {  // z = nz+1 wall and nz+2 ghost from the layers nz, nz-1
+      wall_pressure(n.ph.x, n.pl.x, zm1h.x, zm1l.x, zp1h.x, zp1l.x, zp2h.x, zp2l.x);
+      wall_pressure(n.ph.y, n.pl.y, zm1h.y, zm1l.y, zp1h.y, zp1l.y, zp2h.y, zp2l.y);
+      wall_temperature(th.x, tl.x, tzmh.x, tzml.x, tzph.x, tzpl.x);
+      wall_temperature(th.y, tl.y, tzmh.y, tzml.y, tzph.y, tzpl.y);
+    } else {  // k == nz-1: z = nz+1 wall from nz, nz-1
+      wall_pressure(zp1h.x, zp1l.x, n.ph.x, n.pl.x, zp2h.x, zp2l.x, hg, lg);
+      wall_pressure(zp1h.y, zp1l.y, n.ph.y, n.pl.y, zp2h.y, zp2l.y, hg, lg);
+    }
+  }
+  n.pzp1 = pdiff(zp1h, zp1l, n.ph, n.pl);
+  n.pzm1 = pdiff(zm1h, zm1l, n.ph, n.pl);
+  n.pzp2 = pdiff(zp2h, zp2l, n.ph, n.pl);
+  n.pzm2 = pdiff(zm2h, zm2l, n.ph, n.pl);
+  {
+    const float *H = S0, *L = S0 + AS;
+    const float2 ah = ld2(H, col - 2), al = ld2(L, col - 2), dh = ld2(H, col + 2), dl = ld2(L, col + 2);
+    n.pxp1 = make_float2(pdiff(n.ph.y, n.pl.y, n.ph.x, n.pl.x), pdiff(dh.x, dl.x, n.ph.y, n.pl.y));
+    n.pxm1 = make_float2(pdiff(ah.y, al.y, n.ph.x, n.pl.x), pdiff(n.ph.x, n.pl.x, n.ph.y, n.pl.y));
+    n.pxp2 = pdiff(dh, dl, n.ph, n.pl);
+    n.pxm2 = pdiff(ah, al, n.ph, n.pl);
+    n.pyp1 = pdiff(ld2(H, col + BX), ld2(L, col + BX), n.ph, n.pl);
+    n.pym1 = pdiff(ld2(H, col - BX), ld2(L, col - BX), n.ph, n.pl);
+    n.pyp2 = pdiff(ld2(H, col + 2 * BX), ld2(L, col + 2 * BX), n.ph, n.pl);
+    n.pym2 = pdiff(ld2(H, col - 2 * BX), ld2(L, col - 2 * BX), n.ph, n.pl);
+  }
+  // velocity: x differences per node, y and z packed
+#define BDC_F32Q_VEL(F, c0, xp, xm, yp, ym, zp, zm)                                                  \
+  {                                                                                                \
+    const float *Q = S0 + F * AS;                                                                  \
+    c0 = ld2(Q, col);                                                                              \
+    const float qm = Q[col - 1], qp = Q[col + 2];                                                  \
+    xp = make_float2(vsub(c0.y, c0.x), vsub(qp, c0.y));                                            \
+    xm = make_float2(vsub(qm, c0.x), vsub(c0.x, c0.y));                                            \
+    yp = vsub(ld2(Q, col + BX), c0);                                                               \
+    ym = vsub(ld2(Q, col - BX), c0);                                                               \
+    zp = vsub(ld2(Sp1 + F * AS, col), c0);                                                         \
+    zm = vsub(qm1[F], c0);                                                         \
+  }
+  BDC_F32Q_VEL(2, n.u, n.uxp, n.uxm, n.uyp, n.uym, n.uzp, n.uzm)
+  BDC_F32Q_VEL(3, n.v, n.vxp, n.vxm, n.vyp, n.vym, n.vzp, n.vzm)
+  BDC_F32Q_VEL(4, n.w, n.wxp, n.wxm, n.wyp, n.wym, n.wzp, n.wzm)
+#undef BDC_F32Q_VEL
+  // temperature pair
+  n.th = th;
+  n.tl = tl;
+  {
+    const float *TH = S0 + 5 * AS, *TL = S0 + 6 * AS;
+    n.txp = make_float2(pdiff(th.y, tl.y, th.x, tl.x), pdiff(TH[col + 2], TL[col + 2], th.y, tl.y));
+    n.txm = make_float2(pdiff(TH[col - 1], TL[col - 1], th.x, tl.x), pdiff(th.x, tl.x, th.y, tl.y));
+    n.typ = pdiff(ld2(TH, col + BX), ld2(TL, col + BX), th, tl);
+    n.tym = pdiff(ld2(TH, col - BX), ld2(TL, col - BX), th, tl);
+    n.tzp = pdiff(tzph, tzpl, th, tl);
+    n.tzm = pdiff(tzmh, tzml, th, tl);
+  }
+  F32Out<float2> o;
+  float2 dtn = K.dt, mdtn = K.mdt;
+  if (local_dt) {  // each node's own stable step
+    dtn = make_float2(__fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.x, n.v.x, n.w.x)),
+                      __fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.y, n.v.y, n.w.y)));
+    mdtn = make_float2(-dtn.x, -dtn.y);
+  }
+  f32_update(K, n, dtn, mdtn, o);
+  const float2 bound = f32_spectral_bound(K, o.u, o.v, o.w);
+  f32_spectral_max(K1, bound.x, o.u.x, o.v.x, o.w.x, smax);
+  if (act1) {
+    st2(out, o.ph);
+    st2(out + fs, o.pl);
+    st2(out + 2 * fs, o.u);
+    st2(out + 3 * fs, o.v);
+    st2(out + 4 * fs, o.w);
+    st2(out + 5 * fs, o.th);
+    st2(out + 6 * fs, o.tl);
+    f32_spectral_max(K1, bound.y, o.u.y, o.v.y, o.w.y, smax);
+  } else {  // the x extent is odd: the pair's second node is a wall or beyond
+    out[0] = o.ph.x;
+    out[fs] = o.pl.x;
+    out[2 * fs] = o.u.x;
+    out[3 * fs] = o.v.x;
+    out[4 * fs] = o.w.x;
+    out[5 * fs] = o.th.x;
+    out[6 * fs] = o.tl.x;
+    o.rp.y = o.ru.y = o.rv.y = o.rw.y = o.rt.y = 0.f;
+  }
+  s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
+  s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
+  if (nus_warp) {
+    acc_pair(ch, cl, o.th, o.tl);
+    acc_pair(wsh, wsl, S0[5 * AS + col + wofs], S0[6 * AS + col + wofs]);
+  }
+  // the register queues move one plane: z - 2 <- z - 1 (p), z - 1 <- this plane
+  qm2h = qm1[0];
+  qm2l = qm1[1];
+  qm1[0] = n.ph; qm1[1] = n.pl; qm1[2] = n.u; qm1[3] = n.v; qm1[4] = n.w; qm1[5] = th; qm1[6] = tl;
+}
+
+// The node pair of one thread in a tile of the register-queue kernels and
+// its Nusselt weights (the two columns' weights in 3 T_w - 4 T_1 + T_2).
+struct F32QCol {
+  int i, j, col, wofs;
+  bool act0, act1, nus, nus_warp, hot_next, cold_next;
+  double wh0, wh1, wc0, wc1;
+};
+
+// Called by every thread of the CTA (a warp vote).
+__device__ __forceinline__ F32QCol f32q_column(const BlockDev &B, const F32Tile &T, int li, int lj) {
+  F32QCol c;
+  const int i = T.i0 + 2 * li, j = T.j0 + lj;
+  c.i = i;
+  c.j = j;
+  c.act0 = (i <= B.nx) && (j <= B.ny);
+  c.act1 = (i + 1 <= B.nx) && (j <= B.ny);
+  const bool xw0 = B.wall[0], xw1 = B.wall[1];
+  c.wh0 = (xw0 && c.act0) ? (i == 1 ? -4.0 : (i == 2 ? 1.0 : 0.0)) : 0.0;
+  c.wh1 = (xw0 && c.act1) ? (i + 1 == 2 ? 1.0 : 0.0) : 0.0;
+  c.wc0 = (xw1 && c.act0) ? (i == B.nx ? -4.0 : (i == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
+  c.wc1 = (xw1 && c.act1) ? (i + 1 == B.nx ? -4.0 : (i + 1 == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
+  c.nus = (xw0 && c.act0 && i <= 2) || (xw0 && c.act1 && i + 1 == 2) || (xw1 && c.act0 && i >= B.nx - 1) ||
+          (xw1 && c.act1 && i + 1 >= B.nx - 1);
+  // the column beside a wall: node i next to x = 0 or x = nx + 1, or node i + 1 next to x = nx + 1
+  c.hot_next = xw0 && c.act0 && i == 1;
+  const bool cold_next0 = xw1 && c.act0 && i == B.nx, cold_next1 = xw1 && c.act1 && i + 1 == B.nx;
+  c.cold_next = cold_next0 || cold_next1;
+  c.wofs = c.hot_next ? -1 : (cold_next0 ? 1 : 2);
+  c.nus_warp = __any_sync(0xffffffffu, c.nus);
+  c.col = (lj + 2) * kF32BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
+  return c;
+}
+
+__device__ __forceinline__ void f32q_clear(F32QAcc &acc) {
+  const float2 z = make_float2(0.f, 0.f);
+  for (int q = 0; q < 7; ++q) acc.qm1[q] = z;
+  acc.qm2h = acc.qm2l = z;
+  acc.s0 = acc.s1 = acc.s2 = acc.s3 = acc.s4 = z;
+  acc.smax = 0.f;
+  acc.ch = acc.cl = z;
+  acc.wsh = acc.wsl = 0.f;
+}
+
+// The tile's partials (every thread of the CTA calls it: a CTA reduction).
+template <int NT>
+__device__ __forceinline__ void f32q_finish(double *partials, int tile, int tid, const F32Tile &T, const F32QCol &c,
+                                            const F32QAcc &acc) {
+  double nuh = 0.0, nuc = 0.0;
+  if (c.nus) {
+    const double t0 = pair_value(acc.ch.x, acc.cl.x), t1 = c.act1 ? pair_value(acc.ch.y, acc.cl.y) : 0.0;
+    const double wall_t = 3.0 * pair_value(acc.wsh, acc.wsl);
+    nuh = c.wh0 * t0 + c.wh1 * t1 + (c.hot_next ? wall_t : 0.0);
+    nuc = c.wc0 * t0 + c.wc1 * t1 + (c.cold_next ? wall_t : 0.0);
+  }
+  f32_partials<NT>(partials, tile, tid, vadd(acc.s0.x, acc.s0.y), vadd(acc.s1.x, acc.s1.y), vadd(acc.s2.x, acc.s2.y),
+                   vadd(acc.s3.x, acc.s3.y), vadd(acc.s4.x, acc.s4.y), acc.smax, nuh, nuc, T.wxl || T.wxh);
+}
+
+// The tile's prologue reads once planes 0 .. 3 (z = k0-2 .. k0+1) are resident
+// in their slots (S0 .. S3): the x and y walls of the interior planes 2 and 3
+// are formed in place, and the register queues take plane 1 (z - 1, seven
+// arrays) and plane 0 (z - 2, p).
+template <int NT, int BY>
+__device__ __forceinline__ void f32q_prologue_plane(int pl, float *S, const F32Tile &T, const F32QCol &c, int tid,
+                                                    F32QAcc &acc) {
+  constexpr int AS = kF32BX * BY;
+  if (T.fix && pl >= 2) fix_plane_walls<NT, BY>(S, tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+  if (c.act0 && pl == 0) {
+    acc.qm2h = ld2(S, c.col);
+    acc.qm2l = ld2(S + AS, c.col);
+  }
+  if (c.act0 && pl == 1)
+    for (int q = 0; q < 7; ++q) acc.qm1[q] = ld2(S + q * AS, c.col);
 }
 
 // Two nodes per thread as k_step_f32p, with the pair's z - 1 values (all
 // seven arrays) and p's z - 2 values carried in registers from the previous
 // planes: only planes k .. k+2 stay resident, so a ring of R = 5 slots keeps
 // two planes in flight in 67 KB and three CTAs share an SM (12 warps instead
-// of 8).  Slots are indexed modulo R.
+// of 8).  Slots are indexed modulo R.  One CTA per tile.
 template <int TY, int KC, int R>
 __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_step_f32q(StepF32Args a) {
   static_assert(R >= 4, "ring depth: three planes resident and at least one in flight");
   constexpr int NTX = kF32TX / 2, NT = NTX * TY;
-  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;
+  constexpr int BY = f32_box_y(TY);
   constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float *ring = reinterpret_cast<float *>(smem_raw);
@@ -893,22 +1118,7 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
   const CavConst &C = a.cc[B.cav];
   const int k0 = T.k0, k1 = T.k1;
   const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
-  const int i = T.i0 + 2 * li, j = T.j0 + lj;
-  const bool act0 = (i <= B.nx) && (j <= B.ny), act1 = (i + 1 <= B.nx) && (j <= B.ny);
-  // Nusselt sums of the new state: weights of the two columns in 3 T_w - 4 T_1 + T_2
-  const bool xw0 = B.wall[0], xw1 = B.wall[1];
-  const double wh0 = (xw0 && act0) ? (i == 1 ? -4.0 : (i == 2 ? 1.0 : 0.0)) : 0.0;
-  const double wh1 = (xw0 && act1) ? (i + 1 == 2 ? 1.0 : 0.0) : 0.0;
-  const double wc0 = (xw1 && act0) ? (i == B.nx ? -4.0 : (i == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
-  const double wc1 = (xw1 && act1) ? (i + 1 == B.nx ? -4.0 : (i + 1 == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
-  const bool nus = wh0 != 0.0 || wh1 != 0.0 || wc0 != 0.0 || wc1 != 0.0;
-  // the column beside a wall: node i next to x = 0 or x = nx + 1, or node i + 1 next to x = nx + 1
-  const bool hot_next = xw0 && act0 && i == 1, cold_next0 = xw1 && act0 && i == B.nx;
-  const bool cold_next1 = xw1 && act1 && i + 1 == B.nx;
-  const int wofs = hot_next ? -1 : (cold_next0 ? 1 : 2);
-  const bool nus_warp = __any_sync(0xffffffffu, nus);
-  float2 ch = make_float2(0.f, 0.f), cl = ch;
-  float wsh = 0.f, wsl = 0.f;
+  const F32QCol c = f32q_column(B, T, li, lj);
   const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
 
   if (tid == 0) {
@@ -928,30 +1138,19 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
   }
   auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl % R], (uint32_t)((pl / R) & 1)); };
   auto slot = [&](int pl) { return ring + (pl % R) * SF; };
-  const int col = (lj + 2) * BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
 
   const long long fs = B.fstride, plane = B.plane;
   const int nz = B.nz;
   // i is odd, so the pair starts on an 8-byte boundary of the row
-  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
+  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(c.i, B.nx), min(c.j, B.ny), k0);
 
   bool bad = false;
-  // prologue: planes k0-2 .. k0+1; the x and y walls of the interior planes;
-  // the register queues (z - 1: seven arrays of plane k0-1; z - 2: p of plane k0-2)
-  float2 qm1[7], qm2h = make_float2(0.f, 0.f), qm2l = qm2h;
-  for (int q = 0; q < 7; ++q) qm1[q] = qm2h;
+  F32QAcc acc;
+  f32q_clear(acc);
   for (int pl = 0; pl < 4; ++pl) {
     if (!bad && !wait_plane(pl)) bad = true;
-    if (!bad && T.fix && pl >= 2) fix_plane_walls<NT, BY>(slot(pl), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
-    if (!bad && act0 && pl == 0) {
-      qm2h = ld2(slot(0), col);
-      qm2l = ld2(slot(0) + AS, col);
-    }
-    if (!bad && act0 && pl == 1)
-      for (int q = 0; q < 7; ++q) qm1[q] = ld2(slot(1) + q * AS, col);
+    if (!bad) f32q_prologue_plane<NT, BY>(pl, slot(pl), T, c, tid, acc);
   }
-  float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
-  float smax = 0.f;
   bad = __syncthreads_or(bad);
   // a programmatic dependent of the previous step's finalise: only now are its
   // dt, centre shift and reads of the partials complete (nothing global was
@@ -969,126 +1168,9 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
     if (!wait_plane(pk + 2)) bad = true;
     if (!bad) {
       if (T.fix) fix_plane_walls<NT, BY>(slot(pk + 2), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
-      if (act0) {
-        const float *S0 = slot(pk), *Sp1 = slot(pk + 1), *Sp2 = slot(pk + 2);
-        F32Nb<float2> n;
-        // pressure: centre pair and its z neighbours (walls formed in place)
-        n.ph = ld2(S0, col);
-        n.pl = ld2(S0 + AS, col);
-        float2 zm2h = qm2h, zm2l = qm2l, zm1h = qm1[0], zm1l = qm1[1];
-        float2 zp1h = ld2(Sp1, col), zp1l = ld2(Sp1 + AS, col), zp2h = ld2(Sp2, col), zp2l = ld2(Sp2 + AS, col);
-        float2 th = ld2(S0 + 5 * AS, col), tl = ld2(S0 + 6 * AS, col);
-        float2 tzmh = qm1[5], tzml = qm1[6];
-        float2 tzph = ld2(Sp1 + 5 * AS, col), tzpl = ld2(Sp1 + 6 * AS, col);
-        if (T.wzl && k <= 2) {
-          float hg, lg;
-          if (k == 1) {  // z = 0 wall and z = -1 ghost from the layers z = 1, 2
-            wall_pressure(n.ph.x, n.pl.x, zp1h.x, zp1l.x, zm1h.x, zm1l.x, zm2h.x, zm2l.x);
-            wall_pressure(n.ph.y, n.pl.y, zp1h.y, zp1l.y, zm1h.y, zm1l.y, zm2h.y, zm2l.y);
-            wall_temperature(th.x, tl.x, tzph.x, tzpl.x, tzmh.x, tzml.x);
-            wall_temperature(th.y, tl.y, tzph.y, tzpl.y, tzmh.y, tzml.y);
-          } else {  // k == 2: z = 0 wall from z = 1, 2
-            wall_pressure(zm1h.x, zm1l.x, n.ph.x, n.pl.x, zm2h.x, zm2l.x, hg, lg);
-            wall_pressure(zm1h.y, zm1l.y, n.ph.y, n.pl.y, zm2h.y, zm2l.y, hg, lg);
-          }
-        }
-        if (T.wzh && k >= nz - 1) {
-          float hg, lg;
-          if (k == nz) {  // z = nz+1 wall and nz+2 ghost from the layers nz, nz-1
-            wall_pressure(n.ph.x, n.pl.x, zm1h.x, zm1l.x, zp1h.x, zp1l.x, zp2h.x, zp2l.x);
-            wall_pressure(n.ph.y, n.pl.y, zm1h.y, zm1l.y, zp1h.y, zp1l.y, zp2h.y, zp2l.y);
-            wall_temperature(th.x, tl.x, tzmh.x, tzml.x, tzph.x, tzpl.x);
-            wall_temperature(th.y, tl.y, tzmh.y, tzml.y, tzph.y, tzpl.y);
-          } else {  // k == nz-1: z = nz+1 wall from nz, nz-1
-            wall_pressure(zp1h.x, zp1l.x, n.ph.x, n.pl.x, zp2h.x, zp2l.x, hg, lg);
-            wall_pressure(zp1h.y, zp1l.y, n.ph.y, n.pl.y, zp2h.y, zp2l.y, hg, lg);
-          }
-        }
-        n.pzp1 = pdiff(zp1h, zp1l, n.ph, n.pl);
-        n.pzm1 = pdiff(zm1h, zm1l, n.ph, n.pl);
-        n.pzp2 = pdiff(zp2h, zp2l, n.ph, n.pl);
-        n.pzm2 = pdiff(zm2h, zm2l, n.ph, n.pl);
-        {
-          const float *H = S0, *L = S0 + AS;
-          const float2 ah = ld2(H, col - 2), al = ld2(L, col - 2), dh = ld2(H, col + 2), dl = ld2(L, col + 2);
-          n.pxp1 = make_float2(pdiff(n.ph.y, n.pl.y, n.ph.x, n.pl.x), pdiff(dh.x, dl.x, n.ph.y, n.pl.y));
-          n.pxm1 = make_float2(pdiff(ah.y, al.y, n.ph.x, n.pl.x), pdiff(n.ph.x, n.pl.x, n.ph.y, n.pl.y));
-          n.pxp2 = pdiff(dh, dl, n.ph, n.pl);
-          n.pxm2 = pdiff(ah, al, n.ph, n.pl);
-          n.pyp1 = pdiff(ld2(H, col + BX), ld2(L, col + BX), n.ph, n.pl);
-          n.pym1 = pdiff(ld2(H, col - BX), ld2(L, col - BX), n.ph, n.pl);
-          n.pyp2 = pdiff(ld2(H, col + 2 * BX), ld2(L, col + 2 * BX), n.ph, n.pl);
-          n.pym2 = pdiff(ld2(H, col - 2 * BX), ld2(L, col - 2 * BX), n.ph, n.pl);
-        }
-        // velocity: x differences per node, y and z packed
-#define BDC_F32Q_VEL(F, c0, xp, xm, yp, ym, zp, zm)                                                  \
-  {                                                                                                \
-    const float *Q = S0 + F * AS;                                                                  \
-    c0 = ld2(Q, col);                                                                              \
-    const float qm = Q[col - 1], qp = Q[col + 2];                                                  \
-    xp = make_float2(vsub(c0.y, c0.x), vsub(qp, c0.y));                                            \
-    xm = make_float2(vsub(qm, c0.x), vsub(c0.x, c0.y));                                            \
-    yp = vsub(ld2(Q, col + BX), c0);                                                               \
-    ym = vsub(ld2(Q, col - BX), c0);                                                               \
-    zp = vsub(ld2(Sp1 + F * AS, col), c0);                                                         \
-    zm = vsub(qm1[F], c0);                                                         \
-  }
-        BDC_F32Q_VEL(2, n.u, n.uxp, n.uxm, n.uyp, n.uym, n.uzp, n.uzm)
-        BDC_F32Q_VEL(3, n.v, n.vxp, n.vxm, n.vyp, n.vym, n.vzp, n.vzm)
-        BDC_F32Q_VEL(4, n.w, n.wxp, n.wxm, n.wyp, n.wym, n.wzp, n.wzm)
-#undef BDC_F32Q_VEL
-        // temperature pair
-        n.th = th;
-        n.tl = tl;
-        {
-          const float *TH = S0 + 5 * AS, *TL = S0 + 6 * AS;
-          n.txp = make_float2(pdiff(th.y, tl.y, th.x, tl.x), pdiff(TH[col + 2], TL[col + 2], th.y, tl.y));
-          n.txm = make_float2(pdiff(TH[col - 1], TL[col - 1], th.x, tl.x), pdiff(th.x, tl.x, th.y, tl.y));
-          n.typ = pdiff(ld2(TH, col + BX), ld2(TL, col + BX), th, tl);
-          n.tym = pdiff(ld2(TH, col - BX), ld2(TL, col - BX), th, tl);
-          n.tzp = pdiff(tzph, tzpl, th, tl);
-          n.tzm = pdiff(tzmh, tzml, th, tl);
-        }
-        F32Out<float2> o;
-        float2 dtn = K.dt, mdtn = K.mdt;
-        if (a.local_dt) {  // each node's own stable step
-          dtn = make_float2(__fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.x, n.v.x, n.w.x)),
-                            __fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.y, n.v.y, n.w.y)));
-          mdtn = make_float2(-dtn.x, -dtn.y);
-        }
-        f32_update(K, n, dtn, mdtn, o);
-        const float2 bound = f32_spectral_bound(K, o.u, o.v, o.w);
-        f32_spectral_max(K1, bound.x, o.u.x, o.v.x, o.w.x, smax);
-        if (act1) {
-          st2(out, o.ph);
-          st2(out + fs, o.pl);
-          st2(out + 2 * fs, o.u);
-          st2(out + 3 * fs, o.v);
-          st2(out + 4 * fs, o.w);
-          st2(out + 5 * fs, o.th);
-          st2(out + 6 * fs, o.tl);
-          f32_spectral_max(K1, bound.y, o.u.y, o.v.y, o.w.y, smax);
-        } else {  // the x extent is odd: the pair's second node is a wall or beyond
-          out[0] = o.ph.x;
-          out[fs] = o.pl.x;
-          out[2 * fs] = o.u.x;
-          out[3 * fs] = o.v.x;
-          out[4 * fs] = o.w.x;
-          out[5 * fs] = o.th.x;
-          out[6 * fs] = o.tl.x;
-          o.rp.y = o.ru.y = o.rv.y = o.rw.y = o.rt.y = 0.f;
-        }
-        s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
-        s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
-        if (nus_warp) {
-          acc_pair(ch, cl, o.th, o.tl);
-          acc_pair(wsh, wsl, S0[5 * AS + col + wofs], S0[6 * AS + col + wofs]);
-        }
-        // the register queues move one plane: z - 2 <- z - 1 (p), z - 1 <- this plane
-        qm2h = qm1[0];
-        qm2l = qm1[1];
-        qm1[0] = n.ph; qm1[1] = n.pl; qm1[2] = n.u; qm1[3] = n.v; qm1[4] = n.w; qm1[5] = th; qm1[6] = tl;
-      }
+      if (c.act0)
+        f32q_pair<TY>(slot(pk), slot(pk + 1), slot(pk + 2), K, K1, k, nz, T.wzl, T.wzh, a.local_dt, out, fs, c.col,
+                      c.wofs, c.act1, c.nus_warp, acc);
       out += plane;
     }
     bad = __syncthreads_or(bad);
@@ -1105,15 +1187,141 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
     }
     __syncthreads();
   }
-  double nuh = 0.0, nuc = 0.0;
-  if (nus) {
-    const double t0 = pair_value(ch.x, cl.x), t1 = act1 ? pair_value(ch.y, cl.y) : 0.0;
-    const double wall_t = 3.0 * pair_value(wsh, wsl);
-    nuh = wh0 * t0 + wh1 * t1 + (hot_next ? wall_t : 0.0);
-    nuc = wc0 * t0 + wc1 * t1 + (cold_next0 || cold_next1 ? wall_t : 0.0);
+  f32q_finish<NT>(a.partials, cta, tid, T, c, acc);
+}
+
+// Persistent form of k_step_f32q.  The grid holds only the CTAs resident at
+// once; CTA b takes the tiles b, b + G, b + 2G, ... (G CTAs: a static order,
+// so every tile's partial slot and sums are those of k_step_f32q), and thread
+// 0 streams the planes of the CTA's successive tiles through one ring: the
+// first planes of the next tile load while the current one finishes, so no
+// tile starts on an empty ring and the grid has no launch waves.  Planes
+// carry a sequence number g over the CTA's tiles: slot g mod R, mbarrier
+// phase (g / R) mod 2.  A tile has at least 5 planes, so with R = 5 the
+// producer runs at most one tile ahead of the consumers.
+template <int TY, int KC>
+__global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_step_f32s(StepF32Args a) {
+  constexpr int R = 5;
+  constexpr int NTX = kF32TX / 2, NT = NTX * TY;
+  constexpr int BY = f32_box_y(TY);
+  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float *ring = reinterpret_cast<float *>(smem_raw);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
+  const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
+  const int G = gridDim.x, ntiles = a.ntiles;
+  if ((int)blockIdx.x >= ntiles) return;
+
+  if (tid == 0) {
+    for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  f32_partials<NT>(a.partials, cta, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
-                   vadd(s4.x, s4.y), smax, nuh, nuc);
+  __syncthreads();
+
+  // producer (thread 0; in shared memory, off the register budget): sequence
+  // number of the next plane, its tile, that tile's first sequence number,
+  // plane count, box origin and tensor map
+  struct Producer {
+    int g_issued, tile, g0, np, x0, y0, zb;
+    const CUtensorMap *map;
+  };
+  __shared__ Producer pr;
+  auto producer_tile = [&]() {
+    const F32Tile PT = f32_tile<TY, KC>(a, pr.tile);
+    pr.np = PT.nplanes;
+    pr.x0 = PT.x0;
+    pr.y0 = PT.y0;
+    pr.zb = PT.zbase;
+    const CUtensorMap *m = a.maps + 2 * PT.b + a.parity;
+    if (m != pr.map) {
+      pr.map = m;
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+    }
+  };
+  // issue planes while fewer than R are outstanding beyond the freed ones
+  auto produce = [&](int freed) {
+    int g = pr.g_issued;
+    while (g < freed + R && pr.tile < ntiles) {
+      if (g - pr.g0 == pr.np) {  // the producer's tile is fully issued: the CTA's next tile
+        pr.tile += G;
+        pr.g0 = g;
+        if (pr.tile >= ntiles) break;
+        producer_tile();
+      }
+      const int s = g % R;
+      mbar_expect_tx(&bars[s], SB);
+      tma_load_4d(ring + s * SF, pr.map, &bars[s], pr.x0, pr.y0, pr.zb + (g - pr.g0), 0);
+      ++g;
+    }
+    pr.g_issued = g;
+  };
+  if (tid == 0) {
+    pr.g_issued = 0;
+    pr.tile = blockIdx.x;
+    pr.g0 = 0;
+    pr.map = nullptr;
+    producer_tile();
+    produce(0);
+  }
+
+  bool bad = false;
+  int g0 = 0, cav = 0;  // sequence number of the current tile's plane 0; its cavity
+  for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+    const F32Tile T = f32_tile<TY, KC>(a, tile);
+    const BlockDev &B = a.blocks[T.b];
+    const CavConst &C = a.cc[B.cav];
+    cav = B.cav;
+    const F32QCol c = f32q_column(B, T, li, lj);
+    auto wait_plane = [&](int pl) {
+      const int g = g0 + pl;
+      return mbar_wait_bounded(&bars[g % R], (uint32_t)((g / R) & 1));
+    };
+    auto slot = [&](int pl) { return ring + ((g0 + pl) % R) * SF; };
+    const long long fs = B.fstride, plane = B.plane;
+    const int nz = B.nz;
+    float *__restrict__ out =
+        (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(c.i, B.nx), min(c.j, B.ny), T.k0);
+    F32QAcc acc;
+    f32q_clear(acc);
+    for (int pl = 0; pl < 4; ++pl) {
+      if (!bad && !wait_plane(pl)) bad = true;
+      if (!bad) f32q_prologue_plane<NT, BY>(pl, slot(pl), T, c, tid, acc);
+    }
+    bad = __syncthreads_or(bad);
+    // a programmatic dependent of the previous step's finalise (see k_step_f32q)
+    if (tile == (int)blockIdx.x) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (bad) break;
+    const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
+    const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
+    if (tid == 0) produce(g0 + 2);  // the slots of planes 0 and 1 are free again
+
+    for (int k = T.k0; k <= T.k1; ++k) {
+      const int pk = k - T.k0 + 2;  // plane index of k
+      if (!wait_plane(pk + 2)) bad = true;
+      if (!bad) {
+        if (T.fix) fix_plane_walls<NT, BY>(slot(pk + 2), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+        if (c.act0)
+          f32q_pair<TY>(slot(pk), slot(pk + 1), slot(pk + 2), K, K1, k, nz, T.wzl, T.wzh, a.local_dt, out, fs,
+                        c.col, c.wofs, c.act1, c.nus_warp, acc);
+        out += plane;
+      }
+      bad = __syncthreads_or(bad);
+      if (bad) break;
+      if (tid == 0) produce(g0 + pk + 1);  // the slot of plane pk is free
+    }
+    if (bad) break;
+    g0 += T.nplanes;
+    if (tid == 0) produce(g0);  // every plane of the tile is free: stream the next tile's
+    f32q_finish<NT>(a.partials, tile, tid, T, c, acc);
+  }
+  if (bad) {
+    if (tid == 0) {
+      atomicOr(&a.cs[cav].flags, 2);
+      for (int g = max(0, pr.g_issued - R); g < pr.g_issued; ++g)
+        (void)mbar_wait_bounded(&bars[g % R], (uint32_t)((g / R) & 1));
+    }
+    __syncthreads();
+  }
 }
 
 // Spectral-radius partials of the current state (no update), with the step

@@ -32,11 +32,11 @@ using namespace bdc;
 namespace {
 
 constexpr int kTX = 32, kTY = 8, kKC = 16;  // the tile of the FP64 step kernel
-constexpr int kDescBytes = 1024;           // BlockDev + CavConst + CavState, 256-byte aligned slots
+constexpr int kDescBytes = 1280;           // BlockDev (256) + CavConst (768) + CavState (256), aligned slots
 constexpr size_t kScratchBytes = kDescBytes + (size_t)CAVITY_NOALLOC_MAX_TILES * kPartStride * sizeof(double);
 constexpr int kMaxDevices = 64;
 
-static_assert(sizeof(BlockDev) <= 256 && sizeof(CavConst) <= 512 && sizeof(CavState) <= 256,
+static_assert(sizeof(BlockDev) <= 256 && sizeof(CavConst) <= 768 && sizeof(CavState) <= 256,
               "descriptor slots too small");
 
 // reduction scratch and descriptors of the allocation-free entry point
@@ -111,7 +111,7 @@ extern "C" CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *
   unsigned char *s = (unsigned char *)scratch;
   BlockDev *d_block = (BlockDev *)s;
   CavConst *d_cc = (CavConst *)(s + 256);
-  CavState *d_cs = (CavState *)(s + 768);
+  CavState *d_cs = (CavState *)(s + 1024);
   double *d_part = (double *)(s + kDescBytes);
 
   // dense caller layout: node (i, j, k), i in [-1, n+2], at (i+1) + (nx+4)((j+1) + (ny+4)(k+1));
