@@ -40,9 +40,17 @@ struct BlockDev {
   int nbr[6];            // neighbour block across a cut face, -1 on walls
   int cav;               // cavity this block belongs to
   int tiles_x, tiles_y, tiles_z;
-  int tile_begin;        // first k_step CTA of this block
+  int tile_begin;        // first partial slot (k_step tile) of this block
+  // z chunking of the FP64 step: chunks 0 .. tiles_zc-1 of KC planes cover
+  // planes 1 .. zsplit, the other tiles_z - tiles_zc chunks split planes
+  // zsplit+1 .. nz into kFineKC planes.  The persistent FP64 kernel takes
+  // every block's coarse tiles first (scheduling index coarse_begin + local)
+  // and the fine ones last (ncoarse + fine_begin + local), so its last round
+  // is made of short tiles.  (The FP32 kernels: tiles_zc = tiles_z, zsplit = nz.)
+  int tiles_zc, zsplit, coarse_begin, fine_begin;
   void *base[2];         // buffer sets (field f at base + f * fstride)
 };
+constexpr int kFineKC = 2;
 
 struct CavConst {
   double h[3], ih[3], ih2[3], ihh[3];
@@ -362,6 +370,7 @@ struct StepArgs {
   int ntiles;
   int local_dt;                // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
   int skip_shell;              // 1: leave the nodes within two layers of a cut face to k_shell_f64
+  int ncoarse;                 // coarse tiles of all blocks (scheduling indices below it)
 };
 
 // whether local node (i, j, k) of B lies within two layers of one of B's cut
@@ -385,20 +394,50 @@ __device__ __forceinline__ int find_block(const BlockDev *blocks, int nblocks, i
   return lo;
 }
 
+// The FP64 tile of scheduling index c: its block, x/y tile, plane range and
+// partial slot (coarse and fine tiles as described at BlockDev).
+struct F64Tile {
+  int b, tx, ty, k0, k1, slot;
+};
+
+template <int KC>
+__device__ __forceinline__ F64Tile f64_tile(const StepArgs &a, int c) {
+  const bool coarse = c < a.ncoarse;
+  const int u = coarse ? c : c - a.ncoarse;
+  // the last block whose first tile of this class is at or before u (blocks
+  // without tiles of the class share their successor's start and are passed)
+  int lo = 0, hi = a.nblocks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int begin = coarse ? a.blocks[mid].coarse_begin : a.blocks[mid].fine_begin;
+    if (begin <= u) lo = mid; else hi = mid - 1;
+  }
+  const BlockDev &B = a.blocks[lo];
+  const int l = u - (coarse ? B.coarse_begin : B.fine_begin);
+  F64Tile T;
+  T.b = lo;
+  T.tx = l % B.tiles_x;
+  T.ty = (l / B.tiles_x) % B.tiles_y;
+  const int zl = l / (B.tiles_x * B.tiles_y);
+  T.k0 = coarse ? zl * KC + 1 : B.zsplit + zl * kFineKC + 1;
+  T.k1 = coarse ? min(T.k0 + KC - 1, B.zsplit) : min(T.k0 + kFineKC - 1, B.nz);
+  const int tz = coarse ? zl : B.tiles_zc + zl;
+  T.slot = B.tile_begin + T.tx + B.tiles_x * (T.ty + B.tiles_y * tz);
+  return T;
+}
+
 // wfloor: a warp-uniform FP32 value at or below an exact spectral value some
 // lane of the warp has already recorded (carried across the warp's tiles)
 template <int TX, int TY, int KC>
 __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float &wfloor) {
   constexpr int NT = TX * TY;
-  const int b = find_block(a.blocks, a.nblocks, cta);
-  const BlockDev &B = a.blocks[b];
+  const F64Tile tile = f64_tile<KC>(a, cta);
+  const BlockDev &B = a.blocks[tile.b];
   const CavConst &C = a.cc[B.cav];
-  const int t = cta - B.tile_begin;
-  const int tx = t % B.tiles_x, ty = (t / B.tiles_x) % B.tiles_y, tz = t / (B.tiles_x * B.tiles_y);
-  const int i = tx * TX + threadIdx.x + 1;
-  const int j = ty * TY + threadIdx.y + 1;
-  const int k0 = tz * KC + 1;
-  const int k1 = min(k0 + KC - 1, B.nz);
+  const int i = tile.tx * TX + threadIdx.x + 1;
+  const int j = tile.ty * TY + threadIdx.y + 1;
+  const int k0 = tile.k0;
+  const int k1 = tile.k1;
   const bool active = (i <= B.nx) && (j <= B.ny);
   const double dt = a.cs[B.cav].dt;
   const double cshift = a.cs[B.cav].c;
@@ -477,7 +516,7 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
   if (tid < 6) {
     double acc = red[0][tid];
     for (int q = 1; q < NT / 32; ++q) acc = (tid == 5) ? fmax(acc, red[q][tid]) : acc + red[q][tid];
-    a.partials[(long long)cta * kPartStride + tid] = acc;
+    a.partials[(long long)tile.slot * kPartStride + tid] = acc;
   }
 }
 

@@ -120,6 +120,7 @@ struct cavity {
   std::vector<CutFace> hcut;
   long long xbuf_elems = 0;
   int n_step = 0, n_bc = 0, n_cut = 0;
+  int n_coarse = 0;  // FP64 step tiles of KC planes (scheduled before the fine ones)
   int part_cap = 0;  // step partials allocated (CTAs)
 
   BlockDev *d_blocks = nullptr;
@@ -208,20 +209,36 @@ int check_desc(const cavity_desc &d) {
 // ---------------------------------------------------------------------------
 // layout: blocks of every cavity, wall / cut face lists, centre nodes
 
+// Step-kernel tiles and their partial slots, block by block (a cavity's
+// slots are contiguous).  FP64: the planes below the last KC-plane boundary
+// in KC-plane chunks, the rest in kFineKC-plane chunks, scheduled after every
+// block's coarse tiles; FP32: KC-plane chunks only.
 void assign_tiles(cavity *h) {
-  int tile = 0;
+  int tile = 0, coarse = 0, fine = 0;
   for (int c = 0; c < h->ncav; ++c) h->hcc[c].tile_begin = -1;
   for (BlockDev &B : h->hb) {
     B.tiles_x = ceil_div(B.nx, h->tx);
     B.tiles_y = ceil_div(B.ny, h->ty);
-    B.tiles_z = ceil_div(B.nz, h->kc);
+    if (h->f32) {
+      B.tiles_zc = ceil_div(B.nz, h->kc);
+      B.zsplit = B.nz;
+    } else {
+      B.tiles_zc = (B.nz - 1) / h->kc;
+      B.zsplit = B.tiles_zc * h->kc;
+    }
+    B.tiles_z = B.tiles_zc + ceil_div(B.nz - B.zsplit, kFineKC);
     B.tile_begin = tile;
+    B.coarse_begin = coarse;
+    B.fine_begin = fine;
     CavConst &C = h->hcc[B.cav];
     if (C.tile_begin < 0) C.tile_begin = tile;
     tile += B.tiles_x * B.tiles_y * B.tiles_z;
+    coarse += B.tiles_x * B.tiles_y * B.tiles_zc;
+    fine += B.tiles_x * B.tiles_y * (B.tiles_z - B.tiles_zc);
     C.tile_end = tile;
   }
   h->n_step = tile;
+  h->n_coarse = coarse;
 }
 
 int build_layout(cavity *h) {
@@ -467,6 +484,7 @@ StepArgs step_args(cavity *h, int parity, int mode) {
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.partials = h->d_step_part; a.parity = parity; a.mode = mode;
   a.tile_counter = h->d_counter + h->ncav; a.ntiles = h->n_step; a.local_dt = h->local_dt;
+  a.ncoarse = h->n_coarse;
   a.skip_shell = 0;
   return a;
 }

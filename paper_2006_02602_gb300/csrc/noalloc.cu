@@ -126,6 +126,10 @@ extern "C" CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *
   B.tiles_x = ceil_div(nx, kTX);
   B.tiles_y = ceil_div(ny, kTY);
   B.tiles_z = ceil_div(nz, kKC);
+  B.tiles_zc = B.tiles_z;  // one CTA per tile: KC-plane chunks only
+  B.zsplit = nz;
+  B.coarse_begin = 0;
+  B.fine_begin = 0;
   B.base[0] = (void *)(q_in - (XO<double>::v - 2));
   B.base[1] = (void *)(q_out - (XO<double>::v - 2));
 
@@ -145,6 +149,7 @@ extern "C" CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *
   StepArgs a{};  // tile_counter null: one CTA per tile
   a.blocks = d_block; a.nblocks = 1; a.cc = d_cc; a.cs = d_cs;
   a.partials = d_part; a.parity = 0; a.mode = 0; a.ntiles = (int)ntiles;
+  a.ncoarse = (int)ntiles;
   k_step_f64<kTX, kTY, kKC><<<(int)ntiles, dim3(kTX, kTY), 0, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return CAVITY_ERR_CUDA;
   k_noalloc_reduce<<<1, 256, 0, st>>>(d_part, (int)ntiles, d_cc, out6);
