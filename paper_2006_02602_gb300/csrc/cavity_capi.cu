@@ -28,7 +28,10 @@ using namespace bdc;
 
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kKC = 8;  // k_step tile of the FP64 form
+// k_step tile of the FP64 form: 32 x 4 threads (166 registers each: three
+// CTAs, 12 warps, per SM hide the FP64 pipe's latency better than one CTA of
+// 32 x 8), 8-plane chunks
+constexpr int kTX = 32, kTY = 4, kKC = 8;
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -443,7 +446,10 @@ int alloc_device(cavity *h) {
   {
     int nsm = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_f64<kTX, kTY, kKC>, kTX * kTY, 0));
+    if (h->ty == 4)
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_f64<kTX, 4, kKC>, kTX * 4, 0));
+    else
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_f64<kTX, 8, kKC>, kTX * 8, 0));
     h->persist_ctas = std::max(1, nsm * per_sm);
     h->nsm = nsm;
   }
@@ -517,6 +523,16 @@ ExchArgs exch_args(cavity *h, int parity) {
   return a;
 }
 
+// The persistent FP64 step kernel of the handle's tile height (8 or 4 rows;
+// 32 x TY threads, as many CTAs as fit on the GPU at once).
+void launch_step_f64(cavity *h, const StepArgs &a) {
+  const int grid = std::min(h->n_step, h->persist_ctas);
+  if (h->ty == 4)
+    k_step_f64<kTX, 4, kKC><<<grid, dim3(kTX, 4), 0, h->stream>>>(a);
+  else
+    k_step_f64<kTX, 8, kKC><<<grid, dim3(kTX, 8), 0, h->stream>>>(a);
+}
+
 // `after_finalise`: the launch directly follows, in the same stream capture,
 // the finalise of the previous step (the second step of a two-step graph with
 // no cut faces).  The FP32 step kernel is then launched as a programmatic
@@ -545,8 +561,7 @@ void launch_step_kernel(cavity *h, int parity, bool after_finalise = false) {
     BDC_F32_VARIANTS(BDC_LAUNCH)
 #undef BDC_LAUNCH
   } else {
-    k_step_f64<kTX, kTY, kKC><<<std::min(h->n_step, h->persist_ctas), dim3(kTX, kTY), 0, h->stream>>>(
-        step_args(h, parity, 0));
+    launch_step_f64(h, step_args(h, parity, 0));
   }
 }
 
@@ -559,7 +574,7 @@ void launch_spectral(cavity *h) {
     BDC_F32_VARIANTS(BDC_SPEC)
 #undef BDC_SPEC
   } else {
-    k_step_f64<kTX, kTY, kKC><<<std::min(h->n_step, h->persist_ctas), dim3(kTX, kTY), 0, h->stream>>>(sa);
+    launch_step_f64(h, sa);
   }
 }
 
@@ -620,7 +635,7 @@ int launch_step_overlapped(cavity *h, int parity) {
   CK(cudaEventRecord(h->ev_exch, h->side));
   StepArgs st = step_args(h, parity, 0);
   st.skip_shell = 1;
-  k_step_f64<kTX, kTY, kKC><<<std::min(h->n_step, h->persist_ctas), dim3(kTX, kTY), 0, h->stream>>>(st);
+  launch_step_f64(h, st);
   CK(cudaGetLastError());
   CK(cudaStreamWaitEvent(h->stream, h->ev_exch, 0));
   BcArgs ba = bc_args(h, parity ^ 1, 0);
@@ -853,6 +868,13 @@ int create_common(const cavity_desc *descs, const cavity_params *params, int n, 
   h->esize = h->f32 ? 4 : 8;
   h->na = h->f32 ? Store<float>::NA : Store<double>::NA;
   h->np = h->f32 ? Store<float>::NP : Store<double>::NP;
+  if (!h->f32) {
+    // tile-height override for tuning sweeps: BDC_F64_TY=4 or 8
+    if (const char *env = std::getenv("BDC_F64_TY")) {
+      const int ty = std::atoi(env);
+      if (ty == 4 || ty == 8) h->ty = ty;
+    }
+  }
   if (h->f32) {
     h->tx = kF32TX;
     h->ty = kF32TY;
