@@ -49,10 +49,16 @@ FP64_FLOP_PER_POINT = 190
 # u, v, w and the hi/lo pairs of p and T)
 BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the same workload (profiles/k_step_f64_cavity128_2x2x2.md,
-# profiles/k_step_f32p_cavity256.md); None where no capture of the current
-# kernel exists
-TRAFFIC = {}
+# capture of the same workload and kernel shape (profiles/k_step_f64_cavity128_2x2x2.md,
+# profiles/k_step_f32q_cavity256.md); None where no capture of the current
+# kernel exists.  Key: (precision, workload, blocks, shape); the FP32 shape is
+# the autotuner's "TY,KC,R,form"
+FP64_SHAPE = "32x4x8"
+TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.825472e6 + 55.842816e6,
+           ("fp32", "cfg3", (1, 1, 1), "8,40,5,3"): 580.006656e6 + 434.687232e6}
+F32_FORMS = {1: "k_step_f32 (one node per thread; z neighbours from the TMA ring)",
+             2: "k_step_f32p (two nodes per thread, f32x2; z neighbours from the TMA ring)",
+             3: "k_step_f32q (two nodes per thread, f32x2; z neighbours below the plane in registers)"}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129e6
@@ -217,16 +223,15 @@ def run_reference(args):
     return 0
 
 
-def roofline_for(precision, pts, step_ms, hbm, traffic=None):
+def roofline_for(precision, pts, step_ms, hbm, traffic=None, form=3):
     step_s = step_ms / 1e3
     bpp = BYTES_PER_POINT[precision]
     gbs = bpp * pts / step_s / 1e9
     hbm_obj = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if hbm else None,
                "bytes_per_point": bpp, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if precision == "fp32":
-        return dict(kernel="k_step_f32q (TMA-staged fused residual + update + partials; two nodes per thread, "
-                           "f32x2, z neighbours below the plane in registers)", traffic=traffic, kernel_ms=step_ms,
-                    **hbm_obj)
+        return dict(kernel=F32_FORMS.get(form, f"FP32 step kernel form {form}") +
+                    ": TMA-staged fused residual + update + partials", traffic=traffic, kernel_ms=step_ms, **hbm_obj)
     tf = FP64_FLOP_PER_POINT * pts / step_s / 1e12
     return {"kernel": "k_step_f64 (fused residual + update + reductions)", "bound": "alu", "achieved": tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
@@ -258,6 +263,7 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
             torch.distributed.barrier()
 
     tuned = m.cavity_autotune(c.h, 10) if precision == "fp32" else None  # FP32: the autotuner picks the shape
+    shape = (f"{tuned['tile_y']},{tuned['kc']},{tuned['ring']},{tuned['kernel_form']}" if tuned else FP64_SHAPE)
     c.step(warmup)
     c.sync()
     kms = m.cavity_time_kernels(c.h, 20)
@@ -292,7 +298,8 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
            "l2": ("L2 flushed (2 x L2 buffer written) before every timed step: the state fits in L2" if flush else
                   f"no flush: the two state buffers ({both_buffers / 1e6:.0f} MB) exceed the 129 MB L2"),
            "roofline": roofline_for(precision, pts, kms[0], measured_peaks().get("hbm_gbs"),
-                                    TRAFFIC.get((precision, workload, tuple(blocks))))}
+                                    TRAFFIC.get((precision, workload, tuple(blocks), shape)),
+                                    tuned["kernel_form"] if tuned else 3)}
     if e2e:
         # end to end through the public API with host buffers: initial state
         # from host, every step followed by the residual + Nusselt read, final

@@ -47,7 +47,6 @@ struct StepF32Args {
   double *partials;           // [cta][kPartStride]: 5 rate sums, spectral max, 2 Nusselt sums
   int parity;
   int local_dt;               // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
-  int ntiles;                 // tiles of the step (the persistent form's grid may be smaller)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -1188,140 +1187,6 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
     __syncthreads();
   }
   f32q_finish<NT>(a.partials, cta, tid, T, c, acc);
-}
-
-// Persistent form of k_step_f32q.  The grid holds only the CTAs resident at
-// once; CTA b takes the tiles b, b + G, b + 2G, ... (G CTAs: a static order,
-// so every tile's partial slot and sums are those of k_step_f32q), and thread
-// 0 streams the planes of the CTA's successive tiles through one ring: the
-// first planes of the next tile load while the current one finishes, so no
-// tile starts on an empty ring and the grid has no launch waves.  Planes
-// carry a sequence number g over the CTA's tiles: slot g mod R, mbarrier
-// phase (g / R) mod 2.  A tile has at least 5 planes, so with R = 5 the
-// producer runs at most one tile ahead of the consumers.
-template <int TY, int KC>
-__global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_step_f32s(StepF32Args a) {
-  constexpr int R = 5;
-  constexpr int NTX = kF32TX / 2, NT = NTX * TY;
-  constexpr int BY = f32_box_y(TY);
-  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float *ring = reinterpret_cast<float *>(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
-  const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
-  const int G = gridDim.x, ntiles = a.ntiles;
-  if ((int)blockIdx.x >= ntiles) return;
-
-  if (tid == 0) {
-    for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  // producer (thread 0; in shared memory, off the register budget): sequence
-  // number of the next plane, its tile, that tile's first sequence number,
-  // plane count, box origin and tensor map
-  struct Producer {
-    int g_issued, tile, g0, np, x0, y0, zb;
-    const CUtensorMap *map;
-  };
-  __shared__ Producer pr;
-  auto producer_tile = [&]() {
-    const F32Tile PT = f32_tile<TY, KC>(a, pr.tile);
-    pr.np = PT.nplanes;
-    pr.x0 = PT.x0;
-    pr.y0 = PT.y0;
-    pr.zb = PT.zbase;
-    const CUtensorMap *m = a.maps + 2 * PT.b + a.parity;
-    if (m != pr.map) {
-      pr.map = m;
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
-    }
-  };
-  // issue planes while fewer than R are outstanding beyond the freed ones
-  auto produce = [&](int freed) {
-    int g = pr.g_issued;
-    while (g < freed + R && pr.tile < ntiles) {
-      if (g - pr.g0 == pr.np) {  // the producer's tile is fully issued: the CTA's next tile
-        pr.tile += G;
-        pr.g0 = g;
-        if (pr.tile >= ntiles) break;
-        producer_tile();
-      }
-      const int s = g % R;
-      mbar_expect_tx(&bars[s], SB);
-      tma_load_4d(ring + s * SF, pr.map, &bars[s], pr.x0, pr.y0, pr.zb + (g - pr.g0), 0);
-      ++g;
-    }
-    pr.g_issued = g;
-  };
-  if (tid == 0) {
-    pr.g_issued = 0;
-    pr.tile = blockIdx.x;
-    pr.g0 = 0;
-    pr.map = nullptr;
-    producer_tile();
-    produce(0);
-  }
-
-  bool bad = false;
-  int g0 = 0, cav = 0;  // sequence number of the current tile's plane 0; its cavity
-  for (int tile = blockIdx.x; tile < ntiles; tile += G) {
-    const F32Tile T = f32_tile<TY, KC>(a, tile);
-    const BlockDev &B = a.blocks[T.b];
-    const CavConst &C = a.cc[B.cav];
-    cav = B.cav;
-    const F32QCol c = f32q_column(B, T, li, lj);
-    auto wait_plane = [&](int pl) {
-      const int g = g0 + pl;
-      return mbar_wait_bounded(&bars[g % R], (uint32_t)((g / R) & 1));
-    };
-    auto slot = [&](int pl) { return ring + ((g0 + pl) % R) * SF; };
-    const long long fs = B.fstride, plane = B.plane;
-    const int nz = B.nz;
-    float *__restrict__ out =
-        (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(c.i, B.nx), min(c.j, B.ny), T.k0);
-    F32QAcc acc;
-    f32q_clear(acc);
-    for (int pl = 0; pl < 4; ++pl) {
-      if (!bad && !wait_plane(pl)) bad = true;
-      if (!bad) f32q_prologue_plane<NT, BY>(pl, slot(pl), T, c, tid, acc);
-    }
-    bad = __syncthreads_or(bad);
-    // a programmatic dependent of the previous step's finalise (see k_step_f32q)
-    if (tile == (int)blockIdx.x) asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (bad) break;
-    const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
-    const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
-    if (tid == 0) produce(g0 + 2);  // the slots of planes 0 and 1 are free again
-
-    for (int k = T.k0; k <= T.k1; ++k) {
-      const int pk = k - T.k0 + 2;  // plane index of k
-      if (!wait_plane(pk + 2)) bad = true;
-      if (!bad) {
-        if (T.fix) fix_plane_walls<NT, BY>(slot(pk + 2), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
-        if (c.act0)
-          f32q_pair<TY>(slot(pk), slot(pk + 1), slot(pk + 2), K, K1, k, nz, T.wzl, T.wzh, a.local_dt, out, fs,
-                        c.col, c.wofs, c.act1, c.nus_warp, acc);
-        out += plane;
-      }
-      bad = __syncthreads_or(bad);
-      if (bad) break;
-      if (tid == 0) produce(g0 + pk + 1);  // the slot of plane pk is free
-    }
-    if (bad) break;
-    g0 += T.nplanes;
-    if (tid == 0) produce(g0);  // every plane of the tile is free: stream the next tile's
-    f32q_finish<NT>(a.partials, tile, tid, T, c, acc);
-  }
-  if (bad) {
-    if (tid == 0) {
-      atomicOr(&a.cs[cav].flags, 2);
-      for (int g = max(0, pr.g_issued - R); g < pr.g_issued; ++g)
-        (void)mbar_wait_bounded(&bars[g % R], (uint32_t)((g / R) & 1));
-    }
-    __syncthreads();
-  }
 }
 
 // Spectral-radius partials of the current state (no update), with the step

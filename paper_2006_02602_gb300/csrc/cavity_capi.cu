@@ -48,12 +48,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // FP32 step-kernel shapes compiled in: (kernel form P, tile height TY, z
 // chunk KC, ring depth R); P = 1 is k_step_f32 (one node per thread), P = 2
 // k_step_f32p (two, z neighbours from the ring), P = 3 k_step_f32q (two, z
-// neighbours below the plane in registers), P = 4 k_step_f32s (P = 3 as a
-// persistent grid streaming successive tiles through one ring; R = 5)
+// neighbours below the plane in registers)
 #define BDC_F32_VARIANTS(X)                                                                       \
   X(1, 8, 16, 8) X(1, 8, 32, 8) X(1, 8, 64, 8) X(1, 4, 32, 8) X(1, 4, 64, 8) X(2, 8, 32, 8) X(2, 8, 64, 8) \
       X(2, 16, 32, 8) X(2, 16, 64, 8) X(3, 8, 16, 5) X(3, 8, 24, 5) X(3, 8, 32, 5) X(3, 8, 40, 5) X(3, 8, 64, 5) \
-      X(3, 8, 32, 6) X(4, 8, 8, 5) X(4, 8, 16, 5) X(4, 8, 24, 5) X(4, 8, 32, 5) X(4, 8, 40, 5)
+      X(3, 8, 32, 6)
 struct F32Shape {
   int p, ty, kc, r;
 };
@@ -136,8 +135,6 @@ struct cavity {
   double *d_fin = nullptr;  // k_finalize slice totals [ncav][kFinSlices][8]
   unsigned int *d_counter = nullptr;  // [ncav] k_bc CTAs done per cavity, then the FP64 step's tile counter
   int persist_ctas = 0;               // CTAs of the persistent FP64 step kernel that fit on the GPU
-  int nsm = 0;                        // SMs of the device
-  int f32_ctas = 0;                   // CTAs of the FP32 step kernel's shape that fit on the GPU at once
   void *d_fields = nullptr, *d_xbuf = nullptr;
   size_t field_bytes = 0;
   size_t stage_elems = 0;
@@ -377,30 +374,18 @@ template <int P, int TY, int KC, int R>
 auto f32_kernel() {
   if constexpr (P == 1) return k_step_f32<TY, KC, R>;
   else if constexpr (P == 2) return k_step_f32p<TY, KC, R>;
-  else if constexpr (P == 3) return k_step_f32q<TY, KC, R>;
-  else {
-    static_assert(R == 5, "the persistent form streams through a 5-slot ring");
-    return k_step_f32s<TY, KC>;
-  }
+  else return k_step_f32q<TY, KC, R>;
 }
 
-// dynamic shared memory of the FP32 step kernel's shape, and how many of its
-// CTAs fit on the GPU at once (the persistent form's grid)
-cudaError_t f32_set_smem(cavity *h, int p, int ty, int kc, int r) {
-  int per_sm = 0;
-  cudaError_t e = cudaErrorInvalidValue;
+// dynamic shared memory of the FP32 step kernel's shape
+cudaError_t f32_set_smem(int p, int ty, int kc, int r) {
 #define BDC_ATTR(P, TY, KC, R)                                                                                   \
-  if (p == P && ty == TY && kc == KC && r == R) {                                                                \
-    e = cudaFuncSetAttribute(f32_kernel<P, TY, KC, R>(), cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                             f32_smem_bytes(TY, R));                                                             \
-    if (e == cudaSuccess)                                                                                        \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32_kernel<P, TY, KC, R>(),                   \
-                                                        (P == 1 ? kF32TX : kF32TX / 2) * TY, f32_smem_bytes(TY, R)); \
-  }
+  if (p == P && ty == TY && kc == KC && r == R)                                                                  \
+    return cudaFuncSetAttribute(f32_kernel<P, TY, KC, R>(), cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                f32_smem_bytes(TY, R));
   BDC_F32_VARIANTS(BDC_ATTR)
 #undef BDC_ATTR
-  h->f32_ctas = std::max(1, per_sm) * std::max(1, h->nsm);
-  return e;
+  return cudaErrorInvalidValue;
 }
 
 int upload_tables(cavity *h) {
@@ -451,7 +436,6 @@ int alloc_device(cavity *h) {
     else
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_f64<kTX, 8, kKC>, kTX * 8, 0));
     h->persist_ctas = std::max(1, nsm * per_sm);
-    h->nsm = nsm;
   }
   CK(cudaMalloc(&h->d_twall, sizeof(double) * std::max<size_t>(1, h->twall.size())));
   if (h->xbuf_elems > 0) CK(cudaMalloc(&h->d_xbuf, h->esize * (size_t)h->xbuf_elems));
@@ -462,7 +446,7 @@ int alloc_device(cavity *h) {
   if (h->f32) {
     rc = encode_maps(h);
     if (rc != CAVITY_OK) return rc;
-    CK(f32_set_smem(h, h->f32_p, h->ty, h->kc, h->f32_r));
+    CK(f32_set_smem(h->f32_p, h->ty, h->kc, h->f32_r));
   }
   return CAVITY_OK;
 }
@@ -499,7 +483,6 @@ StepF32Args step_f32_args(cavity *h, int parity) {
   StepF32Args a;
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.maps = h->d_maps; a.partials = h->d_step_part; a.parity = parity; a.local_dt = h->local_dt;
-  a.ntiles = h->n_step;
   return a;
 }
 
@@ -547,7 +530,7 @@ void launch_step_kernel(cavity *h, int parity, bool after_finalise = false) {
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(h->f32_p == 4 ? std::min(h->n_step, h->f32_ctas) : h->n_step);
+    cfg.gridDim = dim3(h->n_step);
     cfg.stream = h->stream;
     cfg.attrs = attr;
     cfg.numAttrs = after_finalise && h->n_cut == 0 ? 1 : 0;
@@ -713,7 +696,7 @@ int retile(cavity *h, int p, int ty, int kc, int r) {
   if (rc == CAVITY_OK) rc = upload_tables(h);
   if (rc == CAVITY_OK) rc = encode_maps(h);
   if (rc != CAVITY_OK) return rc;
-  CK(f32_set_smem(h, p, ty, kc, r));
+  CK(f32_set_smem(p, ty, kc, r));
   return build_graphs(h);
 }
 

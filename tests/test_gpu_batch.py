@@ -105,7 +105,7 @@ def test_autotune_restores_state_and_keeps_fields(m):
         choice = m.cavity_autotune(h, 5)
         assert choice["tile_y"] in (4, 8, 16) and choice["kc"] in (8, 16, 24, 32, 40, 64)
         assert choice["us_per_step"] > 0
-        assert choice["kernel_form"] in (1, 2, 3, 4)
+        assert choice["kernel_form"] in (1, 2, 3)
         for b, s in enumerate(sizes):
             assert np.array_equal(m.cavity_batch_get_fields(h, b, s), before[b])
             assert m.cavity_batch_state(h, b)["step"] == 3
@@ -125,7 +125,7 @@ def test_fp32_tile_shapes_give_identical_fields(m, monkeypatch):
     n = (45, 38, 70)
     out = []
     for shape in ("8,16,8", "8,64,8", "4,32,8", "8,32,8,2", "8,64,8,2", "16,32,8,2", "8,32,5,3", "8,64,5,3",
-                  "8,32,6,3", "8,8,5,4", "8,24,5,4"):
+                  "8,32,6,3", "8,40,5,3"):
         monkeypatch.setenv("BDC_F32_TILE", shape)
         with m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=4, noise_amp=1e-3, Ra=2e5) as c:
             c.step(40)
@@ -133,26 +133,6 @@ def test_fp32_tile_shapes_give_identical_fields(m, monkeypatch):
     for f, t in out[1:]:
         assert np.array_equal(f, out[0][0])
         assert t == out[0][1]
-
-
-def test_fp32_persistent_form_streams_many_tiles(m, monkeypatch):
-    """The persistent FP32 kernel with several tiles per CTA (more tiles than
-    resident CTAs), from several blocks (a tensor map per block): the same
-    fields as one CTA per tile, and a 2 x 2 x 1 decomposition bit-equal to one
-    block."""
-    n = (150, 100, 90)
-    kw = dict(precision=m.CAVITY_FP32_MIXED, seed=6, noise_amp=1e-3, Ra=1e5)
-    out = []
-    for shape, blocks in (("8,32,5,3", (1, 1, 1)), ("8,8,5,4", (1, 1, 1)), ("8,8,5,4", (2, 2, 1)),
-                          ("8,16,5,4", (2, 2, 1))):
-        monkeypatch.setenv("BDC_F32_TILE", shape)
-        with m.Cavity(*n, blocks=blocks, **kw) as c:
-            c.step(12)
-            out.append((c.fields(), c.time, c.residual))
-    for f, t, r in out[1:]:
-        assert np.array_equal(f, out[0][0])
-        assert t == out[0][1]
-        assert np.allclose(r, out[0][2], rtol=1e-5)
 
 
 def test_batch_rejects_mixed_precision_and_split_members(m):
