@@ -398,8 +398,8 @@ def measure_adjoint(m, torch, rank, world, local, stream):
             "forward_ms_per_step": 1e3 * fwd / steps, "backward_ms_per_step": 1e3 * bwd / steps,
             "J": J, "dJ_dRa": gra, "grad_wall_norm": float(np.linalg.norm(g)), "clocks": clk.summary(), "status": rc,
             "config": {"workload": f"adjoint of {steps} steps, cavity {n[0]}^3 Ra {cfg['Ra']:g}, FP32-mixed forward, "
-                                   f"FP64 reverse sweep, checkpoints every {cfg['ckpt']}"},
-            "dtype": "f32 forward (p, T as f32 pairs), f64 adjoint"}
+                                   f"FP32 reverse sweep (FP64 reductions), checkpoints every {cfg['ckpt']}"},
+            "dtype": "f32 forward (p, T as f32 pairs), f32 adjoint sweep with f64 reductions"}
 
 
 def run_ours(args):
