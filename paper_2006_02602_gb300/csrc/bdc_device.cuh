@@ -41,16 +41,18 @@ struct BlockDev {
   int cav;               // cavity this block belongs to
   int tiles_x, tiles_y, tiles_z;
   int tile_begin;        // first partial slot (k_step tile) of this block
-  // z chunking of the FP64 step: chunks 0 .. tiles_zc-1 of KC planes cover
+  // z chunking of the step kernels: chunks 0 .. tiles_zc-1 of KC planes cover
   // planes 1 .. zsplit, the other tiles_z - tiles_zc chunks split planes
-  // zsplit+1 .. nz into kFineKC planes.  The persistent FP64 kernel takes
-  // every block's coarse tiles first (scheduling index coarse_begin + local)
-  // and the fine ones last (ncoarse + fine_begin + local), so its last round
-  // is made of short tiles.  (The FP32 kernels: tiles_zc = tiles_z, zsplit = nz.)
+  // zsplit+1 .. nz into fine chunks (kFineKC planes in the FP64 form,
+  // kFineKC32 in the FP32 form).  Scheduling index c runs over every block's
+  // coarse tiles first (coarse_begin + local) and the fine ones last
+  // (ncoarse + fine_begin + local): the persistent FP64 grid's counter and
+  // the FP32 grids' block order both end on short tiles.  Partial slots stay
+  // block-major (tile_begin + local tile index), so a cavity's are contiguous.
   int tiles_zc, zsplit, coarse_begin, fine_begin;
   void *base[2];         // buffer sets (field f at base + f * fstride)
 };
-constexpr int kFineKC = 2;
+constexpr int kFineKC = 2, kFineKC32 = 8;
 
 struct CavConst {
   double h[3], ih[3], ih2[3], ihh[3];
@@ -394,36 +396,42 @@ __device__ __forceinline__ int find_block(const BlockDev *blocks, int nblocks, i
   return lo;
 }
 
-// The FP64 tile of scheduling index c: its block, x/y tile, plane range and
-// partial slot (coarse and fine tiles as described at BlockDev).
-struct F64Tile {
+// The tile of scheduling index c: its block, x/y tile, plane range and
+// partial slot (coarse chunks of KC planes, fine chunks of KF planes, as
+// described at BlockDev).
+struct TileRef {
   int b, tx, ty, k0, k1, slot;
 };
 
-template <int KC>
-__device__ __forceinline__ F64Tile f64_tile(const StepArgs &a, int c) {
-  const bool coarse = c < a.ncoarse;
-  const int u = coarse ? c : c - a.ncoarse;
+template <int KC, int KF>
+__device__ __forceinline__ TileRef tile_ref(const BlockDev *blocks, int nblocks, int ncoarse, int c) {
+  const bool coarse = c < ncoarse;
+  const int u = coarse ? c : c - ncoarse;
   // the last block whose first tile of this class is at or before u (blocks
   // without tiles of the class share their successor's start and are passed)
-  int lo = 0, hi = a.nblocks - 1;
+  int lo = 0, hi = nblocks - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    const int begin = coarse ? a.blocks[mid].coarse_begin : a.blocks[mid].fine_begin;
+    const int begin = coarse ? blocks[mid].coarse_begin : blocks[mid].fine_begin;
     if (begin <= u) lo = mid; else hi = mid - 1;
   }
-  const BlockDev &B = a.blocks[lo];
+  const BlockDev &B = blocks[lo];
   const int l = u - (coarse ? B.coarse_begin : B.fine_begin);
-  F64Tile T;
+  TileRef T;
   T.b = lo;
   T.tx = l % B.tiles_x;
   T.ty = (l / B.tiles_x) % B.tiles_y;
   const int zl = l / (B.tiles_x * B.tiles_y);
-  T.k0 = coarse ? zl * KC + 1 : B.zsplit + zl * kFineKC + 1;
-  T.k1 = coarse ? min(T.k0 + KC - 1, B.zsplit) : min(T.k0 + kFineKC - 1, B.nz);
+  T.k0 = coarse ? zl * KC + 1 : B.zsplit + zl * KF + 1;
+  T.k1 = coarse ? min(T.k0 + KC - 1, B.zsplit) : min(T.k0 + KF - 1, B.nz);
   const int tz = coarse ? zl : B.tiles_zc + zl;
   T.slot = B.tile_begin + T.tx + B.tiles_x * (T.ty + B.tiles_y * tz);
   return T;
+}
+
+template <int KC>
+__device__ __forceinline__ TileRef f64_tile(const StepArgs &a, int c) {
+  return tile_ref<KC, kFineKC>(a.blocks, a.nblocks, a.ncoarse, c);
 }
 
 // wfloor: a warp-uniform FP32 value at or below an exact spectral value some
@@ -431,7 +439,7 @@ __device__ __forceinline__ F64Tile f64_tile(const StepArgs &a, int c) {
 template <int TX, int TY, int KC>
 __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float &wfloor) {
   constexpr int NT = TX * TY;
-  const F64Tile tile = f64_tile<KC>(a, cta);
+  const TileRef tile = f64_tile<KC>(a, cta);
   const BlockDev &B = a.blocks[tile.b];
   const CavConst &C = a.cc[B.cav];
   const int i = tile.tx * TX + threadIdx.x + 1;

@@ -44,9 +44,10 @@ struct StepF32Args {
   const CavConst *cc;
   CavState *cs;               // dt and c read; flags bit 1 set on a timed-out wait
   const CUtensorMap *maps;    // [2 * block + parity], in global memory
-  double *partials;           // [cta][kPartStride]: 5 rate sums, spectral max, 2 Nusselt sums
+  double *partials;           // [slot][kPartStride]: 5 rate sums, spectral max, 2 Nusselt sums
   int parity;
   int local_dt;               // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
+  int ncoarse;                // coarse tiles of all blocks (scheduling indices below it)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -399,25 +400,27 @@ __device__ __forceinline__ void acc_pair(V &sh, V &sl, V h, V l) {
   sh = s;
 }
 
-// Tile of one CTA and the walls that fall inside its boxes.
+// Tile of one CTA (scheduling index = blockIdx.x: coarse chunks of every
+// block, then the fine chunks), its partial slot, and the walls that fall
+// inside its boxes.
 struct F32Tile {
-  int b, i0, j0, k0, k1, tx, ty, nplanes, x0, y0, zbase, lxh, lyh;
+  int b, slot, i0, j0, k0, k1, tx, ty, nplanes, x0, y0, zbase, lxh, lyh;
   bool wxl, wxh, wyl, wyh, wzl, wzh, fix;
 };
 
 template <int TY, int KC>
 __device__ __forceinline__ F32Tile f32_tile(const StepF32Args &a, int cta) {
   F32Tile T;
-  T.b = find_block(a.blocks, a.nblocks, cta);
+  const TileRef R = tile_ref<KC, kFineKC32>(a.blocks, a.nblocks, a.ncoarse, cta);
+  T.b = R.b;
+  T.slot = R.slot;
   const BlockDev &B = a.blocks[T.b];
-  const int t = cta - B.tile_begin;
-  T.tx = t % B.tiles_x;
-  T.ty = (t / B.tiles_x) % B.tiles_y;
-  const int tz = t / (B.tiles_x * B.tiles_y);
+  T.tx = R.tx;
+  T.ty = R.ty;
   T.i0 = T.tx * kF32TX + 1;
   T.j0 = T.ty * TY + 1;
-  T.k0 = tz * KC + 1;
-  T.k1 = min(T.k0 + KC - 1, B.nz);
+  T.k0 = R.k0;
+  T.k1 = R.k1;
   T.nplanes = (T.k1 - T.k0 + 1) + 4;  // z = k0-2 .. k1+2
   T.x0 = XO<float>::v - 1 + T.i0 - 4;
   T.y0 = (T.j0 - 2) + 1;
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
     nuh = wh * col_t + (hot_next ? wall_t : 0.0);
     nuc = wc * col_t + (cold_next ? wall_t : 0.0);
   }
-  f32_partials<NT>(a.partials, cta, tid, s0, s1, s2, s3, s4, smax, nuh, nuc, T.wxl || T.wxh);
+  f32_partials<NT>(a.partials, T.slot, tid, s0, s1, s2, s3, s4, smax, nuh, nuc, T.wxl || T.wxh);
 }
 
 __device__ __forceinline__ float2 ld2(const float *s, int idx) { return *reinterpret_cast<const float2 *>(s + idx); }
@@ -870,7 +873,7 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
     nuh = wh0 * t0 + wh1 * t1 + (hot_next ? wall_t : 0.0);
     nuc = wc0 * t0 + wc1 * t1 + (cold_next0 || cold_next1 ? wall_t : 0.0);
   }
-  f32_partials<NT>(a.partials, cta, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
+  f32_partials<NT>(a.partials, T.slot, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
                    vadd(s4.x, s4.y), smax, nuh, nuc, T.wxl || T.wxh);
 }
 
@@ -1186,7 +1189,7 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
     }
     __syncthreads();
   }
-  f32q_finish<NT>(a.partials, cta, tid, T, c, acc);
+  f32q_finish<NT>(a.partials, T.slot, tid, T, c, acc);
 }
 
 // Spectral-radius partials of the current state (no update), with the step
@@ -1194,14 +1197,11 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_st
 template <class S, int TX, int TY, int KC>
 __global__ void __launch_bounds__(TX *TY) k_spectral(StepArgs a) {
   constexpr int NT = TX * TY;
-  const int cta = blockIdx.x;
-  const int b = find_block(a.blocks, a.nblocks, cta);
-  const BlockDev &B = a.blocks[b];
+  const TileRef R = tile_ref<KC, kFineKC32>(a.blocks, a.nblocks, a.ncoarse, blockIdx.x);
+  const BlockDev &B = a.blocks[R.b];
   const CavConst &C = a.cc[B.cav];
-  const int t = cta - B.tile_begin;
-  const int tx = t % B.tiles_x, ty = (t / B.tiles_x) % B.tiles_y, tz = t / (B.tiles_x * B.tiles_y);
-  const int i = tx * TX + threadIdx.x + 1, j = ty * TY + threadIdx.y + 1;
-  const int k0 = tz * KC + 1, k1 = min(k0 + KC - 1, B.nz);
+  const int i = R.tx * TX + threadIdx.x + 1, j = R.ty * TY + threadIdx.y + 1;
+  const int k0 = R.k0, k1 = R.k1;
   double smax = 0.0;
   if (i <= B.nx && j <= B.ny) {
     const S *q = (const S *)B.base[a.parity];
@@ -1222,7 +1222,7 @@ __global__ void __launch_bounds__(TX *TY) k_spectral(StepArgs a) {
     double acc = 0.0;
     if (tid == 5)
       for (int q = 0; q < NT / 32; ++q) acc = fmax(acc, red[q]);
-    a.partials[(long long)cta * kPartStride + tid] = acc;
+    a.partials[(long long)R.slot * kPartStride + tid] = acc;
   }
 }
 

@@ -210,23 +210,26 @@ int check_desc(const cavity_desc &d) {
 // layout: blocks of every cavity, wall / cut face lists, centre nodes
 
 // Step-kernel tiles and their partial slots, block by block (a cavity's
-// slots are contiguous).  FP64: the planes below the last KC-plane boundary
-// in KC-plane chunks, the rest in kFineKC-plane chunks, scheduled after every
-// block's coarse tiles; FP32: KC-plane chunks only.
+// slots are contiguous).  The planes below the last KC-plane boundary go in
+// KC-plane chunks, the rest in fine chunks scheduled after every block's
+// coarse tiles: kFineKC planes in the FP64 form; kFineKC32 planes in the
+// FP32 form, and only in blocks deeper than one chunk (a shallower block is
+// one chunk: the ring's fill is paid per tile).
 void assign_tiles(cavity *h) {
   int tile = 0, coarse = 0, fine = 0;
   for (int c = 0; c < h->ncav; ++c) h->hcc[c].tile_begin = -1;
   for (BlockDev &B : h->hb) {
     B.tiles_x = ceil_div(B.nx, h->tx);
     B.tiles_y = ceil_div(B.ny, h->ty);
-    if (h->f32) {
-      B.tiles_zc = ceil_div(B.nz, h->kc);
+    const int kf = h->f32 ? kFineKC32 : kFineKC;
+    if (h->f32 && B.nz <= h->kc) {
+      B.tiles_zc = 1;
       B.zsplit = B.nz;
     } else {
       B.tiles_zc = (B.nz - 1) / h->kc;
       B.zsplit = B.tiles_zc * h->kc;
     }
-    B.tiles_z = B.tiles_zc + ceil_div(B.nz - B.zsplit, kFineKC);
+    B.tiles_z = B.tiles_zc + ceil_div(B.nz - B.zsplit, kf);
     B.tile_begin = tile;
     B.coarse_begin = coarse;
     B.fine_begin = fine;
@@ -483,6 +486,7 @@ StepF32Args step_f32_args(cavity *h, int parity) {
   StepF32Args a;
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.maps = h->d_maps; a.partials = h->d_step_part; a.parity = parity; a.local_dt = h->local_dt;
+  a.ncoarse = h->n_coarse;
   return a;
 }
 
