@@ -368,8 +368,8 @@ def measure_adjoint(m, torch, rank, world, local, stream):
     """Configuration 5: gradient of the mean hot-wall Nusselt number over 500
     FP32-mixed steps of a 128^3 cavity w.r.t. the 128x128 hot-wall temperature
     field and Ra, checkpoints every 50 steps.  Wall time of the checkpointed
-    forward run and of the reverse sweep (segment recomputation + FP64
-    adjoint kernels), through the public API."""
+    forward run and of the reverse sweep (segment recomputation + FP32
+    adjoint kernels with FP64 reductions), through the public API."""
     cfg = workloads.CFG5
     n = cfg["n"]
     pts = n[0] * n[1] * n[2]

@@ -222,8 +222,9 @@ CAVITY_API int cavity_autotune(cavity_t *h, int steps, double out[5]);
  * return J = (1/nsteps) sum over steps 1..nsteps of the hot-wall Nusselt
  * number.  The state every ckpt steps is kept on the device (checkpoints)
  * for cavity_adjoint_backward.  Single-block, single-cavity handles with
- * global time stepping only (CAVITY_ERR_UNSUPPORTED otherwise).  The state
- * afterwards is the state after the nsteps steps. */
+ * global time stepping and (nx+4)(ny+4)(nz+4) < 2^31 only
+ * (CAVITY_ERR_UNSUPPORTED otherwise).  The state afterwards is the state
+ * after the nsteps steps. */
 CAVITY_API int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J);
 
 /* Discrete adjoint, part 2: gradient of the J of the last

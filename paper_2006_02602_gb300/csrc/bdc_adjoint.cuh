@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "bdc_device.cuh"
+#include "bdc_step_f32.cuh"
 
 namespace bdc {
 
@@ -60,6 +61,8 @@ struct AdjArgs {
   double *scal;      // kSc* scalars
   double *thetabar;  // ny*nz, (j-1) + ny (k-1)
   double *argpart;   // per-CTA (max, index) pairs of k_adj_argmax
+  double *gpart;     // per-CTA (dtbar, g sigma bar, floor bar) sums of k_adj_gather
+  int ngpart;        // k_adj_gather CTAs (0: the sums go to scal by atomics, k_adj_rates)
   double dt;         // dt of this step
   double coef;       // 1 / (N ny nz 2 h_x dT)
   double dfloor;     // d(beta^2 floor)/dRa
@@ -108,14 +111,17 @@ __global__ void k_adj_sum_p(AdjArgs a) {
   if ((threadIdx.x & 31) == 0) atomicAdd(&a.scal[kScSumP], s);
 }
 
-template <class A>
+// Grid: x over the padded nodes of one field (fewer than 2^31: 32-bit index
+// arithmetic), y over the five fields.  WQ: also initialise the scatter
+// target Q (k_adj_rates adds into it; k_adj_gather writes every Q itself).
+template <class A, bool WQ>
 __global__ void k_adj_prepare(AdjArgs a) {
-  const long long n = a.g.fs * 5;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const int f = (int)(e / a.g.fs);
-  const long long r = e % a.g.fs;
-  const int i = (int)(r % a.g.ex) - 1, j = (int)((r / a.g.ex) % a.g.ey) - 1, k = (int)(r / (a.g.ex * a.g.ey)) - 1;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (unsigned)a.g.fs) return;
+  const int f = blockIdx.y;
+  const long long e = (long long)f * a.g.fs + r;
+  const unsigned ex = (unsigned)a.g.ex, ey = (unsigned)a.g.ey, rq = r / ex;
+  const int i = (int)(r - rq * ex) - 1, j = (int)(rq % ey) - 1, k = (int)(rq / ey) - 1;
   A v = 0;
   if (i >= 1 && i <= a.g.nx && j >= 1 && j <= a.g.ny && k >= 1 && k <= a.g.nz) {
     v = arr<A>(a.X)[e];
@@ -128,7 +134,7 @@ __global__ void k_adj_prepare(AdjArgs a) {
     }
   }
   arr<A>(a.Yt)[e] = v;
-  arr<A>(a.Q)[e] = v;
+  if (WQ) arr<A>(a.Q)[e] = v;
 }
 
 // The node's stencil as the reverse of the rates needs it: the velocities,
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(256) k_adj_rates(AdjArgs a) {
 // Q(m) = Yt(m) + sum of incoming contributions (Yt is zero off the interior).
 __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double dtbar = 0.0, gsbar = 0.0, floorbar = 0.0;
+  float dtbsum = 0.f, gsbsum = 0.f, flbsum = 0.f;
   if (e < a.g.fs) {
     const int i = (int)(e % a.g.ex) - 1, j = (int)((e / a.g.ex) % a.g.ey) - 1, k = (int)(e / (a.g.ex * a.g.ey)) - 1;
     const CavConst &C = a.C;
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
         dtb += yt[f] * Rf[f];
         rb[f] = dt * yt[f];
       }
-      dtbar = (double)dtb;
+      dtbsum = dtb;
       float abar[3] = {0.f, 0.f, 0.f}, gsb = 0.f;
       for (int f = 1; f <= 4; ++f) {
         for (int d = 0; d < 3; ++d) {
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
           gsb += st_.tb * rb[f];
         }
       }
-      gsbar = (double)gsb;
+      gsbsum = gsb;
       for (int d = 0; d < 3; ++d) out[1 + d] += abar[d] * ih2[d];
       float b2bar = -divV * rb[0];
       for (int d = 0; d < 3; ++d) {
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
         b2bar += lambar * isq[d];
       }
       if (floored) {
-        floorbar = (double)b2bar;
+        flbsum = b2bar;
       } else {
         for (int d = 0; d < 3; ++d) out[1 + d] += 2.f * V[d] * b2bar;
       }
@@ -445,13 +451,19 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
     float *Q = arr<float>(a.Q);
     for (int f = 0; f < 5; ++f) Q[aidx(a.g, f, i, j, k)] = out[f];
   }
-  dtbar = warp_sum(dtbar);
-  gsbar = warp_sum(gsbar);
-  floorbar = warp_sum(floorbar);
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&a.scal[kScDtbar], dtbar);
-    atomicAdd(&a.scal[kScGs], gsbar);
-    atomicAdd(&a.scal[kScFloor], floorbar);
+  // node sums: FP32 within a warp (32 terms), FP64 across the CTA's warps,
+  // one partial per CTA (no same-address atomics; k_adj_dt reduces the
+  // partials in a fixed order)
+  float s3[3] = {dtbsum, gsbsum, flbsum};
+  for (int q = 0; q < 3; ++q) s3[q] = warp_sum_f(s3[q]);
+  __shared__ double red[256 / 32][3];
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 3; ++q) red[threadIdx.x >> 5][q] = (double)s3[q];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double acc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
+    a.gpart[3 * (long long)blockIdx.x + threadIdx.x] = acc;
   }
 }
 
@@ -462,6 +474,7 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
   const long long n = (long long)a.g.nx * a.g.ny * a.g.nz;
   double best = -1.0, bidx = 0.0;
   float wfloor = 0.f;  // at or below an exact bound a lane of this warp reached
+  const F32K<float> K32 = f32_spectral_consts(a.C);
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     unflat(a.g, (unsigned)e, i, j, k);
@@ -469,20 +482,30 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
     const long long o = node_index<S>(a.B, i, j, k), fs = a.B.fstride;
     constexpr int NP = Store<S>::NP;  // u, v, w follow the p array(s)
     const S u = q[NP * fs + o], v = q[(NP + 1) * fs + o], w = q[(NP + 2) * fs + o];
-    // exact FP64 bound only where an FP32 estimate (relative error < 1e-6)
-    // raised by 1e-5 could reach the running maximum: the argmax is unchanged
-    if (__fmul_rn(spectral_est_f32(a.C, u, v, w), 1.00001f) >= wfloor) {
+    if constexpr (std::is_same<S, float>::value) {
+      // the FP32-mixed step sets dt from the FP32 bound f32_spectral_exact
+      // (also its initial dt): the argmax of that same value, at every node
+      const double s = (double)f32_spectral_exact(K32, u, v, w);
+      if (s > best) {
+        best = s;
+        bidx = (double)e;
+      }
+    } else if (__fmul_rn(spectral_est_f32(a.C, u, v, w), 1.00001f) >= wfloor) {
+      // exact FP64 bound only where an FP32 estimate (relative error < 1e-6)
+      // raised by 1e-5 could reach the running maximum: the argmax is unchanged
       const double s = spectral_f64(a.C, u, v, w);
       if (s > best) {
         best = s;
         bidx = (double)e;
       }
     }
-    // a warp-shared floor (a value some lane's node attained exactly), so that
-    // the FP64 path runs only when a node of the warp could reach it:
-    // non-negative floats order like their bit patterns
-    const float bf = best > 0.0 ? __double2float_rd(best) : 0.f;
-    wfloor = fmaxf(wfloor, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(bf))));
+    if constexpr (!std::is_same<S, float>::value) {
+      // a warp-shared floor (a value some lane's node attained exactly), so that
+      // the FP64 path runs only when a node of the warp could reach it:
+      // non-negative floats order like their bit patterns
+      const float bf = best > 0.0 ? __double2float_rd(best) : 0.f;
+      wfloor = fmaxf(wfloor, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(bf))));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     const double ob = __shfl_xor_sync(0xffffffffu, best, o), oi = __shfl_xor_sync(0xffffffffu, bidx, o);
@@ -517,15 +540,30 @@ __global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts)
     }
   sb[tid] = best;
   si[tid] = bidx;
+  // the FP32 gather's node sums (dtbar, g sigma bar, floor bar): its per-CTA
+  // partials, reduced in a fixed order
+  __shared__ double sg[3][kAdjDtThreads];
+  double g3[3] = {0.0, 0.0, 0.0};
+  for (int q = tid; q < a.ngpart; q += kAdjDtThreads)
+    for (int c = 0; c < 3; ++c) g3[c] += a.gpart[3 * (long long)q + c];
+  for (int c = 0; c < 3; ++c) sg[c][tid] = g3[c];
   __syncthreads();
   for (int o = kAdjDtThreads / 2; o > 0; o >>= 1) {
-    if (tid < o && (sb[tid + o] > sb[tid] || (sb[tid + o] == sb[tid] && si[tid + o] < si[tid]))) {
-      sb[tid] = sb[tid + o];
-      si[tid] = si[tid + o];
+    if (tid < o) {
+      if (sb[tid + o] > sb[tid] || (sb[tid + o] == sb[tid] && si[tid + o] < si[tid])) {
+        sb[tid] = sb[tid + o];
+        si[tid] = si[tid + o];
+      }
+      for (int c = 0; c < 3; ++c) sg[c][tid] += sg[c][tid + o];
     }
     __syncthreads();
   }
   if (tid != 0) return;
+  if (a.ngpart > 0) {
+    a.scal[kScDtbar] = sg[0][0];
+    a.scal[kScGs] = sg[1][0];
+    a.scal[kScFloor] = sg[2][0];
+  }
   best = sb[0];
   bidx = si[0];
   const long long e = (long long)bidx;

@@ -26,6 +26,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "bdc_device.cuh"
 
 namespace bdc {
@@ -351,6 +353,17 @@ __device__ __forceinline__ float f32_spectral_exact(const F32K<float> &K, float 
   const float sy = vfma(qy, vrsqrt(qy), vabs(vn));
   const float sz = vfma(qz, vrsqrt(qz), vabs(wn));
   return vfma(0.5f, vfma(sx, K.ihx, vfma(sy, K.ihy, vmul(sz, K.ihz))), K.diffsr);
+}
+
+// the constants f32_spectral_exact reads (beta_min^2, 1/h, the diffusive term)
+__device__ __forceinline__ F32K<float> f32_spectral_consts(const CavConst &C) {
+  F32K<float> K{};
+  K.b2min = C.fb2min;
+  K.ihx = C.fih[0];
+  K.ihy = C.fih[1];
+  K.ihz = C.fih[2];
+  K.diffsr = C.fdiffsr;
+  return K;
 }
 
 __device__ __forceinline__ void f32_spectral_max(const F32K<float> &K, float bound, float un, float vn, float wn,
@@ -1202,6 +1215,9 @@ __global__ void __launch_bounds__(TX *TY) k_spectral(StepArgs a) {
   const CavConst &C = a.cc[B.cav];
   const int i = R.tx * TX + threadIdx.x + 1, j = R.ty * TY + threadIdx.y + 1;
   const int k0 = R.k0, k1 = R.k1;
+  static_assert(std::is_same<S, float>::value, "the FP64 form refreshes its spectral radius in k_step_f64");
+  // the FP32 bound the FP32-mixed step uses for every later dt
+  const F32K<float> K = f32_spectral_consts(C);
   double smax = 0.0;
   if (i <= B.nx && j <= B.ny) {
     const S *q = (const S *)B.base[a.parity];
@@ -1209,8 +1225,7 @@ __global__ void __launch_bounds__(TX *TY) k_spectral(StepArgs a) {
     constexpr int NP = Store<S>::NP;
     for (int k = k0; k <= k1; ++k) {
       const long long o = node_index<S>(B, i, j, k);
-      smax = fmax(smax, spectral_f64(C, (double)q[NP * fs + o], (double)q[(NP + 1) * fs + o],
-                                     (double)q[(NP + 2) * fs + o]));
+      smax = fmax(smax, (double)f32_spectral_exact(K, q[NP * fs + o], q[(NP + 1) * fs + o], q[(NP + 2) * fs + o]));
     }
   }
   __shared__ double red[NT / 32];

@@ -83,6 +83,7 @@ struct AdjointStore {
   long long final_steps = 0;
   void *X = nullptr, *Yt = nullptr, *Q = nullptr;  // adjoint arrays: FP64 (FP64 forward) or FP32 (FP32-mixed)
   double *thetabar = nullptr, *scal = nullptr, *argpart = nullptr;
+  double *gpart = nullptr;     // per-CTA node sums of the FP32 gather (3 per CTA)
   double *dts = nullptr;       // dt of every step (device)
   BlockDev *block = nullptr;   // descriptor of a segment slot (wall pass of FP32 states)
   bool have_forward = false;
@@ -809,7 +810,7 @@ void release(cavity *h) {
     if (p) cudaFree(p);
   AdjointStore &A = h->adj;
   void *aptrs[] = {A.ckpt_mem, A.ckpt_cs, A.seg_mem, A.final_mem, A.X, A.Yt, A.Q, A.thetabar, A.scal,
-                   A.argpart, A.dts, A.block};
+                   A.argpart, A.gpart, A.dts, A.block};
   for (void *p : aptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -913,7 +914,8 @@ template <class S, class Ad>
 void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint, long long nfold) {
   k_adj_objective<Ad><<<ceil_div((long long)a.g.ny * a.g.nz, 256), 256, 0, h->stream>>>(a);
   k_adj_sum_p<Ad><<<nparts, 256, 0, h->stream>>>(a);
-  k_adj_prepare<Ad><<<ceil_div(5 * a.g.fs, 256), 256, 0, h->stream>>>(a);
+  constexpr bool kGather = std::is_same<Ad, float>::value;
+  k_adj_prepare<Ad, !kGather><<<dim3((unsigned)ceil_div(a.g.fs, 256), 5), 256, 0, h->stream>>>(a);
   if constexpr (std::is_same<Ad, float>::value)  // FP32 sweep: gather, no atomics
     k_adj_gather<<<ceil_div(a.g.fs, 256), 256, 0, h->stream>>>(a);
   else
@@ -1244,8 +1246,8 @@ int cavity_autotune(cavity_t *h, int steps, double out[5]) {
 int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
   if (!h || nsteps < 1 || ckpt < 1) return CAVITY_ERR_INVALID_ARG;
   if (h->local_dt) return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: global time stepping only");
-  if ((long long)h->descs[0].nx * h->descs[0].ny * h->descs[0].nz >= (1LL << 31))
-    return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: fewer than 2^31 interior nodes");
+  if ((long long)(h->descs[0].nx + 4) * (h->descs[0].ny + 4) * (h->descs[0].nz + 4) >= (1LL << 31))
+    return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: fewer than 2^31 nodes with the two-node halo");
   if (h->ncav != 1 || h->nblocks != 1) return fail(h, CAVITY_ERR_UNSUPPORTED, "adjoint: single-block cavity only");
   DeviceGuard g(h->dev);
   AdjointStore &A = h->adj;
@@ -1258,7 +1260,7 @@ int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
   CK(cudaStreamSynchronize(h->stream));
   if (A.set_bytes != set_bytes || A.ncp < ncp || A.ckpt < ckpt || A.nsteps < nsteps) {
     void *aptrs[] = {A.ckpt_mem, A.ckpt_cs, A.seg_mem, A.final_mem, A.X, A.Yt, A.Q, A.thetabar, A.scal,
-                     A.argpart, A.dts, A.block};
+                     A.argpart, A.gpart, A.dts, A.block};
     for (void *p : aptrs)
       if (p) cudaFree(p);
     A = AdjointStore{};
@@ -1273,6 +1275,7 @@ int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
     CK(cudaMalloc(&A.thetabar, sizeof(double) * d.ny * d.nz));
     CK(cudaMalloc(&A.scal, sizeof(double) * kScCount));
     CK(cudaMalloc(&A.argpart, sizeof(double) * 2 * nparts));
+    CK(cudaMalloc(&A.gpart, sizeof(double) * 3 * ceil_div(fs, 256)));
     CK(cudaMalloc(&A.dts, sizeof(double) * nsteps));
     CK(cudaMalloc(&A.block, sizeof(BlockDev)));
     A.set_bytes = set_bytes;
@@ -1325,6 +1328,8 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
   a.scal = A.scal;
   a.thetabar = A.thetabar;
   a.argpart = A.argpart;
+  a.gpart = A.gpart;
+  a.ngpart = h->f32 ? (int)ceil_div(a.g.fs, 256) : 0;
   a.coef = 1.0 / ((double)A.nsteps * d.ny * d.nz * 2.0 * a.C.h[0] * (p.t_hot - p.t_cold));
   a.dfloor = (h->u_ref_auto && p.Ra * p.Pr > 1.0) ? p.kappa * p.Pr : 0.0;
   void *X = A.X, *Q = A.Q;
