@@ -377,6 +377,7 @@ def measure_adjoint(m, torch, rank, world, local, stream):
     c = m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=cfg["seed"] + rank, noise_amp=cfg["noise"], device=local,
                  stream=stream.cuda_stream, Ra=cfg["Ra"], Pr=cfg["Pr"])
     m.cavity_set_wall_temperature(c.h, 0, theta)
+    tuned = m.cavity_autotune(c.h, 10)  # the FP32 step's tile shape (forward and recomputation)
     m.cavity_adjoint_forward(c.h, 20, 10)  # warm-up (allocations, graphs)
     m.cavity_adjoint_backward(c.h, n[1], n[2])
     if world > 1:
@@ -397,6 +398,7 @@ def measure_adjoint(m, torch, rank, world, local, stream):
             "unit": "point-steps/s", "steps": steps, "checkpoint_every": cfg["ckpt"],
             "forward_ms_per_step": 1e3 * fwd / steps, "backward_ms_per_step": 1e3 * bwd / steps,
             "J": J, "dJ_dRa": gra, "grad_wall_norm": float(np.linalg.norm(g)), "clocks": clk.summary(), "status": rc,
+            "autotune": tuned,
             "config": {"workload": f"adjoint of {steps} steps, cavity {n[0]}^3 Ra {cfg['Ra']:g}, FP32-mixed forward, "
                                    f"FP32 reverse sweep (FP64 reductions), checkpoints every {cfg['ckpt']}"},
             "dtype": "f32 forward (p, T as f32 pairs), f32 adjoint sweep with f64 reductions"}

@@ -111,6 +111,26 @@ __global__ void k_adj_sum_p(AdjArgs a) {
   if ((threadIdx.x & 31) == 0) atomicAdd(&a.scal[kScSumP], s);
 }
 
+// The centre-shift transpose in place, for the gather sweep: X(p) at the
+// (at most 8) centre nodes less sum_p / ncentre; everywhere else Yt = X on
+// the interior, and the gather never uses a value off the interior.  One
+// thread per centre node: bit d of the thread index picks the upper of two
+// centre indices along axis d (threads whose axis has one centre index
+// with the bit set return).
+template <class A>
+__global__ void k_adj_centre(AdjArgs a) {
+  const int t = threadIdx.x;
+  int x[3];
+  for (int d = 0; d < 3; ++d) {
+    const int n = a.C.gn[d], up = (t >> d) & 1;
+    if ((n % 2) && up) return;
+    x[d] = (n % 2) ? (n + 1) / 2 : n / 2 + up;
+  }
+  A *X = arr<A>(a.X);
+  const long long e = aidx(a.g, 0, x[0], x[1], x[2]);
+  X[e] = (A)((double)X[e] - a.scal[kScSumP] / (double)a.C.ncentre);
+}
+
 // Grid: x over the padded nodes of one field (fewer than 2^31: 32-bit index
 // arithmetic), y over the five fields.  WQ: also initialise the scatter
 // target Q (k_adj_rates adds into it; k_adj_gather writes every Q itself).
@@ -527,7 +547,7 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
 // CTA of kAdjDtThreads: the per-CTA (max, index) pairs of k_adj_argmax are
 // reduced in parallel (largest value, smallest index among equals), then one
 // thread differentiates the bound at that node (FP64).
-constexpr int kAdjDtThreads = 256;
+constexpr int kAdjDtThreads = 1024;
 template <class S, class A>
 __global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts) {
   __shared__ double sb[kAdjDtThreads], si[kAdjDtThreads];

@@ -914,12 +914,17 @@ template <class S, class Ad>
 void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint, long long nfold) {
   k_adj_objective<Ad><<<ceil_div((long long)a.g.ny * a.g.nz, 256), 256, 0, h->stream>>>(a);
   k_adj_sum_p<Ad><<<nparts, 256, 0, h->stream>>>(a);
-  constexpr bool kGather = std::is_same<Ad, float>::value;
-  k_adj_prepare<Ad, !kGather><<<dim3((unsigned)ceil_div(a.g.fs, 256), 5), 256, 0, h->stream>>>(a);
-  if constexpr (std::is_same<Ad, float>::value)  // FP32 sweep: gather, no atomics
-    k_adj_gather<<<ceil_div(a.g.fs, 256), 256, 0, h->stream>>>(a);
-  else
+  if constexpr (std::is_same<Ad, float>::value) {
+    // FP32 sweep: the centre-shift transpose in place on X, then the gather
+    // reads X as Yt (no atomics, no full prepare pass)
+    k_adj_centre<Ad><<<1, 8, 0, h->stream>>>(a);
+    AdjArgs g = a;
+    g.Yt = a.X;
+    k_adj_gather<<<ceil_div(a.g.fs, 256), 256, 0, h->stream>>>(g);
+  } else {
+    k_adj_prepare<Ad, true><<<dim3((unsigned)ceil_div(a.g.fs, 256), 5), 256, 0, h->stream>>>(a);
     k_adj_rates<S, Ad><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
+  }
   k_adj_argmax<S><<<nparts, 256, 0, h->stream>>>(a);
   k_adj_dt<S, Ad><<<1, kAdjDtThreads, 0, h->stream>>>(a, nparts);
   k_adj_fold<Ad><<<ceil_div(nfold, 256), 256, 0, h->stream>>>(a);
