@@ -296,13 +296,15 @@ __device__ __forceinline__ void rates_f64(const CavConst &C, const NodeF64 &n, d
 #undef BDC_TRANSPORT
 }
 
-// spectral-radius bound of one node's state (the dt denominator)
+// spectral-radius bound of one node's state (the dt denominator); square
+// roots within one unit in the last place (sqrt_newton), so dt is the
+// correctly rounded formula's to a few ulp
 __device__ __forceinline__ double spectral_f64(const CavConst &C, double u, double v, double w) {
   const double b2 = fmax(u * u + v * v + w * w, C.b2min);
   const double f4 = 4.0 * b2;
-  const double sx = fabs(u) + sqrt(u * u + f4);
-  const double sy = fabs(v) + sqrt(v * v + f4);
-  const double sz = fabs(w) + sqrt(w * w + f4);
+  const double sx = fabs(u) + sqrt_newton(u * u + f4);
+  const double sy = fabs(v) + sqrt_newton(v * v + f4);
+  const double sz = fabs(w) + sqrt_newton(w * w + f4);
   return 0.5 * (sx * C.ih[0] + sy * C.ih[1] + sz * C.ih[2]) + C.diffsr;
 }
 
