@@ -62,6 +62,7 @@ struct AdjArgs {
   double *thetabar;  // ny*nz, (j-1) + ny (k-1)
   double *argpart;   // per-CTA (max, index) pairs of k_adj_argmax
   double *gpart;     // per-CTA (dtbar, g sigma bar, floor bar) sums of k_adj_gather
+  double *gpart2;    // the same, summed over contiguous runs of gpart by k_adj_argmax's CTAs
   int ngpart;        // k_adj_gather CTAs (0: the sums go to scal by atomics, k_adj_rates)
   double dt;         // dt of this step
   double coef;       // 1 / (N ny nz 2 h_x dT)
@@ -541,13 +542,33 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
     a.argpart[2 * blockIdx.x] = best;
     a.argpart[2 * blockIdx.x + 1] = bidx;
   }
+  if (a.ngpart > 0) {
+    // second level of the gather's node sums: this CTA's contiguous run of
+    // its per-CTA partials, in a fixed order (strided thread sums, a fixed
+    // shuffle tree, warps in order)
+    const long long lo = (long long)blockIdx.x * a.ngpart / gridDim.x;
+    const long long hi = (long long)(blockIdx.x + 1) * a.ngpart / gridDim.x;
+    double g3[3] = {0.0, 0.0, 0.0};
+    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x)
+      for (int c = 0; c < 3; ++c) g3[c] += a.gpart[3 * q + c];
+    __shared__ double sg[8][3];
+    for (int c = 0; c < 3; ++c) g3[c] = warp_sum(g3[c]);
+    if ((threadIdx.x & 31) == 0)
+      for (int c = 0; c < 3; ++c) sg[w][c] = g3[c];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double acc = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) acc += sg[q][threadIdx.x];
+      a.gpart2[3 * blockIdx.x + threadIdx.x] = acc;
+    }
+  }
 }
 
 // dt = cfl / S: add (-cfl dtbar / S^2) d(bound)/dV at the argmax node.  One
 // CTA of kAdjDtThreads: the per-CTA (max, index) pairs of k_adj_argmax are
 // reduced in parallel (largest value, smallest index among equals), then one
 // thread differentiates the bound at that node (FP64).
-constexpr int kAdjDtThreads = 1024;
+constexpr int kAdjDtThreads = 256;
 template <class S, class A>
 __global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts) {
   __shared__ double sb[kAdjDtThreads], si[kAdjDtThreads];
@@ -564,8 +585,9 @@ __global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts)
   // partials, reduced in a fixed order
   __shared__ double sg[3][kAdjDtThreads];
   double g3[3] = {0.0, 0.0, 0.0};
-  for (int q = tid; q < a.ngpart; q += kAdjDtThreads)
-    for (int c = 0; c < 3; ++c) g3[c] += a.gpart[3 * (long long)q + c];
+  const int ng2 = a.ngpart > 0 ? nparts : 0;  // k_adj_argmax's second-level sums
+  for (int q = tid; q < ng2; q += kAdjDtThreads)
+    for (int c = 0; c < 3; ++c) g3[c] += a.gpart2[3 * (long long)q + c];
   for (int c = 0; c < 3; ++c) sg[c][tid] = g3[c];
   __syncthreads();
   for (int o = kAdjDtThreads / 2; o > 0; o >>= 1) {

@@ -1280,7 +1280,7 @@ int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
     CK(cudaMalloc(&A.thetabar, sizeof(double) * d.ny * d.nz));
     CK(cudaMalloc(&A.scal, sizeof(double) * kScCount));
     CK(cudaMalloc(&A.argpart, sizeof(double) * 2 * nparts));
-    CK(cudaMalloc(&A.gpart, sizeof(double) * 3 * ceil_div(fs, 256)));
+    CK(cudaMalloc(&A.gpart, sizeof(double) * 3 * (ceil_div(fs, 256) + nparts)));
     CK(cudaMalloc(&A.dts, sizeof(double) * nsteps));
     CK(cudaMalloc(&A.block, sizeof(BlockDev)));
     A.set_bytes = set_bytes;
@@ -1335,6 +1335,7 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
   a.argpart = A.argpart;
   a.gpart = A.gpart;
   a.ngpart = h->f32 ? (int)ceil_div(a.g.fs, 256) : 0;
+  a.gpart2 = A.gpart + 3 * ceil_div(a.g.fs, 256);
   a.coef = 1.0 / ((double)A.nsteps * d.ny * d.nz * 2.0 * a.C.h[0] * (p.t_hot - p.t_cold));
   a.dfloor = (h->u_ref_auto && p.Ra * p.Pr > 1.0) ? p.kappa * p.Pr : 0.0;
   void *X = A.X, *Q = A.Q;
