@@ -19,6 +19,7 @@
 // so that node 1 of every row starts on a 32-byte boundary.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -69,6 +70,11 @@ struct CavConst {
   float fih[3], fh2[3], fnh[3], fah[3];
   float fc4h, fgs, ftinf, fb2min, fdiffsr, fcfl;
   float fihh[3], fc4, fnu, falpha;
+  // the spectral bound at rest, S0 = beta_min (1/h_x + 1/h_y + 1/h_z) + the
+  // diffusive term (FP64), and 2 beta_min (FP32): the FP64 step's dt filter
+  // works on S - S0
+  double s0;
+  float f2b0;
   int gaxis;
   int gn[3];
   int ncentre;
@@ -122,6 +128,11 @@ inline void set_cav_physics(CavConst &C, const int gn[3], const cavity_params &p
   C.fc4 = (float)C.c4;
   C.fnu = (float)C.nu;
   C.falpha = (float)C.alpha;
+  {
+    const double b0 = std::sqrt(C.b2min);
+    C.s0 = b0 * (C.ih[0] + C.ih[1] + C.ih[2]) + C.diffsr;
+    C.f2b0 = (float)(2.0 * b0);
+  }
   C.fc4h = (float)(0.5 * C.c4);
   C.fgs = (float)C.gs;
   C.ftinf = (float)C.t_inf;
@@ -356,6 +367,40 @@ __device__ __forceinline__ float spectral_est_f32(const CavConst &C, double u, d
   return spectral_est_f32(C, abs_f32_trunc(u), abs_f32_trunc(v), abs_f32_trunc(w));
 }
 
+// FP32 estimate of D = S - S0, the spectral bound less its value at rest,
+// from |u|, |v|, |w| >= 0.  With beta^2 = max(|V|^2, beta_min^2),
+// sqrt(V_d^2 + 4 beta^2) - 2 beta_min = (V_d^2 + 4 (beta^2 - beta_min^2)) /
+// (sqrt(V_d^2 + 4 beta^2) + 2 beta_min): every term is non-negative, so D
+// comes out with a relative error of a few 1e-7 however small it is next to
+// S0 (an estimate of S itself has its error on the scale of S0, which near
+// rest exceeds the spread of S over the nodes).
+__device__ __forceinline__ float spectral_dev_f32(const CavConst &C, float uf, float vf, float wf) {
+  const float vv = __fmaf_rn(uf, uf, __fmaf_rn(vf, vf, __fmul_rn(wf, wf)));
+  const float f4 = __fmul_rn(4.f, fmaxf(vv, C.fb2min));
+  const float d4 = __fmul_rn(4.f, fmaxf(__fsub_rn(vv, C.fb2min), 0.f));  // 4 (beta^2 - beta_min^2)
+  const float V[3] = {uf, vf, wf};
+  float acc = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float q = __fmaf_rn(V[d], V[d], f4);
+    float r, rd;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+    const float den = __fmaf_rn(q, r, C.f2b0);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(den));
+    const float term = __fmaf_rn(__fmaf_rn(V[d], V[d], d4), rd, V[d]);
+    acc = __fmaf_rn(term, C.fih[d], acc);
+  }
+  return __fmul_rn(0.5f, acc);
+}
+
+// Order-preserving map of a float (either sign) to a signed int, so that a
+// warp can take a float maximum with __reduce_max_sync, and its inverse.
+__device__ __forceinline__ int float_key(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
 // ---------------------------------------------------------------------------
 // k_step, FP64: one thread per (i, j) column of a TX x TY tile, sweeping a
 // chunk of KC planes in k.  The z-neighbours live in register queues
@@ -436,14 +481,25 @@ __device__ __forceinline__ TileRef f64_tile(const StepArgs &a, int c) {
   return tile_ref<KC, kFineKC>(a.blocks, a.nblocks, a.ncoarse, c);
 }
 
-// wfloor: a warp-uniform FP32 value at or below an exact spectral value some
-// lane of the warp has already recorded (carried across the warp's tiles)
+// wfloor: a warp-uniform FP32 value of D = S - S0 at or below the one of an
+// exact spectral value some lane of the warp has already recorded, lowered
+// by 1e-13 of that value (more than the FP64 rounding of S, of S0 and of
+// their difference); -inf before the first.  A node whose estimate of D,
+// raised by 1e-5 (over 10x its error), stays at or below wfloor cannot raise
+// the maximum, so only the others are evaluated in FP64 and the maximum --
+// hence dt -- is exactly the FP64 one.  Carried across the warp's tiles of
+// one cavity (`fcav`: the cavity it belongs to; a tile of another cavity,
+// in a batch, starts again from -inf).
 template <int TX, int TY, int KC>
-__device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float &wfloor) {
+__device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float &wfloor, int &fcav) {
   constexpr int NT = TX * TY;
   const TileRef tile = f64_tile<KC>(a, cta);
   const BlockDev &B = a.blocks[tile.b];
   const CavConst &C = a.cc[B.cav];
+  if (B.cav != fcav) {
+    wfloor = -INFINITY;
+    fcav = B.cav;
+  }
   const int i = tile.tx * TX + threadIdx.x + 1;
   const int j = tile.ty * TY + threadIdx.y + 1;
   const int k0 = tile.k0;
@@ -497,15 +553,15 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
         const double un = qn[1], vn = qn[2], wn = qn[3];
         for (int f = 0; f < 5; ++f) dst[o + f * fs] = qn[f];
         s0 += r[0] * r[0]; s1 += r[1] * r[1]; s2 += r[2] * r[2]; s3 += r[3] * r[3]; s4 += r[4] * r[4];
-        float best = 0.f;
-        if (__fmul_rn(spectral_est_f32(C, un, vn, wn), 1.00001f) > wfloor) {
+        float best = -INFINITY;
+        const float dest = spectral_dev_f32(C, abs_f32_trunc(un), abs_f32_trunc(vn), abs_f32_trunc(wn));
+        if (__fmul_rn(dest, 1.00001f) > wfloor) {
           const double e = spectral_f64(C, un, vn, wn);
           smax = fmax(smax, e);
-          best = __double2float_rd(e);
+          best = __double2float_rd((e - C.s0) - 1e-13 * e);
         }
-        // share over the lanes sweeping this tile (all active lanes run the same k range):
-        // non-negative floats order like their bit patterns
-        wfloor = fmaxf(wfloor, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(best))));
+        // share over the lanes sweeping this tile (all active lanes run the same k range)
+        wfloor = fmaxf(wfloor, key_float(__reduce_max_sync(__activemask(), float_key(best))));
       } else {
         smax = fmax(smax, spectral_f64(C, uq1, vq1, wq1));
       }
@@ -536,9 +592,10 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
 // indexed by tile: the reductions do not depend on which CTA took a tile.
 template <int TX, int TY, int KC>
 __global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
-  float wfloor = 0.f;
+  float wfloor = -INFINITY;
+  int fcav = -1;
   if (!a.tile_counter) {
-    step_tile_f64<TX, TY, KC>(a, blockIdx.x, wfloor);
+    step_tile_f64<TX, TY, KC>(a, blockIdx.x, wfloor, fcav);
     return;
   }
   __shared__ int s_tile;
@@ -548,7 +605,7 @@ __global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
     __syncthreads();
     const int tile = s_tile;
     if (tile >= a.ntiles) break;
-    step_tile_f64<TX, TY, KC>(a, tile, wfloor);
+    step_tile_f64<TX, TY, KC>(a, tile, wfloor, fcav);
     __syncthreads();
   }
 }

@@ -135,6 +135,28 @@ def test_fp32_tile_shapes_give_identical_fields(m, monkeypatch):
         assert t == out[0][1]
 
 
+def test_fp64_batch_with_more_tiles_than_resident_ctas(m):
+    """The persistent FP64 step takes many tiles per CTA, from several cavities
+    whose spectral bounds differ by orders of magnitude (Ra 1e3 .. 1e6): every
+    member of the batch stays bit-equal to the same cavity stepped alone
+    (fields and dt), so no state of the dt maximum leaks between cavities."""
+    cavs = [dict(n=(64, 48, 56), Ra=1e6, seed=1), dict(n=(40, 64, 64), Ra=1e3, seed=2),
+            dict(n=(64, 64, 40), Ra=3e4, seed=3), dict(n=(48, 40, 64), Ra=1e5, seed=4)]
+    params = [m.cavity_default_params(Ra=c["Ra"], Pr=0.71) for c in cavs]
+    h = m.cavity_create_batch([c["n"] for c in cavs], params, precision=m.CAVITY_FP64,
+                              seeds=[c["seed"] for c in cavs], noise_amp=1e-3)
+    try:
+        m.cavity_step(h, 25)
+        for b, c in enumerate(cavs):
+            with m.Cavity(*c["n"], seed=c["seed"], noise_amp=1e-3, Ra=c["Ra"], Pr=0.71) as single:
+                single.step(25)
+                assert np.array_equal(m.cavity_batch_get_fields(h, b, c["n"]), single.fields()), b
+                st = m.cavity_batch_state(h, b)
+                assert (st["step"], st["t"], st["dt"]) == single.time, b
+    finally:
+        m.cavity_destroy(h)
+
+
 def test_batch_rejects_mixed_precision_and_split_members(m):
     import ctypes
     L = m.load_library()
