@@ -414,6 +414,8 @@ struct StepArgs {
   double *partials;  // [tile][kPartStride]
   int parity;        // read base[parity], write base[parity ^ 1]
   int mode;          // 0 = step, 1 = spectral radius of the current state only
+  unsigned int *sfloor;        // per cavity: the largest published dt-filter floor of this step
+                               // (float_key ^ 0x80000000, 0 = none; reset by the next k_bc); null: none
   unsigned int *tile_counter;  // persistent CTAs fetch tiles from it (reset by the next k_bc);
                                // null: one CTA per tile
   int ntiles;
@@ -500,6 +502,14 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
     wfloor = -INFINITY;
     fcav = B.cav;
   }
+  // the cavity's floor as published by every CTA so far this step (a value
+  // at or below an exact spectral value some warp recorded): warps far from
+  // the maximum start near it too
+  if (a.mode == 0 && a.sfloor) {
+    const unsigned u = *(volatile const unsigned *)&a.sfloor[B.cav];
+    if (u != 0u) wfloor = fmaxf(wfloor, key_float((int)(u ^ 0x80000000u)));
+  }
+  float published = wfloor;
   const int i = tile.tx * TX + threadIdx.x + 1;
   const int j = tile.ty * TY + threadIdx.y + 1;
   const int k0 = tile.k0;
@@ -561,7 +571,13 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
           best = __double2float_rd((e - C.s0) - 1e-13 * e);
         }
         // share over the lanes sweeping this tile (all active lanes run the same k range)
-        wfloor = fmaxf(wfloor, key_float(__reduce_max_sync(__activemask(), float_key(best))));
+        const unsigned am = __activemask();
+        wfloor = fmaxf(wfloor, key_float(__reduce_max_sync(am, float_key(best))));
+        if (wfloor > published && a.sfloor) {  // publish a rise for the other warps
+          if ((int)(threadIdx.x & 31) == __ffs(am) - 1)
+            atomicMax(&a.sfloor[B.cav], (unsigned)float_key(wfloor) ^ 0x80000000u);
+          published = wfloor;
+        }
       } else {
         smax = fmax(smax, spectral_f64(C, uq1, vq1, wq1));
       }
@@ -710,6 +726,7 @@ struct BcArgs {
   unsigned int *counter;      // per cavity: k_finalize slices done
   const double *t_wall;       // hot walls then cold walls, per cavity at wall_off
   unsigned int *tile_counter; // the persistent step kernel's tile counter: reset here
+  unsigned int *sfloor;       // the step kernel's per-cavity dt-filter floors: reset here
   long long shell_begin, shell_end;  // k_shell_f64 partial slots of this step (single cavity; empty if equal)
   int parity;                 // buffer set holding the new state
   int mode;                   // 0 after a step, 1 after init / set_fields,
@@ -889,6 +906,8 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
   __shared__ double sh[(kBcThreads / 32) * 2];
   const int cta = blockIdx.x, tid = threadIdx.x;
   if (cta == 0 && tid == 0 && a.tile_counter) *a.tile_counter = 0u;  // the step kernel has finished
+  if (cta == 0 && a.sfloor)
+    for (int c = tid; c < a.ncav; c += kBcThreads) a.sfloor[c] = 0u;
   double nu_h = 0.0, nu_c = 0.0;
   if (a.nfaces > 0) {
     const int fi = find_face(a.faces, a.nfaces, cta);

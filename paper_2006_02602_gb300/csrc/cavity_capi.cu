@@ -134,7 +134,8 @@ struct cavity {
   CUtensorMap *d_maps = nullptr;
   double *d_step_part = nullptr, *d_bc_part = nullptr, *d_twall = nullptr, *d_stage = nullptr;
   double *d_fin = nullptr;  // k_finalize slice totals [ncav][kFinSlices][8]
-  unsigned int *d_counter = nullptr;  // [ncav] k_bc CTAs done per cavity, then the FP64 step's tile counter
+  unsigned int *d_counter = nullptr;  // [ncav] k_bc CTAs done per cavity, the FP64 step's tile counter,
+                                      // [ncav] the FP64 step's dt-filter floors
   int persist_ctas = 0;               // CTAs of the persistent FP64 step kernel that fit on the GPU
   void *d_fields = nullptr, *d_xbuf = nullptr;
   size_t field_bytes = 0;
@@ -430,8 +431,8 @@ int alloc_device(cavity *h) {
   if (rc != CAVITY_OK) return rc;
   CK(cudaMalloc(&h->d_bc_part, sizeof(double) * 2 * std::max(1, h->n_bc)));
   CK(cudaMalloc(&h->d_fin, sizeof(double) * 8 * kFinSlices * h->ncav));
-  CK(cudaMalloc(&h->d_counter, sizeof(unsigned int) * (h->ncav + 1)));
-  CK(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int) * (h->ncav + 1), h->stream));
+  CK(cudaMalloc(&h->d_counter, sizeof(unsigned int) * (2 * h->ncav + 1)));
+  CK(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int) * (2 * h->ncav + 1), h->stream));
   {
     int nsm = 0, per_sm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
@@ -478,6 +479,7 @@ StepArgs step_args(cavity *h, int parity, int mode) {
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.partials = h->d_step_part; a.parity = parity; a.mode = mode;
   a.tile_counter = h->d_counter + h->ncav; a.ntiles = h->n_step; a.local_dt = h->local_dt;
+  a.sfloor = h->d_counter + h->ncav + 1;
   a.ncoarse = h->n_coarse;
   a.skip_shell = 0;
   return a;
@@ -499,6 +501,7 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.cc = h->d_cc; a.cs = h->d_cs; a.ncav = h->ncav;
   a.step_partials = h->d_step_part; a.bc_partials = h->d_bc_part; a.counter = h->d_counter;
   a.tile_counter = h->d_counter + h->ncav;
+  a.sfloor = h->d_counter + h->ncav + 1;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
   a.shell_begin = a.shell_end = 0;
   return a;
