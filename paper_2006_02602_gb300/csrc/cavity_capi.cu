@@ -613,6 +613,15 @@ int launch_exchange(cavity *h, int parity) {
 // The overlapped step (FP64, cut faces): shell nodes first, then the
 // exchange of the new ghost layers on the side stream while the persistent
 // kernel steps the remaining nodes; walls and the finalise after both.
+// second stream and the fork/join events of the step graphs (created once)
+cudaError_t ensure_side(cavity *h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->side) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !h->ev_shell) e = cudaEventCreateWithFlags(&h->ev_shell, cudaEventDisableTiming);
+  if (e == cudaSuccess && !h->ev_exch) e = cudaEventCreateWithFlags(&h->ev_exch, cudaEventDisableTiming);
+  return e;
+}
+
 int launch_step_overlapped(cavity *h, int parity) {
   const ShellArgs sa{h->d_blocks, h->d_shell, (int)h->hshell.size(), h->d_cc, h->d_cs, h->d_step_part,
                      (long long)h->n_step, parity, h->local_dt};
@@ -641,6 +650,26 @@ int launch_step_overlapped(cavity *h, int parity) {
 // one explicit step reading buffer set `parity`, leaving the new state in parity ^ 1
 int launch_step(cavity *h, int parity, bool after_finalise = false) {
   if (h->overlap) return launch_step_overlapped(h, parity);
+  if (!h->f32 && h->n_cut > 0 && h->side) {
+    // FP64 with cut faces: after the wall kernel the exchange (pack + unpack,
+    // which read the walls and write ghost layers) and the finalise (which
+    // reads the partials and writes the per-cavity scalars) share no data:
+    // two branches of the step graph
+    launch_step_kernel(h, parity);
+    CK(cudaGetLastError());
+    k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0));
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->ev_shell, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_shell, 0));
+    launch_pack(h, parity ^ 1, h->side);
+    launch_unpack(h, parity ^ 1, h->side);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->ev_exch, h->side));
+    k_finalize<double><<<h->ncav * kFinSlices, kFinThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0), h->d_fin);
+    CK(cudaGetLastError());
+    CK(cudaStreamWaitEvent(h->stream, h->ev_exch, 0));
+    return CAVITY_OK;
+  }
   launch_step_kernel(h, parity, after_finalise);
   CK(cudaGetLastError());
   launch_bc_kernel(h, parity ^ 1, 0);
@@ -666,6 +695,7 @@ void drop_graphs(cavity *h) {
 
 int build_graphs(cavity *h) {
   drop_graphs(h);
+  if (!h->f32 && h->n_cut > 0) CK(ensure_side(h));
   for (int par = 0; par < 2; ++par) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -1425,9 +1455,7 @@ int cavity_set_overlap(cavity_t *h, int on) {
     h->n_shell = cta;
     CK(cudaMalloc(&h->d_shell, sizeof(ShellFace) * h->hshell.size()));
     CK(cudaMemcpy(h->d_shell, h->hshell.data(), sizeof(ShellFace) * h->hshell.size(), cudaMemcpyHostToDevice));
-    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&h->ev_shell, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->ev_exch, cudaEventDisableTiming));
+    CK(ensure_side(h));
   }
   const int rc = ensure_partials(h);
   if (rc != CAVITY_OK) return rc;
