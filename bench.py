@@ -54,7 +54,7 @@ BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
 # kernel exists.  Key: (precision, workload, blocks, shape); the FP32 shape is
 # the autotuner's "TY,KC,R,form"
 FP64_SHAPE = "32x4x8"
-TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.936064e6 + 55.825152e6,
+TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.855680e6 + 55.964416e6,
            ("fp32", "cfg3", (1, 1, 1), "8,40,5,3"): 580.006656e6 + 434.687232e6}
 F32_FORMS = {1: "k_step_f32 (one node per thread; z neighbours from the TMA ring)",
              2: "k_step_f32p (two nodes per thread, f32x2; z neighbours from the TMA ring)",
