@@ -14,8 +14,14 @@
 //                    applied to dt Yt, added with atomics into Q at the
 //                    stencil's inputs; sums of Yt R (for dt), of the
 //                    buoyancy and beta^2-floor adjoints
+//     (FP32 sweep instead: k_adj_centre applies the centre correction to
+//     Xbar in place, and k_adj_gather reads it as Yt and writes every Q once,
+//     gathering what the stencils would scatter; its node sums go out as
+//     per-CTA partials)
 //   k_adj_argmax + k_adj_dt  dt's dependence: -cfl dtbar / S^2 times the
-//                    gradient of the spectral bound at its largest node
+//                    gradient of the spectral bound at its largest node (the
+//                    FP32 bound f32_spectral_exact after an FP32-mixed forward,
+//                    which sets that forward's dt)
 //   k_adj_fold       wall and ghost adjoints moved onto interior nodes 1, 2
 //                    through p_w = 2 p1 - p2, p_g = 2 p_w - p1,
 //                    T_w = (4 T1 - T2)/3, and the hot wall's T onto theta

@@ -335,10 +335,9 @@ __device__ __forceinline__ void update_node_f64(const CavConst &C, const NodeF64
 
 // FP32 estimate of spectral_f64 (the same formula: relative error below
 // 1e-6; beta_min^2 = kappa u_ref^2 is at least FP32's smallest normal, so the
-// estimate is finite).  A node whose estimate, raised by 1e-5, stays at or below a value
-// the exact FP64 maximum already reached cannot raise that maximum, so only
-// the few candidates are evaluated in FP64 (GB300's FP64 pipe is narrow) and
-// the maximum -- hence dt -- is exactly the FP64 one.
+// estimate is finite).  The FP64 adjoint's argmax skips a node whose estimate,
+// raised by 1e-5, stays below a value the exact FP64 maximum already reached
+// (the FP64 step filters on spectral_dev_f32 below instead).
 __device__ __forceinline__ float spectral_est_f32(const CavConst &C, float uf, float vf, float wf) {
   const float b2 = fmaxf(__fmaf_rn(uf, uf, __fmaf_rn(vf, vf, __fmul_rn(wf, wf))), C.fb2min);
   const float f4 = __fmul_rn(4.f, b2);
