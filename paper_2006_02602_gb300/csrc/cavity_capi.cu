@@ -650,22 +650,28 @@ int launch_step_overlapped(cavity *h, int parity) {
 // one explicit step reading buffer set `parity`, leaving the new state in parity ^ 1
 int launch_step(cavity *h, int parity, bool after_finalise = false) {
   if (h->overlap) return launch_step_overlapped(h, parity);
-  if (!h->f32 && h->n_cut > 0 && h->side) {
-    // FP64 with cut faces: after the wall kernel the exchange (pack + unpack,
-    // which read the walls and write ghost layers) and the finalise (which
-    // reads the partials and writes the per-cavity scalars) share no data:
-    // two branches of the step graph
+  if (h->n_cut > 0 && h->side) {
+    // With cut faces the exchange (pack + unpack, which read the new state --
+    // FP64: after the wall kernel -- and write ghost layers) and the finalise
+    // (which reads the partials and writes the per-cavity scalars) share no
+    // data: two branches of the step graph, joined before the next step
     launch_step_kernel(h, parity);
     CK(cudaGetLastError());
-    k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0));
-    CK(cudaGetLastError());
+    if (!h->f32) {
+      k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0));
+      CK(cudaGetLastError());
+    }
     CK(cudaEventRecord(h->ev_shell, h->stream));
     CK(cudaStreamWaitEvent(h->side, h->ev_shell, 0));
     launch_pack(h, parity ^ 1, h->side);
     launch_unpack(h, parity ^ 1, h->side);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->ev_exch, h->side));
-    k_finalize<double><<<h->ncav * kFinSlices, kFinThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0), h->d_fin);
+    const int nfin = h->ncav * kFinSlices;
+    if (h->f32)
+      k_finalize<float><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 4), h->d_fin);
+    else
+      k_finalize<double><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0), h->d_fin);
     CK(cudaGetLastError());
     CK(cudaStreamWaitEvent(h->stream, h->ev_exch, 0));
     return CAVITY_OK;
@@ -695,7 +701,7 @@ void drop_graphs(cavity *h) {
 
 int build_graphs(cavity *h) {
   drop_graphs(h);
-  if (!h->f32 && h->n_cut > 0) CK(ensure_side(h));
+  if (h->n_cut > 0) CK(ensure_side(h));
   for (int par = 0; par < 2; ++par) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
