@@ -346,7 +346,10 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float dtbsum = 0.f, gsbsum = 0.f, flbsum = 0.f;
   if (e < a.g.fs) {
-    const int i = (int)(e % a.g.ex) - 1, j = (int)((e / a.g.ex) % a.g.ey) - 1, k = (int)(e / (a.g.ex * a.g.ey)) - 1;
+    // (i, j, k) from the padded linear index: 32-bit arithmetic (fewer than
+    // 2^31 padded nodes; 64-bit division is a long software sequence)
+    const unsigned r = (unsigned)e, ex = (unsigned)a.g.ex, ey = (unsigned)a.g.ey, rq = r / ex;
+    const int i = (int)(r - rq * ex) - 1, j = (int)(rq % ey) - 1, k = (int)(rq / ey) - 1;
     const CavConst &C = a.C;
     const float *q = (const float *)a.B.base[0];
     const long long fs = a.B.fstride;
