@@ -32,7 +32,7 @@
 
 namespace bdc {
 
-constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 32, kF32R = 5, kF32P = 3;  // default shape: tile height, z chunk, ring depth, nodes per thread
+constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 32, kF32R = 4, kF32P = 3;  // default shape: tile height, z chunk, ring depth, nodes per thread
 constexpr int kF32BX = kF32TX + 8;  // x halo 4 on each side: the box starts on a 16-byte boundary
 constexpr int kF32NA = 7;           // p_hi, p_lo, u, v, w, T_hi, T_lo
 __host__ __device__ constexpr int f32_box_y(int TY) { return TY + 4; }  // y halo 2 (pressure star)
@@ -1114,11 +1114,14 @@ __device__ __forceinline__ void f32q_prologue_plane(int pl, float *S, const F32T
 
 // Two nodes per thread as k_step_f32p, with the pair's z - 1 values (all
 // seven arrays) and p's z - 2 values carried in registers from the previous
-// planes: only planes k .. k+2 stay resident, so a ring of R = 5 slots keeps
+// planes: only planes k .. k+2 stay resident.  A ring of R = 5 slots keeps
 // two planes in flight in 67 KB and three CTAs share an SM (12 warps instead
-// of 8).  Slots are indexed modulo R.  One CTA per tile.
+// of 8); with R = 4 (one plane in flight, 54 KB) the launch bounds ask for
+// four CTAs per SM, which the compiler meets in 123 registers without spills
+// (16 warps per SM: the other CTAs hide a plane's wait).  Slots are indexed
+// modulo R.  One CTA per tile.
 template <int TY, int KC, int R>
-__global__ void __launch_bounds__(kF32TX / 2 * TY, 384 / (kF32TX / 2 * TY)) k_step_f32q(StepF32Args a) {
+__global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32TX / 2 * TY)) k_step_f32q(StepF32Args a) {
   static_assert(R >= 4, "ring depth: three planes resident and at least one in flight");
   constexpr int NTX = kF32TX / 2, NT = NTX * TY;
   constexpr int BY = f32_box_y(TY);

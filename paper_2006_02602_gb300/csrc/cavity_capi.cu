@@ -52,7 +52,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 #define BDC_F32_VARIANTS(X)                                                                       \
   X(1, 8, 16, 8) X(1, 8, 32, 8) X(1, 8, 64, 8) X(1, 4, 32, 8) X(1, 4, 64, 8) X(2, 8, 32, 8) X(2, 8, 64, 8) \
       X(2, 16, 32, 8) X(2, 16, 64, 8) X(3, 8, 16, 5) X(3, 8, 24, 5) X(3, 8, 32, 5) X(3, 8, 40, 5) X(3, 8, 64, 5) \
-      X(3, 8, 32, 6)
+      X(3, 8, 32, 6) X(3, 8, 16, 4) X(3, 8, 24, 4) X(3, 8, 32, 4) X(3, 8, 40, 4) X(3, 8, 64, 4)
 struct F32Shape {
   int p, ty, kc, r;
 };

@@ -125,7 +125,7 @@ def test_fp32_tile_shapes_give_identical_fields(m, monkeypatch):
     n = (45, 38, 70)
     out = []
     for shape in ("8,16,8", "8,64,8", "4,32,8", "8,32,8,2", "8,64,8,2", "16,32,8,2", "8,32,5,3", "8,64,5,3",
-                  "8,32,6,3", "8,40,5,3"):
+                  "8,32,6,3", "8,40,5,3", "8,32,4,3"):
         monkeypatch.setenv("BDC_F32_TILE", shape)
         with m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=4, noise_amp=1e-3, Ra=2e5) as c:
             c.step(40)

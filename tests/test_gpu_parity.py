@@ -320,7 +320,7 @@ def test_fp32_blocks_bit_identical(m, blocks):
         assert c.time == ref.time
 
 
-@pytest.mark.parametrize("shape", ["8,32,8,2", "16,64,8,2", "8,32,5,3", "8,40,5,3"])
+@pytest.mark.parametrize("shape", ["8,32,8,2", "16,64,8,2", "8,32,5,3", "8,40,5,3", "8,40,4,3"])
 def test_fp32_two_node_kernel(m, monkeypatch, shape):
     """The kernel with two nodes per thread: ragged sizes against the oracle
     (odd nx leaves a lone node in the last pair), and a decomposition with odd
