@@ -55,7 +55,7 @@ BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
 # the autotuner's "TY,KC,R,form"
 FP64_SHAPE = "32x4x8"
 TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.855680e6 + 55.964416e6,
-           ("fp32", "cfg3", (1, 1, 1), "8,40,5,3"): 580.006656e6 + 434.687232e6}
+           ("fp32", "cfg3", (1, 1, 1), "8,32,4,3"): 590.065920e6 + 435.272704e6}
 F32_FORMS = {1: "k_step_f32 (one node per thread; z neighbours from the TMA ring)",
              2: "k_step_f32p (two nodes per thread, f32x2; z neighbours from the TMA ring)",
              3: "k_step_f32q (two nodes per thread, f32x2; z neighbours below the plane in registers)"}
