@@ -298,7 +298,9 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
            "l2": ("L2 flushed (2 x L2 buffer written) before every timed step: the state fits in L2" if flush else
                   f"no flush: the two state buffers ({both_buffers / 1e6:.0f} MB) exceed the 129 MB L2"),
            "roofline": roofline_for(precision, pts, kms[0], measured_peaks().get("hbm_gbs"),
-                                    TRAFFIC.get((precision, workload, tuple(blocks), shape)),
+                                    # the overlapped schedule's step kernel skips the shell
+                                    # nodes: no capture of it
+                                    None if overlap else TRAFFIC.get((precision, workload, tuple(blocks), shape)),
                                     tuned["kernel_form"] if tuned else 3)}
     if e2e:
         # end to end through the public API with host buffers: initial state
