@@ -105,17 +105,26 @@ __global__ void k_adj_objective(AdjArgs a) {
 }
 
 template <class A>
-__global__ void k_adj_sum_p(AdjArgs a) {
-  const long long n = (long long)a.g.nx * a.g.ny * a.g.nz;
+__global__ void __launch_bounds__(256) k_adj_sum_p(AdjArgs a) {
+  // a warp per interior row (j, k), strided over the grid's warps: no index
+  // division; each lane sums its values in A (the sweep's type), the warp
+  // and the CTA in FP64, one atomic per CTA
   const A *X = arr<A>(a.X);
-  double s = 0.0;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    unflat(a.g, (unsigned)e, i, j, k);
-    s += (double)X[aidx(a.g, 0, i, j, k)];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rows = a.g.ny * a.g.nz;
+  A s = 0;
+  for (int r = blockIdx.x * nw + w; r < rows; r += gridDim.x * nw) {
+    const A *row = X + aidx(a.g, 0, 0, r % a.g.ny + 1, r / a.g.ny + 1);
+    for (int i = 1 + lane; i <= a.g.nx; i += 32) s += row[i];
   }
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&a.scal[kScSumP], s);
+  double d = warp_sum((double)s);
+  __shared__ double red[8];
+  if (lane == 0) red[w] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < nw; ++q) d += red[q];
+    atomicAdd(&a.scal[kScSumP], d);
+  }
 }
 
 // The centre-shift transpose in place, for the gather sweep: X(p) at the
