@@ -36,7 +36,9 @@
 // neighbour-minus-centre differences; for the FP32-mixed state the p and T
 // differences are formed from their hi/lo pairs (as the forward step does),
 // so FP32 arithmetic loses no cancellation.  The sums over nodes (dt, g sigma,
-// beta^2 floor, the p adjoint) and the wall gradient stay FP64.
+// beta^2 floor, the p adjoint) are FP64 beyond a warp (the FP32 sweep adds at
+// most a few dozen terms in FP32 per lane or warp first); the wall gradient
+// stays FP64.
 #pragma once
 
 #include <type_traits>
