@@ -512,40 +512,54 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
 // equal values: each thread visits its nodes in increasing index)
 template <class S>
 __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
-  const long long n = (long long)a.g.nx * a.g.ny * a.g.nz;
+  // a warp per interior row (j, k), strided over the grid's warps (no index
+  // division); a thread visits its nodes in increasing linear interior index
+  // e = (i - 1) + nx ((j - 1) + ny (k - 1)), so it keeps the first of equal values
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nwq = blockDim.x >> 5;
+  const int nx = a.g.nx, ny = a.g.ny, rows = ny * a.g.nz;
+  const S *q = (const S *)a.B.base[0];
+  const long long fs = a.B.fstride;
+  constexpr int NP = Store<S>::NP;  // u, v, w follow the p array(s)
   double best = -1.0, bidx = 0.0;
-  float wfloor = 0.f;  // at or below an exact bound a lane of this warp reached
+  float bestf = -1.f;               // FP32 path: the running maximum in FP32
+  long long bidxl = 0;
+  float wfloor = 0.f;  // FP64 path: at or below an exact bound a lane of this warp reached
   const F32K<float> K32 = f32_spectral_consts(a.C);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    unflat(a.g, (unsigned)e, i, j, k);
-    const S *q = (const S *)a.B.base[0];
-    const long long o = node_index<S>(a.B, i, j, k), fs = a.B.fstride;
-    constexpr int NP = Store<S>::NP;  // u, v, w follow the p array(s)
-    const S u = q[NP * fs + o], v = q[(NP + 1) * fs + o], w = q[(NP + 2) * fs + o];
-    if constexpr (std::is_same<S, float>::value) {
-      // the FP32-mixed step sets dt from the FP32 bound f32_spectral_exact
-      // (also its initial dt): the argmax of that same value, at every node
-      const double s = (double)f32_spectral_exact(K32, u, v, w);
-      if (s > best) {
-        best = s;
-        bidx = (double)e;
-      }
-    } else if (__fmul_rn(spectral_est_f32(a.C, u, v, w), 1.00001f) >= wfloor) {
-      // exact FP64 bound only where an FP32 estimate (relative error < 1e-6)
-      // raised by 1e-5 could reach the running maximum: the argmax is unchanged
-      const double s = spectral_f64(a.C, u, v, w);
-      if (s > best) {
-        best = s;
-        bidx = (double)e;
+  for (int r = blockIdx.x * nwq + wq; r < rows; r += gridDim.x * nwq) {
+    const long long o0 = node_index<S>(a.B, 0, r % ny + 1, r / ny + 1), e0 = (long long)nx * r - 1;
+    for (int i = 1 + lane; i <= nx; i += 32) {
+      const long long o = o0 + i;
+      const S u = q[NP * fs + o], v = q[(NP + 1) * fs + o], w = q[(NP + 2) * fs + o];
+      if constexpr (std::is_same<S, float>::value) {
+        // the FP32-mixed step sets dt from the FP32 bound f32_spectral_exact
+        // (also its initial dt): the argmax of that same value, at every node
+        const float sv = f32_spectral_exact(K32, u, v, w);
+        if (sv > bestf) {
+          bestf = sv;
+          bidxl = e0 + i;
+        }
+      } else {
+        if (__fmul_rn(spectral_est_f32(a.C, u, v, w), 1.00001f) >= wfloor) {
+          // exact FP64 bound only where an FP32 estimate (relative error < 1e-6)
+          // raised by 1e-5 could reach the running maximum: the argmax is unchanged
+          const double sv = spectral_f64(a.C, u, v, w);
+          if (sv > best) {
+            best = sv;
+            bidx = (double)(e0 + i);
+          }
+        }
+        // a warp-shared floor (a value some lane's node attained exactly), so that
+        // the FP64 path runs only when a node of the warp could reach it:
+        // non-negative floats order like their bit patterns
+        const float bf = best > 0.0 ? __double2float_rd(best) : 0.f;
+        wfloor = fmaxf(wfloor, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(bf))));
       }
     }
-    if constexpr (!std::is_same<S, float>::value) {
-      // a warp-shared floor (a value some lane's node attained exactly), so that
-      // the FP64 path runs only when a node of the warp could reach it:
-      // non-negative floats order like their bit patterns
-      const float bf = best > 0.0 ? __double2float_rd(best) : 0.f;
-      wfloor = fmaxf(wfloor, __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(bf))));
+  }
+  if constexpr (std::is_same<S, float>::value) {
+    if (bestf >= 0.f) {
+      best = (double)bestf;
+      bidx = (double)bidxl;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
