@@ -266,7 +266,10 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
     shape = (f"{tuned['tile_y']},{tuned['kc']},{tuned['ring']},{tuned['kernel_form']}" if tuned else FP64_SHAPE)
     c.step(warmup)
     c.sync()
-    kms = m.cavity_time_kernels(c.h, 20)
+    # per-kernel durations: CUDA events around every launch on the handle's
+    # stream over 20 steps just before and 20 just after the timed region,
+    # averaged (the FP64 step's cost drifts with the state along a run)
+    kms_before = m.cavity_time_kernels(c.h, 20)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -291,6 +294,7 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
             ms = sum(a.elapsed_time(b) for a, b in ev)
     barrier()
     rc = c.sync()
+    kms = [0.5 * (x + y) for x, y in zip(kms_before, m.cavity_time_kernels(c.h, 20))]
     ms, = max_over_ranks([ms], world, f"cuda:{local}")
     out = {"value": job_value(pts * steps, world, ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
            "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
@@ -341,7 +345,7 @@ def measure_batch(m, torch, steps, warmup, rank, world, local, stream):
     tuned = m.cavity_autotune(h, 10)
     m.cavity_step(h, warmup)
     m.cavity_sync(h)
-    kms = m.cavity_time_kernels(h, 10)
+    kms_before = m.cavity_time_kernels(h, 10)  # averaged with 10 steps after the timed region
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -353,12 +357,14 @@ def measure_batch(m, torch, steps, warmup, rank, world, local, stream):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     rc = m.cavity_sync(h)
+    kms = [0.5 * (x + y) for x, y in zip(kms_before, m.cavity_time_kernels(h, 10))]
     ms, = max_over_ranks([ms], world, f"cuda:{local}")
     m.cavity_destroy(h)
     return {"value": job_value(pts * steps, world, ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
             "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
             "gpu_launches": 2 * steps, "clocks": clk.summary(), "status": rc, "autotune": tuned,
-            "roofline": roofline_for("fp32", pts, kms[0], measured_peaks().get("hbm_gbs")),
+            "roofline": roofline_for("fp32", pts, kms[0], measured_peaks().get("hbm_gbs"), None,
+                                     tuned["kernel_form"]),
             "config": {"workload": f"batch of {len(cavs)} cavities, n_d in [24, 96], Ra log-uniform in [1e3, 1e6], "
                                    f"{pts} interior points, FP32-mixed, one graph launch per step",
                        "l2": ("inputs larger than L2" if both_buffers > 1.2 * L2_BYTES else
