@@ -214,7 +214,8 @@ CAVITY_API int cavity_batch_get_fields(cavity_t *h, int cav, int field_mask, dou
  * neighbours below the plane in registers) and microseconds per step.  Every
  * shape gives the same fields.  With the environment variable BDC_F32_TILE
  * ("TY,KC,R,form", a compiled shape, read at creation) the shape is pinned and
- * no trials run (out[4] = 0).  FP64 handles have a single shape:
+ * no trials run (out[4] = 0).  FP64 handles have a single shape (32 x 4
+ * threads, 8-plane chunks; BDC_F64_TY=8, read at creation, selects 32 x 8):
  * CAVITY_ERR_UNSUPPORTED. */
 CAVITY_API int cavity_autotune(cavity_t *h, int steps, double out[5]);
 
