@@ -55,7 +55,9 @@ BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
 # the autotuner's "TY,KC,R,form"
 FP64_SHAPE = "32x4x8"
 TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.855680e6 + 55.964416e6,
-           ("fp32", "cfg3", (1, 1, 1), "8,32,4,3"): 590.065920e6 + 435.272704e6}
+           ("fp32", "cfg3", (1, 1, 1), "8,32,4,3"): 590.065920e6 + 435.272704e6,
+           # the batch of 64 (profiles/k_step_f32q_batch64.md)
+           ("fp32", "cfg4", None, "8,64,5,3"): 622.304256e6 + 327.072512e6}
 F32_FORMS = {1: "k_step_f32 (one node per thread; z neighbours from the TMA ring)",
              2: "k_step_f32p (two nodes per thread, f32x2; z neighbours from the TMA ring)",
              3: "k_step_f32q (two nodes per thread, f32x2; z neighbours below the plane in registers)"}
@@ -363,7 +365,9 @@ def measure_batch(m, torch, steps, warmup, rank, world, local, stream):
     return {"value": job_value(pts * steps, world, ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
             "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
             "gpu_launches": 2 * steps, "clocks": clk.summary(), "status": rc, "autotune": tuned,
-            "roofline": roofline_for("fp32", pts, kms[0], measured_peaks().get("hbm_gbs"), None,
+            "roofline": roofline_for("fp32", pts, kms[0], measured_peaks().get("hbm_gbs"),
+                                     TRAFFIC.get(("fp32", "cfg4", None, f"{tuned['tile_y']},{tuned['kc']},"
+                                                  f"{tuned['ring']},{tuned['kernel_form']}")),
                                      tuned["kernel_form"]),
             "config": {"workload": f"batch of {len(cavs)} cavities, n_d in [24, 96], Ra log-uniform in [1e3, 1e6], "
                                    f"{pts} interior points, FP32-mixed, one graph launch per step",

@@ -48,10 +48,14 @@ def test_flop_count_is_the_sum_of_its_parts():
 
 def test_traffic_entries_are_keyed_by_a_compiled_shape_and_are_near_the_algorithmic_bytes():
     for (prec, wl, blocks, shape), traffic in bench.TRAFFIC.items():
-        cfg = bench.WORKLOADS[wl]
-        n = cfg["n"]
-        algorithmic = bench.BYTES_PER_POINT[prec] * n[0] * n[1] * n[2]
-        assert 0.95 * algorithmic <= traffic <= 1.2 * algorithmic, (prec, wl, traffic / algorithmic)
+        if wl == "cfg4":  # the batch: halos of many small tiles re-read from DRAM
+            pts = sum(a * b * c for a, b, c in (cv["n"] for cv in workloads.batch_cavities()))
+            hi = 1.5
+        else:
+            n = bench.WORKLOADS[wl]["n"]
+            pts, hi = n[0] * n[1] * n[2], 1.2
+        algorithmic = bench.BYTES_PER_POINT[prec] * pts
+        assert 0.95 * algorithmic <= traffic <= hi * algorithmic, (prec, wl, traffic / algorithmic)
         if prec == "fp64":
             assert shape == bench.FP64_SHAPE
         else:
