@@ -483,7 +483,8 @@ __device__ __forceinline__ TileRef f64_tile(const StepArgs &a, int c) {
 }
 
 // wfloor: a warp-uniform FP32 value of D = S - S0 at or below the one of an
-// exact spectral value some lane of the warp has already recorded, lowered
+// exact spectral value of this step that some lane of the warp -- or, through
+// the cavity's published floor, of any CTA -- has already recorded, lowered
 // by 1e-13 of that value (more than the FP64 rounding of S, of S0 and of
 // their difference); -inf before the first.  A node whose estimate of D,
 // raised by 1e-5 (over 10x its error), stays at or below wfloor cannot raise
@@ -603,8 +604,10 @@ __device__ __forceinline__ void step_tile_f64(const StepArgs &a, int cta, float 
 
 // Persistent form: as many CTAs as fit on the GPU at once take tiles in
 // order from a counter, so the last round is short (one CTA per tile left a
-// partial wave of up to a third of the step on 152 SMs).  Partials stay
-// indexed by tile: the reductions do not depend on which CTA took a tile.
+// partial wave of up to a third of the step on 152 SMs); the counter hands
+// out every block's 8-plane tiles before the 2-plane tail tiles.  Partials
+// stay indexed by tile slot: the reductions do not depend on which CTA took
+// a tile.
 template <int TX, int TY, int KC>
 __global__ void __launch_bounds__(TX *TY) k_step_f64(StepArgs a) {
   float wfloor = -INFINITY;
