@@ -375,3 +375,80 @@ def test_face_buffer_layout_brute_force(global_run):
                 for v in range(4):
                     assert buf[2 * nb * nc + v * nb * nc + ic * nb + ib] == \
                         G[1 + v, node[2] + 1, node[1] + 1, node[0] + 1]
+
+
+# --------------------------------------------------------------------------
+# The stable step (Section 2: explicit Euler with the local acoustic wave
+# speeds and the viscous/thermal diffusion limit) against values worked out
+# by hand, not from the oracle's spectral routine.
+@pytest.mark.parametrize("Pr", [0.71, 2.0])
+def test_dt_at_rest_closed_form(Pr):
+    # fluid at rest: beta^2 = kappa u_ref^2 everywhere and each wave speed
+    # (|V_d| + sqrt(V_d^2 + 4 beta^2)) / 2 is beta itself.  Sizes 7, 9, 11
+    # give 1/h = 8, 10, 12, so sum 1/h = 30 and sum 1/h^2 = 308.
+    kappa, u_ref, cfl = 0.25, 6.0, 0.5           # beta = 3
+    o = oracle.OracleCavity(7, 9, 11, dict(Ra=0.0, Pr=Pr, kappa=kappa, u_ref=u_ref, cfl=cfl), noise=0.0)
+    diff = 2.0 * max(Pr, 1.0) * 308.0            # the larger of nu = Pr and alpha = 1
+    S = 3.0 * 30.0 + diff
+    assert o.spectral_max() == pytest.approx(S, rel=1e-14)
+    o.step(1)
+    assert o.dt == pytest.approx(cfl / S, rel=1e-14)
+
+
+def test_dt_uniform_velocity_floor_branch():
+    # beta^2 = kappa u_ref^2 = 900 (so 4 beta^2 = 60^2) exceeds |V|^2 = 11^2 + 25^2 = 746.
+    # V = (11, -25, 0): sqrt(11^2 + 3600) = 61, sqrt(25^2 + 3600) = 65, sqrt(3600) = 60,
+    # wave speeds (11 + 61)/2 = 36, (25 + 65)/2 = 45, 60/2 = 30.
+    # 1/h = 8, 10, 12: 36*8 + 45*10 + 30*12 = 1098; diffusion 2 * 1 * 308 = 616.
+    n = (7, 9, 11)
+    o = oracle.OracleCavity(*n, dict(Ra=0.0, Pr=0.71, kappa=1.0, u_ref=30.0, cfl=0.5), noise=0.0)
+    f = o.fields()
+    f[1], f[2], f[3] = 11.0, -25.0, 0.0
+    o.set_fields(f)
+    assert o.spectral_max() == pytest.approx(1098.0 + 616.0, rel=1e-14)
+    # the same wave speeds with the axes permuted: V = (0, 11, -25)
+    f[1], f[2], f[3] = 0.0, 11.0, -25.0
+    o.set_fields(f)
+    assert o.spectral_max() == pytest.approx(30 * 8 + 36 * 10 + 45 * 12 + 616.0, rel=1e-14)
+
+
+def test_dt_uniform_velocity_velocity_branch():
+    # V = (0, 0, w) with w^2 above the floor: beta^2 = w^2, the transverse wave
+    # speeds are sqrt(4 w^2)/2 = w and the streamwise one (w + sqrt(5) w)/2 =
+    # w phi, phi the golden ratio.
+    w = 40.0
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    o = oracle.OracleCavity(7, 9, 11, dict(Ra=0.0, Pr=0.71, kappa=0.01, u_ref=1.0, cfl=0.5), noise=0.0)
+    f = o.fields()
+    f[3] = -w
+    o.set_fields(f)
+    S = w * 8 + w * 10 + w * phi * 12 + 616.0
+    assert o.spectral_max() == pytest.approx(S, rel=1e-14)
+    o.step(1)
+    assert o.dt == pytest.approx(0.5 / S, rel=1e-14)
+
+
+def test_residual_is_rms_of_applied_increment():
+    # Section 4.2 residual norms, read as the RMS over the N interior nodes of
+    # dq/dt: after one step it must equal ||q^{n+1} - q^n||_2 / (dt sqrt(N))
+    # for the fields the centre rescale does not touch (u, v, w, T), using only
+    # field differences.
+    import workloads
+    n = (13, 11, 9)
+    N = n[0] * n[1] * n[2]
+    o = oracle.OracleCavity(*n, dict(Ra=1e4), noise=0.0)
+    o.set_fields(workloads.smooth_state(n, seed=5))
+    before = o.fields().copy()
+    o.step(1)
+    after = o.fields()
+    for f in (1, 2, 3, 4):
+        inc = after[f] - before[f]
+        expect = math.sqrt(float(np.sum(inc * inc)) / N) / o.dt
+        assert expect > 0
+        assert o.residual[f] == pytest.approx(expect, rel=1e-8), oracle.FIELDS[f]
+    # p: the increment is dt dp/dt less the centre value c of the updated p,
+    # one constant over the interior; removing the mean of the increment
+    # removes c, so the RMS of dp/dt bounds the RMS of the centred increment.
+    incp = after[0] - before[0]
+    cen = incp - incp.mean()
+    assert math.sqrt(float(np.sum(cen * cen)) / N) / o.dt <= o.residual[0] * (1 + 1e-8)
