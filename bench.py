@@ -48,15 +48,19 @@ FP64_FLOP_PER_POINT = 190
 # stored array read once and written once (FP64: 5 x 8 B; FP32-mixed: 7 x 4 B,
 # u, v, w and the hi/lo pairs of p and T)
 BYTES_PER_POINT = {"fp64": 80, "fp32": 56}
+# algorithmic HBM bytes per interior point of one launch of the adjoint's
+# dominant kernel (the reverse of the rates, FP32 sweep): read the stored
+# FP32-mixed state (7 x 4 B) and the adjoint of the state after the step
+# (5 x 4 B), write the adjoint of the state before it (5 x 4 B)
+ADJ_BYTES_PER_POINT = 68
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the same workload and kernel shape (profiles/k_step_f64_cavity128_2x2x2.md,
-# profiles/k_step_f32q_cavity256.md); None where no capture of the current
-# kernel exists.  Key: (precision, workload, blocks, shape); the FP32 shape is
-# the autotuner's "TY,KC,R,form"
+# capture of the same workload and kernel shape, kept with the capture's
+# summary; None where no capture of the current kernel exists.  Key:
+# (precision, workload, blocks, shape); the FP32 shape is the autotuner's
+# "TY,KC,R,form"
 FP64_SHAPE = "32x4x8"
 TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.855680e6 + 55.964416e6,
            ("fp32", "cfg3", (1, 1, 1), "8,32,4,3"): 590.065920e6 + 435.272704e6,
-           # the batch of 64 (profiles/k_step_f32q_batch64.md)
            ("fp32", "cfg4", None, "8,64,5,3"): 622.304256e6 + 327.072512e6}
 F32_FORMS = {1: "k_step_f32 (one node per thread; z neighbours from the TMA ring)",
              2: "k_step_f32p (two nodes per thread, f32x2; z neighbours from the TMA ring)",
@@ -64,7 +68,9 @@ F32_FORMS = {1: "k_step_f32 (one node per thread; z neighbours from the TMA ring
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129e6
-WORKLOADS = {"cfg2": workloads.CFG2, "cfg3": workloads.CFG3}
+# the paper's timed single-GPU size (Section 4.6, Tables 3-4): 256^3 at Ra 1e5, FP64
+CAVITY256_FP64 = dict(name="cavity256_ra1e5_fp64", n=(256, 256, 256), Ra=1e5, Pr=0.71, noise=1e-3, seed=0)
+WORKLOADS = {"cfg2": workloads.CFG2, "cfg3": workloads.CFG3, "cav256": CAVITY256_FP64}
 
 
 def parse(argv=None):
@@ -174,9 +180,28 @@ def default_blocks(workload: str, blocks: str | None):
     return (2, 2, 2) if workload == "cfg2" else (1, 1, 1)
 
 
-def cpu_baseline(cfg, blocks, min_seconds=10.0, max_steps=200):
-    """The oracle as it stands on a bounded sample: steps of the same workload
-    until about min_seconds of CPU work."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_rate(cfg, blocks, min_seconds=10.0, max_steps=200):
+    """Point-updates/s of the oracle as it stands: steps of the workload until
+    about min_seconds of CPU work (threads: OMP_NUM_THREADS, default all cores)."""
     import oracle
     n = cfg["n"]
     o = oracle.OracleCavity(*n, dict(Ra=cfg["Ra"], Pr=cfg["Pr"]), blocks=blocks, noise=cfg["noise"], seed=cfg["seed"])
@@ -187,11 +212,32 @@ def cpu_baseline(cfg, blocks, min_seconds=10.0, max_steps=200):
         o.step(1)
         steps += 1
     dt = time.perf_counter() - t0
+    return n[0] * n[1] * n[2] * steps / dt, steps, dt
+
+
+def cpu_baseline(workload, blocks, min_seconds=10.0, max_steps=200):
+    """The oracle on the host cores (all of them, OpenMP over k) on a bounded
+    sample, plus the same oracle on one thread in a child process."""
+    cfg = WORKLOADS[workload]
+    value, steps, dt = oracle_rate(cfg, blocks, min_seconds, max_steps)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    pts = n[0] * n[1] * n[2]
-    return {"value": pts * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    n = cfg["n"]
+    one = None
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, workloads; "
+            "v, s, t = bench.oracle_rate(bench.WORKLOADS[%r], %r, %r, %r); "
+            "print(json.dumps([v, s, t]))" % (ROOT, workload, tuple(blocks), min_seconds / 2, max_steps))
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=120 + 4 * min_seconds)
+        v1, s1, t1 = json.loads(r.stdout.strip().splitlines()[-1])
+        one = {"value": v1, "threads": 1, "sample": f"{s1} oracle steps ({t1:.1f} s)"}
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        one = None
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{steps} oracle steps of the {n[0]}x{n[1]}x{n[2]} cavity in {blocks} blocks "
-                      f"({dt:.1f} s, FP64, OpenMP over k)"}
+                      f"({dt:.1f} s, FP64, OpenMP over k on {cores} threads)",
+            "one_thread": one}
 
 
 def run_reference(args):
@@ -225,7 +271,18 @@ def run_reference(args):
     return 0
 
 
-def roofline_for(precision, pts, step_ms, hbm, traffic=None, form=3):
+_FP64_PEAK = {}
+
+
+def fp64_peak(m, device: int):
+    """FP64 FMA throughput of this GPU measured by the library's DFMA chains
+    (cavity_measure_fp64_peak), once per process."""
+    if device not in _FP64_PEAK:
+        _FP64_PEAK[device] = m.cavity_measure_fp64_peak(device)
+    return _FP64_PEAK[device]
+
+
+def roofline_for(precision, pts, step_ms, hbm, traffic=None, form=3, fp64_measured=None):
     step_s = step_ms / 1e3
     bpp = BYTES_PER_POINT[precision]
     gbs = bpp * pts / step_s / 1e9
@@ -235,10 +292,16 @@ def roofline_for(precision, pts, step_ms, hbm, traffic=None, form=3):
         return dict(kernel=F32_FORMS.get(form, f"FP32 step kernel form {form}") +
                     ": TMA-staged fused residual + update + partials", traffic=traffic, kernel_ms=step_ms, **hbm_obj)
     tf = FP64_FLOP_PER_POINT * pts / step_s / 1e12
+    peak = fp64_measured or FP64_PEAK_TFLOPS
     return {"kernel": "k_step_f64 (fused residual + update + reductions)", "bound": "alu", "achieved": tf,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
-            "peak_source": "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure measured)",
-            "kernel_ms": step_ms, "flop_per_point": FP64_FLOP_PER_POINT, "hbm_view": hbm_obj}
+            "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "traffic": traffic,
+            "peak_source": ("measured FP64 FMA throughput (cavity_measure_fp64_peak: independent DFMA chains on "
+                            "every SM, of measured)" if fp64_measured else
+                            "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"),
+            "peak_derived": FP64_PEAK_TFLOPS, "frac_of_derived": tf / FP64_PEAK_TFLOPS,
+            "kernel_ms": step_ms, "flop_per_point": FP64_FLOP_PER_POINT,
+            "flop_per_point_note": "counted on the kernel's formulation; the oracle's plain formulation of "
+                                   "Eqs. 1-3 counts about 212", "hbm_view": hbm_obj}
 
 
 def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, local, stream, e2e=True,
@@ -257,7 +320,9 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
         m.cavity_set_overlap(c.h, True)
         launches_per_step += 1
     both_buffers = pts * BYTES_PER_POINT[precision]  # the two buffer sets of the state
-    flush = both_buffers < 1.2 * L2_BYTES
+    # one step reads one buffer set (half of both_buffers) and writes the
+    # other, which the next step reads: flush L2 unless that set exceeds it
+    flush = both_buffers / 2 < 1.2 * L2_BYTES
     scratch = torch.empty(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=f"cuda:{local}") if flush else None
 
     def barrier():
@@ -301,13 +366,15 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
     out = {"value": job_value(pts * steps, world, ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
            "kernel_ms": {"step": kms[0], "bc_finalize": kms[1], "pack": kms[2], "unpack": kms[3]},
            "gpu_launches": launches_per_step * steps, "clocks": clk.summary(), "status": rc, "autotune": tuned,
-           "l2": ("L2 flushed (2 x L2 buffer written) before every timed step: the state fits in L2" if flush else
-                  f"no flush: the two state buffers ({both_buffers / 1e6:.0f} MB) exceed the 129 MB L2"),
+           "l2": (f"L2 flushed (2 x L2 buffer written) before every timed step: a step reads one buffer set "
+                  f"({both_buffers / 2e6:.0f} MB), which fits in the 129 MB L2" if flush else
+                  f"no flush: a step reads one buffer set ({both_buffers / 2e6:.0f} MB), more than the 129 MB L2"),
            "roofline": roofline_for(precision, pts, kms[0], measured_peaks().get("hbm_gbs"),
                                     # the overlapped schedule's step kernel skips the shell
                                     # nodes: no capture of it
                                     None if overlap else TRAFFIC.get((precision, workload, tuple(blocks), shape)),
-                                    tuned["kernel_form"] if tuned else 3)}
+                                    tuned["kernel_form"] if tuned else 3,
+                                    fp64_peak(m, local) if precision == "fp64" else None)}
     if e2e:
         # end to end through the public API with host buffers: initial state
         # from host, every step followed by the residual + Nusselt read, final
@@ -371,7 +438,8 @@ def measure_batch(m, torch, steps, warmup, rank, world, local, stream):
                                      tuned["kernel_form"]),
             "config": {"workload": f"batch of {len(cavs)} cavities, n_d in [24, 96], Ra log-uniform in [1e3, 1e6], "
                                    f"{pts} interior points, FP32-mixed, one graph launch per step",
-                       "l2": ("inputs larger than L2" if both_buffers > 1.2 * L2_BYTES else
+                       "l2": (f"no flush: a step reads one buffer set ({both_buffers / 2e6:.0f} MB), more than "
+                              f"the 129 MB L2" if both_buffers / 2 > 1.2 * L2_BYTES else
                               "state smaller than L2: not flushed")},
             "dtype": "f32 (p as f32 hi/lo pair, f64 reductions)"}
 
@@ -402,18 +470,37 @@ def measure_adjoint(m, torch, rank, world, local, stream):
         g, gra = m.cavity_adjoint_backward(c.h, n[1], n[2])
         t2 = time.perf_counter()
     rc = c.sync()
+    gather_ms = m.cavity_adjoint_kernel_ms(c.h)
     c.close()
     fwd, bwd = t1 - t0, t2 - t1
     fwd, bwd = max_over_ranks([fwd, bwd], world, f"cuda:{local}")
     steps = cfg["steps"]
+    hbm = measured_peaks().get("hbm_gbs")
+    gbs = ADJ_BYTES_PER_POINT * pts / (gather_ms / 1e3) / 1e9
     return {"metric": "gradient point-steps/s (forward + reverse sweep)", "value": job_value(pts * steps, world, fwd + bwd),
             "unit": "point-steps/s", "steps": steps, "checkpoint_every": cfg["ckpt"],
             "forward_ms_per_step": 1e3 * fwd / steps, "backward_ms_per_step": 1e3 * bwd / steps,
             "J": J, "dJ_dRa": gra, "grad_wall_norm": float(np.linalg.norm(g)), "clocks": clk.summary(), "status": rc,
             "autotune": tuned,
+            "roofline": {"kernel": "k_adj_gather (reverse of the rates, FP32 gather form)", "bound": "hbm",
+                         "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm if hbm else None,
+                         "traffic": None, "kernel_ms": gather_ms, "bytes_per_point": ADJ_BYTES_PER_POINT,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "config": {"workload": f"adjoint of {steps} steps, cavity {n[0]}^3 Ra {cfg['Ra']:g}, FP32-mixed forward, "
                                    f"FP32 reverse sweep (FP64 reductions), checkpoints every {cfg['ckpt']}"},
             "dtype": "f32 forward (p, T as f32 pairs), f32 adjoint sweep with f64 reductions"}
+
+
+def summary(line) -> dict:
+    """One short entry per measured workload (value, time per step, roofline
+    fraction), printed last so that a truncated tail of the line still shows
+    every workload."""
+    out = {}
+    for name, v in [("headline", line)] + list(line.get("variants", {}).items()):
+        r = v.get("roofline") or {}
+        out[name] = {"value": v.get("value"), "ms_per_step": v.get("ms_per_step", v.get("backward_ms_per_step")),
+                     "bound": r.get("bound"), "frac": r.get("frac"), "kernel_ms": r.get("kernel_ms")}
+    return out
 
 
 def run_ours(args):
@@ -462,12 +549,20 @@ def run_ours(args):
         v["dtype"] = "f64"
         v["kernel_ms_note"] = "kernel_ms from the plain (non-overlapped) launch sequence"
         variants["fp64_cfg2_overlap"] = v
+        v = measure(m, torch, "fp64", "cav256", (1, 1, 1), min(args.steps, 200), args.warmup, rank, world, local,
+                    stream, e2e=False)
+        v["config"] = {"workload": "cavity 256^3 Ra 1e+05 one block FP64: the paper's timed single-GPU size "
+                                   "(Section 4.6, Tables 3-4)", "l2": v.pop("l2")}
+        v["dtype"] = "f64"
+        variants["fp64_cavity256"] = v
         variants["batch64_fp32"] = measure_batch(m, torch, min(args.steps, 500), args.warmup, rank, world, local,
                                                  stream)
         variants["adjoint_cfg5"] = measure_adjoint(m, torch, rank, world, local, stream)
         line["variants"] = variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, blocks)
+        line["cpu_baseline"] = cpu_baseline(args.workload, blocks)
+    if "variants" in line:
+        line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

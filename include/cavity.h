@@ -118,12 +118,23 @@ CAVITY_API int cavity_create(const cavity_desc *desc, cavity_t **out);
  * fields are kept and only the walls and the next dt are recomputed. */
 CAVITY_API int cavity_set_params(cavity_t *h, const cavity_params *p);
 
-/* Temperature of an isothermal wall: wall 0 = hot (x = 0), 1 = cold (x = 1).
- * host holds ny*nz values, (j-1) + ny (k-1) order; n must equal ny*nz.
- * Replaces the uniform t_hot / t_cold on that wall; walls are re-applied. */
+/* Temperature of an isothermal wall (Section 2: the left and right vertical
+ * walls are held at fixed temperatures): wall 0 = hot (x = 0), 1 = cold
+ * (x = 1).  host holds ny*nz values, (j-1) + ny (k-1) order; n must equal
+ * ny*nz (CAVITY_ERR_INVALID_ARG otherwise, or for a wall other than 0 or 1).
+ * Replaces the uniform t_hot / t_cold on that wall; walls are re-applied.
+ * The caller keeps the host array; the call copies it and synchronises. */
 CAVITY_API int cavity_set_wall_temperature(cavity_t *h, int wall, const double *host, size_t n);
 
-/* Enqueue nsteps explicit steps (nsteps >= 0) on the handle's stream. */
+/* Enqueue nsteps explicit steps (nsteps >= 0) on the handle's stream.  One
+ * step is the first-order explicit update in (pseudo) time of Section 2 with
+ * the second-order central differences and fourth-difference pressure
+ * dissipation of Eqs. 1-3 on the stencils of Section 3.1 (Fig. 1), the
+ * centre-pressure rescale and wall extrapolations of Section 2, and, for a
+ * decomposed cavity, the ghost-face pack/unpack of Section 4.5 (Listings
+ * 1-2, V3).  Asynchronous: errors of the device work (non-finite state, a
+ * timed-out wait) surface at the next getter or cavity_sync();
+ * CAVITY_ERR_INVALID_ARG for nsteps < 0. */
 CAVITY_API int cavity_step(cavity_t *h, int nsteps);
 
 /* RMS over the interior of dq/dt of the last step, p, u, v, w, T
@@ -134,11 +145,19 @@ CAVITY_API int cavity_residual(cavity_t *h, double out[5]);
 
 /* Hot- and cold-wall Nusselt numbers of the current state: mean over the
  * ny*nz wall nodes of the one-sided second-order wall heat flux divided by
- * (t_hot - t_cold).  Either pointer may be NULL. */
+ * (t_hot - t_cold).  The paper defines no Nusselt number; this is the
+ * hot-wall Nusselt number the benchmark configurations of this cavity ask
+ * for (the 32^3, Ra 1e4 run reports it), taken with the second-order
+ * one-sided difference that matches the scheme's order (Section 2).  Either
+ * pointer may be NULL.  Synchronises; returns the sticky status. */
 CAVITY_API int cavity_nusselt(cavity_t *h, double *hot, double *cold);
 
 /* Copy interior fields of the whole cavity to host (FP64; FP32 fields
- * widened, the p pair summed).  count must equal popcount(mask)*nx*ny*nz. */
+ * widened, the p pair summed): the state p, u, v, w, T of Eqs. 1-3 on the
+ * interior nodes of Section 3.1's grid, gathered across the blocks of the
+ * Section 3.2 decomposition, p after the centre rescale (Section 2).  count
+ * must equal popcount(mask)*nx*ny*nz (CAVITY_ERR_INVALID_ARG otherwise).
+ * Synchronises the stream; the caller owns host. */
 CAVITY_API int cavity_get_fields(cavity_t *h, int field_mask, double *host, size_t count);
 
 /* Copy a box of interior nodes (global 1-based node ranges i0 .. i0+ni-1,
@@ -149,11 +168,18 @@ CAVITY_API int cavity_get_fields_box(cavity_t *h, int field_mask, int i0, int j0
                                      double *host, size_t count);
 
 /* Overwrite interior fields from host (layout as cavity_get_fields), then
- * re-apply walls, exchange ghosts and recompute dt.  Step count and time
- * are kept. */
+ * re-apply the Section 2 wall conditions, exchange ghosts (Section 4.5) and
+ * recompute dt; the state can then be stepped as if the scheme had reached
+ * it (checkpoint/restart of the Section 2 iteration).  Step count and time
+ * are kept.  FP32-mixed handles round u, v, w to FP32 and split p and T
+ * into FP32 pairs.  count as cavity_get_fields; synchronises. */
 CAVITY_API int cavity_set_fields(cavity_t *h, int field_mask, const double *host, size_t count);
 
-/* Step counter, simulated time and the dt the next step will use. */
+/* Step counter, simulated (pseudo) time t = sum of the global dt of the
+ * steps taken, and the dt the next step will use: cfl over the largest
+ * spectral-radius bound of the current state (the stable explicit step of
+ * Section 2).  Any pointer may be NULL.  Synchronises; returns the sticky
+ * status. */
 CAVITY_API int cavity_get_time(cavity_t *h, long long *step, double *t, double *dt);
 
 /* Number of blocks (px*py*pz). */
@@ -233,11 +259,21 @@ CAVITY_API int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double 
  * (grad_wall: ny*nz host values, (j-1) + ny (k-1) order; n must equal
  * ny*nz; may be NULL) and to Ra (grad_ra, may be NULL).  Reverse sweep of
  * the step (Section 2 scheme; dt, beta^2 and |V| differentiated along the
- * forward branch) in FP64, each ckpt-step segment recomputed from its
- * checkpoint.  When u_ref was left to its default it follows Ra
+ * forward branch), each ckpt-step segment recomputed from its checkpoint.
+ * The sweep runs in the forward form's arithmetic: FP64 after an FP64
+ * forward; FP32 adjoint arrays with FP64 node sums after an FP32-mixed
+ * forward (linearised about its FP32 trajectory); the returned gradients
+ * are FP64 either way.  When u_ref was left to its default it follows Ra
  * (u_ref^2 = Ra Pr) in the derivative.  The state is restored to the one
  * after the forward run. */
 CAVITY_API int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *grad_ra);
+
+/* Measurement: mean duration in ms, from CUDA events on the handle's stream
+ * around every launch, of the dominant kernel of the last
+ * cavity_adjoint_backward: the reverse of the rates (k_adj_gather after an
+ * FP32-mixed forward, k_adj_rates after an FP64 one), one launch per reverse
+ * step.  CAVITY_ERR_INVALID_ARG before the first reverse sweep. */
+CAVITY_API int cavity_adjoint_kernel_ms(cavity_t *h, double *ms);
 
 /* Interior/shell split with overlap (Section 4.7): when on, each step first
  * computes the nodes within two layers of a cut face, then exchanges the new
@@ -278,6 +314,16 @@ CAVITY_API int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]);
  * outside that range; CAVITY_ERR_OOM / CAVITY_ERR_CUDA on a CUDA error. */
 CAVITY_API int cavity_check_sqrt(const double *x, long long n, double *max_rel, long long *n_diff);
 
+/* Measurement (no counterpart in the paper): the FP64 FMA throughput of CUDA
+ * device `device` in TFLOP/s (2 flops per FMA), the ceiling of the FP64 step
+ * kernel, whose 190 FP64 operations per 80 bytes of state put it far on the
+ * arithmetic side of GB300's FP64 roofline.  Independent FMA chains on every
+ * resident thread of every SM, timed with CUDA events over one launch of
+ * about 0.1 s after a warm-up launch; the best of three.  Allocates and frees
+ * a few kilobytes; synchronises its own stream.  CAVITY_ERR_INVALID_ARG for a
+ * null pointer or a device that does not exist. */
+CAVITY_API int cavity_measure_fp64_peak(int device, double *tflops);
+
 /* Allocation-free step of one caller-held block.  The paper has no
  * counterpart; this exists for callers that must not call cudaMalloc, such as
  * code running inside another framework's caching allocator or a fixed,
@@ -314,7 +360,23 @@ CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *q_out, int 
                                          const cavity_params *p, double dt, double pshift, double *out6,
                                          void *stream);
 
-/* Synchronise the handle's stream; returns the sticky non-finite status. */
+/* Test hook of the failure detection (the paper has none): the FP32-mixed
+ * step kernels wait on shared-memory barriers for each TMA plane load, every
+ * wait bounded; a wait that gives up sets the cavity's sticky timeout flag,
+ * lets the CTA's issued copies land (again bounded) and returns, so the
+ * context stays usable and cavity_sync() / the getters report
+ * CAVITY_ERR_TIMEOUT.  This sets the limit of each wait (wait_cycles, SM
+ * clock cycles in [1000, 4e9]; 4e9, about 2 s, is the default) and, with
+ * withhold_plane >= 0, leaves the load of that plane of every tile (0 = the
+ * first halo plane below the tile's z range) unissued, so that its waits run
+ * out; withhold_plane = -1 issues every load.  The step graphs are rebuilt.
+ * FP32-mixed handles only (CAVITY_ERR_UNSUPPORTED otherwise); the state of a
+ * handle whose wait ran out is not a step of the scheme: destroy it. */
+CAVITY_API int cavity_test_wait_timeout(cavity_t *h, long long wait_cycles, int withhold_plane);
+
+/* Synchronise the handle's stream; returns the sticky status: CAVITY_ERR_TIMEOUT
+ * once a bounded device-side wait gave up, else CAVITY_ERR_NONFINITE once a
+ * step produced a non-finite residual or spectral radius, else CAVITY_OK. */
 CAVITY_API int cavity_sync(cavity_t *h);
 
 /* Release everything the handle owns.  NULL is accepted. */

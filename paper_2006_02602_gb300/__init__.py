@@ -45,7 +45,8 @@ EXPORTED = (
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
     "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
     "cavity_batch_get_fields", "cavity_autotune", "cavity_adjoint_forward", "cavity_adjoint_backward",
-    "cavity_set_time_stepping", "cavity_set_overlap", "cavity_check_sqrt",
+    "cavity_set_time_stepping", "cavity_set_overlap", "cavity_check_sqrt", "cavity_test_wait_timeout",
+    "cavity_measure_fp64_peak", "cavity_adjoint_kernel_ms",
 )
 
 
@@ -114,6 +115,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_step_block_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(cavity_params), ctypes.c_double, ctypes.c_double,
                                        ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+        "cavity_test_wait_timeout": ([_H, ctypes.c_longlong, ctypes.c_int], ctypes.c_int),
+        "cavity_measure_fp64_peak": ([ctypes.c_int, _dp], ctypes.c_int),
+        "cavity_adjoint_kernel_ms": ([_H, _dp], ctypes.c_int),
         "cavity_sync": ([_H], ctypes.c_int),
         "cavity_destroy": ([_H], ctypes.c_int),
         "cavity_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -288,6 +292,16 @@ def cavity_step_block_noalloc(q_in_ptr: int, q_out_ptr: int, shape, params: cavi
                                                     out6_ptr, stream))
 
 
+def cavity_measure_fp64_peak(device: int = 0) -> float:
+    out = ctypes.c_double()
+    _check(load_library().cavity_measure_fp64_peak(int(device), ctypes.byref(out)))
+    return out.value
+
+
+def cavity_test_wait_timeout(h, wait_cycles: int, withhold_plane: int = -1) -> None:
+    _check(load_library().cavity_test_wait_timeout(h, int(wait_cycles), int(withhold_plane)), h)
+
+
 def cavity_sync(h) -> int:
     return load_library().cavity_sync(h)
 
@@ -351,6 +365,12 @@ def cavity_adjoint_backward(h, ny: int, nz: int) -> tuple[np.ndarray, float]:
     gra = ctypes.c_double()
     _check(load_library().cavity_adjoint_backward(h, g.ctypes.data_as(_dp), g.size, ctypes.byref(gra)), h)
     return g, gra.value
+
+
+def cavity_adjoint_kernel_ms(h) -> float:
+    out = ctypes.c_double()
+    _check(load_library().cavity_adjoint_kernel_ms(h, ctypes.byref(out)), h)
+    return out.value
 
 
 def cavity_strerror(code: int) -> str:

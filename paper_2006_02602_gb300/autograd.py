@@ -10,7 +10,9 @@ j fastest, or an array [nz, ny]) and Rayleigh number Ra.  The forward pass
 runs the steps on the GPU keeping a checkpoint every ckpt steps; the
 backward pass recomputes each segment from its checkpoint and sweeps the
 discrete adjoint of the step (cavity_adjoint_forward / _backward in the C
-ABI).  Gradients are FP64 whatever the forward form.
+ABI).  The sweep runs in the forward form's arithmetic (FP64 after an FP64
+forward; FP32 adjoint arrays with FP64 sums over nodes after an FP32-mixed
+one); the gradients it returns are FP64 tensors either way.
 """
 from __future__ import annotations
 

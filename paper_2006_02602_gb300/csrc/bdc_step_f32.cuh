@@ -50,6 +50,8 @@ struct StepF32Args {
   int parity;
   int local_dt;               // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
   int ncoarse;                // coarse tiles of all blocks (scheduling indices below it)
+  long long wait_cycles;      // limit of each bounded mbarrier wait (kWaitCycles)
+  int withhold_plane;         // -1; a test of the timeout path sets a plane index whose load is never issued
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -74,12 +76,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// wait for the phase with the given parity, giving up after kWaitCycles
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// wait for the phase with the given parity, giving up after `limit` cycles
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -489,6 +491,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   __syncthreads();
   int issued = 0;
   auto issue = [&](int pl) {
+    if (pl == a.withhold_plane) return;  // the timeout test: this plane never arrives
     const int s = pl & (R - 1);
     mbar_expect_tx(&bars[s], SB);
     tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(St
   if (tid == 0) {
     for (; issued < min(R, T.nplanes); ++issued) issue(issued);
   }
-  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1)); };
+  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1), a.wait_cycles); };
   auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
   const int col = (lj + 2) * BX + (li + 4);  // own column inside a slot
 
@@ -709,6 +712,7 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
   __syncthreads();
   int issued = 0;
   auto issue = [&](int pl) {
+    if (pl == a.withhold_plane) return;  // the timeout test: this plane never arrives
     const int s = pl & (R - 1);
     mbar_expect_tx(&bars[s], SB);
     tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
@@ -716,7 +720,7 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_st
   if (tid == 0) {
     for (; issued < min(R, T.nplanes); ++issued) issue(issued);
   }
-  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1)); };
+  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1), a.wait_cycles); };
   auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
   const int col = (lj + 2) * BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
 
@@ -1147,6 +1151,7 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32T
   __syncthreads();
   int issued = 0;
   auto issue = [&](int pl) {
+    if (pl == a.withhold_plane) return;  // the timeout test: this plane never arrives
     const int s = pl % R;
     mbar_expect_tx(&bars[s], SB);
     tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
@@ -1154,7 +1159,7 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32T
   if (tid == 0) {
     for (; issued < min(R, T.nplanes); ++issued) issue(issued);
   }
-  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl % R], (uint32_t)((pl / R) & 1)); };
+  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl % R], (uint32_t)((pl / R) & 1), a.wait_cycles); };
   auto slot = [&](int pl) { return ring + (pl % R) * SF; };
 
   const long long fs = B.fstride, plane = B.plane;

@@ -94,6 +94,8 @@ struct cavity {
   int dev = 0;
   bool u_ref_auto = true;  // u_ref follows Ra (default)
   AdjointStore adj;
+  std::vector<cudaEvent_t> adj_ev;  // two per reverse step: around the rates' reverse kernel
+  double adj_rates_ms = 0.0;        // its mean duration in the last reverse sweep
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int ncav = 1;
@@ -110,6 +112,8 @@ struct cavity {
   int f32_r = 0;                  // ring depth of the FP32 step kernel
   int f32_p = 1;                  // nodes per thread along x of the FP32 step kernel
   int local_dt = 0;               // CAVITY_DT_LOCAL: each node at its own stable step
+  long long wait_cycles = kWaitCycles;  // limit of the FP32 step kernel's bounded waits
+  int withhold_plane = -1;              // timeout test: tile plane whose load is not issued
   // interior/shell split with overlapped exchange (FP64, single cavity, cut faces)
   bool overlap = false;
   std::vector<ShellFace> hshell;
@@ -490,6 +494,8 @@ StepF32Args step_f32_args(cavity *h, int parity) {
   a.blocks = h->d_blocks; a.nblocks = h->nblocks; a.cc = h->d_cc; a.cs = h->d_cs;
   a.maps = h->d_maps; a.partials = h->d_step_part; a.parity = parity; a.local_dt = h->local_dt;
   a.ncoarse = h->n_coarse;
+  a.wait_cycles = h->wait_cycles;
+  a.withhold_plane = h->withhold_plane;
   return a;
 }
 
@@ -856,6 +862,8 @@ void release(cavity *h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_shell) cudaEventDestroy(h->ev_shell);
   if (h->ev_exch) cudaEventDestroy(h->ev_exch);
+  for (cudaEvent_t e : h->adj_ev) cudaEventDestroy(e);
+  h->adj_ev.clear();
 }
 
 int create_common(const cavity_desc *descs, const cavity_params *params, int n, cavity_t **out) {
@@ -950,7 +958,8 @@ int create_common(const cavity_desc *descs, const cavity_params *params, int n, 
 // ===========================================================================
 // the reverse of one step: state storage S, adjoint arrays and arithmetic Ad
 template <class S, class Ad>
-void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint, long long nfold) {
+void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint, long long nfold, cudaEvent_t eb,
+                         cudaEvent_t ea) {
   k_adj_objective<Ad><<<ceil_div((long long)a.g.ny * a.g.nz, 256), 256, 0, h->stream>>>(a);
   k_adj_sum_p<Ad><<<nparts, 256, 0, h->stream>>>(a);
   if constexpr (std::is_same<Ad, float>::value) {
@@ -959,10 +968,14 @@ void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint
     k_adj_centre<Ad><<<1, 8, 0, h->stream>>>(a);
     AdjArgs g = a;
     g.Yt = a.X;
+    cudaEventRecord(eb, h->stream);
     k_adj_gather<<<ceil_div(a.g.fs, 256), 256, 0, h->stream>>>(g);
+    cudaEventRecord(ea, h->stream);
   } else {
     k_adj_prepare<Ad, true><<<dim3((unsigned)ceil_div(a.g.fs, 256), 5), 256, 0, h->stream>>>(a);
+    cudaEventRecord(eb, h->stream);
     k_adj_rates<S, Ad><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
+    cudaEventRecord(ea, h->stream);
   }
   k_adj_argmax<S><<<nparts, 256, 0, h->stream>>>(a);
   k_adj_dt<S, Ad><<<1, kAdjDtThreads, 0, h->stream>>>(a, nparts);
@@ -976,6 +989,28 @@ __global__ void k_check_sqrt(const double *x, long long n, double *rel) {
   if (i >= n) return;
   const double r = sqrt(x[i]), s = sqrt_newton(x[i]);
   rel[i] = s == r ? 0.0 : fabs(s - r) / r;
+}
+
+// FP64 FMA throughput of the GPU: every thread runs kDfmaChains independent
+// chains x <- x a + b (a = 1 - 2^-20, b = 2^-20: the values stay near 1, no
+// overflow or subnormals), unrolled so that the FP64 pipe always has an
+// independent FMA to issue; the sum is compared with a value it never takes,
+// so no chain can be removed.  FLOPs = 2 per FMA.
+constexpr int kDfmaChains = 8, kDfmaUnroll = 4, kDfmaThreads = 256;
+__global__ void __launch_bounds__(kDfmaThreads) k_dfma_peak(double *sink, int iters, double a, double b) {
+  double x[kDfmaChains];
+#pragma unroll
+  for (int c = 0; c < kDfmaChains; ++c) x[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < kDfmaUnroll; ++r)
+#pragma unroll
+      for (int c = 0; c < kDfmaChains; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kDfmaChains; ++c) s += x[c];
+  if (s == -1.0) sink[blockIdx.x] = s;
 }
 
 extern "C" {
@@ -1384,6 +1419,11 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
   const long long nint = (long long)d.nx * d.ny * d.nz;
   const long long nfold = 2LL * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
   std::vector<double> dts(A.ckpt);
+  while (h->adj_ev.size() < 2 * (size_t)A.nsteps) {
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreate(&e));
+    h->adj_ev.push_back(e);
+  }
   int rc = CAVITY_OK;
   for (int c = A.ncp - 1; c >= 0 && rc == CAVITY_OK; --c) {
     const int s0 = c * A.ckpt, s1 = std::min(s0 + A.ckpt, A.nsteps);
@@ -1418,8 +1458,9 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
         k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(ba);
         CK(cudaGetLastError());
       }
-      if (h->f32) launch_adjoint_step<float, float>(h, a, A.nparts, nint, nfold);
-      else launch_adjoint_step<double, double>(h, a, A.nparts, nint, nfold);
+      cudaEvent_t eb = h->adj_ev[2 * s], ea = h->adj_ev[2 * s + 1];
+      if (h->f32) launch_adjoint_step<float, float>(h, a, A.nparts, nint, nfold, eb, ea);
+      else launch_adjoint_step<double, double>(h, a, A.nparts, nint, nfold, eb, ea);
       if (cudaGetLastError() != cudaSuccess) { rc = fail(h, CAVITY_ERR_CUDA, "adjoint kernel launch failed"); break; }
       std::swap(X, Q);
     }
@@ -1435,7 +1476,23 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
     CK(cudaMemcpyAsync(grad_wall, A.thetabar, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (grad_ra) *grad_ra = ra;
+  if (rc == CAVITY_OK) {
+    double tot = 0.0;
+    for (int s = 0; s < A.nsteps; ++s) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->adj_ev[2 * s], h->adj_ev[2 * s + 1]));
+      tot += ms;
+    }
+    h->adj_rates_ms = tot / A.nsteps;
+  }
   return rc;
+}
+
+int cavity_adjoint_kernel_ms(cavity_t *h, double *ms) {
+  if (!h || !ms) return CAVITY_ERR_INVALID_ARG;
+  if (h->adj_rates_ms <= 0.0) return fail(h, CAVITY_ERR_INVALID_ARG, "adjoint: no reverse sweep timed yet");
+  *ms = h->adj_rates_ms;
+  return CAVITY_OK;
 }
 
 int cavity_set_overlap(cavity_t *h, int on) {
@@ -1536,6 +1593,63 @@ int cavity_check_sqrt(const double *x, long long n, double *max_rel, long long *
   }
   *max_rel = m;
   *n_diff = nd;
+  return CAVITY_OK;
+}
+
+int cavity_test_wait_timeout(cavity_t *h, long long wait_cycles, int withhold_plane) {
+  if (!h) return CAVITY_ERR_INVALID_ARG;
+  if (!h->f32) return fail(h, CAVITY_ERR_UNSUPPORTED, "bounded waits exist in the FP32-mixed step only");
+  if (wait_cycles < 1000 || wait_cycles > kWaitCycles || withhold_plane < -1)
+    return fail(h, CAVITY_ERR_INVALID_ARG, "wait limit outside [1000, 4e9] cycles or plane < -1");
+  DeviceGuard g(h->dev);
+  CK(cudaStreamSynchronize(h->stream));
+  h->wait_cycles = wait_cycles;
+  h->withhold_plane = withhold_plane;
+  return build_graphs(h);
+}
+
+int cavity_measure_fp64_peak(int device, double *tflops) {
+  if (!tflops) return CAVITY_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CAVITY_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  cavity *h = nullptr;  // no handle: CK reports the code only
+  int sms = 0, per_sm = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma_peak, kDfmaThreads, 0));
+  const int grid = sms * std::max(per_sm, 1);
+  const int iters = 4096;
+  double *sink = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = CAVITY_OK;
+  float best = 0.f;
+  if (cudaMalloc(&sink, sizeof(double) * grid) != cudaSuccess) return CAVITY_ERR_OOM;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = CAVITY_ERR_CUDA;
+  } else {
+    const double a = 1.0 - 1.0 / 1048576.0, b = 1.0 / 1048576.0;
+    k_dfma_peak<<<grid, kDfmaThreads, 0, st>>>(sink, iters / 8, a, b);  // warm-up
+    for (int rep = 0; rep < 3 && rc == CAVITY_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      k_dfma_peak<<<grid, kDfmaThreads, 0, st>>>(sink, iters, a, b);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = CAVITY_ERR_CUDA;
+        break;
+      }
+      if (best == 0.f || ms < best) best = ms;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(sink);
+  if (rc != CAVITY_OK) return rc;
+  const double flops = 2.0 * kDfmaChains * kDfmaUnroll * (double)iters * grid * kDfmaThreads;
+  *tflops = flops / (best * 1e-3) / 1e12;
   return CAVITY_OK;
 }
 

@@ -59,6 +59,18 @@ cudaError_t scratch_address(int dev, void **out) {
   return cudaSuccess;
 }
 
+// Writes the three descriptors into the scratch array.  They arrive as kernel
+// parameters, which the launch copies by value, so the call reads no host
+// memory after it returns and makes no host-to-device copy of its own.
+__global__ void k_noalloc_setup(BlockDev B, CavConst C, CavState S, BlockDev *d_block, CavConst *d_cc,
+                                CavState *d_cs) {
+  if (threadIdx.x == 0) {
+    *d_block = B;
+    *d_cc = C;
+    *d_cs = S;
+  }
+}
+
 // RMS of the five rates and the next dt from the per-CTA partials, summed in
 // a fixed order (thread q takes partials q, q + 256, ...; warps in order)
 __global__ void __launch_bounds__(256) k_noalloc_reduce(const double *partials, int ntiles, const CavConst *cc,
@@ -142,10 +154,8 @@ extern "C" CAVITY_API int cavity_step_block_noalloc(const double *q_in, double *
   S.c = pshift;
 
   cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(d_block, &B, sizeof(B), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d_cc, &C, sizeof(C), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d_cs, &S, sizeof(S), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return CAVITY_ERR_CUDA;
+  k_noalloc_setup<<<1, 32, 0, st>>>(B, C, S, d_block, d_cc, d_cs);
+  if (cudaGetLastError() != cudaSuccess) return CAVITY_ERR_CUDA;
   StepArgs a{};  // tile_counter null: one CTA per tile
   a.blocks = d_block; a.nblocks = 1; a.cc = d_cc; a.cs = d_cs;
   a.partials = d_part; a.parity = 0; a.mode = 0; a.ntiles = (int)ntiles;

@@ -297,15 +297,15 @@ def test_fp32_config1_32cube_200_steps(m):
 
 @pytest.mark.parametrize("n", [(37, 21, 18), (2, 2, 2), (65, 9, 40), (33, 17, 70)])
 def test_fp32_ragged_and_degenerate_sizes(m, n):
-    """Small and ragged cavities: p and T against their own max-norm, each
-    velocity component against the maximum speed (a component that the
-    y-mirror symmetry keeps near zero has no scale of its own)."""
+    """Small and ragged cavities: p, u, w and T against their own max-norm; v,
+    which the y-mirror symmetry of the cavity keeps near zero (only the noise
+    breaks it), against the maximum speed."""
     o, c = run_pair32(m, n, 3e4, 25, noise=1e-3, seed=11)
     with c:
         g, ref = c.fields(), o.fields()
         speed = max(np.max(np.abs(ref[f])) for f in (1, 2, 3))
         for f, name in enumerate(oracle.FIELDS):
-            scale = speed if f in (1, 2, 3) else np.max(np.abs(ref[f]))
+            scale = speed if f == 2 else np.max(np.abs(ref[f]))
             e = np.max(np.abs(g[f] - ref[f])) / scale
             assert e <= FP32_TOL, f"fp32 n={n} field {name}: {e:.3e}"
 
@@ -332,7 +332,7 @@ def test_fp32_two_node_kernel(m, monkeypatch, shape):
             g, ref = c.fields(), o.fields()
             speed = max(np.max(np.abs(ref[f])) for f in (1, 2, 3))
             for f, name in enumerate(oracle.FIELDS):
-                scale = speed if f in (1, 2, 3) else np.max(np.abs(ref[f]))
+                scale = speed if f == 2 else np.max(np.abs(ref[f]))
                 e = np.max(np.abs(g[f] - ref[f])) / scale
                 assert e <= FP32_TOL, f"fp32 {shape} n={n} field {name}: {e:.3e}"
     kw = dict(precision=m.CAVITY_FP32_MIXED, seed=9, noise_amp=1e-3, Ra=1e5)
