@@ -59,12 +59,8 @@ ADJ_BYTES_PER_POINT = 68
 # (precision, workload, blocks, shape); the FP32 shape is the autotuner's
 # "TY,KC,R,form"
 FP64_SHAPE = "32x4x8"
-TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.855680e6 + 55.964416e6,
-           ("fp32", "cfg3", (1, 1, 1), "8,32,4,3"): 590.065920e6 + 435.272704e6,
-           ("fp32", "cfg4", None, "8,64,5,3"): 622.304256e6 + 327.072512e6}
-F32_FORMS = {1: "k_step_f32 (one node per thread; z neighbours from the TMA ring)",
-             2: "k_step_f32p (two nodes per thread, f32x2; z neighbours from the TMA ring)",
-             3: "k_step_f32q (two nodes per thread, f32x2; z neighbours below the plane in registers)"}
+TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.855680e6 + 55.964416e6}
+F32_FORMS = {3: "k_step_f32q (two nodes per thread, f32x2; z neighbours below the plane in registers)"}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129e6

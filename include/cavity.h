@@ -235,10 +235,10 @@ CAVITY_API int cavity_batch_get_fields(cavity_t *h, int cav, int field_mask, dou
  * steps on this handle's own cavities and keeps the fastest.  The state is
  * saved before the trials and restored after them (the step counter and the
  * fields are as before the call).  out (optional) receives the chosen tile
- * height, z-chunk, ring depth, kernel form (1: one node per thread; 2: two
- * nodes, z neighbours from the shared-memory ring; 3: two nodes, the z
- * neighbours below the plane in registers) and microseconds per step.  Every
- * shape gives the same fields.  With the environment variable BDC_F32_TILE
+ * height (8 or 16 rows of 32 nodes), z-chunk, ring depth, kernel form (3:
+ * two nodes per thread, the z neighbours below the plane in registers, the
+ * one form) and microseconds per step.  Every shape gives the same fields.
+ * With the environment variable BDC_F32_TILE
  * ("TY,KC,R,form", a compiled shape, read at creation) the shape is pinned and
  * no trials run (out[4] = 0).  FP64 handles have a single shape (32 x 4
  * threads, 8-plane chunks; BDC_F64_TY=8, read at creation, selects 32 x 8):

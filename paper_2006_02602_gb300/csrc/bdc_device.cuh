@@ -45,7 +45,8 @@ struct BlockDev {
   // z chunking of the step kernels: chunks 0 .. tiles_zc-1 of KC planes cover
   // planes 1 .. zsplit, the other tiles_z - tiles_zc chunks split planes
   // zsplit+1 .. nz into fine chunks (kFineKC planes in the FP64 form,
-  // kFineKC32 in the FP32 form).  Scheduling index c runs over every block's
+  // kFineKC32 in the FP32 form, whose KC = zsplit / tiles_zc is set at run
+  // time).  Scheduling index c runs over every block's
   // coarse tiles first (coarse_begin + local) and the fine ones last
   // (ncoarse + fine_begin + local): the persistent FP64 grid's counter and
   // the FP32 grids' block order both end on short tiles.  Partial slots stay
@@ -178,7 +179,7 @@ struct CutFace {      // one cut face of one block, processed by k_pack / k_unpa
 
 template <class S> struct XO;
 template <> struct XO<double> { static constexpr int v = 4; };
-template <> struct XO<float> { static constexpr int v = 8; };
+template <> struct XO<float> { static constexpr int v = 8; };  // node 1 starts a 32-byte sector
 
 template <class S>
 __device__ __forceinline__ long long node_index(const BlockDev &B, int i, int j, int k) {

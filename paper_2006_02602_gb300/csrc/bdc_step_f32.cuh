@@ -14,14 +14,20 @@
 // planes arrive in shared memory (x and y walls) or enter the z queues (z
 // walls).  u = v = w = 0 and the isothermal T never change and stay stored.
 //
-// Data movement (GB300): per CTA a 32 x 8 tile in (x, y) sweeps a KC-plane
-// chunk in z.  One elected thread streams whole planes of the tile plus a
-// two-node halo with TMA (cp.async.bulk.tensor.4d over x, y, z and the array
-// index: all six arrays in one copy) into a ring of R shared-memory slots,
-// each guarded by an mbarrier with a bounded wait; the z-neighbours live in
-// register queues (5 deep for p, 3 for u, v, w, T).  HBM sees each of the
-// seven arrays read once and written once per step: 56 bytes per interior
-// point.
+// Data movement (GB300): per CTA a 32 x TY tile in (x, y) sweeps one chunk of
+// its column in z, 16 x TY threads with two x-neighbouring nodes each.  One
+// elected thread streams every plane of the tile with two TMA copies
+// (cp.async.bulk.tensor.4d over x, y, z and the array index): the pressure
+// pair with the 13-point star's halo (2 nodes in y) and u, v, w and the T
+// pair with the 7-point star's (1 node in y), both 40 nodes wide (4 to the
+// left of the tile: node 1 sits on a 32-byte sector boundary, so each tile's
+// stores cover whole sectors, and the box starts 16-byte aligned; 4 to the
+// right), into a ring of R shared-memory slots, each guarded by an mbarrier
+// with a bounded wait.  A thread keeps its pair's values below the plane (z-1
+// of all seven arrays, z-2 of p) in registers, so only planes k .. k+2 stay
+// resident: a ring of 4 slots (47 KB) keeps one plane in flight at four CTAs
+// per SM, a ring of 5 two planes at three.  HBM sees each of the seven arrays
+// read once and written once per step: 56 bytes per interior point.
 #pragma once
 
 #include <cuda.h>
@@ -32,12 +38,23 @@
 
 namespace bdc {
 
-constexpr int kF32TX = 32, kF32TY = 8, kF32KC = 32, kF32R = 4, kF32P = 3;  // default shape: tile height, z chunk, ring depth, nodes per thread
-constexpr int kF32BX = kF32TX + 8;  // x halo 4 on each side: the box starts on a 16-byte boundary
-constexpr int kF32NA = 7;           // p_hi, p_lo, u, v, w, T_hi, T_lo
-__host__ __device__ constexpr int f32_box_y(int TY) { return TY + 4; }  // y halo 2 (pressure star)
-__host__ __device__ constexpr int f32_slot_floats(int TY) { return kF32NA * f32_box_y(TY) * kF32BX; }
-__host__ __device__ constexpr int f32_smem_bytes(int TY, int R) { return R * f32_slot_floats(TY) * 4 + R * 8; }
+constexpr int kF32TX = 32;                       // tile width: 16 threads x 2 nodes
+constexpr int kF32TY = 8, kF32KC = 32, kF32R = 4;  // default shape: tile height, z chunk, ring depth
+constexpr int kF32HX = 4;                        // x halo of both boxes left of the tile (2 needed)
+constexpr int kF32BX = kF32TX + 8;               // box width: 40 floats, 160 bytes
+constexpr int kF32NA = 7;                        // p_hi, p_lo, u, v, w, T_hi, T_lo
+constexpr int kF32NP = 2, kF32NO = 5;            // arrays of the pressure box and of the other box
+__host__ __device__ constexpr int f32_box_yp(int TY) { return TY + 4; }  // pressure box rows: y halo 2
+__host__ __device__ constexpr int f32_box_yo(int TY) { return TY + 2; }  // u, v, w, T box rows: y halo 1
+__host__ __device__ constexpr int f32_p_bytes(int TY) { return kF32NP * f32_box_yp(TY) * kF32BX * 4; }
+__host__ __device__ constexpr int f32_o_bytes(int TY) { return kF32NO * f32_box_yo(TY) * kF32BX * 4; }
+__host__ __device__ constexpr int f32_tx_bytes(int TY) { return f32_p_bytes(TY) + f32_o_bytes(TY); }
+__host__ __device__ constexpr int f32_slot_bytes(int TY) { return (f32_tx_bytes(TY) + 127) / 128 * 128; }
+__host__ __device__ constexpr int f32_smem_bytes(int TY, int R) { return R * f32_slot_bytes(TY) + R * 8; }
+// a box starts at node i0 - 4 (array index XO - 5 + i0, i0 = 32 t + 1): a multiple of four floats
+static_assert((XO<float>::v - kF32HX) % 4 == 0, "the TMA box must start on a 16-byte boundary");
+static_assert(XO<float>::v % 8 == 0, "node 1 on a 32-byte sector boundary: a tile's stores fill whole sectors");
+static_assert(XO<float>::v % 2 == 0, "node pairs (odd i, i + 1) must be 8-byte aligned");
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier wait, about 2 s
 
 struct StepF32Args {
@@ -45,7 +62,7 @@ struct StepF32Args {
   int nblocks;
   const CavConst *cc;
   CavState *cs;               // dt and c read; flags bit 1 set on a timed-out wait
-  const CUtensorMap *maps;    // [2 * block + parity], in global memory
+  const CUtensorMap *maps;    // [block][parity][pressure box, other box], in global memory
   double *partials;           // [slot][kPartStride]: 5 rate sums, spectral max, 2 Nusselt sums
   int parity;
   int local_dt;               // 1: each node at dt_n = cfl / S_n of its state (pseudo time)
@@ -197,48 +214,123 @@ __device__ __forceinline__ void wall_temperature(float h1, float l1, float h2, f
   pair_add(h1, l1, vmul(d, 1.f / 3.f), hw, lw);
 }
 
+// Tile of FP32 scheduling index c: coarse chunks of every block first, then
+// the fine 8-plane chunks of each block's last planes (they shorten the
+// grid's last wave), x tiles fastest, then y, then z.  The coarse chunk depth
+// is zsplit / tiles_zc (a run-time parameter of the tiling).  The partial slot
+// stays block-major (tile_begin + tx + tiles_x (ty + tiles_y tz)).
+__device__ __forceinline__ TileRef f32_tile_ref(const BlockDev *blocks, int nblocks, int ncoarse, int c) {
+  const bool coarse = c < ncoarse;
+  const int u = coarse ? c : c - ncoarse;
+  // the last block whose first tile of this class is at or before u (blocks
+  // without tiles of the class share their successor's start and are passed)
+  int lo = 0, hi = nblocks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int begin = coarse ? blocks[mid].coarse_begin : blocks[mid].fine_begin;
+    if (begin <= u) lo = mid; else hi = mid - 1;
+  }
+  const BlockDev &B = blocks[lo];
+  const int l = u - (coarse ? B.coarse_begin : B.fine_begin);
+  const int kc = B.zsplit / B.tiles_zc;
+  TileRef T;
+  T.b = lo;
+  T.tx = l % B.tiles_x;
+  T.ty = (l / B.tiles_x) % B.tiles_y;
+  const int zl = l / (B.tiles_x * B.tiles_y);
+  T.k0 = coarse ? zl * kc + 1 : B.zsplit + zl * kFineKC32 + 1;
+  T.k1 = coarse ? min(T.k0 + kc - 1, B.zsplit) : min(T.k0 + kFineKC32 - 1, B.nz);
+  const int tz = coarse ? zl : B.tiles_zc + zl;
+  T.slot = B.tile_begin + T.tx + B.tiles_x * (T.ty + B.tiles_y * tz);
+  return T;
+}
+
+// Tile of one CTA, its partial slot and the walls that fall inside its
+// boxes.  Pressure box: nodes i0-4 .. i0+35, j0-2 .. j0+TY+1; other box:
+// nodes i0-4 .. i0+35, j0-1 .. j0+TY; both over planes k0-2 .. k1+2 (plane
+// 0 = k0-2).
+struct F32Tile {
+  int b, slot, i0, j0, k0, k1, tx, ty, nplanes, x0, y0, zbase, lxh, lyh;
+  bool wxl, wxh, wyl, wyh, wzl, wzh, fix;
+};
+
+template <int TY>
+__device__ __forceinline__ F32Tile f32_tile(const StepF32Args &a, int cta) {
+  F32Tile T;
+  const TileRef R = f32_tile_ref(a.blocks, a.nblocks, a.ncoarse, cta);
+  T.b = R.b;
+  T.slot = R.slot;
+  const BlockDev &B = a.blocks[T.b];
+  T.tx = R.tx;
+  T.ty = R.ty;
+  T.i0 = T.tx * kF32TX + 1;
+  T.j0 = T.ty * TY + 1;
+  T.k0 = R.k0;
+  T.k1 = R.k1;
+  T.nplanes = (T.k1 - T.k0 + 1) + 4;       // z = k0-2 .. k1+2
+  T.x0 = XO<float>::v - 1 + T.i0 - kF32HX;  // array index of node i0 - 4
+  T.y0 = (T.j0 - 2) + 1;                    // array row of node j0 - 2 (the pressure box)
+  T.zbase = (T.k0 - 2) + 1;                 // array plane of the tile's plane 0
+  T.wxl = B.wall[0] && T.tx == 0;
+  T.wxh = B.wall[1] && B.nx + 1 <= T.i0 + kF32TX + 3;  // the wall node nx + 1 inside the boxes
+  T.wyl = B.wall[2] && T.ty == 0;
+  T.wyh = B.wall[3] && B.ny + 1 <= T.j0 + TY + 1;      // the wall node ny + 1 inside the pressure box
+  T.wzl = B.wall[4];
+  T.wzh = B.wall[5];
+  T.fix = T.wxl || T.wxh || T.wyl || T.wyh;
+  T.lxh = B.nx - T.i0 + kF32HX;  // box column of node nx
+  T.lyh = B.ny - T.j0 + 2;       // pressure-box row of node ny (other box: one row less)
+  return T;
+}
+
 // Apply the x and y wall conditions to one freshly loaded plane slot.
-// Slot coordinates: lx = i - i0 + 4, ly = j - j0 + 2.  Threads [0, BX) take
-// the low y wall, [BX, 2BX) the high y wall, the next BY the low x wall and
-// the next BY the high x wall (x walls: pressure only; their temperature is
-// prescribed and stored).
-template <int NT, int BY>
-__device__ __forceinline__ void fix_plane_walls(float *s, int tid, bool wxl, bool wxh, bool wyl, bool wyh,
-                                                int lxh, int lyh) {
-  constexpr int BX = kF32BX, AS = BX * BY;
-  float *H = s, *L = s + AS, *TH = s + 5 * AS, *TL = s + 6 * AS;
-  static_assert(NT >= 2 * (BX + BY), "thread groups");
-  if (wyl && tid < BX) {
+// Pressure-box coordinates: column i - i0 + 4, row j - j0 + 2; other box:
+// the same columns, row j - j0 + 1.  Threads [0, BX) take the low y wall,
+// [BX, 2BX) the high y wall, the next BYP the low x wall and the next BYP the
+// high x wall (x walls: pressure only; their temperature is prescribed and
+// stored).  Groups that read a corner another group writes only produce
+// corner values, which no star stencil reads.
+template <int NT, int TY>
+__device__ __forceinline__ void fix_plane_walls(float *s, int tid, const F32Tile &T) {
+  constexpr int BX = kF32BX, BYP = f32_box_yp(TY), BYO = f32_box_yo(TY);
+  constexpr int APS = BX * BYP, AOS = BX * BYO;
+  float *H = s, *L = s + APS;                    // p pair
+  float *TH = s + 2 * APS + 3 * AOS, *TL = TH + AOS;  // T pair
+  static_assert(NT >= 2 * (BX + BYP), "thread groups");
+  float hw, lw, hg, lg;
+  if (T.wyl && tid < BX) {
     const int x = tid;
-    float hw, lw, hg, lg;
+    // nodes 1, 2 at pressure rows 2, 3: wall (row 1) and ghost (row 0)
     wall_pressure(H[2 * BX + x], L[2 * BX + x], H[3 * BX + x], L[3 * BX + x], hw, lw, hg, lg);
     H[BX + x] = hw; L[BX + x] = lw; H[x] = hg; L[x] = lg;
-    wall_temperature(TH[2 * BX + x], TL[2 * BX + x], TH[3 * BX + x], TL[3 * BX + x], TH[BX + x], TL[BX + x]);
-  } else if (wyh && tid >= BX && tid < 2 * BX) {
+    // nodes 1, 2 at rows 1, 2 of the other box: wall at row 0
+    wall_temperature(TH[BX + x], TL[BX + x], TH[2 * BX + x], TL[2 * BX + x], TH[x], TL[x]);
+  } else if (T.wyh && tid >= BX && tid < 2 * BX) {
     const int x = tid - BX;
-    const int r1 = lyh, r2 = lyh - 1;  // rows of nodes ny and ny - 1
-    float hw, lw, hg, lg;
+    const int r1 = T.lyh, r2 = r1 - 1;  // pressure rows of nodes ny and ny - 1
     wall_pressure(H[r1 * BX + x], L[r1 * BX + x], H[r2 * BX + x], L[r2 * BX + x], hw, lw, hg, lg);
     H[(r1 + 1) * BX + x] = hw; L[(r1 + 1) * BX + x] = lw;
-    if (r1 + 2 < BY) { H[(r1 + 2) * BX + x] = hg; L[(r1 + 2) * BX + x] = lg; }
-    wall_temperature(TH[r1 * BX + x], TL[r1 * BX + x], TH[r2 * BX + x], TL[r2 * BX + x], TH[(r1 + 1) * BX + x],
-                     TL[(r1 + 1) * BX + x]);
-  } else if (wxl && tid >= 2 * BX && tid < 2 * BX + BY) {
+    if (r1 + 2 < BYP) { H[(r1 + 2) * BX + x] = hg; L[(r1 + 2) * BX + x] = lg; }
+    const int o1 = r1 - 1;  // other-box row of node ny
+    if (o1 + 1 < BYO)
+      wall_temperature(TH[o1 * BX + x], TL[o1 * BX + x], TH[(o1 - 1) * BX + x], TL[(o1 - 1) * BX + x],
+                       TH[(o1 + 1) * BX + x], TL[(o1 + 1) * BX + x]);
+  } else if (T.wxl && tid >= 2 * BX && tid < 2 * BX + BYP) {
     const int y = tid - 2 * BX;
-    float hw, lw, hg, lg;
-    wall_pressure(H[y * BX + 4], L[y * BX + 4], H[y * BX + 5], L[y * BX + 5], hw, lw, hg, lg);
-    H[y * BX + 3] = hw; L[y * BX + 3] = lw; H[y * BX + 2] = hg; L[y * BX + 2] = lg;
-  } else if (wxh && tid >= 2 * BX + BY && tid < 2 * (BX + BY)) {
-    const int y = tid - 2 * BX - BY;
-    const int c1 = lxh, c2 = lxh - 1;  // columns of nodes nx and nx - 1
-    float hw, lw, hg, lg;
+    // nodes 1, 2 at columns 4, 5: wall (column 3) and ghost (column 2)
+    constexpr int c1 = kF32HX;
+    wall_pressure(H[y * BX + c1], L[y * BX + c1], H[y * BX + c1 + 1], L[y * BX + c1 + 1], hw, lw, hg, lg);
+    H[y * BX + c1 - 1] = hw; L[y * BX + c1 - 1] = lw; H[y * BX + c1 - 2] = hg; L[y * BX + c1 - 2] = lg;
+  } else if (T.wxh && tid >= 2 * BX + BYP && tid < 2 * (BX + BYP)) {
+    const int y = tid - 2 * BX - BYP;
+    const int c1 = T.lxh, c2 = c1 - 1;  // columns of nodes nx and nx - 1
     wall_pressure(H[y * BX + c1], L[y * BX + c1], H[y * BX + c2], L[y * BX + c2], hw, lw, hg, lg);
     H[y * BX + c1 + 1] = hw; L[y * BX + c1 + 1] = lw;
     if (c1 + 2 < BX) { H[y * BX + c1 + 2] = hg; L[y * BX + c1 + 2] = lg; }
   }
   // the slot is refilled by TMA later: order these generic-proxy writes
   // before the async proxy's
-  if (tid < 2 * (BX + BY)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (tid < 2 * (BX + BYP)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -415,486 +507,9 @@ __device__ __forceinline__ void acc_pair(V &sh, V &sl, V h, V l) {
   sh = s;
 }
 
-// Tile of one CTA (scheduling index = blockIdx.x: coarse chunks of every
-// block, then the fine chunks), its partial slot, and the walls that fall
-// inside its boxes.
-struct F32Tile {
-  int b, slot, i0, j0, k0, k1, tx, ty, nplanes, x0, y0, zbase, lxh, lyh;
-  bool wxl, wxh, wyl, wyh, wzl, wzh, fix;
-};
-
-template <int TY, int KC>
-__device__ __forceinline__ F32Tile f32_tile(const StepF32Args &a, int cta) {
-  F32Tile T;
-  const TileRef R = tile_ref<KC, kFineKC32>(a.blocks, a.nblocks, a.ncoarse, cta);
-  T.b = R.b;
-  T.slot = R.slot;
-  const BlockDev &B = a.blocks[T.b];
-  T.tx = R.tx;
-  T.ty = R.ty;
-  T.i0 = T.tx * kF32TX + 1;
-  T.j0 = T.ty * TY + 1;
-  T.k0 = R.k0;
-  T.k1 = R.k1;
-  T.nplanes = (T.k1 - T.k0 + 1) + 4;  // z = k0-2 .. k1+2
-  T.x0 = XO<float>::v - 1 + T.i0 - 4;
-  T.y0 = (T.j0 - 2) + 1;
-  T.zbase = (T.k0 - 2) + 1;
-  T.wxl = B.wall[0] && T.tx == 0;
-  T.wxh = B.wall[1] && B.nx + 1 <= T.i0 + kF32TX + 3;
-  T.wyl = B.wall[2] && T.ty == 0;
-  T.wyh = B.wall[3] && B.ny + 1 <= T.j0 + TY + 1;
-  T.wzl = B.wall[4];
-  T.wzh = B.wall[5];
-  T.fix = T.wxl || T.wxh || T.wyl || T.wyh;
-  T.lxh = B.nx - T.i0 + 4;
-  T.lyh = B.ny - T.j0 + 2;
-  return T;
-}
-
-// One node per thread: a 32 x TY tile of threads; the z neighbours of the
-// thread's column live in register queues (5 deep for p, 3 for u, v, w, T).
-template <int TY, int KC, int R>
-__global__ void __launch_bounds__(kF32TX *TY, 512 / (kF32TX * TY)) k_step_f32(StepF32Args a) {
-  static_assert(R >= 4 && (R & (R - 1)) == 0, "ring depth: a power of two >= 4");
-  constexpr int TX = kF32TX, NT = TX * TY;
-  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;  // array stride inside a slot
-  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float *ring = reinterpret_cast<float *>(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
-
-  const int cta = blockIdx.x;
-  const F32Tile T = f32_tile<TY, KC>(a, cta);
-  const BlockDev &B = a.blocks[T.b];
-  const CavConst &C = a.cc[B.cav];
-  const int k0 = T.k0, k1 = T.k1;
-  const int li = threadIdx.x, lj = threadIdx.y, tid = lj * TX + li;
-  const int i = T.i0 + li, j = T.j0 + lj;
-  const bool active = (i <= B.nx) && (j <= B.ny);
-  // Nusselt sums of the new state: weights of this column in 3 T_w - 4 T_1 + T_2
-  const bool xw0 = B.wall[0], xw1 = B.wall[1];
-  const double wh = xw0 ? (i == 1 ? -4.0 : (i == 2 ? 1.0 : 0.0)) : 0.0;
-  const double wc = xw1 ? (i == B.nx ? -4.0 : (i == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
-  const bool nus = active && (wh != 0.0 || wc != 0.0);
-  const bool hot_next = xw0 && i == 1, cold_next = xw1 && i == B.nx;  // the column beside the wall
-  const int wofs = hot_next ? -1 : 1;
-  const bool nus_warp = __any_sync(0xffffffffu, nus);
-  float ch = 0.f, cl = 0.f, wsh = 0.f, wsl = 0.f;  // column sums of T and of the wall T beside it
-  const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
-
-  if (tid == 0) {
-    for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
-  }
-  __syncthreads();
-  int issued = 0;
-  auto issue = [&](int pl) {
-    if (pl == a.withhold_plane) return;  // the timeout test: this plane never arrives
-    const int s = pl & (R - 1);
-    mbar_expect_tx(&bars[s], SB);
-    tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
-  };
-  if (tid == 0) {
-    for (; issued < min(R, T.nplanes); ++issued) issue(issued);
-  }
-  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1), a.wait_cycles); };
-  auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
-  const int col = (lj + 2) * BX + (li + 4);  // own column inside a slot
-
-  const long long fs = B.fstride, plane = B.plane;
-  const int nz = B.nz;
-  // output pointer of this thread's node at plane k0 (advanced one plane per k)
-  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
-
-  bool bad = false;
-  // prologue: planes k0-2 .. k0+1 give the initial z queues
-  float ph[5], pq[5], uq[3], vq[3], wq[3], Tq[3], Tl[3];
-  float T2next = 0.f, T2next_lo = 0.f;  // T at plane k0+1 (z-wall temperature of the bottom chunk)
-  for (int pl = 0; pl < 4; ++pl) {
-    if (!bad && !wait_plane(pl)) bad = true;
-    if (!bad) {
-      float *s = slot(pl);
-      ph[pl] = s[col];
-      pq[pl] = s[AS + col];
-      if (pl >= 1 && pl <= 2) {
-        uq[pl - 1] = s[2 * AS + col];
-        vq[pl - 1] = s[3 * AS + col];
-        wq[pl - 1] = s[4 * AS + col];
-        Tq[pl - 1] = s[5 * AS + col];
-        Tl[pl - 1] = s[6 * AS + col];
-      }
-      if (pl == 3) { T2next = s[5 * AS + col]; T2next_lo = s[6 * AS + col]; }
-      if (T.fix && pl >= 2) fix_plane_walls<NT, BY>(s, tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
-    }
-  }
-  // bottom z wall inside the queue (queue slot q holds plane k0 - 2 + q);
-  // constant indices keep the queues in registers
-  if (T.wzl && k0 == 1) {
-    wall_pressure(ph[2], pq[2], ph[3], pq[3], ph[1], pq[1], ph[0], pq[0]);
-    wall_temperature(Tq[1], Tl[1], T2next, T2next_lo, Tq[0], Tl[0]);
-  } else if (T.wzl && k0 == 2) {
-    float hg, lg;
-    wall_pressure(ph[1], pq[1], ph[2], pq[2], ph[0], pq[0], hg, lg);
-  }
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f, smax = 0.f;
-  bad = __syncthreads_or(bad);
-  // a programmatic dependent of the previous step's finalise: only now are its
-  // dt, centre shift and reads of the partials complete (nothing global was
-  // read from the state it writes, nor written, before this point)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const F32K<float> K = f32_consts<float>(C, a.cs[B.cav]);
-  if (!bad && tid == 0) {
-    // slots of planes 0 and 1 are free again
-    for (; issued < min(R + 2, T.nplanes); ++issued) issue(issued);
-  }
-
-#pragma unroll 2
-  for (int k = k0; k <= k1 && !bad; ++k) {
-    const int pk = k - k0 + 2;  // plane index of k
-    if (!wait_plane(pk + 2)) bad = true;
-    if (!bad) {
-      float *sk2 = slot(pk + 2);
-      const float *sk = slot(pk), *sk1 = slot(pk + 1);
-      ph[4] = sk2[col];
-      pq[4] = sk2[AS + col];
-      uq[2] = sk1[2 * AS + col];
-      vq[2] = sk1[3 * AS + col];
-      wq[2] = sk1[4 * AS + col];
-      Tq[2] = sk1[5 * AS + col];
-      Tl[2] = sk1[6 * AS + col];
-      if (T.wzh) {
-        if (k + 2 == nz + 1) {
-          float hg, lg;
-          wall_pressure(ph[3], pq[3], ph[2], pq[2], ph[4], pq[4], hg, lg);
-        } else if (k + 2 == nz + 2) {
-          extrapolate_pair(ph[3], pq[3], ph[2], pq[2], ph[4], pq[4]);  // ghost = 2 p_w - p_nz
-        }
-        if (k + 1 == nz + 1) wall_temperature(Tq[1], Tl[1], Tq[0], Tl[0], Tq[2], Tl[2]);
-      }
-      if (T.fix) fix_plane_walls<NT, BY>(sk2, tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
-      if (active) {
-        F32Nb<float> n;
-        n.ph = ph[2];
-        n.pl = pq[2];
-        const float *H = sk, *L = sk + AS;
-        n.pxp1 = pdiff(H[col + 1], L[col + 1], n.ph, n.pl);
-        n.pxm1 = pdiff(H[col - 1], L[col - 1], n.ph, n.pl);
-        n.pxp2 = pdiff(H[col + 2], L[col + 2], n.ph, n.pl);
-        n.pxm2 = pdiff(H[col - 2], L[col - 2], n.ph, n.pl);
-        n.pyp1 = pdiff(H[col + BX], L[col + BX], n.ph, n.pl);
-        n.pym1 = pdiff(H[col - BX], L[col - BX], n.ph, n.pl);
-        n.pyp2 = pdiff(H[col + 2 * BX], L[col + 2 * BX], n.ph, n.pl);
-        n.pym2 = pdiff(H[col - 2 * BX], L[col - 2 * BX], n.ph, n.pl);
-        n.pzp1 = pdiff(ph[3], pq[3], n.ph, n.pl);
-        n.pzm1 = pdiff(ph[1], pq[1], n.ph, n.pl);
-        n.pzp2 = pdiff(ph[4], pq[4], n.ph, n.pl);
-        n.pzm2 = pdiff(ph[0], pq[0], n.ph, n.pl);
-        n.u = uq[1]; n.v = vq[1]; n.w = wq[1]; n.th = Tq[1]; n.tl = Tl[1];
-        const float *Us = sk + 2 * AS, *Vs = sk + 3 * AS, *Ws = sk + 4 * AS, *Ts = sk + 5 * AS, *Tls = sk + 6 * AS;
-        n.uxp = vsub(Us[col + 1], n.u); n.uxm = vsub(Us[col - 1], n.u);
-        n.uyp = vsub(Us[col + BX], n.u); n.uym = vsub(Us[col - BX], n.u);
-        n.uzp = vsub(uq[2], n.u); n.uzm = vsub(uq[0], n.u);
-        n.vxp = vsub(Vs[col + 1], n.v); n.vxm = vsub(Vs[col - 1], n.v);
-        n.vyp = vsub(Vs[col + BX], n.v); n.vym = vsub(Vs[col - BX], n.v);
-        n.vzp = vsub(vq[2], n.v); n.vzm = vsub(vq[0], n.v);
-        n.wxp = vsub(Ws[col + 1], n.w); n.wxm = vsub(Ws[col - 1], n.w);
-        n.wyp = vsub(Ws[col + BX], n.w); n.wym = vsub(Ws[col - BX], n.w);
-        n.wzp = vsub(wq[2], n.w); n.wzm = vsub(wq[0], n.w);
-        n.txp = pdiff(Ts[col + 1], Tls[col + 1], n.th, n.tl);
-        n.txm = pdiff(Ts[col - 1], Tls[col - 1], n.th, n.tl);
-        n.typ = pdiff(Ts[col + BX], Tls[col + BX], n.th, n.tl);
-        n.tym = pdiff(Ts[col - BX], Tls[col - BX], n.th, n.tl);
-        n.tzp = pdiff(Tq[2], Tl[2], n.th, n.tl);
-        n.tzm = pdiff(Tq[0], Tl[0], n.th, n.tl);
-        F32Out<float> o;
-        float dtn = K.dt, mdtn = K.mdt;
-        if (a.local_dt) {  // this node's own stable step
-          dtn = __fdiv_rn(K.cfl, f32_spectral_exact(K, n.u, n.v, n.w));
-          mdtn = -dtn;
-        }
-        f32_update(K, n, dtn, mdtn, o);
-        out[0] = o.ph;
-        out[fs] = o.pl;
-        out[2 * fs] = o.u;
-        out[3 * fs] = o.v;
-        out[4 * fs] = o.w;
-        out[5 * fs] = o.th;
-        out[6 * fs] = o.tl;
-        s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
-        s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
-        f32_spectral_max(K, f32_spectral_bound(K, o.u, o.v, o.w), o.u, o.v, o.w, smax);
-        if (nus_warp) {
-          acc_pair(ch, cl, o.th, o.tl);
-          acc_pair(wsh, wsl, Ts[col + wofs], Tls[col + wofs]);
-        }
-      }
-      out += plane;
-      ph[0] = ph[1]; ph[1] = ph[2]; ph[2] = ph[3]; ph[3] = ph[4];
-      pq[0] = pq[1]; pq[1] = pq[2]; pq[2] = pq[3]; pq[3] = pq[4];
-      uq[0] = uq[1]; uq[1] = uq[2]; vq[0] = vq[1]; vq[1] = vq[2];
-      wq[0] = wq[1]; wq[1] = wq[2]; Tq[0] = Tq[1]; Tq[1] = Tq[2]; Tl[0] = Tl[1]; Tl[1] = Tl[2];
-    }
-    bad = __syncthreads_or(bad);
-    if (!bad && tid == 0 && issued < T.nplanes) {
-      // the slot of plane pk is free: refill it with the next plane
-      issue(issued);
-      ++issued;
-    }
-  }
-  if (bad) {
-    // a wait gave up: record it, let this CTA's copies in flight land
-    // (again bounded) before the shared memory is released
-    if (tid == 0) {
-      atomicOr(&a.cs[B.cav].flags, 2);
-      for (int pl = max(0, issued - R); pl < issued; ++pl) (void)wait_plane(pl);
-    }
-    __syncthreads();
-  }
-  double nuh = 0.0, nuc = 0.0;
-  if (nus) {
-    const double col_t = pair_value(ch, cl), wall_t = 3.0 * pair_value(wsh, wsl);
-    nuh = wh * col_t + (hot_next ? wall_t : 0.0);
-    nuc = wc * col_t + (cold_next ? wall_t : 0.0);
-  }
-  f32_partials<NT>(a.partials, T.slot, tid, s0, s1, s2, s3, s4, smax, nuh, nuc, T.wxl || T.wxh);
-}
-
 __device__ __forceinline__ float2 ld2(const float *s, int idx) { return *reinterpret_cast<const float2 *>(s + idx); }
 __device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
-
-// Two nodes per thread: a 16 x TY tile of threads covers the same 32 x TY
-// nodes, thread (li, lj) the nodes i = i0 + 2 li and i + 1 of row j, packed
-// in register pairs (f32x2 arithmetic, 64-bit shared loads and global
-// stores).  The z neighbours are read from the ring (planes k-2 .. k+2 stay
-// resident while plane k is computed), so no register queues rotate; walls
-// in z are formed from the loaded interior layers where they are read.
-template <int TY, int KC, int R>
-__global__ void __launch_bounds__(kF32TX / 2 * TY, 256 / (kF32TX / 2 * TY)) k_step_f32p(StepF32Args a) {
-  static_assert(R >= 8 && (R & (R - 1)) == 0, "ring depth: a power of two >= 8 (five planes resident)");
-  constexpr int NTX = kF32TX / 2, NT = NTX * TY;
-  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;
-  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float *ring = reinterpret_cast<float *>(smem_raw);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
-
-  const int cta = blockIdx.x;
-  const F32Tile T = f32_tile<TY, KC>(a, cta);
-  const BlockDev &B = a.blocks[T.b];
-  const CavConst &C = a.cc[B.cav];
-  const int k0 = T.k0, k1 = T.k1;
-  const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
-  const int i = T.i0 + 2 * li, j = T.j0 + lj;
-  const bool act0 = (i <= B.nx) && (j <= B.ny), act1 = (i + 1 <= B.nx) && (j <= B.ny);
-  // Nusselt sums of the new state: weights of the two columns in 3 T_w - 4 T_1 + T_2
-  const bool xw0 = B.wall[0], xw1 = B.wall[1];
-  const double wh0 = (xw0 && act0) ? (i == 1 ? -4.0 : (i == 2 ? 1.0 : 0.0)) : 0.0;
-  const double wh1 = (xw0 && act1) ? (i + 1 == 2 ? 1.0 : 0.0) : 0.0;
-  const double wc0 = (xw1 && act0) ? (i == B.nx ? -4.0 : (i == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
-  const double wc1 = (xw1 && act1) ? (i + 1 == B.nx ? -4.0 : (i + 1 == B.nx - 1 ? 1.0 : 0.0)) : 0.0;
-  const bool nus = wh0 != 0.0 || wh1 != 0.0 || wc0 != 0.0 || wc1 != 0.0;
-  // the column beside a wall: node i next to x = 0 or x = nx + 1, or node i + 1 next to x = nx + 1
-  const bool hot_next = xw0 && act0 && i == 1, cold_next0 = xw1 && act0 && i == B.nx;
-  const bool cold_next1 = xw1 && act1 && i + 1 == B.nx;
-  const int wofs = hot_next ? -1 : (cold_next0 ? 1 : 2);
-  const bool nus_warp = __any_sync(0xffffffffu, nus);
-  float2 ch = make_float2(0.f, 0.f), cl = ch;
-  float wsh = 0.f, wsl = 0.f;
-  const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
-
-  if (tid == 0) {
-    for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
-  }
-  __syncthreads();
-  int issued = 0;
-  auto issue = [&](int pl) {
-    if (pl == a.withhold_plane) return;  // the timeout test: this plane never arrives
-    const int s = pl & (R - 1);
-    mbar_expect_tx(&bars[s], SB);
-    tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
-  };
-  if (tid == 0) {
-    for (; issued < min(R, T.nplanes); ++issued) issue(issued);
-  }
-  auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl & (R - 1)], (uint32_t)((pl / R) & 1), a.wait_cycles); };
-  auto slot = [&](int pl) { return ring + (pl & (R - 1)) * SF; };
-  const int col = (lj + 2) * BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
-
-  const long long fs = B.fstride, plane = B.plane;
-  const int nz = B.nz;
-  // i is odd, so the pair starts on an 8-byte boundary of the row
-  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(i, B.nx), min(j, B.ny), k0);
-
-  bool bad = false;
-  // prologue: planes k0-2 .. k0+1; the x and y walls of the interior planes
-  for (int pl = 0; pl < 4; ++pl) {
-    if (!bad && !wait_plane(pl)) bad = true;
-    if (!bad && T.fix && pl >= 2) fix_plane_walls<NT, BY>(slot(pl), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
-  }
-  float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
-  float smax = 0.f;
-  bad = __syncthreads_or(bad);
-  // a programmatic dependent of the previous step's finalise: only now are its
-  // dt, centre shift and reads of the partials complete (nothing global was
-  // read from the state it writes, nor written, before this point)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const F32K<float2> K = f32_consts<float2>(C, a.cs[B.cav]);
-  const F32K<float> K1 = f32_consts<float>(C, a.cs[B.cav]);
-
-  for (int k = k0; k <= k1 && !bad; ++k) {
-    const int pk = k - k0 + 2;  // plane index of k
-    if (!wait_plane(pk + 2)) bad = true;
-    if (!bad) {
-      if (T.fix) fix_plane_walls<NT, BY>(slot(pk + 2), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
-      if (act0) {
-        const float *S0 = slot(pk), *Sm1 = slot(pk - 1), *Sm2 = slot(pk - 2), *Sp1 = slot(pk + 1),
-                    *Sp2 = slot(pk + 2);
-        F32Nb<float2> n;
-        // pressure: centre pair and its z neighbours (walls formed in place)
-        n.ph = ld2(S0, col);
-        n.pl = ld2(S0 + AS, col);
-        float2 zm2h = ld2(Sm2, col), zm2l = ld2(Sm2 + AS, col), zm1h = ld2(Sm1, col), zm1l = ld2(Sm1 + AS, col);
-        float2 zp1h = ld2(Sp1, col), zp1l = ld2(Sp1 + AS, col), zp2h = ld2(Sp2, col), zp2l = ld2(Sp2 + AS, col);
-        float2 th = ld2(S0 + 5 * AS, col), tl = ld2(S0 + 6 * AS, col);
-        float2 tzmh = ld2(Sm1 + 5 * AS, col), tzml = ld2(Sm1 + 6 * AS, col);
-        float2 tzph = ld2(Sp1 + 5 * AS, col), tzpl = ld2(Sp1 + 6 * AS, col);
-        if (T.wzl && k <= 2) {
-          float hg, lg;
-          if (k == 1) {  // z = 0 wall and z = -1 ghost from the layers z = 1, 2
-            wall_pressure(n.ph.x, n.pl.x, zp1h.x, zp1l.x, zm1h.x, zm1l.x, zm2h.x, zm2l.x);
-            wall_pressure(n.ph.y, n.pl.y, zp1h.y, zp1l.y, zm1h.y, zm1l.y, zm2h.y, zm2l.y);
-            wall_temperature(th.x, tl.x, tzph.x, tzpl.x, tzmh.x, tzml.x);
-            wall_temperature(th.y, tl.y, tzph.y, tzpl.y, tzmh.y, tzml.y);
-          } else {  // k == 2: z = 0 wall from z = 1, 2
-            wall_pressure(zm1h.x, zm1l.x, n.ph.x, n.pl.x, zm2h.x, zm2l.x, hg, lg);
-            wall_pressure(zm1h.y, zm1l.y, n.ph.y, n.pl.y, zm2h.y, zm2l.y, hg, lg);
-          }
-        }
-        if (T.wzh && k >= nz - 1) {
-          float hg, lg;
-          if (k == nz) {  // z = nz+1 wall and nz+2 ghost from the layers nz, nz-1
-            wall_pressure(n.ph.x, n.pl.x, zm1h.x, zm1l.x, zp1h.x, zp1l.x, zp2h.x, zp2l.x);
-            wall_pressure(n.ph.y, n.pl.y, zm1h.y, zm1l.y, zp1h.y, zp1l.y, zp2h.y, zp2l.y);
-            wall_temperature(th.x, tl.x, tzmh.x, tzml.x, tzph.x, tzpl.x);
-            wall_temperature(th.y, tl.y, tzmh.y, tzml.y, tzph.y, tzpl.y);
-          } else {  // k == nz-1: z = nz+1 wall from nz, nz-1
-            wall_pressure(zp1h.x, zp1l.x, n.ph.x, n.pl.x, zp2h.x, zp2l.x, hg, lg);
-            wall_pressure(zp1h.y, zp1l.y, n.ph.y, n.pl.y, zp2h.y, zp2l.y, hg, lg);
-          }
-        }
-        n.pzp1 = pdiff(zp1h, zp1l, n.ph, n.pl);
-        n.pzm1 = pdiff(zm1h, zm1l, n.ph, n.pl);
-        n.pzp2 = pdiff(zp2h, zp2l, n.ph, n.pl);
-        n.pzm2 = pdiff(zm2h, zm2l, n.ph, n.pl);
-        {
-          const float *H = S0, *L = S0 + AS;
-          const float2 ah = ld2(H, col - 2), al = ld2(L, col - 2), dh = ld2(H, col + 2), dl = ld2(L, col + 2);
-          n.pxp1 = make_float2(pdiff(n.ph.y, n.pl.y, n.ph.x, n.pl.x), pdiff(dh.x, dl.x, n.ph.y, n.pl.y));
-          n.pxm1 = make_float2(pdiff(ah.y, al.y, n.ph.x, n.pl.x), pdiff(n.ph.x, n.pl.x, n.ph.y, n.pl.y));
-          n.pxp2 = pdiff(dh, dl, n.ph, n.pl);
-          n.pxm2 = pdiff(ah, al, n.ph, n.pl);
-          n.pyp1 = pdiff(ld2(H, col + BX), ld2(L, col + BX), n.ph, n.pl);
-          n.pym1 = pdiff(ld2(H, col - BX), ld2(L, col - BX), n.ph, n.pl);
-          n.pyp2 = pdiff(ld2(H, col + 2 * BX), ld2(L, col + 2 * BX), n.ph, n.pl);
-          n.pym2 = pdiff(ld2(H, col - 2 * BX), ld2(L, col - 2 * BX), n.ph, n.pl);
-        }
-        // velocity: x differences per node, y and z packed
-#define BDC_F32P_VEL(F, c0, xp, xm, yp, ym, zp, zm)                                                  \
-  {                                                                                                \
-    const float *Q = S0 + F * AS;                                                                  \
-    c0 = ld2(Q, col);                                                                              \
-    const float qm = Q[col - 1], qp = Q[col + 2];                                                  \
-    xp = make_float2(vsub(c0.y, c0.x), vsub(qp, c0.y));                                            \
-    xm = make_float2(vsub(qm, c0.x), vsub(c0.x, c0.y));                                            \
-    yp = vsub(ld2(Q, col + BX), c0);                                                               \
-    ym = vsub(ld2(Q, col - BX), c0);                                                               \
-    zp = vsub(ld2(Sp1 + F * AS, col), c0);                                                         \
-    zm = vsub(ld2(Sm1 + F * AS, col), c0);                                                         \
-  }
-        BDC_F32P_VEL(2, n.u, n.uxp, n.uxm, n.uyp, n.uym, n.uzp, n.uzm)
-        BDC_F32P_VEL(3, n.v, n.vxp, n.vxm, n.vyp, n.vym, n.vzp, n.vzm)
-        BDC_F32P_VEL(4, n.w, n.wxp, n.wxm, n.wyp, n.wym, n.wzp, n.wzm)
-#undef BDC_F32P_VEL
-        // temperature pair
-        n.th = th;
-        n.tl = tl;
-        {
-          const float *TH = S0 + 5 * AS, *TL = S0 + 6 * AS;
-          n.txp = make_float2(pdiff(th.y, tl.y, th.x, tl.x), pdiff(TH[col + 2], TL[col + 2], th.y, tl.y));
-          n.txm = make_float2(pdiff(TH[col - 1], TL[col - 1], th.x, tl.x), pdiff(th.x, tl.x, th.y, tl.y));
-          n.typ = pdiff(ld2(TH, col + BX), ld2(TL, col + BX), th, tl);
-          n.tym = pdiff(ld2(TH, col - BX), ld2(TL, col - BX), th, tl);
-          n.tzp = pdiff(tzph, tzpl, th, tl);
-          n.tzm = pdiff(tzmh, tzml, th, tl);
-        }
-        F32Out<float2> o;
-        float2 dtn = K.dt, mdtn = K.mdt;
-        if (a.local_dt) {  // each node's own stable step
-          dtn = make_float2(__fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.x, n.v.x, n.w.x)),
-                            __fdiv_rn(K1.cfl, f32_spectral_exact(K1, n.u.y, n.v.y, n.w.y)));
-          mdtn = make_float2(-dtn.x, -dtn.y);
-        }
-        f32_update(K, n, dtn, mdtn, o);
-        const float2 bound = f32_spectral_bound(K, o.u, o.v, o.w);
-        f32_spectral_max(K1, bound.x, o.u.x, o.v.x, o.w.x, smax);
-        if (act1) {
-          st2(out, o.ph);
-          st2(out + fs, o.pl);
-          st2(out + 2 * fs, o.u);
-          st2(out + 3 * fs, o.v);
-          st2(out + 4 * fs, o.w);
-          st2(out + 5 * fs, o.th);
-          st2(out + 6 * fs, o.tl);
-          f32_spectral_max(K1, bound.y, o.u.y, o.v.y, o.w.y, smax);
-        } else {  // the x extent is odd: the pair's second node is a wall or beyond
-          out[0] = o.ph.x;
-          out[fs] = o.pl.x;
-          out[2 * fs] = o.u.x;
-          out[3 * fs] = o.v.x;
-          out[4 * fs] = o.w.x;
-          out[5 * fs] = o.th.x;
-          out[6 * fs] = o.tl.x;
-          o.rp.y = o.ru.y = o.rv.y = o.rw.y = o.rt.y = 0.f;
-        }
-        s0 = vfma(o.rp, o.rp, s0); s1 = vfma(o.ru, o.ru, s1); s2 = vfma(o.rv, o.rv, s2);
-        s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
-        if (nus_warp) {
-          acc_pair(ch, cl, o.th, o.tl);
-          acc_pair(wsh, wsl, S0[5 * AS + col + wofs], S0[6 * AS + col + wofs]);
-        }
-      }
-      out += plane;
-    }
-    bad = __syncthreads_or(bad);
-    if (!bad && tid == 0 && issued < T.nplanes) {
-      // the slot of plane pk - 2 is free: refill it with the next plane
-      issue(issued);
-      ++issued;
-    }
-  }
-  if (bad) {
-    if (tid == 0) {
-      atomicOr(&a.cs[B.cav].flags, 2);
-      for (int pl = max(0, issued - R); pl < issued; ++pl) (void)wait_plane(pl);
-    }
-    __syncthreads();
-  }
-  double nuh = 0.0, nuc = 0.0;
-  if (nus) {
-    const double t0 = pair_value(ch.x, cl.x), t1 = act1 ? pair_value(ch.y, cl.y) : 0.0;
-    const double wall_t = 3.0 * pair_value(wsh, wsl);
-    nuh = wh0 * t0 + wh1 * t1 + (hot_next ? wall_t : 0.0);
-    nuc = wc0 * t0 + wc1 * t1 + (cold_next0 || cold_next1 ? wall_t : 0.0);
-  }
-  f32_partials<NT>(a.partials, T.slot, tid, vadd(s0.x, s0.y), vadd(s1.x, s1.y), vadd(s2.x, s2.y), vadd(s3.x, s3.y),
-                   vadd(s4.x, s4.y), smax, nuh, nuc, T.wxl || T.wxh);
-}
-
-// Per-thread state of the register-queue FP32 kernels (two nodes per thread):
+// Per-thread state of the FP32 step kernel (two nodes per thread):
 // the pair's z - 1 values of all seven arrays and p's z - 2 values, the
 // running residual sums and spectral maximum, and the Nusselt column sums.
 struct F32QAcc {
@@ -907,15 +522,18 @@ struct F32QAcc {
 
 // One plane of one thread's node pair: rates and update of the pair at plane
 // k from the resident slots of planes k, k+1, k+2 (S0, Sp1, Sp2) and the
-// register queues; writes the new state at `out`, accumulates the sums and
-// moves the queues one plane up.  `col`: the pair's first node inside a slot;
+// register queues (planes k-1, k-2); writes the new state at `out`,
+// accumulates the sums and moves the queues one plane up.  `colp` / `col`:
+// the pair's first node in the pressure box / the other box of a slot;
 // `wofs`: offset of the wall value read for the Nusselt sum.
 template <int TY>
 __device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, const float *Sp2, const F32K<float2> &K,
                                           const F32K<float> &K1, int k, int nz, bool wzl, bool wzh, int local_dt,
-                                          float *out, long long fs, int col, int wofs, bool act1, bool nus_warp,
-                                          F32QAcc &acc) {
-  constexpr int BX = kF32BX, BY = f32_box_y(TY), AS = BX * BY;
+                                          float *out, long long fs, int colp, int col, int wofs, bool act1,
+                                          bool nus_warp, F32QAcc &acc) {
+  constexpr int BX = kF32BX, APS = BX * f32_box_yp(TY), AOS = BX * f32_box_yo(TY);
+  constexpr int OO = 2 * APS;            // the other box inside a slot: u, v, w, T_hi, T_lo
+  constexpr int TO = OO + 3 * AOS;       // T_hi inside a slot
   float2(&qm1)[7] = acc.qm1;
   float2 &qm2h = acc.qm2h, &qm2l = acc.qm2l;
   float2 &s0 = acc.s0, &s1 = acc.s1, &s2 = acc.s2, &s3 = acc.s3, &s4 = acc.s4;
@@ -924,13 +542,13 @@ __device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, con
   float &wsh = acc.wsh, &wsl = acc.wsl;
   F32Nb<float2> n;
   // pressure: centre pair and its z neighbours (walls formed in place)
-  n.ph = ld2(S0, col);
-  n.pl = ld2(S0 + AS, col);
+  n.ph = ld2(S0, colp);
+  n.pl = ld2(S0 + APS, colp);
   float2 zm2h = qm2h, zm2l = qm2l, zm1h = qm1[0], zm1l = qm1[1];
-  float2 zp1h = ld2(Sp1, col), zp1l = ld2(Sp1 + AS, col), zp2h = ld2(Sp2, col), zp2l = ld2(Sp2 + AS, col);
-  float2 th = ld2(S0 + 5 * AS, col), tl = ld2(S0 + 6 * AS, col);
+  float2 zp1h = ld2(Sp1, colp), zp1l = ld2(Sp1 + APS, colp), zp2h = ld2(Sp2, colp), zp2l = ld2(Sp2 + APS, colp);
+  float2 th = ld2(S0 + TO, col), tl = ld2(S0 + TO + AOS, col);
   float2 tzmh = qm1[5], tzml = qm1[6];
-  float2 tzph = ld2(Sp1 + 5 * AS, col), tzpl = ld2(Sp1 + 6 * AS, col);
+  float2 tzph = ld2(Sp1 + TO, col), tzpl = ld2(Sp1 + TO + AOS, col);
   if (wzl && k <= 2) {
     float hg, lg;
     if (k == 1) {  // z = 0 wall and z = -1 ghost from the layers z = 1, 2
@@ -960,29 +578,29 @@ __device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, con
   n.pzp2 = pdiff(zp2h, zp2l, n.ph, n.pl);
   n.pzm2 = pdiff(zm2h, zm2l, n.ph, n.pl);
   {
-    const float *H = S0, *L = S0 + AS;
-    const float2 ah = ld2(H, col - 2), al = ld2(L, col - 2), dh = ld2(H, col + 2), dl = ld2(L, col + 2);
+    const float *H = S0, *L = S0 + APS;
+    const float2 ah = ld2(H, colp - 2), al = ld2(L, colp - 2), dh = ld2(H, colp + 2), dl = ld2(L, colp + 2);
     n.pxp1 = make_float2(pdiff(n.ph.y, n.pl.y, n.ph.x, n.pl.x), pdiff(dh.x, dl.x, n.ph.y, n.pl.y));
     n.pxm1 = make_float2(pdiff(ah.y, al.y, n.ph.x, n.pl.x), pdiff(n.ph.x, n.pl.x, n.ph.y, n.pl.y));
     n.pxp2 = pdiff(dh, dl, n.ph, n.pl);
     n.pxm2 = pdiff(ah, al, n.ph, n.pl);
-    n.pyp1 = pdiff(ld2(H, col + BX), ld2(L, col + BX), n.ph, n.pl);
-    n.pym1 = pdiff(ld2(H, col - BX), ld2(L, col - BX), n.ph, n.pl);
-    n.pyp2 = pdiff(ld2(H, col + 2 * BX), ld2(L, col + 2 * BX), n.ph, n.pl);
-    n.pym2 = pdiff(ld2(H, col - 2 * BX), ld2(L, col - 2 * BX), n.ph, n.pl);
+    n.pyp1 = pdiff(ld2(H, colp + BX), ld2(L, colp + BX), n.ph, n.pl);
+    n.pym1 = pdiff(ld2(H, colp - BX), ld2(L, colp - BX), n.ph, n.pl);
+    n.pyp2 = pdiff(ld2(H, colp + 2 * BX), ld2(L, colp + 2 * BX), n.ph, n.pl);
+    n.pym2 = pdiff(ld2(H, colp - 2 * BX), ld2(L, colp - 2 * BX), n.ph, n.pl);
   }
   // velocity: x differences per node, y and z packed
 #define BDC_F32Q_VEL(F, c0, xp, xm, yp, ym, zp, zm)                                                  \
   {                                                                                                \
-    const float *Q = S0 + F * AS;                                                                  \
+    const float *Q = S0 + OO + (F - 2) * AOS;                                                      \
     c0 = ld2(Q, col);                                                                              \
     const float qm = Q[col - 1], qp = Q[col + 2];                                                  \
     xp = make_float2(vsub(c0.y, c0.x), vsub(qp, c0.y));                                            \
     xm = make_float2(vsub(qm, c0.x), vsub(c0.x, c0.y));                                            \
     yp = vsub(ld2(Q, col + BX), c0);                                                               \
     ym = vsub(ld2(Q, col - BX), c0);                                                               \
-    zp = vsub(ld2(Sp1 + F * AS, col), c0);                                                         \
-    zm = vsub(qm1[F], c0);                                                         \
+    zp = vsub(ld2(Sp1 + OO + (F - 2) * AOS, col), c0);                                             \
+    zm = vsub(qm1[F], c0);                                                                         \
   }
   BDC_F32Q_VEL(2, n.u, n.uxp, n.uxm, n.uyp, n.uym, n.uzp, n.uzm)
   BDC_F32Q_VEL(3, n.v, n.vxp, n.vxm, n.vyp, n.vym, n.vzp, n.vzm)
@@ -992,7 +610,7 @@ __device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, con
   n.th = th;
   n.tl = tl;
   {
-    const float *TH = S0 + 5 * AS, *TL = S0 + 6 * AS;
+    const float *TH = S0 + TO, *TL = S0 + TO + AOS;
     n.txp = make_float2(pdiff(th.y, tl.y, th.x, tl.x), pdiff(TH[col + 2], TL[col + 2], th.y, tl.y));
     n.txm = make_float2(pdiff(TH[col - 1], TL[col - 1], th.x, tl.x), pdiff(th.x, tl.x, th.y, tl.y));
     n.typ = pdiff(ld2(TH, col + BX), ld2(TL, col + BX), th, tl);
@@ -1033,7 +651,7 @@ __device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, con
   s3 = vfma(o.rw, o.rw, s3); s4 = vfma(o.rt, o.rt, s4);
   if (nus_warp) {
     acc_pair(ch, cl, o.th, o.tl);
-    acc_pair(wsh, wsl, S0[5 * AS + col + wofs], S0[6 * AS + col + wofs]);
+    acc_pair(wsh, wsl, S0[TO + col + wofs], S0[TO + AOS + col + wofs]);
   }
   // the register queues move one plane: z - 2 <- z - 1 (p), z - 1 <- this plane
   qm2h = qm1[0];
@@ -1041,10 +659,10 @@ __device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, con
   qm1[0] = n.ph; qm1[1] = n.pl; qm1[2] = n.u; qm1[3] = n.v; qm1[4] = n.w; qm1[5] = th; qm1[6] = tl;
 }
 
-// The node pair of one thread in a tile of the register-queue kernels and
-// its Nusselt weights (the two columns' weights in 3 T_w - 4 T_1 + T_2).
+// The node pair of one thread in a tile and its Nusselt weights (the two
+// columns' weights in 3 T_w - 4 T_1 + T_2).
 struct F32QCol {
-  int i, j, col, wofs;
+  int i, j, colp, col, wofs;
   bool act0, act1, nus, nus_warp, hot_next, cold_next;
   double wh0, wh1, wc0, wc1;
 };
@@ -1070,7 +688,9 @@ __device__ __forceinline__ F32QCol f32q_column(const BlockDev &B, const F32Tile 
   c.cold_next = cold_next0 || cold_next1;
   c.wofs = c.hot_next ? -1 : (cold_next0 ? 1 : 2);
   c.nus_warp = __any_sync(0xffffffffu, c.nus);
-  c.col = (lj + 2) * kF32BX + (2 * li + 4);  // the pair's first node inside a slot (even: 8-byte aligned)
+  // the pair's first node in the pressure box and in the other box (even: 8-byte aligned)
+  c.colp = (lj + 2) * kF32BX + (2 * li + kF32HX);
+  c.col = (lj + 1) * kF32BX + (2 * li + kF32HX);
   return c;
 }
 
@@ -1100,61 +720,67 @@ __device__ __forceinline__ void f32q_finish(double *partials, int tile, int tid,
 }
 
 // The tile's prologue reads once planes 0 .. 3 (z = k0-2 .. k0+1) are resident
-// in their slots (S0 .. S3): the x and y walls of the interior planes 2 and 3
-// are formed in place, and the register queues take plane 1 (z - 1, seven
-// arrays) and plane 0 (z - 2, p).
-template <int NT, int BY>
+// in their slots: the x and y walls of the interior planes 2 and 3 are formed
+// in place, and the register queues take plane 1 (z - 1, seven arrays) and
+// plane 0 (z - 2, p).
+template <int NT, int TY>
 __device__ __forceinline__ void f32q_prologue_plane(int pl, float *S, const F32Tile &T, const F32QCol &c, int tid,
                                                     F32QAcc &acc) {
-  constexpr int AS = kF32BX * BY;
-  if (T.fix && pl >= 2) fix_plane_walls<NT, BY>(S, tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+  constexpr int APS = kF32BX * f32_box_yp(TY), AOS = kF32BX * f32_box_yo(TY);
+  if (T.fix && pl >= 2) fix_plane_walls<NT, TY>(S, tid, T);
   if (c.act0 && pl == 0) {
-    acc.qm2h = ld2(S, c.col);
-    acc.qm2l = ld2(S + AS, c.col);
+    acc.qm2h = ld2(S, c.colp);
+    acc.qm2l = ld2(S + APS, c.colp);
   }
-  if (c.act0 && pl == 1)
-    for (int q = 0; q < 7; ++q) acc.qm1[q] = ld2(S + q * AS, c.col);
+  if (c.act0 && pl == 1) {
+    acc.qm1[0] = ld2(S, c.colp);
+    acc.qm1[1] = ld2(S + APS, c.colp);
+    for (int q = 2; q < 7; ++q) acc.qm1[q] = ld2(S + 2 * APS + (q - 2) * AOS, c.col);
+  }
 }
 
-// Two nodes per thread as k_step_f32p, with the pair's z - 1 values (all
-// seven arrays) and p's z - 2 values carried in registers from the previous
-// planes: only planes k .. k+2 stay resident.  A ring of R = 5 slots keeps
-// two planes in flight in 67 KB and three CTAs share an SM (12 warps instead
-// of 8); with R = 4 (one plane in flight, 54 KB) the launch bounds ask for
-// four CTAs per SM, which the compiler meets in 123 registers without spills
-// (16 warps per SM: the other CTAs hide a plane's wait).  Slots are indexed
-// modulo R.  One CTA per tile.
-template <int TY, int KC, int R>
-__global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32TX / 2 * TY)) k_step_f32q(StepF32Args a) {
+// The fused FP32-mixed step: one CTA per tile (a 32 x TY tile of nodes, one
+// z chunk of its column), 16 x TY threads with two nodes each.  Planes arrive
+// in a ring of R slots: the slot of plane p is refilled with
+// plane p + R once plane p is done, so with three planes resident R - 3
+// planes are in flight.  R = 4 at 47 KB per CTA keeps one plane in flight
+// with four CTAs (16 warps) per SM, R = 5 at 59 KB two planes with three; the
+// launch bounds ask for 512 threads per SM, which the compiler meets in at
+// most 128 registers.
+template <int TY, int R>
+__global__ void __launch_bounds__(kF32TX / 2 * TY, 512 / (kF32TX / 2 * TY)) k_step_f32q(StepF32Args a) {
   static_assert(R >= 4, "ring depth: three planes resident and at least one in flight");
   constexpr int NTX = kF32TX / 2, NT = NTX * TY;
-  constexpr int BY = f32_box_y(TY);
-  constexpr int SF = f32_slot_floats(TY), SB = SF * 4;
+  constexpr int SB = f32_slot_bytes(TY), SF = SB / 4, PF = f32_p_bytes(TY) / 4;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float *ring = reinterpret_cast<float *>(smem_raw);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + R * SB);
 
   const int cta = blockIdx.x;
-  const F32Tile T = f32_tile<TY, KC>(a, cta);
+  const F32Tile T = f32_tile<TY>(a, cta);
   const BlockDev &B = a.blocks[T.b];
   const CavConst &C = a.cc[B.cav];
-  const int k0 = T.k0, k1 = T.k1;
   const int li = threadIdx.x, lj = threadIdx.y, tid = lj * NTX + li;
   const F32QCol c = f32q_column(B, T, li, lj);
-  const CUtensorMap *map = a.maps + 2 * T.b + a.parity;
+  const CUtensorMap *mapp = a.maps + 2 * (2 * T.b + a.parity), *mapo = mapp + 1;
 
   if (tid == 0) {
     for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapp) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mapo) : "memory");
   }
   __syncthreads();
   int issued = 0;
+  // plane pl of the tile: the pressure box (arrays 0, 1; rows from node
+  // j0-2) and the other box (arrays 2 .. 6; rows from node j0-1), one barrier
   auto issue = [&](int pl) {
     if (pl == a.withhold_plane) return;  // the timeout test: this plane never arrives
     const int s = pl % R;
-    mbar_expect_tx(&bars[s], SB);
-    tma_load_4d(ring + s * SF, map, &bars[s], T.x0, T.y0, T.zbase + pl, 0);
+    const int z = T.zbase + pl;
+    mbar_expect_tx(&bars[s], f32_tx_bytes(TY));
+    tma_load_4d(ring + s * SF, mapp, &bars[s], T.x0, T.y0, z, 0);
+    tma_load_4d(ring + s * SF + PF, mapo, &bars[s], T.x0, T.y0 + 1, z, kF32NP);
   };
   if (tid == 0) {
     for (; issued < min(R, T.nplanes); ++issued) issue(issued);
@@ -1165,14 +791,14 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32T
   const long long fs = B.fstride, plane = B.plane;
   const int nz = B.nz;
   // i is odd, so the pair starts on an 8-byte boundary of the row
-  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(c.i, B.nx), min(c.j, B.ny), k0);
+  float *__restrict__ out = (float *)B.base[a.parity ^ 1] + node_index<float>(B, min(c.i, B.nx), min(c.j, B.ny), T.k0);
 
   bool bad = false;
   F32QAcc acc;
   f32q_clear(acc);
   for (int pl = 0; pl < 4; ++pl) {
     if (!bad && !wait_plane(pl)) bad = true;
-    if (!bad) f32q_prologue_plane<NT, BY>(pl, slot(pl), T, c, tid, acc);
+    if (!bad) f32q_prologue_plane<NT, TY>(pl, slot(pl), T, c, tid, acc);
   }
   bad = __syncthreads_or(bad);
   // a programmatic dependent of the previous step's finalise: only now are its
@@ -1186,14 +812,14 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32T
     for (; issued < min(R + 2, T.nplanes); ++issued) issue(issued);
   }
 
-  for (int k = k0; k <= k1 && !bad; ++k) {
-    const int pk = k - k0 + 2;  // plane index of k
+  for (int k = T.k0; k <= T.k1 && !bad; ++k) {
+    const int pk = k - T.k0 + 2;  // plane index of k
     if (!wait_plane(pk + 2)) bad = true;
     if (!bad) {
-      if (T.fix) fix_plane_walls<NT, BY>(slot(pk + 2), tid, T.wxl, T.wxh, T.wyl, T.wyh, T.lxh, T.lyh);
+      if (T.fix) fix_plane_walls<NT, TY>(slot(pk + 2), tid, T);
       if (c.act0)
-        f32q_pair<TY>(slot(pk), slot(pk + 1), slot(pk + 2), K, K1, k, nz, T.wzl, T.wzh, a.local_dt, out, fs, c.col,
-                      c.wofs, c.act1, c.nus_warp, acc);
+        f32q_pair<TY>(slot(pk), slot(pk + 1), slot(pk + 2), K, K1, k, nz, T.wzl, T.wzh, a.local_dt, out, fs, c.colp,
+                      c.col, c.wofs, c.act1, c.nus_warp, acc);
       out += plane;
     }
     bad = __syncthreads_or(bad);
@@ -1204,6 +830,8 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32T
     }
   }
   if (bad) {
+    // a wait gave up: record it, let this CTA's copies in flight land
+    // (again bounded) before the shared memory is released
     if (tid == 0) {
       atomicOr(&a.cs[B.cav].flags, 2);
       for (int pl = max(0, issued - R); pl < issued; ++pl) (void)wait_plane(pl);
@@ -1215,10 +843,10 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, (R == 4 ? 512 : 384) / (kF32T
 
 // Spectral-radius partials of the current state (no update), with the step
 // kernel's tiling so that the finalise reduction reads the same layout.
-template <class S, int TX, int TY, int KC>
+template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) k_spectral(StepArgs a) {
   constexpr int NT = TX * TY;
-  const TileRef R = tile_ref<KC, kFineKC32>(a.blocks, a.nblocks, a.ncoarse, blockIdx.x);
+  const TileRef R = f32_tile_ref(a.blocks, a.nblocks, a.ncoarse, blockIdx.x);
   const BlockDev &B = a.blocks[R.b];
   const CavConst &C = a.cc[B.cav];
   const int i = R.tx * TX + threadIdx.x + 1, j = R.ty * TY + threadIdx.y + 1;

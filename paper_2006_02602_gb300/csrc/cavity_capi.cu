@@ -45,27 +45,34 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// FP32 step-kernel shapes compiled in: (kernel form P, tile height TY, z
-// chunk KC, ring depth R); P = 1 is k_step_f32 (one node per thread), P = 2
-// k_step_f32p (two, z neighbours from the ring), P = 3 k_step_f32q (two, z
-// neighbours below the plane in registers)
-#define BDC_F32_VARIANTS(X)                                                                       \
-  X(1, 8, 16, 8) X(1, 8, 32, 8) X(1, 8, 64, 8) X(1, 4, 32, 8) X(1, 4, 64, 8) X(2, 8, 32, 8) X(2, 8, 64, 8) \
-      X(2, 16, 32, 8) X(2, 16, 64, 8) X(3, 8, 16, 5) X(3, 8, 24, 5) X(3, 8, 32, 5) X(3, 8, 40, 5) X(3, 8, 64, 5) \
-      X(3, 8, 32, 6) X(3, 8, 16, 4) X(3, 8, 24, 4) X(3, 8, 32, 4) X(3, 8, 40, 4) X(3, 8, 64, 4)
+// FP32 step-kernel variants compiled in: (kernel form P, tile height TY, ring
+// depth R); P = 3 is k_step_f32q (two nodes per thread, the nodes behind the
+// plane in registers), the one form.  The z-chunk depth is a run-time
+// parameter of the tiling (the autotuner tries kF32Chunks).
+#define BDC_F32_VARIANTS(X) X(3, 8, 4) X(3, 8, 5) X(3, 16, 4) X(3, 16, 5)
 struct F32Shape {
   int p, ty, kc, r;
 };
-const F32Shape kF32Shapes[] = {
-#define BDC_SHAPE(P, TY, KC, R) {P, TY, KC, R},
-    BDC_F32_VARIANTS(BDC_SHAPE)
-#undef BDC_SHAPE
-};
+const int kF32Chunks[] = {16, 24, 32, 40, 48, 64, 96};
+constexpr int kF32MaxChunk = 4096;
 
 bool f32_variant_ok(int p, int ty, int kc, int r) {
-  for (const F32Shape &s : kF32Shapes)
-    if (s.p == p && s.ty == ty && s.kc == kc && s.r == r) return true;
+  if (kc < 1 || kc > kF32MaxChunk) return false;
+#define BDC_OK(P, TY, R) \
+  if (p == P && ty == TY && r == R) return true;
+  BDC_F32_VARIANTS(BDC_OK)
+#undef BDC_OK
   return false;
+}
+
+// every (variant, chunk depth) pair the autotuner times
+std::vector<F32Shape> f32_shapes() {
+  std::vector<F32Shape> out;
+#define BDC_SHAPE(P, TY, R) \
+  for (int kc : kF32Chunks) out.push_back({P, TY, kc, R});
+  BDC_F32_VARIANTS(BDC_SHAPE)
+#undef BDC_SHAPE
+  return out;
 }
 
 }  // namespace
@@ -351,47 +358,57 @@ int build_layout(cavity *h) {
   return CAVITY_OK;
 }
 
-// TMA descriptors of the FP32-mixed step kernel: one 4-D map per block and
-// buffer set over (x, y, z, array), box = one tile plane with its halo for
-// all six arrays
+// TMA descriptors of the FP32-mixed step kernel: two 4-D maps per block and
+// buffer set over (x, y, z, array): the pressure box (40 x (TY+4) nodes of
+// p_hi and p_lo) and the box of the other five arrays (40 x (TY+2) nodes)
 int encode_maps(cavity *h) {
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
   if (q != cudaDriverEntryPointSuccess || !fn) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   EncodeTiledFn encode = (EncodeTiledFn)fn;
-  std::vector<CUtensorMap> maps(2 * h->nblocks);
+  std::vector<CUtensorMap> maps(4 * h->nblocks);
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
-    for (int s = 0; s < 2; ++s) {
-      const cuuint64_t dims[4] = {(cuuint64_t)B.pitch, (cuuint64_t)B.rows, (cuuint64_t)(B.nz + 4), (cuuint64_t)kF32NA};
-      const cuuint64_t strides[3] = {(cuuint64_t)B.pitch * 4, (cuuint64_t)B.plane * 4, (cuuint64_t)B.fstride * 4};
-      const cuuint32_t box[4] = {(cuuint32_t)kF32BX, (cuuint32_t)f32_box_y(h->ty), 1, (cuuint32_t)kF32NA};
-      const cuuint32_t estr[4] = {1, 1, 1, 1};
-      const CUresult r = encode(&maps[2 * id + s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.base[s], dims, strides, box,
-                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    }
+    for (int s = 0; s < 2; ++s)
+      for (int kind = 0; kind < 2; ++kind) {
+        // columns up to node nx + 2: the row's padding lies outside the map,
+        // so a box reaching past it is zero-filled, not read from HBM
+        const cuuint64_t dims[4] = {(cuuint64_t)(XO<float>::v + B.nx + 2), (cuuint64_t)B.rows,
+                                    (cuuint64_t)(B.nz + 4), (cuuint64_t)kF32NA};
+        const cuuint64_t strides[3] = {(cuuint64_t)B.pitch * 4, (cuuint64_t)B.plane * 4, (cuuint64_t)B.fstride * 4};
+        const cuuint32_t box[4] = {(cuuint32_t)kF32BX,
+                                   (cuuint32_t)(kind == 0 ? f32_box_yp(h->ty) : f32_box_yo(h->ty)), 1,
+                                   (cuuint32_t)(kind == 0 ? kF32NP : kF32NO)};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const CUresult r = encode(&maps[2 * (2 * id + s) + kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.base[s], dims,
+                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+      }
   }
   if (!h->d_maps) CK(cudaMalloc(&h->d_maps, sizeof(CUtensorMap) * maps.size()));
   CK(cudaMemcpy(h->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
   return CAVITY_OK;
 }
 
-template <int P, int TY, int KC, int R>
+template <int P, int TY, int R>
 auto f32_kernel() {
-  if constexpr (P == 1) return k_step_f32<TY, KC, R>;
-  else if constexpr (P == 2) return k_step_f32p<TY, KC, R>;
-  else return k_step_f32q<TY, KC, R>;
+  static_assert(P == 3, "the FP32 step kernel has one form");
+  return k_step_f32q<TY, R>;
 }
 
-// dynamic shared memory of the FP32 step kernel's shape
-cudaError_t f32_set_smem(int p, int ty, int kc, int r) {
-#define BDC_ATTR(P, TY, KC, R)                                                                                   \
-  if (p == P && ty == TY && kc == KC && r == R)                                                                  \
-    return cudaFuncSetAttribute(f32_kernel<P, TY, KC, R>(), cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                                f32_smem_bytes(TY, R));
+// dynamic shared memory of the FP32 step kernel's shape, and the largest
+// shared-memory carveout (four 47 KB CTAs per SM)
+cudaError_t f32_set_smem(int p, int ty, int r) {
+#define BDC_ATTR(P, TY, R)                                                                                       \
+  if (p == P && ty == TY && r == R) {                                                                            \
+    const cudaError_t e = cudaFuncSetAttribute(f32_kernel<P, TY, R>(),                                           \
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, f32_smem_bytes(TY, R)); \
+    if (e != cudaSuccess) return e;                                                                              \
+    return cudaFuncSetAttribute(f32_kernel<P, TY, R>(), cudaFuncAttributePreferredSharedMemoryCarveout,         \
+                                (int)cudaSharedmemCarveoutMaxShared);                                            \
+  }
   BDC_F32_VARIANTS(BDC_ATTR)
 #undef BDC_ATTR
   return cudaErrorInvalidValue;
@@ -455,7 +472,7 @@ int alloc_device(cavity *h) {
   if (h->f32) {
     rc = encode_maps(h);
     if (rc != CAVITY_OK) return rc;
-    CK(f32_set_smem(h->f32_p, h->ty, h->kc, h->f32_r));
+    CK(f32_set_smem(h->f32_p, h->ty, h->f32_r));
   }
   return CAVITY_OK;
 }
@@ -549,11 +566,11 @@ void launch_step_kernel(cavity *h, int parity, bool after_finalise = false) {
     cfg.attrs = attr;
     cfg.numAttrs = after_finalise && h->n_cut == 0 ? 1 : 0;
     const StepF32Args sa = step_f32_args(h, parity);
-#define BDC_LAUNCH(P, TY, KC, R)                                                 \
-  if (h->f32_p == P && h->ty == TY && h->kc == KC && h->f32_r == R) {             \
-    cfg.blockDim = dim3(P == 1 ? kF32TX : kF32TX / 2, TY);                        \
+#define BDC_LAUNCH(P, TY, R)                                                     \
+  if (h->f32_p == P && h->ty == TY && h->f32_r == R) {                            \
+    cfg.blockDim = dim3(kF32TX / 2, TY);                                          \
     cfg.dynamicSmemBytes = f32_smem_bytes(TY, R);                                 \
-    cudaLaunchKernelEx(&cfg, f32_kernel<P, TY, KC, R>(), sa);                     \
+    cudaLaunchKernelEx(&cfg, f32_kernel<P, TY, R>(), sa);                         \
   }
     BDC_F32_VARIANTS(BDC_LAUNCH)
 #undef BDC_LAUNCH
@@ -565,9 +582,9 @@ void launch_step_kernel(cavity *h, int parity, bool after_finalise = false) {
 void launch_spectral(cavity *h) {
   const StepArgs sa = step_args(h, h->parity, 1);
   if (h->f32) {
-#define BDC_SPEC(P, TY, KC, R)                                                                                   \
-  if (h->f32_p == P && h->ty == TY && h->kc == KC && h->f32_r == R)                                              \
-    k_spectral<float, kF32TX, TY, KC><<<h->n_step, dim3(kF32TX, TY), 0, h->stream>>>(sa);
+#define BDC_SPEC(P, TY, R)                                                                                       \
+  if (h->f32_p == P && h->ty == TY && h->f32_r == R)                                                             \
+    k_spectral<float, kF32TX, TY><<<h->n_step, dim3(kF32TX, TY), 0, h->stream>>>(sa);
     BDC_F32_VARIANTS(BDC_SPEC)
 #undef BDC_SPEC
   } else {
@@ -746,7 +763,7 @@ int retile(cavity *h, int p, int ty, int kc, int r) {
   if (rc == CAVITY_OK) rc = upload_tables(h);
   if (rc == CAVITY_OK) rc = encode_maps(h);
   if (rc != CAVITY_OK) return rc;
-  CK(f32_set_smem(p, ty, kc, r));
+  CK(f32_set_smem(p, ty, r));
   return build_graphs(h);
 }
 
@@ -915,10 +932,10 @@ int create_common(const cavity_desc *descs, const cavity_params *params, int n, 
     h->ty = kF32TY;
     h->kc = kF32KC;
     h->f32_r = kF32R;
-    h->f32_p = kF32P;
+    h->f32_p = 3;
     // shape override for tuning sweeps: BDC_F32_TILE="TY,KC,R[,P]" (a compiled shape)
     if (const char *env = std::getenv("BDC_F32_TILE")) {
-      int ty = 0, kc = 0, r = 0, p = 1;
+      int ty = 0, kc = 0, r = 0, p = 3;
       const int got = std::sscanf(env, "%d,%d,%d,%d", &ty, &kc, &r, &p);
       if (got >= 3 && f32_variant_ok(p, ty, kc, r)) {
         h->ty = ty;
@@ -1287,7 +1304,7 @@ int cavity_autotune(cavity_t *h, int steps, double out[5]) {
     rc = fail(h, CAVITY_ERR_CUDA, "event creation failed");
   double best_us = 1e300;
   F32Shape best = {h->f32_p, h->ty, h->kc, h->f32_r};
-  for (const F32Shape &s : kF32Shapes) {
+  for (const F32Shape &s : f32_shapes()) {
     if (rc != CAVITY_OK) break;
     rc = retile(h, s.p, s.ty, s.kc, s.r);
     if (rc != CAVITY_OK) break;

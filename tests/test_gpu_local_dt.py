@@ -5,8 +5,8 @@ oracle's local mode.
  * FP64: fields within 1e-12 of the oracle (ragged size, 60 steps), time and
    residuals as the oracle's; 2x2x2 and 3x2x2 blocks bit-equal to one block;
    switching back to global steps mid-run matches the oracle doing the same;
- * FP32-mixed: within the form's 1e-5 of the FP64 oracle; the one- and
-   two-node kernels give identical fields.
+ * FP32-mixed: within the form's 1e-5 of the FP64 oracle; two tile shapes
+   (8 and 16 rows) give identical fields.
 """
 import numpy as np
 import pytest
@@ -86,7 +86,7 @@ def test_switch_back_to_global(m):
 def test_fp32_local_matches_oracle_and_shapes_agree(m, monkeypatch):
     n = (37, 21, 18)
     out = []
-    for shape in ("8,64,8,1", "8,32,8,2"):
+    for shape in ("8,64,5,3", "16,32,4,3"):
         monkeypatch.setenv("BDC_F32_TILE", shape)
         o, c = local_pair(m, n, 3e4, 40, precision=m.CAVITY_FP32_MIXED)
         with c:

@@ -320,11 +320,11 @@ def test_fp32_blocks_bit_identical(m, blocks):
         assert c.time == ref.time
 
 
-@pytest.mark.parametrize("shape", ["8,32,8,2", "16,64,8,2", "8,32,5,3", "8,40,5,3", "8,40,4,3"])
-def test_fp32_two_node_kernel(m, monkeypatch, shape):
-    """The kernel with two nodes per thread: ragged sizes against the oracle
-    (odd nx leaves a lone node in the last pair), and a decomposition with odd
-    per-block x extents bit-equal to one block."""
+@pytest.mark.parametrize("shape", ["8,32,4,3", "8,40,4,3", "8,32,5,3", "16,32,4,3", "8,96,5,3"])
+def test_fp32_tile_shapes_ragged(m, monkeypatch, shape):
+    """Each compiled tile shape (two nodes per thread): ragged sizes against
+    the oracle (odd nx leaves a lone node in the last pair), and a
+    decomposition with odd per-block x extents bit-equal to one block."""
     monkeypatch.setenv("BDC_F32_TILE", shape)
     for n in [(37, 21, 18), (2, 2, 2), (65, 9, 40)]:
         o, c = run_pair32(m, n, 3e4, 25, noise=1e-3, seed=11)

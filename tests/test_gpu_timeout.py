@@ -30,8 +30,8 @@ def m():
     return mod
 
 
-# one shape of each kernel form: register queues (3), ring neighbours (2), one node per thread (1)
-@pytest.mark.parametrize("shape", ["8,32,4,3", "8,32,8,2", "8,32,8,1"])
+# the default shape (one plane in flight) and a tall tile with two in flight
+@pytest.mark.parametrize("shape", ["8,32,4,3", "16,64,5,3"])
 def test_wait_runs_out_and_reports_timeout(m, monkeypatch, shape):
     monkeypatch.setenv("BDC_F32_TILE", shape)
     n = (40, 20, 36)
