@@ -14,19 +14,21 @@
 //                    applied to dt Yt, added with atomics into Q at the
 //                    stencil's inputs; sums of Yt R (for dt), of the
 //                    buoyancy and beta^2-floor adjoints
-//     (FP32 sweep instead: k_adj_centre applies the centre correction to
-//     Xbar in place, and k_adj_gather reads it as Yt and writes every Q once,
-//     gathering what the stencils would scatter; its node sums go out as
-//     per-CTA partials)
+//     (FP32 sweep instead: k_adj_pre does the objective, the sum and, in its
+//     last CTA, the centre correction to Xbar in place; k_adj_gather reads
+//     Xbar as Yt and writes every Q once, gathering what the stencils would
+//     scatter; its node sums go out as per-CTA partials)
 //   k_adj_argmax + k_adj_dt  dt's dependence: -cfl dtbar / S^2 times the
 //                    gradient of the spectral bound at its largest node (the
 //                    FP32 bound f32_spectral_exact after an FP32-mixed forward,
-//                    which sets that forward's dt)
+//                    which sets that forward's dt; the FP32 sweep takes the
+//                    argmax of a whole recomputed segment in one launch,
+//                    k_adj_argmax_seg); then the Ra adjoint from the buoyancy
+//                    (g sigma = Ra Pr) and floor (kappa u_ref^2 = kappa Ra
+//                    Pr) sums, and the per-step scalars reset
 //   k_adj_fold       wall and ghost adjoints moved onto interior nodes 1, 2
 //                    through p_w = 2 p1 - p2, p_g = 2 p_w - p1,
 //                    T_w = (4 T1 - T2)/3, and the hot wall's T onto theta
-//   k_adj_finish     Ra adjoint from the buoyancy (g sigma = Ra Pr) and floor
-//                    (kappa u_ref^2 = kappa Ra Pr) sums; reset the scalars
 // Subgradients at kinks follow the forward branch (|x| with sign(0) = 0, the
 // beta^2 floor, the argmax node).
 //
@@ -127,6 +129,56 @@ __global__ void __launch_bounds__(256) k_adj_sum_p(AdjArgs a) {
     for (int q = 1; q < nw; ++q) d += red[q];
     atomicAdd(&a.scal[kScSumP], d);
   }
+}
+
+// The FP32 sweep's first kernel of a reverse step, three steps in one: the
+// objective's terms (as k_adj_objective), the sum of the p adjoint (as
+// k_adj_sum_p, one FP64 atomic per CTA), and, in the CTA that finishes last,
+// the centre-shift transpose in place (as k_adj_centre).  The objective
+// touches T only and the sum reads p only, so the two share no data; `cnt`
+// counts the finished CTAs (zero between launches).
+template <class A>
+__global__ void __launch_bounds__(256) k_adj_pre(AdjArgs a, unsigned int *cnt) {
+  A *X = arr<A>(a.X);
+  const int tid = threadIdx.x;
+  for (int e = blockIdx.x * blockDim.x + tid; e < a.g.ny * a.g.nz; e += gridDim.x * blockDim.x) {
+    const int j = e % a.g.ny + 1, k = e / a.g.ny + 1;
+    X[aidx(a.g, 4, 1, j, k)] += (A)(-4.0 * a.coef);
+    X[aidx(a.g, 4, 2, j, k)] += (A)a.coef;
+    a.thetabar[e] += 3.0 * a.coef;
+  }
+  const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  const int rows = a.g.ny * a.g.nz;
+  A s = 0;
+  for (int r = blockIdx.x * nw + w; r < rows; r += gridDim.x * nw) {
+    const A *row = X + aidx(a.g, 0, 0, r % a.g.ny + 1, r / a.g.ny + 1);
+    for (int i = 1 + lane; i <= a.g.nx; i += 32) s += row[i];
+  }
+  double d = warp_sum((double)s);
+  __shared__ double red[8];
+  __shared__ bool last;
+  if (lane == 0) red[w] = d;
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 1; q < nw; ++q) d += red[q];
+    atomicAdd(&a.scal[kScSumP], d);
+    __threadfence();
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (tid < 8) {
+    int x[3];
+    for (int dd = 0; dd < 3; ++dd) {
+      const int n = a.C.gn[dd], up = (tid >> dd) & 1;
+      if ((n % 2) && up) return;
+      x[dd] = (n % 2) ? (n + 1) / 2 : n / 2 + up;
+    }
+    const long long e = aidx(a.g, 0, x[0], x[1], x[2]);
+    X[e] = (A)((double)X[e] - __ldcg(&a.scal[kScSumP]) / (double)a.C.ncentre);
+  }
+  if (tid == 0) *cnt = 0u;
 }
 
 // The centre-shift transpose in place, for the gather sweep: X(p) at the
@@ -508,25 +560,28 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
   }
 }
 
-// largest spectral bound of Q^n and its node (smallest linear index among
-// equal values: each thread visits its nodes in increasing index)
+// Largest spectral bound of the state in buffer set 0 of block B and its
+// node (smallest linear index among equal values: each thread visits its
+// nodes in increasing index), over the rows of CTA `cta` of `ncta`; thread 0
+// writes (max, index) to out2.  Every thread of the CTA calls it.
 template <class S>
-__global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
+__device__ __forceinline__ void adj_argmax_part(const BlockDev &B, const CavConst &C, const AdjGeom &g, int cta, int ncta,
+                                                double *out2) {
   // a warp per interior row (j, k), strided over the grid's warps (no index
   // division); a thread visits its nodes in increasing linear interior index
   // e = (i - 1) + nx ((j - 1) + ny (k - 1)), so it keeps the first of equal values
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nwq = blockDim.x >> 5;
-  const int nx = a.g.nx, ny = a.g.ny, rows = ny * a.g.nz;
-  const S *q = (const S *)a.B.base[0];
-  const long long fs = a.B.fstride;
+  const int nx = g.nx, ny = g.ny, rows = ny * g.nz;
+  const S *q = (const S *)B.base[0];
+  const long long fs = B.fstride;
   constexpr int NP = Store<S>::NP;  // u, v, w follow the p array(s)
   double best = -1.0, bidx = 0.0;
   float bestf = -1.f;               // FP32 path: the running maximum in FP32
   long long bidxl = 0;
   float wfloor = 0.f;  // FP64 path: at or below an exact bound a lane of this warp reached
-  const F32K<float> K32 = f32_spectral_consts(a.C);
-  for (int r = blockIdx.x * nwq + wq; r < rows; r += gridDim.x * nwq) {
-    const long long o0 = node_index<S>(a.B, 0, r % ny + 1, r / ny + 1), e0 = (long long)nx * r - 1;
+  const F32K<float> K32 = f32_spectral_consts(C);
+  for (int r = cta * nwq + wq; r < rows; r += ncta * nwq) {
+    const long long o0 = node_index<S>(B, 0, r % ny + 1, r / ny + 1), e0 = (long long)nx * r - 1;
     for (int i = 1 + lane; i <= nx; i += 32) {
       const long long o = o0 + i;
       const S u = q[NP * fs + o], v = q[(NP + 1) * fs + o], w = q[(NP + 2) * fs + o];
@@ -539,10 +594,10 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
           bidxl = e0 + i;
         }
       } else {
-        if (__fmul_rn(spectral_est_f32(a.C, u, v, w), 1.00001f) >= wfloor) {
+        if (__fmul_rn(spectral_est_f32(C, u, v, w), 1.00001f) >= wfloor) {
           // exact FP64 bound only where an FP32 estimate (relative error < 1e-6)
           // raised by 1e-5 could reach the running maximum: the argmax is unchanged
-          const double sv = spectral_f64(a.C, u, v, w);
+          const double sv = spectral_f64(C, u, v, w);
           if (sv > best) {
             best = sv;
             bidx = (double)(e0 + i);
@@ -573,9 +628,17 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
   if (threadIdx.x == 0) {
     for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
       if (sb[q] > best || (sb[q] == best && si[q] < bidx)) { best = sb[q]; bidx = si[q]; }
-    a.argpart[2 * blockIdx.x] = best;
-    a.argpart[2 * blockIdx.x + 1] = bidx;
+    out2[0] = best;
+    out2[1] = bidx;
   }
+}
+
+// the argmax of the state being reversed, with the FP32 sweep's second level
+// of the gather's node sums
+template <class S>
+__global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
+  adj_argmax_part<S>(a.B, a.C, a.g, blockIdx.x, gridDim.x, a.argpart + 2 * blockIdx.x);
+  const int w = threadIdx.x >> 5;
   if (a.ngpart > 0) {
     // second level of the gather's node sums: this CTA's contiguous run of
     // its per-CTA partials, in a fixed order (strided thread sums, a fixed
@@ -596,6 +659,16 @@ __global__ void __launch_bounds__(256) k_adj_argmax(AdjArgs a) {
       a.gpart2[3 * blockIdx.x + threadIdx.x] = acc;
     }
   }
+}
+
+// The argmax of every state of a recomputed segment (it depends on the
+// forward state only): grid (parts, slots), slot s's state in buffer set 0 of
+// blocks[s]; (max, index) pairs at argpart[2 (s parts + part)].
+template <class S>
+__global__ void __launch_bounds__(256) k_adj_argmax_seg(const BlockDev *blocks, CavConst C, AdjGeom g,
+                                                         double *argpart) {
+  adj_argmax_part<S>(blocks[blockIdx.y], C, g, blockIdx.x, gridDim.x,
+                     argpart + 2 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 // dt = cfl / S: add (-cfl dtbar / S^2) d(bound)/dV at the argmax node.  One
@@ -619,9 +692,12 @@ __global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts)
   // partials, reduced in a fixed order
   __shared__ double sg[3][kAdjDtThreads];
   double g3[3] = {0.0, 0.0, 0.0};
-  const int ng2 = a.ngpart > 0 ? nparts : 0;  // k_adj_argmax's second-level sums
+  // k_adj_argmax's second-level sums, or (gpart2 null) the gather's per-CTA
+  // partials themselves
+  const double *gp = a.gpart2 ? a.gpart2 : a.gpart;
+  const int ng2 = a.ngpart > 0 ? (a.gpart2 ? nparts : a.ngpart) : 0;
   for (int q = tid; q < ng2; q += kAdjDtThreads)
-    for (int c = 0; c < 3; ++c) g3[c] += a.gpart2[3 * (long long)q + c];
+    for (int c = 0; c < 3; ++c) g3[c] += gp[3 * (long long)q + c];
   for (int c = 0; c < 3; ++c) sg[c][tid] = g3[c];
   __syncthreads();
   for (int o = kAdjDtThreads / 2; o > 0; o >>= 1) {
@@ -661,6 +737,13 @@ __global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts)
   A *Q = arr<A>(a.Q);
   for (int d = 0; d < 3; ++d)
     Q[aidx(a.g, 1 + d, i, j, k)] += (A)(vbar[d] + (floored ? 0.0 : 2.0 * V[d] * b2bar));
+  // the step's Ra adjoint from the buoyancy (g sigma = Ra Pr) and floor
+  // (kappa u_ref^2 = kappa Ra Pr) sums; the per-step scalars reset
+  a.scal[kScRa] += a.C.nu * a.scal[kScGs] + a.dfloor * a.scal[kScFloor];
+  a.scal[kScDtbar] = 0.0;
+  a.scal[kScSumP] = 0.0;
+  a.scal[kScGs] = 0.0;
+  a.scal[kScFloor] = 0.0;
 }
 
 // wall and ghost adjoints onto the interior nodes they are formed from
@@ -695,14 +778,6 @@ __global__ void k_adj_fold(AdjArgs a) {
     atomicAdd(&Q[aidx(a.g, 4, i1[0], i1[1], i1[2])], (A)(4.0 / 3.0) * tw);
     atomicAdd(&Q[aidx(a.g, 4, i2[0], i2[1], i2[2])], (A)(-1.0 / 3.0) * tw);
   }
-}
-
-__global__ void k_adj_finish(AdjArgs a) {
-  a.scal[kScRa] += a.C.nu * a.scal[kScGs] + a.dfloor * a.scal[kScFloor];
-  a.scal[kScDtbar] = 0.0;
-  a.scal[kScSumP] = 0.0;
-  a.scal[kScGs] = 0.0;
-  a.scal[kScFloor] = 0.0;
 }
 
 // J accumulation during the forward run: J += Nu_hot of cavity 0

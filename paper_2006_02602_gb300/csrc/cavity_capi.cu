@@ -84,6 +84,9 @@ struct AdjointStore {
   char *ckpt_mem = nullptr;    // ncp buffer sets: the state at steps 0, ckpt, 2 ckpt, ...
   CavState *ckpt_cs = nullptr;  // their scalars (device)
   char *seg_mem = nullptr;     // ckpt buffer sets: one recomputed segment
+  BlockDev *seg_blocks = nullptr;   // ckpt block descriptors, slot s's state as buffer set 0 (walls pass)
+  WallFace *seg_faces = nullptr;    // the block's wall faces once per slot (one walls launch per segment)
+  CUtensorMap *seg_maps = nullptr;  // FP32 form: the step kernel's two maps of every slot
   char *final_mem = nullptr;   // the state after the forward run
   CavState final_cs{};
   int final_parity = 0;
@@ -92,6 +95,7 @@ struct AdjointStore {
   double *thetabar = nullptr, *scal = nullptr, *argpart = nullptr;
   double *gpart = nullptr;     // per-CTA node sums of the FP32 gather (3 per CTA)
   double *dts = nullptr;       // dt of every step (device)
+  unsigned int *cnt = nullptr; // finished CTAs of k_adj_pre (zero between launches)
   BlockDev *block = nullptr;   // descriptor of a segment slot (wall pass of FP32 states)
   bool have_forward = false;
   double J = 0.0;
@@ -361,32 +365,38 @@ int build_layout(cavity *h) {
 // TMA descriptors of the FP32-mixed step kernel: two 4-D maps per block and
 // buffer set over (x, y, z, array): the pressure box (40 x (TY+4) nodes of
 // p_hi and p_lo) and the box of the other five arrays (40 x (TY+2) nodes)
-int encode_maps(cavity *h) {
+// The pressure-box and other-box maps (out[0], out[1]) of a buffer set of
+// block B's layout at `base`.
+int encode_block_maps(cavity *h, const BlockDev &B, void *base, CUtensorMap out[2]) {
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
   if (q != cudaDriverEntryPointSuccess || !fn) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   EncodeTiledFn encode = (EncodeTiledFn)fn;
-  std::vector<CUtensorMap> maps(4 * h->nblocks);
-  for (int id = 0; id < h->nblocks; ++id) {
-    const BlockDev &B = h->hb[id];
-    for (int s = 0; s < 2; ++s)
-      for (int kind = 0; kind < 2; ++kind) {
-        // columns up to node nx + 2: the row's padding lies outside the map,
-        // so a box reaching past it is zero-filled, not read from HBM
-        const cuuint64_t dims[4] = {(cuuint64_t)(XO<float>::v + B.nx + 2), (cuuint64_t)B.rows,
-                                    (cuuint64_t)(B.nz + 4), (cuuint64_t)kF32NA};
-        const cuuint64_t strides[3] = {(cuuint64_t)B.pitch * 4, (cuuint64_t)B.plane * 4, (cuuint64_t)B.fstride * 4};
-        const cuuint32_t box[4] = {(cuuint32_t)kF32BX,
-                                   (cuuint32_t)(kind == 0 ? f32_box_yp(h->ty) : f32_box_yo(h->ty)), 1,
-                                   (cuuint32_t)(kind == 0 ? kF32NP : kF32NO)};
-        const cuuint32_t estr[4] = {1, 1, 1, 1};
-        const CUresult r = encode(&maps[2 * (2 * id + s) + kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B.base[s], dims,
-                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-      }
+  for (int kind = 0; kind < 2; ++kind) {
+    // columns up to node nx + 2: the row's padding lies outside the map, so a
+    // box reaching past it is zero-filled, not read from HBM
+    const cuuint64_t dims[4] = {(cuuint64_t)(XO<float>::v + B.nx + 2), (cuuint64_t)B.rows, (cuuint64_t)(B.nz + 4),
+                                (cuuint64_t)kF32NA};
+    const cuuint64_t strides[3] = {(cuuint64_t)B.pitch * 4, (cuuint64_t)B.plane * 4, (cuuint64_t)B.fstride * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)kF32BX, (cuuint32_t)(kind == 0 ? f32_box_yp(h->ty) : f32_box_yo(h->ty)), 1,
+                               (cuuint32_t)(kind == 0 ? kF32NP : kF32NO)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(&out[kind], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, CAVITY_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   }
+  return CAVITY_OK;
+}
+
+int encode_maps(cavity *h) {
+  std::vector<CUtensorMap> maps(4 * h->nblocks);
+  for (int id = 0; id < h->nblocks; ++id)
+    for (int s = 0; s < 2; ++s) {
+      const int rc = encode_block_maps(h, h->hb[id], h->hb[id].base[s], &maps[2 * (2 * id + s)]);
+      if (rc != CAVITY_OK) return rc;
+    }
   if (!h->d_maps) CK(cudaMalloc(&h->d_maps, sizeof(CUtensorMap) * maps.size()));
   CK(cudaMemcpy(h->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
   return CAVITY_OK;
@@ -872,7 +882,7 @@ void release(cavity *h) {
     if (p) cudaFree(p);
   AdjointStore &A = h->adj;
   void *aptrs[] = {A.ckpt_mem, A.ckpt_cs, A.seg_mem, A.final_mem, A.X, A.Yt, A.Q, A.thetabar, A.scal,
-                   A.argpart, A.gpart, A.dts, A.block};
+                   A.argpart, A.gpart, A.dts, A.block, A.seg_blocks, A.seg_faces, A.seg_maps, A.cnt};
   for (void *p : aptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -977,27 +987,32 @@ int create_common(const cavity_desc *descs, const cavity_params *params, int n, 
 template <class S, class Ad>
 void launch_adjoint_step(cavity *h, const AdjArgs &a, int nparts, long long nint, long long nfold, cudaEvent_t eb,
                          cudaEvent_t ea) {
-  k_adj_objective<Ad><<<ceil_div((long long)a.g.ny * a.g.nz, 256), 256, 0, h->stream>>>(a);
-  k_adj_sum_p<Ad><<<nparts, 256, 0, h->stream>>>(a);
   if constexpr (std::is_same<Ad, float>::value) {
-    // FP32 sweep: the centre-shift transpose in place on X, then the gather
-    // reads X as Yt (no atomics, no full prepare pass)
-    k_adj_centre<Ad><<<1, 8, 0, h->stream>>>(a);
+    // FP32 sweep: the objective, the p-adjoint sum and the centre-shift
+    // transpose in place on X in one launch, then the gather reads X as Yt
+    // (no atomics, no full prepare pass); the argmax of this state came with
+    // its segment's (a.argpart), and the dt kernel reduces the gather's
+    // partials itself
+    k_adj_pre<Ad><<<nparts, 256, 0, h->stream>>>(a, h->adj.cnt);
     AdjArgs g = a;
     g.Yt = a.X;
     cudaEventRecord(eb, h->stream);
     k_adj_gather<<<ceil_div(a.g.fs, 256), 256, 0, h->stream>>>(g);
     cudaEventRecord(ea, h->stream);
+    AdjArgs d = a;
+    d.gpart2 = nullptr;
+    k_adj_dt<S, Ad><<<1, kAdjDtThreads, 0, h->stream>>>(d, nparts);
   } else {
+    k_adj_objective<Ad><<<ceil_div((long long)a.g.ny * a.g.nz, 256), 256, 0, h->stream>>>(a);
+    k_adj_sum_p<Ad><<<nparts, 256, 0, h->stream>>>(a);
     k_adj_prepare<Ad, true><<<dim3((unsigned)ceil_div(a.g.fs, 256), 5), 256, 0, h->stream>>>(a);
     cudaEventRecord(eb, h->stream);
     k_adj_rates<S, Ad><<<ceil_div(nint, 256), 256, 0, h->stream>>>(a);
     cudaEventRecord(ea, h->stream);
+    k_adj_argmax<S><<<nparts, 256, 0, h->stream>>>(a);
+    k_adj_dt<S, Ad><<<1, kAdjDtThreads, 0, h->stream>>>(a, nparts);
   }
-  k_adj_argmax<S><<<nparts, 256, 0, h->stream>>>(a);
-  k_adj_dt<S, Ad><<<1, kAdjDtThreads, 0, h->stream>>>(a, nparts);
   k_adj_fold<Ad><<<ceil_div(nfold, 256), 256, 0, h->stream>>>(a);
-  k_adj_finish<<<1, 1, 0, h->stream>>>(a);
 }
 
 // cavity_check_sqrt: relative difference of sqrt_newton from CUDA's sqrt
@@ -1006,6 +1021,25 @@ __global__ void k_check_sqrt(const double *x, long long n, double *rel) {
   if (i >= n) return;
   const double r = sqrt(x[i]), s = sqrt_newton(x[i]);
   rel[i] = s == r ? 0.0 : fabs(s - r) / r;
+}
+
+// Recomputation of a checkpointed segment without copies: points block 0 of
+// the step graph's descriptor table at two buffer sets -- base[0] (read) = b0,
+// base[1] (written) = b1 -- and, in the FP32 form, replaces the parity-0
+// tensor maps with b0's (src[0], src[1]), so the captured one-step graph of
+// parity 0 steps the state in slot s straight into slot s + 1.  One warp.
+__global__ void k_adj_point(BlockDev *blk, CUtensorMap *maps, const CUtensorMap *src, void *b0, void *b1) {
+  if (threadIdx.x == 0) {
+    blk->base[0] = b0;
+    blk->base[1] = b1;
+  }
+  if (maps) {
+    static_assert(sizeof(CUtensorMap) == 128, "two 128-byte maps, 8 bytes per lane");
+    reinterpret_cast<unsigned long long *>(maps)[threadIdx.x] =
+        reinterpret_cast<const unsigned long long *>(src)[threadIdx.x];
+    // the maps are read through the tensor-map proxy by the next kernel
+    asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+  }
 }
 
 // FP64 FMA throughput of the GPU: every thread runs kDfmaChains independent
@@ -1356,7 +1390,7 @@ int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
   CK(cudaStreamSynchronize(h->stream));
   if (A.set_bytes != set_bytes || A.ncp < ncp || A.ckpt < ckpt || A.nsteps < nsteps) {
     void *aptrs[] = {A.ckpt_mem, A.ckpt_cs, A.seg_mem, A.final_mem, A.X, A.Yt, A.Q, A.thetabar, A.scal,
-                     A.argpart, A.gpart, A.dts, A.block};
+                     A.argpart, A.gpart, A.dts, A.block, A.seg_blocks, A.seg_faces, A.seg_maps, A.cnt};
     for (void *p : aptrs)
       if (p) cudaFree(p);
     A = AdjointStore{};
@@ -1370,16 +1404,50 @@ int cavity_adjoint_forward(cavity_t *h, int nsteps, int ckpt, double *J) {
     CK(cudaMalloc(&A.Q, abytes));
     CK(cudaMalloc(&A.thetabar, sizeof(double) * d.ny * d.nz));
     CK(cudaMalloc(&A.scal, sizeof(double) * kScCount));
-    CK(cudaMalloc(&A.argpart, sizeof(double) * 2 * nparts));
+    CK(cudaMalloc(&A.argpart, sizeof(double) * 2 * nparts * ckpt));  // one set per segment slot
+    CK(cudaMalloc(&A.cnt, sizeof(unsigned int)));
+    CK(cudaMemset(A.cnt, 0, sizeof(unsigned int)));
     CK(cudaMalloc(&A.gpart, sizeof(double) * 3 * (ceil_div(fs, 256) + nparts)));
     CK(cudaMalloc(&A.dts, sizeof(double) * nsteps));
     CK(cudaMalloc(&A.block, sizeof(BlockDev)));
     A.set_bytes = set_bytes;
+    // per segment slot: its block descriptor, its wall faces (one walls
+    // launch covers the segment) and, in the FP32 form, its tensor maps
+    std::vector<BlockDev> sb(ckpt, h->hb[0]);
+    std::vector<WallFace> sf;
+    for (int s = 0; s < ckpt; ++s) {
+      sb[s].base[0] = A.seg_mem + (size_t)s * set_bytes;
+      for (WallFace f : h->hwall) {
+        f.block = s;
+        f.cta_begin += s * h->n_bc;
+        sf.push_back(f);
+      }
+    }
+    CK(cudaMalloc(&A.seg_blocks, sizeof(BlockDev) * ckpt));
+    CK(cudaMalloc(&A.seg_faces, sizeof(WallFace) * sf.size()));
+    CK(cudaMemcpy(A.seg_blocks, sb.data(), sizeof(BlockDev) * ckpt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(A.seg_faces, sf.data(), sizeof(WallFace) * sf.size(), cudaMemcpyHostToDevice));
+    if (h->f32) {
+      std::vector<CUtensorMap> sm(2 * (size_t)ckpt);
+      for (int s = 0; s < ckpt; ++s) {
+        const int rc = encode_block_maps(h, h->hb[0], A.seg_mem + (size_t)s * set_bytes, &sm[2 * s]);
+        if (rc != CAVITY_OK) return rc;
+      }
+      CK(cudaMalloc(&A.seg_maps, sizeof(CUtensorMap) * sm.size()));
+      CK(cudaMemcpy(A.seg_maps, sm.data(), sizeof(CUtensorMap) * sm.size(), cudaMemcpyHostToDevice));
+    }
   }
   A.nsteps = nsteps;
   A.ckpt = ckpt;
   A.ncp = ncp;
   A.nparts = nparts;
+  // every segment slot starts as a copy of the initial state: the step
+  // writes interior nodes and the walls that change (p, adiabatic T), so the
+  // constant wall values (u = v = w = 0, the isothermal T) a recomputed state
+  // is read with must already be in its slot
+  for (int s = 0; s < ckpt; ++s)
+    CK(cudaMemcpyAsync(A.seg_mem + (size_t)s * set_bytes, h->hb[0].base[h->parity], set_bytes,
+                       cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemsetAsync(A.scal, 0, sizeof(double) * kScCount, h->stream));
   for (int n = 0; n < nsteps; ++n) {
     if (n % ckpt == 0) {
@@ -1442,39 +1510,49 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
     h->adj_ev.push_back(e);
   }
   int rc = CAVITY_OK;
+  auto slot = [&](int s) { return (void *)(A.seg_mem + (size_t)s * A.set_bytes); };
   for (int c = A.ncp - 1; c >= 0 && rc == CAVITY_OK; --c) {
     const int s0 = c * A.ckpt, s1 = std::min(s0 + A.ckpt, A.nsteps);
-    // recompute the segment from its checkpoint, keeping every state
-    CK(cudaMemcpyAsync(B0.base[0], A.ckpt_mem + (size_t)c * A.set_bytes, A.set_bytes, cudaMemcpyDeviceToDevice,
+    // recompute the segment from its checkpoint (copied to slot 0), each step
+    // of the parity-0 graph reading slot s - s0 and writing slot s - s0 + 1
+    CK(cudaMemcpyAsync(slot(0), A.ckpt_mem + (size_t)c * A.set_bytes, A.set_bytes, cudaMemcpyDeviceToDevice,
                        h->stream));
     CK(cudaMemcpyAsync(h->d_cs, A.ckpt_cs + c, sizeof(CavState), cudaMemcpyDeviceToDevice, h->stream));
-    h->parity = 0;
     for (int s = s0; s < s1; ++s) {
-      CK(cudaMemcpyAsync(A.seg_mem + (size_t)(s - s0) * A.set_bytes, B0.base[h->parity], A.set_bytes,
-                         cudaMemcpyDeviceToDevice, h->stream));
       CK(cudaMemcpyAsync(A.dts + s, &h->d_cs->dt, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
       if (s < s1 - 1) {
-        CK(cudaGraphLaunch(h->graph[h->parity], h->stream));
-        h->parity ^= 1;
+        k_adj_point<<<1, 32, 0, h->stream>>>(h->d_blocks, h->f32 ? h->d_maps : nullptr,
+                                             h->f32 ? A.seg_maps + 2 * (s - s0) : nullptr, slot(s - s0),
+                                             slot(s - s0 + 1));
+        CK(cudaGetLastError());
+        CK(cudaGraphLaunch(h->graph[0], h->stream));
       }
+    }
+    if (h->f32) {
+      // the FP32-mixed step forms p's and T's wall values where it reads
+      // them: write them into every stored state of the segment, one launch
+      BcArgs ba = bc_args(h, 0, 3);
+      ba.blocks = A.seg_blocks;
+      ba.faces = A.seg_faces;
+      ba.nfaces = (int)h->hwall.size() * (s1 - s0);
+      ba.tile_counter = nullptr;
+      ba.sfloor = nullptr;
+      k_bc<float><<<h->n_bc * (s1 - s0), kBcThreads, 0, h->stream>>>(ba);
+      CK(cudaGetLastError());
+      // the argmax of every state of the segment's spectral bound, one launch
+      k_adj_argmax_seg<float><<<dim3(A.nparts, s1 - s0), 256, 0, h->stream>>>(A.seg_blocks, h->hcc[0], a.g, A.argpart);
+      CK(cudaGetLastError());
     }
     CK(cudaMemcpyAsync(dts.data(), A.dts + s0, sizeof(double) * (s1 - s0), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     // reverse sweep over the segment
     for (int s = s1 - 1; s >= s0; --s) {
       a.B = B0;
-      a.B.base[0] = A.seg_mem + (size_t)(s - s0) * A.set_bytes;
+      a.B.base[0] = slot(s - s0);
       a.dt = dts[s - s0];
+      a.argpart = h->f32 ? A.argpart + 2 * (size_t)A.nparts * (s - s0) : A.argpart;
       a.X = X;
       a.Q = Q;
-      if (h->f32) {
-        // the FP32-mixed step forms p and T wall values on the fly: write them into the stored state
-        CK(cudaMemcpyAsync(A.block, &a.B, sizeof(BlockDev), cudaMemcpyHostToDevice, h->stream));
-        BcArgs ba = bc_args(h, 0, 3);
-        ba.blocks = A.block;
-        k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(ba);
-        CK(cudaGetLastError());
-      }
       cudaEvent_t eb = h->adj_ev[2 * s], ea = h->adj_ev[2 * s + 1];
       if (h->f32) launch_adjoint_step<float, float>(h, a, A.nparts, nint, nfold, eb, ea);
       else launch_adjoint_step<double, double>(h, a, A.nparts, nint, nfold, eb, ea);
@@ -1482,7 +1560,16 @@ int cavity_adjoint_backward(cavity_t *h, double *grad_wall, size_t n, double *gr
       std::swap(X, Q);
     }
   }
-  // back to the state after the forward run
+  // the step graph's table and maps back to the handle's buffers, and the
+  // state after the forward run
+  {
+    const int r2 = upload_tables(h);
+    if (r2 != CAVITY_OK) return r2;
+    if (h->f32) {
+      const int r3 = encode_maps(h);
+      if (r3 != CAVITY_OK) return r3;
+    }
+  }
   CK(cudaMemcpyAsync(h->hb[0].base[A.final_parity], A.final_mem, A.set_bytes, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_cs, &A.final_cs, sizeof(CavState), cudaMemcpyHostToDevice, h->stream));
   h->parity = A.final_parity;
