@@ -454,7 +454,9 @@ def measure_adjoint(m, torch, rank, world, local, stream):
                  stream=stream.cuda_stream, Ra=cfg["Ra"], Pr=cfg["Pr"])
     m.cavity_set_wall_temperature(c.h, 0, theta)
     tuned = m.cavity_autotune(c.h, 10)  # the FP32 step's tile shape (forward and recomputation)
-    m.cavity_adjoint_forward(c.h, 20, 10)  # warm-up (allocations, graphs)
+    # warm-up with the timed run's own step count and checkpoint interval, so
+    # that the timed run reuses the checkpoint and segment memory
+    m.cavity_adjoint_forward(c.h, cfg["steps"], cfg["ckpt"])
     m.cavity_adjoint_backward(c.h, n[1], n[2])
     if world > 1:
         torch.distributed.barrier()

@@ -435,9 +435,12 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
     // Sources n = m + s e_d and m + 2 s e_d.  Every load is unconditional
     // (at n when n is interior, else at m, which is always in range), so the
     // loads issue together; a select drops the contributions of non-interior n.
-    const long long astr[3] = {1, a.g.ex, a.g.ex * a.g.ey};
-    const long long sstr[3] = {1, a.B.pitch, a.B.plane};
-    const long long om = node_index<float>(a.B, i, j, k);
+    // Offsets in 32 bits: both the adjoint arrays (5 fs) and the state (7
+    // fstride) have fewer than 2^31 elements.
+    const int astr[3] = {1, (int)a.g.ex, (int)(a.g.ex * a.g.ey)};
+    const int sstr[3] = {1, a.B.pitch, (int)a.B.plane};
+    const int om = (int)node_index<float>(a.B, i, j, k);
+    const int ei = (int)e, fsa = (int)a.g.fs, fs32 = (int)fs;
     const int xm[3] = {i, j, k};
     for (int d = 0; d < 3; ++d) {
       for (int s = -1; s <= 1; s += 2) {
@@ -447,11 +450,11 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
           int x3[3] = {i, j, k};
           x3[d] = c;
           const bool in = interior(x3[0], x3[1], x3[2]);
-          const long long ea = in ? e + s * astr[d] : e, es = in ? om + s * sstr[d] : om;
-          const float V[3] = {q[2 * fs + es], q[3 * fs + es], q[4 * fs + es]};
+          const int ea = in ? ei + s * astr[d] : ei, es = in ? om + s * sstr[d] : om;
+          const float V[3] = {q[2 * fs32 + es], q[3 * fs32 + es], q[4 * fs32 + es]};
           const float b2 = fmaxf(V[0] * V[0] + V[1] * V[1] + V[2] * V[2], b2min);
           float rb[5];
-          for (int f = 0; f < 5; ++f) rb[f] = dt * Yt[ea + f * a.g.fs];
+          for (int f = 0; f < 5; ++f) rb[f] = dt * Yt[ea + f * fsa];
           const float ad = V[d] * ih2[d];
           for (int f = 1; f <= 4; ++f) {
             const float cf = rb[f] * (Dq[f] * ihh[d] + (float)s * ad);
@@ -467,8 +470,8 @@ __global__ void __launch_bounds__(256) k_adj_gather(AdjArgs a) {
           int x3[3] = {i, j, k};
           x3[d] = xm[d] + 2 * s;
           const bool in = interior(x3[0], x3[1], x3[2]);
-          const long long ea = in ? e + 2 * s * astr[d] : e, es = in ? om + 2 * s * sstr[d] : om;
-          const float V[3] = {q[2 * fs + es], q[3 * fs + es], q[4 * fs + es]};
+          const int ea = in ? ei + 2 * s * astr[d] : ei, es = in ? om + 2 * s * sstr[d] : om;
+          const float V[3] = {q[2 * fs32 + es], q[3 * fs32 + es], q[4 * fs32 + es]};
           const float b2 = fmaxf(V[0] * V[0] + V[1] * V[1] + V[2] * V[2], b2min);
           const float c0 = -dt * Yt[ea] * c4 * lambda(V[d], b2) * ih[d];
           out[0] += in ? c0 : 0.f;
@@ -675,7 +678,7 @@ __global__ void __launch_bounds__(256) k_adj_argmax_seg(const BlockDev *blocks, 
 // CTA of kAdjDtThreads: the per-CTA (max, index) pairs of k_adj_argmax are
 // reduced in parallel (largest value, smallest index among equals), then one
 // thread differentiates the bound at that node (FP64).
-constexpr int kAdjDtThreads = 256;
+constexpr int kAdjDtThreads = 1024;
 template <class S, class A>
 __global__ void __launch_bounds__(kAdjDtThreads) k_adj_dt(AdjArgs a, int nparts) {
   __shared__ double sb[kAdjDtThreads], si[kAdjDtThreads];
