@@ -717,6 +717,15 @@ static __global__ void __launch_bounds__(kShellThreads) k_shell_f64(ShellArgs a)
 // k_bc (wall conditions + Nusselt partials) and k_finalize (reduction of the
 // partials, state advance).
 
+// k_pack / k_unpack / the finalise's exchange CTAs (below)
+struct ExchArgs {
+  const BlockDev *blocks;
+  const CutFace *faces;
+  int nfaces;
+  double *buf;   // FP64 storage: values; FP32 storage: reinterpreted as float
+  int parity;
+};
+
 struct BcArgs {
   const BlockDev *blocks;
   const WallFace *faces;
@@ -732,6 +741,9 @@ struct BcArgs {
   unsigned int *sfloor;       // the step kernel's per-cavity dt-filter floors: reset here
   long long shell_begin, shell_end;  // k_shell_f64 partial slots of this step (single cavity; empty if equal)
   int parity;                 // buffer set holding the new state
+  const CutFace *cuts;        // after a step with cut faces: the exchange of the new state, run by
+  int ncuts;                  //   the CTAs after the finalise CTAs (null / 0: none)
+  void *xbuf;
   int mode;                   // 0 after a step, 1 after init / set_fields,
                               // 3 walls only (k_bc), no reductions,
                               // 4 after an FP32 step (k_finalize only): Nusselt
@@ -790,12 +802,13 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
 // per cavity (contiguous slices of the partials), and the last of them
 // combines the slices in order.  Nusselt sums: the wall kernel's partials
 // (modes 0, 1) or the step partials' slots 6 and 7, sums of
-// 3 T_w - 4 T_1 + T_2 (mode 4, FP32 step).
+// 3 T_w - 4 T_1 + T_2 (mode 4, FP32 step).  After a step of a decomposed
+// cavity, CTAs after the finalise CTAs exchange the new state's cut faces.
 constexpr int kFinThreads = 128, kFinSlices = 16;
 
 template <int NT>
 __device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long long b0, long long b1,
-                             long long s0, long long s1, double tot[8], double *sh, int tid) {
+                             long long s0, long long s1, double &tot, double *sh, int tid) {
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (long long q = q0 + tid; q < q1; q += NT) {
     const double *pp = a.step_partials + q * kPartStride;
@@ -820,12 +833,18 @@ __device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long l
   if (lane == 0)
     for (int f = 0; f < 8; ++f) sh[wid * 8 + f] = acc[f];
   __syncthreads();
-  if (tid == 0) {
-    for (int f = 0; f < 8; ++f) tot[f] = sh[f];
-    for (int q = 1; q < NT / 32; ++q)
-      for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], sh[q * 8 + f]) : tot[f] + sh[q * 8 + f];
+  // the warps' totals folded in warp order, field f by thread f (one thread's
+  // dependent FP64 chain is slow on this part's narrow FP64 pipe)
+  if (tid < 8) {
+    const int f = tid;
+    double t = sh[f];
+    for (int q = 1; q < NT / 32; ++q) t = (f == 5) ? fmax(t, sh[q * 8 + f]) : t + sh[q * 8 + f];
+    tot = t;
   }
 }
+
+template <class S, int NT>
+__device__ __forceinline__ void exchange_cta(const ExchArgs &a, int cta);
 
 // mid: [ncav][kFinSlices][8] slice totals; a.counter: per cavity, zero between launches
 template <class S>
@@ -833,26 +852,34 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   __shared__ double sh[kFinThreads / 32 * 8];
   __shared__ double shm[kFinSlices * 8];
   __shared__ double shc[8];
+  __shared__ double sht[8];
   __shared__ bool am_last;
   static_assert(kFinSlices * 8 <= kFinThreads, "one slice total per thread");
   // the next step kernel (a programmatic dependent) may start its prologue now;
   // it waits for this grid's completion before it reads the state advanced here
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (blockIdx.x >= a.ncav * kFinSlices) {
+    // the exchange of the new state's cut faces, beside the reductions
+    const ExchArgs x{a.blocks, a.cuts, a.ncuts, (double *)a.xbuf, a.parity};
+    exchange_cta<S, kFinThreads>(x, blockIdx.x - a.ncav * kFinSlices);
+    return;
+  }
   const int cav = blockIdx.x / kFinSlices, g = blockIdx.x % kFinSlices, tid = threadIdx.x;
   const CavConst &C = a.cc[cav];
   const long long nt = C.tile_end - C.tile_begin, nb = a.mode == 4 ? 0 : C.bc_end - C.bc_begin;
   const long long ns = a.shell_end - a.shell_begin;
-  double tot[8];
+  double tf = 0.0;  // thread f < 8: this slice's total of field f
   reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / kFinSlices, C.tile_begin + nt * (g + 1) / kFinSlices,
                             C.bc_begin + nb * g / kFinSlices, C.bc_begin + nb * (g + 1) / kFinSlices,
-                            a.shell_begin + ns * g / kFinSlices, a.shell_begin + ns * (g + 1) / kFinSlices, tot, sh,
+                            a.shell_begin + ns * g / kFinSlices, a.shell_begin + ns * (g + 1) / kFinSlices, tf, sh,
                             tid);
   double *my = mid + ((long long)cav * kFinSlices + g) * 8;
-  if (tid == 0) {
-    for (int f = 0; f < 8; ++f) my[f] = tot[f];
+  if (tid < 8) {
+    my[tid] = tf;
     __threadfence();
-    am_last = atomicAdd(a.counter + cav, 1u) == (unsigned int)kFinSlices - 1u;
   }
+  __syncthreads();
+  if (tid == 0) am_last = atomicAdd(a.counter + cav, 1u) == (unsigned int)kFinSlices - 1u;
   __syncthreads();
   if (!am_last) return;
   __threadfence();
@@ -864,21 +891,22 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
     shc[tid] = load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[tid]);
   }
   __syncthreads();
-  if (tid != 0) return;
-  for (int f = 0; f < 8; ++f) tot[f] = shm[f];
-  for (int q = 1; q < kFinSlices; ++q)
-    for (int f = 0; f < 8; ++f) tot[f] = (f == 5) ? fmax(tot[f], shm[q * 8 + f]) : tot[f] + shm[q * 8 + f];
-  if (a.mode == 4) {  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
-    tot[6] *= 0.5 * C.ih[0] * C.inv_dT;
-    tot[7] *= -0.5 * C.ih[0] * C.inv_dT;
-  }
   CavState &st = a.cs[cav];
-  bool bad = !isfinite(tot[5]);
+  // the slice totals folded in slice order, field f by thread f; threads
+  // 0..4 take the residual norms
+  if (tid < 8) {
+    const int f = tid;
+    double t = shm[f];
+    for (int q = 1; q < kFinSlices; ++q) t = (f == 5) ? fmax(t, shm[q * 8 + f]) : t + shm[q * 8 + f];
+    if (a.mode == 4 && f >= 6) t *= (f == 6 ? 0.5 : -0.5) * C.ih[0] * C.inv_dT;  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
+    sht[f] = t;
+    if (a.mode != 1 && f < 5) st.res[f] = sqrt(t * C.inv_nint);
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  bool bad = !isfinite(sht[5]);
   if (a.mode != 1) {
-    for (int f = 0; f < 5; ++f) {
-      st.res[f] = sqrt(tot[f] * C.inv_nint);
-      bad = bad || !isfinite(tot[f]);
-    }
+    for (int f = 0; f < 5; ++f) bad = bad || !isfinite(sht[f]);
     st.t += st.dt;
     st.step += 1;
     // centre pressure of the new state, lexicographic (k, j, i) order
@@ -886,9 +914,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
     for (int m = 0; m < C.ncentre; ++m) csum += shc[m];
     st.c = csum / (double)C.ncentre;
   }
-  st.dt = C.cfl / tot[5];
-  st.nu_hot = tot[6] * C.inv_nwall;
-  st.nu_cold = tot[7] * C.inv_nwall;
+  st.dt = C.cfl / sht[5];
+  st.nu_hot = sht[6] * C.inv_nwall;
+  st.nu_cold = sht[7] * C.inv_nwall;
   if (bad) st.flags |= 1;
   a.counter[cav] = 0u;
 }
@@ -941,14 +969,6 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
 // var[2 nb nc + v nb nc + ic nb + ib].  Depth d counts layers in increasing
 // index order.  Pure copies: bit exact.
 
-struct ExchArgs {
-  const BlockDev *blocks;
-  const CutFace *faces;
-  int nfaces;
-  double *buf;   // FP64 storage: values; FP32 storage: reinterpreted as float
-  int parity;
-};
-
 __device__ __forceinline__ int find_cut(const CutFace *faces, int nfaces, int cta) {
   int lo = 0, hi = nfaces - 1;
   while (lo < hi) {
@@ -961,19 +981,17 @@ __device__ __forceinline__ int find_cut(const CutFace *faces, int nfaces, int ct
 template <class S>
 __device__ __forceinline__ void face_geometry(const BlockDev &B, int face, int ib, int ic, bool ghost,
                                               long long &p_first, long long &v_node, long long &dstep) {
+  // face axis a; the face's faster axis (y for x faces, else x) gets ib + 1,
+  // the slower one (z, except y for z faces) ic + 1 (selects rather than an
+  // indexed array, which would live in local memory)
   const int a = face >> 1, high = face & 1;
-  const int n[3] = {B.nx, B.ny, B.nz};
-  const int bb = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
-  int idx[3];
-  idx[bb] = ib + 1;
-  idx[cc] = ic + 1;
+  const int na = a == 0 ? B.nx : (a == 1 ? B.ny : B.nz);
+  const int b1 = ib + 1, c1 = ic + 1;
   int pl, vl;
-  if (!ghost) { pl = high ? n[a] - 1 : 1; vl = high ? n[a] : 1; }
-  else { pl = high ? n[a] + 1 : -1; vl = high ? n[a] + 1 : 0; }
-  idx[a] = pl;
-  p_first = node_index<S>(B, idx[0], idx[1], idx[2]);
-  idx[a] = vl;
-  v_node = node_index<S>(B, idx[0], idx[1], idx[2]);
+  if (!ghost) { pl = high ? na - 1 : 1; vl = high ? na : 1; }
+  else { pl = high ? na + 1 : -1; vl = high ? na + 1 : 0; }
+  p_first = node_index<S>(B, a == 0 ? pl : b1, a == 0 ? b1 : (a == 1 ? pl : c1), a == 2 ? pl : c1);
+  v_node = node_index<S>(B, a == 0 ? vl : b1, a == 0 ? b1 : (a == 1 ? vl : c1), a == 2 ? vl : c1);
   dstep = a == 0 ? 1 : (a == 1 ? (long long)B.pitch : B.plane);
 }
 
@@ -1021,6 +1039,68 @@ __global__ void __launch_bounds__(256) k_unpack(ExchArgs a) {
   }
   for (int v = 0; v < Store<S>::NA - NP; ++v)
     q[(long long)(NP + v) * B.fstride + v_node] = buf[2LL * NP * plane + (long long)v * plane + e];
+}
+
+// Pack and unpack in one pass, one CTA of NT threads per 256 face positions
+// (CutFace::cta_begin counts such CTAs): the same buffer entries and ghost
+// values as k_pack followed by k_unpack.  The step's exchange, run by the
+// finalise kernel's extra CTAs beside its reductions, so it is written for
+// latency: the face found by a warp-wide search, every value of the thread's
+// positions loaded before the first store.
+template <class S, int NT>
+__device__ __forceinline__ void exchange_cta(const ExchArgs &a, int cta) {
+  static_assert(256 % NT == 0, "positions per thread");
+  constexpr int NPOS = 256 / NT, NP = Store<S>::NP, NA = Store<S>::NA, NV = NP + NA;  // p at depth 2
+  // the face of this CTA: the last one whose first CTA is not after it
+  int fi = 0;
+  for (int base = 0; base < a.nfaces; base += 32) {
+    const int l = base + (threadIdx.x & 31);
+    const unsigned m = __ballot_sync(0xffffffffu, l < a.nfaces && a.faces[l].cta_begin <= cta);
+    if (m) fi = base + 31 - __clz(m);
+  }
+  const CutFace F = a.faces[fi];
+  const BlockDev &B = a.blocks[F.src];
+  const BlockDev &D = a.blocks[F.dst];
+  const int plane = F.nb * F.nc;
+  const S *__restrict__ q = (const S *)B.base[a.parity];
+  S *__restrict__ g = (S *)D.base[a.parity];
+  S *__restrict__ buf = (S *)a.buf + F.buf_off;
+  const long long fs = B.fstride, fd = D.fstride;
+  int e[NPOS];
+  long long gp[NPOS], gv[NPOS], gstep = 0;
+  S x[NPOS][NV];
+#pragma unroll
+  for (int r = 0; r < NPOS; ++r) {
+    e[r] = (cta - F.cta_begin) * 256 + r * NT + (int)threadIdx.x;
+    if (e[r] >= plane) continue;
+    const int ib = e[r] % F.nb, ic = e[r] / F.nb;
+    long long p_first, v_node, dstep;
+    face_geometry<S>(B, F.face, ib, ic, false, p_first, v_node, dstep);
+    face_geometry<S>(D, F.face ^ 1, ib, ic, true, gp[r], gv[r], gstep);
+#pragma unroll
+    for (int pa = 0; pa < NP; ++pa) {
+      x[r][2 * pa] = q[pa * fs + p_first];
+      x[r][2 * pa + 1] = q[pa * fs + p_first + dstep];
+    }
+#pragma unroll
+    for (int v = 0; v < NA - NP; ++v) x[r][2 * NP + v] = q[(NP + v) * fs + v_node];
+  }
+#pragma unroll
+  for (int r = 0; r < NPOS; ++r) {
+    if (e[r] >= plane) continue;
+#pragma unroll
+    for (int pa = 0; pa < NP; ++pa) {
+      buf[2LL * pa * plane + 2LL * e[r]] = x[r][2 * pa];
+      buf[2LL * pa * plane + 2LL * e[r] + 1] = x[r][2 * pa + 1];
+      g[pa * fd + gp[r]] = x[r][2 * pa];
+      g[pa * fd + gp[r] + gstep] = x[r][2 * pa + 1];
+    }
+#pragma unroll
+    for (int v = 0; v < NA - NP; ++v) {
+      buf[2LL * NP * plane + (long long)v * plane + e[r]] = x[r][2 * NP + v];
+      g[(NP + v) * fd + gv[r]] = x[r][2 * NP + v];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -69,6 +69,7 @@ struct StepF32Args {
   int ncoarse;                // coarse tiles of all blocks (scheduling indices below it)
   long long wait_cycles;      // limit of each bounded mbarrier wait (kWaitCycles)
   int withhold_plane;         // -1; a test of the timeout path sets a plane index whose load is never issued
+  int ghosts_late;            // cut faces: the previous step's finalise launch writes the ghost layers
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -281,6 +282,15 @@ __device__ __forceinline__ F32Tile f32_tile(const StepF32Args &a, int cta) {
   T.lxh = B.nx - T.i0 + kF32HX;  // box column of node nx
   T.lyh = B.ny - T.j0 + 2;       // pressure-box row of node ny (other box: one row less)
   return T;
+}
+
+// Whether the tile's boxes (x nodes i0-4 .. i0+35, y rows j0-2 .. j0+TY+1,
+// planes k0-2 .. k1+2) reach a ghost layer of a cut face.
+template <int TY>
+__device__ __forceinline__ bool f32_reads_ghosts(const BlockDev &B, const F32Tile &T) {
+  return (!B.wall[0] && T.i0 - kF32HX <= 0) || (!B.wall[1] && T.i0 + kF32BX - kF32HX - 1 >= B.nx + 1) ||
+         (!B.wall[2] && T.j0 - 2 <= 0) || (!B.wall[3] && T.j0 + TY + 1 >= B.ny + 1) ||
+         (!B.wall[4] && T.k0 - 2 <= 0) || (!B.wall[5] && T.k1 + 2 >= B.nz + 1);
 }
 
 // Apply the x and y wall conditions to one freshly loaded plane slot.
@@ -783,6 +793,12 @@ __global__ void __launch_bounds__(kF32TX / 2 * TY, 512 / (kF32TX / 2 * TY)) k_st
     tma_load_4d(ring + s * SF + PF, mapo, &bars[s], T.x0, T.y0 + 1, z, kF32NP);
   };
   if (tid == 0) {
+    if (a.ghosts_late && f32_reads_ghosts<TY>(B, T)) {
+      // the boxes reach a ghost layer, which the previous step's finalise
+      // launch (this launch's programmatic predecessor, if any) writes
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
     for (; issued < min(R, T.nplanes); ++issued) issue(issued);
   }
   auto wait_plane = [&](int pl) { return mbar_wait_bounded(&bars[pl % R], (uint32_t)((pl / R) & 1), a.wait_cycles); };

@@ -523,6 +523,7 @@ StepF32Args step_f32_args(cavity *h, int parity) {
   a.ncoarse = h->n_coarse;
   a.wait_cycles = h->wait_cycles;
   a.withhold_plane = h->withhold_plane;
+  a.ghosts_late = h->n_cut > 0;  // the finalise after each step writes the ghost layers
   return a;
 }
 
@@ -537,6 +538,7 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.sfloor = h->d_counter + h->ncav + 1;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
   a.shell_begin = a.shell_end = 0;
+  a.cuts = nullptr; a.ncuts = 0; a.xbuf = nullptr;
   return a;
 }
 
@@ -558,13 +560,15 @@ void launch_step_f64(cavity *h, const StepArgs &a) {
 }
 
 // `after_finalise`: the launch directly follows, in the same stream capture,
-// the finalise of the previous step (the second step of a two-step graph with
-// no cut faces).  The FP32 step kernel is then launched as a programmatic
-// dependent: its prologue (TMA loads of the state, which the previous step
-// kernel completed before that finalise started) overlaps the finalise, and it
-// waits for the finalise before reading dt and the centre shift.  Every other
-// predecessor (an unpack writing ghost layers, a state upload, a copy) gets a
-// plain launch.
+// the finalise of the previous step (the second step of a two-step graph).
+// The FP32 step kernel is then launched as a programmatic dependent: its
+// prologue (TMA loads of the state, which the previous step kernel completed
+// before that finalise started) overlaps the finalise, and it waits for the
+// finalise before reading dt and the centre shift.  With cut faces that
+// finalise also exchanges the ghost layers, so a tile whose boxes reach a
+// ghost layer waits for it before its first load.  Every other predecessor
+// (an unpack writing ghost layers, a state upload, a copy) gets a plain
+// launch.
 void launch_step_kernel(cavity *h, int parity, bool after_finalise = false) {
   if (h->f32) {
     cudaLaunchAttribute attr[1];
@@ -574,7 +578,7 @@ void launch_step_kernel(cavity *h, int parity, bool after_finalise = false) {
     cfg.gridDim = dim3(h->n_step);
     cfg.stream = h->stream;
     cfg.attrs = attr;
-    cfg.numAttrs = after_finalise && h->n_cut == 0 ? 1 : 0;
+    cfg.numAttrs = after_finalise ? 1 : 0;
     const StepF32Args sa = step_f32_args(h, parity);
 #define BDC_LAUNCH(P, TY, R)                                                     \
   if (h->f32_p == P && h->ty == TY && h->f32_r == R) {                            \
@@ -606,19 +610,31 @@ void launch_spectral(cavity *h) {
 // kernel (k_bc) writes the walls and the Nusselt partials, k_finalize reduces
 // the partials and advances the state.  The FP32 step kernel applies the
 // walls where it reads them and leaves the Nusselt sums in its own partials,
-// so after its steps only k_finalize runs.
+// so after its steps only k_finalize runs.  After a step of a decomposed
+// cavity the finalise launch carries one more CTA per 256 cut-face
+// positions, which exchange the new state's cut faces (Section 4.5 pack and
+// unpack in one pass) beside the reductions: one launch after the step
+// instead of a finalise beside a pack and an unpack.
 void launch_bc_kernel(cavity *h, int parity, int mode) {
   const int nfin = h->ncav * kFinSlices;
+  BcArgs b = bc_args(h, parity, h->f32 && mode == 0 ? 4 : mode);
+  int grid = nfin;
+  if (mode == 0 && h->n_cut > 0) {
+    b.cuts = h->d_cut;
+    b.ncuts = (int)h->hcut.size();
+    b.xbuf = h->d_xbuf;
+    grid += h->n_cut;
+  }
   if (h->f32) {
     if (mode == 0) {
-      k_finalize<float><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity, 4), h->d_fin);
+      k_finalize<float><<<grid, kFinThreads, 0, h->stream>>>(b, h->d_fin);
       return;
     }
     k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
     if (mode != 3) k_finalize<float><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity, mode), h->d_fin);
   } else {
     k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
-    if (mode != 3) k_finalize<double><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity, mode), h->d_fin);
+    if (mode != 3) k_finalize<double><<<grid, kFinThreads, 0, h->stream>>>(b, h->d_fin);
   }
 }
 
@@ -681,39 +697,14 @@ int launch_step_overlapped(cavity *h, int parity) {
 }
 
 // one explicit step reading buffer set `parity`, leaving the new state in parity ^ 1
+// (the exchange of a decomposed cavity runs inside the finalise launch)
 int launch_step(cavity *h, int parity, bool after_finalise = false) {
   if (h->overlap) return launch_step_overlapped(h, parity);
-  if (h->n_cut > 0 && h->side) {
-    // With cut faces the exchange (pack + unpack, which read the new state --
-    // FP64: after the wall kernel -- and write ghost layers) and the finalise
-    // (which reads the partials and writes the per-cavity scalars) share no
-    // data: two branches of the step graph, joined before the next step
-    launch_step_kernel(h, parity);
-    CK(cudaGetLastError());
-    if (!h->f32) {
-      k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0));
-      CK(cudaGetLastError());
-    }
-    CK(cudaEventRecord(h->ev_shell, h->stream));
-    CK(cudaStreamWaitEvent(h->side, h->ev_shell, 0));
-    launch_pack(h, parity ^ 1, h->side);
-    launch_unpack(h, parity ^ 1, h->side);
-    CK(cudaGetLastError());
-    CK(cudaEventRecord(h->ev_exch, h->side));
-    const int nfin = h->ncav * kFinSlices;
-    if (h->f32)
-      k_finalize<float><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 4), h->d_fin);
-    else
-      k_finalize<double><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity ^ 1, 0), h->d_fin);
-    CK(cudaGetLastError());
-    CK(cudaStreamWaitEvent(h->stream, h->ev_exch, 0));
-    return CAVITY_OK;
-  }
   launch_step_kernel(h, parity, after_finalise);
   CK(cudaGetLastError());
   launch_bc_kernel(h, parity ^ 1, 0);
   CK(cudaGetLastError());
-  return launch_exchange(h, parity ^ 1);
+  return CAVITY_OK;
 }
 
 // walls, ghosts, dt and Nusselt of the state in the current buffer set (no step)
@@ -1651,9 +1642,8 @@ int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
     cudaEventRecord(ev[1], h->stream);
     launch_bc_kernel(h, par ^ 1, 0);
     cudaEventRecord(ev[2], h->stream);
-    if (h->n_cut > 0) launch_pack(h, par ^ 1);
+    // (the exchange runs inside the finalise launch: nothing here)
     cudaEventRecord(ev[3], h->stream);
-    if (h->n_cut > 0) launch_unpack(h, par ^ 1);
     cudaEventRecord(ev[4], h->stream);
     cudaError_t e = cudaEventSynchronize(ev[4]);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -1668,7 +1658,7 @@ int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
   }
   for (auto &e : ev) cudaEventDestroy(e);
   for (int q = 0; q < 4; ++q) ms[q] = acc[q] / nsteps;
-  if (h->n_cut == 0) ms[2] = ms[3] = 0.0;
+  ms[2] = ms[3] = 0.0;
   return rc;
 }
 

@@ -386,6 +386,48 @@ def test_fp32_ghosts_and_buffers_bit_exact(m):
                 assert np.array_equal(out, exp), (b, face)
 
 
+@pytest.mark.parametrize("shape", ["8,16,4,3", "16,32,5,3"])
+def test_fp32_exchange_straddling_tiles(m, monkeypatch, shape):
+    """The step's exchange (Section 4.5 pack and unpack) with blocks of
+    33 x 17 x 17, so that these tile shapes split a face's two p layers
+    (n-1, n) across x tiles, y tiles and z chunks: the result equals one
+    block bit for bit, and a second pack + unpack of the same state changes
+    no ghost node and no buffer entry."""
+    monkeypatch.setenv("BDC_F32_TILE", shape)
+    L = m.load_library()
+    kw = dict(precision=m.CAVITY_FP32_MIXED, seed=5, noise_amp=1e-3, Ra=2e5)
+    with m.Cavity(66, 34, 34, **kw) as ref, m.Cavity(66, 34, 34, blocks=(2, 2, 2), **kw) as c:
+        ref.step(40)
+        c.step(40)
+        assert np.array_equal(c.fields(), ref.fields())
+
+        def snapshot():
+            arrs = [[m.cavity_get_block_array(c.h, b, f)[0] for f in range(7)] for b in range(8)]
+            bufs = []
+            for b in range(8):
+                coords = [b % 2, (b // 2) % 2, b // 4]
+                n = m.cavity_get_block_array(c.h, b, 0)[1][:3]
+                for face in range(6):
+                    a, hi = face // 2, face % 2
+                    if not (0 <= coords[a] + (1 if hi else -1) < 2):
+                        continue
+                    nb, nc = [n[d] for d in range(3) if d != a]
+                    out = np.empty(9 * nb * nc)
+                    assert L.cavity_get_face_buffer(c.h, b, face, out.ctypes.data_as(m._dp), out.size) == 0
+                    bufs.append(out)
+            return arrs, bufs
+
+        arrs0, bufs0 = snapshot()
+        m.cavity_exchange(c.h)
+        arrs1, bufs1 = snapshot()
+        for b in range(8):
+            for f in range(7):
+                assert np.array_equal(arrs0[b][f], arrs1[b][f]), (shape, b, f)
+        assert len(bufs0) == 24
+        for x, y in zip(bufs0, bufs1):
+            assert np.array_equal(x, y)
+
+
 def test_fp32_set_fields_wall_field_and_nonfinite(m):
     n = (28, 22, 19)
     q = workloads.smooth_state(n, seed=3)
