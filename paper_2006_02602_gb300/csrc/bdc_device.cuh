@@ -758,14 +758,13 @@ template <class S>
 __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C, S *base, int face,
                                            int c1, int c2, const double *t_wall, double &nu_h,
                                            double &nu_c, S *other = nullptr) {
+  // wall node: coordinate w on the face axis, c1 on the face's faster axis (y
+  // for x faces, else x), c2 on the slower one (z, except y for z faces)
   const int axis = face >> 1, high = face & 1;
-  const int n[3] = {B.nx, B.ny, B.nz};
-  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
-  const int w = high ? n[axis] + 1 : 0;
+  const int na = axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz);
+  const int w = high ? na + 1 : 0;
   const int s = high ? -1 : 1;
-  int iw[3];
-  iw[axis] = w; iw[a1] = c1; iw[a2] = c2;
-  const long long W = node_index<S>(B, iw[0], iw[1], iw[2]);
+  const long long W = node_index<S>(B, axis == 0 ? w : c1, axis == 0 ? c1 : (axis == 1 ? w : c2), axis == 2 ? w : c2);
   const long long step = axis == 0 ? 1 : (axis == 1 ? (long long)B.pitch : B.plane);
   const long long N1 = W + s * step, N2 = W + 2 * s * step, G = W - s * step;
   const long long fs = B.fstride;
@@ -780,7 +779,7 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
   store_p<S>(base, fs, G, 2.0 * pw - p1);
   const double T1 = load_T<S>(base, fs, N1), T2 = load_T<S>(base, fs, N2);
   if (axis == 0) {
-    const int J = B.oy + iw[1], K = B.oz + iw[2];
+    const int J = B.oy + c1, K = B.oz + c2;
     const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
     const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
     if (other) {
@@ -921,15 +920,6 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   a.counter[cav] = 0u;
 }
 
-__device__ __forceinline__ int find_face(const WallFace *faces, int nfaces, int cta) {
-  int lo = 0, hi = nfaces - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (faces[mid].cta_begin <= cta) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // k_bc: wall conditions of every wall face node and the Nusselt partials of
 // the x walls, one partial pair per CTA (reduced by k_finalize).
 template <class S>
@@ -940,10 +930,18 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
   if (cta == 0 && a.sfloor)
     for (int c = tid; c < a.ncav; c += kBcThreads) a.sfloor[c] = 0u;
   double nu_h = 0.0, nu_c = 0.0;
+  bool xwall = false;
   if (a.nfaces > 0) {
-    const int fi = find_face(a.faces, a.nfaces, cta);
+    // the face of this CTA: the last one whose first CTA is not after it (a warp-wide search)
+    int fi = 0;
+    for (int base = 0; base < a.nfaces; base += 32) {
+      const int l = base + (tid & 31);
+      const unsigned m = __ballot_sync(0xffffffffu, l < a.nfaces && a.faces[l].cta_begin <= cta);
+      if (m) fi = base + 31 - __clz(m);
+    }
     const WallFace &F = a.faces[fi];
     const int e = (cta - F.cta_begin) * kBcThreads + tid;
+    xwall = (F.face >> 1) == 0;
     if (e < F.n1 * F.n2) {
       const BlockDev &B = a.blocks[F.block];
       apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
@@ -951,6 +949,13 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
     }
   }
   if (a.mode == 3) return;  // walls only (a stored state's walls made explicit), no reductions
+  if (!xwall) {  // only the x walls carry Nusselt sums (a CTA covers one face)
+    if (tid == 0) {
+      a.bc_partials[2LL * cta] = 0.0;
+      a.bc_partials[2LL * cta + 1] = 0.0;
+    }
+    return;
+  }
   nu_h = warp_sum(nu_h);
   nu_c = warp_sum(nu_c);
   if ((tid & 31) == 0) { sh[(tid >> 5) * 2] = nu_h; sh[(tid >> 5) * 2 + 1] = nu_c; }
