@@ -528,6 +528,7 @@ struct F32QAcc {
   float smax;
   float2 ch, cl;
   float wsh, wsl;
+  float wch, wcl;  // the cold wall's T when the pair also borders the hot wall (nx = 2)
 };
 
 // One plane of one thread's node pair: rates and update of the pair at plane
@@ -662,6 +663,8 @@ __device__ __forceinline__ void f32q_pair(const float *S0, const float *Sp1, con
   if (nus_warp) {
     acc_pair(ch, cl, o.th, o.tl);
     acc_pair(wsh, wsl, S0[TO + col + wofs], S0[TO + AOS + col + wofs]);
+    // a pair (1, 2) with nx = 2 borders both x walls: the cold wall is node 3
+    if (wofs == -1) acc_pair(acc.wch, acc.wcl, S0[TO + col + 2], S0[TO + AOS + col + 2]);
   }
   // the register queues move one plane: z - 2 <- z - 1 (p), z - 1 <- this plane
   qm2h = qm1[0];
@@ -712,6 +715,7 @@ __device__ __forceinline__ void f32q_clear(F32QAcc &acc) {
   acc.smax = 0.f;
   acc.ch = acc.cl = z;
   acc.wsh = acc.wsl = 0.f;
+  acc.wch = acc.wcl = 0.f;
 }
 
 // The tile's partials (every thread of the CTA calls it: a CTA reduction).
@@ -722,8 +726,10 @@ __device__ __forceinline__ void f32q_finish(double *partials, int tile, int tid,
   if (c.nus) {
     const double t0 = pair_value(acc.ch.x, acc.cl.x), t1 = c.act1 ? pair_value(acc.ch.y, acc.cl.y) : 0.0;
     const double wall_t = 3.0 * pair_value(acc.wsh, acc.wsl);
+    // the cold wall's sum: the second accumulator where the pair borders both walls
+    const double wall_c = c.hot_next ? 3.0 * pair_value(acc.wch, acc.wcl) : wall_t;
     nuh = c.wh0 * t0 + c.wh1 * t1 + (c.hot_next ? wall_t : 0.0);
-    nuc = c.wc0 * t0 + c.wc1 * t1 + (c.cold_next ? wall_t : 0.0);
+    nuc = c.wc0 * t0 + c.wc1 * t1 + (c.cold_next ? wall_c : 0.0);
   }
   f32_partials<NT>(partials, tile, tid, vadd(acc.s0.x, acc.s0.y), vadd(acc.s1.x, acc.s1.y), vadd(acc.s2.x, acc.s2.y),
                    vadd(acc.s3.x, acc.s3.y), vadd(acc.s4.x, acc.s4.y), acc.smax, nuh, nuc, T.wxl || T.wxh);

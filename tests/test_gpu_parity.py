@@ -295,11 +295,12 @@ def test_fp32_config1_32cube_200_steps(m):
         assert c.time[2] == pytest.approx(o.p["cfl"] / o.spectral_max(), rel=1e-5)
 
 
-@pytest.mark.parametrize("n", [(37, 21, 18), (2, 2, 2), (65, 9, 40), (33, 17, 70)])
+@pytest.mark.parametrize("n", [(37, 21, 18), (2, 2, 2), (2, 11, 9), (3, 10, 7), (65, 9, 40), (33, 17, 70)])
 def test_fp32_ragged_and_degenerate_sizes(m, n):
     """Small and ragged cavities: p, u, w and T against their own max-norm; v,
     which the y-mirror symmetry of the cavity keeps near zero (only the noise
-    breaks it), against the maximum speed."""
+    breaks it), against the maximum speed; both Nusselt numbers (nx = 2 puts
+    both x walls beside one node pair)."""
     o, c = run_pair32(m, n, 3e4, 25, noise=1e-3, seed=11)
     with c:
         g, ref = c.fields(), o.fields()
@@ -308,6 +309,9 @@ def test_fp32_ragged_and_degenerate_sizes(m, n):
             scale = speed if f == 2 else np.max(np.abs(ref[f]))
             e = np.max(np.abs(g[f] - ref[f])) / scale
             assert e <= FP32_TOL, f"fp32 n={n} field {name}: {e:.3e}"
+        h, cold = c.nusselt
+        assert abs(h - o.nusselt[0]) <= NU32_TOL * abs(o.nusselt[0]), (n, h, o.nusselt)
+        assert abs(cold - o.nusselt[1]) <= NU32_TOL * abs(o.nusselt[1]), (n, cold, o.nusselt)
 
 
 @pytest.mark.parametrize("blocks", DECOMPS)
