@@ -51,6 +51,8 @@ def test_fp64_local_matches_oracle(m):
         assert np.allclose(c.residual, o.residual, rtol=1e-10)
         steps, t, dt = c.time
         assert steps == 60 and t == pytest.approx(o.t, rel=1e-12)
+        for got, want in zip(c.nusselt, o.nusselt):
+            assert got == pytest.approx(want, rel=1e-12)
 
 
 @pytest.mark.parametrize("blocks", [(2, 2, 2), (3, 2, 2)])
@@ -96,5 +98,7 @@ def test_fp32_local_matches_oracle_and_shapes_agree(m, monkeypatch):
                 scale = speed if f == 2 else np.max(np.abs(ref[f]))
                 e = np.max(np.abs(g[f] - ref[f])) / scale
                 assert e <= FP32_TOL, (shape, f, e)
+            for got, want in zip(c.nusselt, o.nusselt):
+                assert abs(got - want) <= 1e-4 * abs(want), (shape, c.nusselt, o.nusselt)
             out.append(g)
     assert np.array_equal(out[0], out[1])

@@ -76,12 +76,17 @@ def test_config1_32cube_200_steps(m):
         assert dt == pytest.approx(o.p["cfl"] / o.spectral_max(), rel=1e-13)
 
 
-@pytest.mark.parametrize("n", [(37, 21, 18), (2, 2, 2), (3, 40, 5), (65, 9, 33)])
+@pytest.mark.parametrize("n", [(37, 21, 18), (2, 2, 2), (2, 11, 9), (3, 40, 5), (65, 9, 33)])
 def test_ragged_and_degenerate_sizes(m, n):
     o, c = run_pair(m, n, 3e4, 25, noise=1e-3, seed=11)
     with c:
         assert_fields_close(c.fields(), o.fields(), FP64_TOL, f"n={n}")
         assert np.allclose(c.residual, o.residual, rtol=1e-10, atol=1e-300)
+        h, cold = c.nusselt
+        assert h == pytest.approx(o.nusselt[0], rel=1e-12) and cold == pytest.approx(o.nusselt[1], rel=1e-12)
+        s_, t, dt = c.time
+        assert s_ == 25 and t == pytest.approx(o.t, rel=1e-13)
+        assert dt == pytest.approx(o.p["cfl"] / o.spectral_max(), rel=1e-13)
 
 
 @pytest.mark.parametrize("gaxis", [1, 2])
@@ -312,6 +317,8 @@ def test_fp32_ragged_and_degenerate_sizes(m, n):
         h, cold = c.nusselt
         assert abs(h - o.nusselt[0]) <= NU32_TOL * abs(o.nusselt[0]), (n, h, o.nusselt)
         assert abs(cold - o.nusselt[1]) <= NU32_TOL * abs(o.nusselt[1]), (n, cold, o.nusselt)
+        assert np.allclose(c.residual, o.residual, rtol=1e-3), (n, c.residual, o.residual)
+        assert c.time[0] == 25 and c.time[1] == pytest.approx(o.t, rel=1e-5)
 
 
 @pytest.mark.parametrize("blocks", DECOMPS)
@@ -339,6 +346,8 @@ def test_fp32_tile_shapes_ragged(m, monkeypatch, shape):
                 scale = speed if f == 2 else np.max(np.abs(ref[f]))
                 e = np.max(np.abs(g[f] - ref[f])) / scale
                 assert e <= FP32_TOL, f"fp32 {shape} n={n} field {name}: {e:.3e}"
+            for got, want in zip(c.nusselt, o.nusselt):
+                assert abs(got - want) <= NU32_TOL * abs(want), (shape, n, c.nusselt, o.nusselt)
     kw = dict(precision=m.CAVITY_FP32_MIXED, seed=9, noise_amp=1e-3, Ra=1e5)
     with m.Cavity(47, 40, 44, **kw) as ref, m.Cavity(47, 40, 44, blocks=(3, 2, 2), **kw) as c:
         ref.step(60)
