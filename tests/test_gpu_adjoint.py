@@ -41,7 +41,7 @@ def gpu_gradient(m, n, Ra, steps, ckpt, theta, precision=None, seed=3, noise=1e-
         return J, g, gra, c.time
 
 
-@pytest.mark.parametrize("n,Ra,steps,ckpt", [((32, 32, 32), 1e5, 40, 10), ((17, 14, 11), 2e4, 23, 6)])
+@pytest.mark.parametrize("n,Ra,steps,ckpt", [((32, 32, 32), 1e5, 40, 10), ((17, 14, 11), 2e4, 23, 6), ((2, 9, 7), 1e4, 12, 5)])
 def test_adjoint_matches_oracle_adjoint(m, n, Ra, steps, ckpt):
     theta = workloads.wall_temperature(n[1], n[2], seed=5)
     Jo, go, grao = oracle.nusselt_gradient(*n, dict(Ra=Ra, Pr=0.71), steps, seed=3, noise=1e-3, t_hot_wall=theta)
@@ -51,11 +51,12 @@ def test_adjoint_matches_oracle_adjoint(m, n, Ra, steps, ckpt):
     assert gra == pytest.approx(grao, rel=1e-9)
 
 
-def test_adjoint_fp32_forward_matches_oracle(m):
-    n, Ra, steps = (32, 32, 32), 1e5, 40
+@pytest.mark.parametrize("n,steps,ckpt", [((32, 32, 32), 40, 8), ((17, 14, 11), 23, 6), ((2, 9, 7), 12, 5)])
+def test_adjoint_fp32_forward_matches_oracle(m, n, steps, ckpt):
+    Ra = 1e5
     theta = workloads.wall_temperature(n[1], n[2], seed=5)
     Jo, go, grao = oracle.nusselt_gradient(*n, dict(Ra=Ra, Pr=0.71), steps, seed=3, noise=1e-3, t_hot_wall=theta)
-    J, g, gra, _ = gpu_gradient(m, n, Ra, steps, 8, theta, precision=m.CAVITY_FP32_MIXED)
+    J, g, gra, _ = gpu_gradient(m, n, Ra, steps, ckpt, theta, precision=m.CAVITY_FP32_MIXED)
     assert J == pytest.approx(Jo, rel=1e-5)
     assert np.max(np.abs(g - go)) <= 1e-4 * np.max(np.abs(go))
     assert gra == pytest.approx(grao, rel=1e-4)
