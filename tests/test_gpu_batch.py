@@ -36,22 +36,25 @@ def relmax(a, b):
 
 
 SMALL = workloads.batch_cavities(ncav=6, nmin=12, nmax=33)
+# degenerate members: two nodes across the x walls, two along y or z
+TINY = [dict(n=(2, 9, 7), Ra=2e4, seed=21), dict(n=(5, 2, 3), Ra=5e3, seed=22), dict(n=(3, 4, 2), Ra=1e4, seed=23)]
 
 
 def _params(m, cav):
     return m.cavity_default_params(Ra=cav["Ra"], Pr=0.71)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_members_match_oracle(m, prec):
+@pytest.mark.parametrize("prec,members", [("fp64", "small"), ("fp32", "small"), ("fp64", "tiny"), ("fp32", "tiny")])
+def test_batch_members_match_oracle(m, prec, members):
     precision = m.CAVITY_FP64 if prec == "fp64" else m.CAVITY_FP32_MIXED
+    cavs = SMALL if members == "small" else SMALL[:2] + TINY
     steps = 30
-    h = m.cavity_create_batch([c["n"] for c in SMALL], [_params(m, c) for c in SMALL], precision=precision,
-                              seeds=[c["seed"] for c in SMALL], noise_amp=1e-3)
+    h = m.cavity_create_batch([c["n"] for c in cavs], [_params(m, c) for c in cavs], precision=precision,
+                              seeds=[c["seed"] for c in cavs], noise_amp=1e-3)
     try:
-        assert m.cavity_batch_size(h) == len(SMALL)
+        assert m.cavity_batch_size(h) == len(cavs)
         m.cavity_step(h, steps)
-        for b, cav in enumerate(SMALL):
+        for b, cav in enumerate(cavs):
             o = oracle.OracleCavity(*cav["n"], dict(Ra=cav["Ra"], Pr=0.71), noise=1e-3, seed=cav["seed"])
             o.step(steps)
             g = m.cavity_batch_get_fields(h, b, cav["n"])
