@@ -137,6 +137,35 @@ CAVITY_API int cavity_set_wall_temperature(cavity_t *h, int wall, const double *
  * CAVITY_ERR_INVALID_ARG for nsteps < 0. */
 CAVITY_API int cavity_step(cavity_t *h, int nsteps);
 
+/* One step's record in a step log (cavity_set_step_log): the state's counters
+ * and diagnostics after the step, as the getters would return them then
+ * (step count, time, the next dt, the residual norms of Section 4.2, the
+ * Nusselt numbers, flags: bit 0 non-finite, bit 1 a timed-out wait). */
+typedef struct {
+  long long step;
+  double t, dt;
+  double res[5];
+  double nu_hot, nu_cold;
+  long long flags;
+} cavity_step_record;
+
+/* Step log in host memory: after each step the device writes that step's
+ * record of cavity c (0 for a single cavity) to host[((step - 1) % capacity)
+ * * ncav + c], in the launch that finishes the step, so a caller that wants
+ * every step's diagnostics reads them from host memory when it next
+ * synchronises, without a synchronising getter per step.  host must be
+ * page-locked host memory (cudaHostAlloc, cudaHostRegister, a pinned torch
+ * tensor) of capacity * ncav records, kept alive while attached; NULL
+ * detaches.  Records of steps the adjoint's reverse sweep recomputes are
+ * written again.  CAVITY_ERR_INVALID_ARG for capacity < 1 or memory the device
+ * cannot address. */
+CAVITY_API int cavity_set_step_log(cavity_t *h, cavity_step_record *host, long long capacity);
+
+/* Page-locked, zeroed host memory for `records` step records (records >= 1),
+ * and its release; CAVITY_ERR_OOM if the allocation fails. */
+CAVITY_API int cavity_step_log_alloc(long long records, cavity_step_record **out);
+CAVITY_API int cavity_step_log_free(cavity_step_record *p);
+
 /* RMS over the interior of dq/dt of the last step, p, u, v, w, T
  * (Section 4.2 residual norms).  Zeros before the first step.
  * Returns CAVITY_ERR_NONFINITE (after filling out) once a step produced

@@ -46,7 +46,8 @@ EXPORTED = (
     "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
     "cavity_batch_get_fields", "cavity_autotune", "cavity_adjoint_forward", "cavity_adjoint_backward",
     "cavity_set_time_stepping", "cavity_set_overlap", "cavity_check_sqrt", "cavity_test_wait_timeout",
-    "cavity_measure_fp64_peak", "cavity_adjoint_kernel_ms",
+    "cavity_measure_fp64_peak", "cavity_adjoint_kernel_ms", "cavity_set_step_log", "cavity_step_log_alloc",
+    "cavity_step_log_free",
 )
 
 
@@ -118,6 +119,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_test_wait_timeout": ([_H, ctypes.c_longlong, ctypes.c_int], ctypes.c_int),
         "cavity_measure_fp64_peak": ([ctypes.c_int, _dp], ctypes.c_int),
         "cavity_adjoint_kernel_ms": ([_H, _dp], ctypes.c_int),
+        "cavity_set_step_log": ([_H, ctypes.c_void_p, ctypes.c_longlong], ctypes.c_int),
+        "cavity_step_log_alloc": ([ctypes.c_longlong, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "cavity_step_log_free": ([ctypes.c_void_p], ctypes.c_int),
         "cavity_sync": ([_H], ctypes.c_int),
         "cavity_destroy": ([_H], ctypes.c_int),
         "cavity_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -379,6 +383,53 @@ def cavity_strerror(code: int) -> str:
 
 def cavity_last_error(h) -> str:
     return load_library().cavity_last_error(h).decode()
+
+
+# the C ABI's cavity_step_record
+STEP_RECORD = np.dtype([("step", np.int64), ("t", np.float64), ("dt", np.float64), ("res", np.float64, (5,)),
+                        ("nu_hot", np.float64), ("nu_cold", np.float64), ("flags", np.int64)])
+
+
+class StepLog:
+    """Page-locked host memory for `records` step records (cavity_step_log_alloc),
+    viewed as a numpy structured array of STEP_RECORD; freed by close()."""
+
+    def __init__(self, records: int):
+        self.records = int(records)
+        ptr = ctypes.c_void_p()
+        _check(load_library().cavity_step_log_alloc(self.records, ctypes.byref(ptr)))
+        self.ptr = ptr.value
+        buf = (ctypes.c_char * (self.records * STEP_RECORD.itemsize)).from_address(self.ptr)
+        self.array = np.frombuffer(buf, dtype=STEP_RECORD)
+
+    def close(self) -> None:
+        if getattr(self, "ptr", None):
+            self.array = None
+            load_library().cavity_step_log_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cavity_step_log_alloc(records: int) -> StepLog:
+    return StepLog(records)
+
+
+def cavity_step_log_free(log: StepLog) -> None:
+    log.close()
+
+
+def cavity_set_step_log(h, log: "StepLog | None", capacity: int | None = None) -> None:
+    """Attach `log` (a StepLog; capacity records per cavity, default all of them) or detach (None)."""
+    if log is None:
+        _check(load_library().cavity_set_step_log(h, None, 0), h)
+    else:
+        cap = log.records if capacity is None else int(capacity)
+        _check(load_library().cavity_set_step_log(h, ctypes.c_void_p(log.ptr), cap), h)
 
 
 # -- convenience object -------------------------------------------------------

@@ -154,6 +154,14 @@ struct CavState {
   int pad;
 };
 
+struct StepRecord {   // one step's record in the host-memory step log (the C ABI's cavity_step_record)
+  long long step;
+  double t, dt;
+  double res[5];
+  double nu_hot, nu_cold;
+  long long flags;
+};
+
 struct WallFace {     // one wall face of one block, processed by k_bc
   int block, face;
   int n1, n2;         // face interior extents (faster, slower face axis)
@@ -744,6 +752,8 @@ struct BcArgs {
   const CutFace *cuts;        // after a step with cut faces: the exchange of the new state, run by
   int ncuts;                  //   the CTAs after the finalise CTAs (null / 0: none)
   void *xbuf;
+  StepRecord *log;            // after a step: the step log (host memory), or null
+  long long log_cap;          // its records per cavity
   int mode;                   // 0 after a step, 1 after init / set_fields,
                               // 3 walls only (k_bc), no reductions,
                               // 4 after an FP32 step (k_finalize only): Nusselt
@@ -917,6 +927,16 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   st.nu_hot = sht[6] * C.inv_nwall;
   st.nu_cold = sht[7] * C.inv_nwall;
   if (bad) st.flags |= 1;
+  if (a.log && a.mode != 1) {  // this step's record, written to host memory
+    StepRecord &r = a.log[((st.step - 1) % a.log_cap) * a.ncav + cav];
+    r.step = st.step;
+    r.t = st.t;
+    r.dt = st.dt;
+    for (int f = 0; f < 5; ++f) r.res[f] = st.res[f];  // written by threads 0..4 before the barrier
+    r.nu_hot = st.nu_hot;
+    r.nu_cold = st.nu_cold;
+    r.flags = st.flags;
+  }
   a.counter[cav] = 0u;
 }
 

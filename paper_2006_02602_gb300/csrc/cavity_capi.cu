@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cfloat>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -149,6 +150,8 @@ struct cavity {
   CUtensorMap *d_maps = nullptr;
   double *d_step_part = nullptr, *d_bc_part = nullptr, *d_twall = nullptr, *d_stage = nullptr;
   double *d_fin = nullptr;  // k_finalize slice totals [ncav][kFinSlices][8]
+  StepRecord *d_log = nullptr;  // the step log (device address of caller-owned host memory), or null
+  long long log_cap = 0;
   unsigned int *d_counter = nullptr;  // [ncav] k_bc CTAs done per cavity, the FP64 step's tile counter,
                                       // [ncav] the FP64 step's dt-filter floors
   int persist_ctas = 0;               // CTAs of the persistent FP64 step kernel that fit on the GPU
@@ -538,6 +541,8 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.sfloor = h->d_counter + h->ncav + 1;
   a.t_wall = h->d_twall; a.parity = parity; a.mode = mode;
   a.shell_begin = a.shell_end = 0;
+  a.log = mode == 1 || mode == 3 ? nullptr : h->d_log;  // after a step (modes 0, 4): the step log
+  a.log_cap = h->log_cap;
   a.cuts = nullptr; a.ncuts = 0; a.xbuf = nullptr;
   return a;
 }
@@ -1138,6 +1143,47 @@ int cavity_batch_state(cavity_t *h, int cav, double out[10]) {
 int cavity_batch_get_fields(cavity_t *h, int cav, int mask, double *host, size_t count) {
   if (!h) return CAVITY_ERR_INVALID_ARG;
   return get_fields_cav(h, cav, mask, host, count);
+}
+
+static_assert(sizeof(StepRecord) == sizeof(cavity_step_record), "step record layout");
+static_assert(offsetof(StepRecord, flags) == offsetof(cavity_step_record, flags), "step record layout");
+
+int cavity_set_step_log(cavity_t *h, cavity_step_record *host, long long capacity) {
+  if (!h) return CAVITY_ERR_INVALID_ARG;
+  DeviceGuard g(h->dev);
+  StepRecord *dev = nullptr;
+  if (host) {
+    if (capacity < 1) return fail(h, CAVITY_ERR_INVALID_ARG, "step log: capacity < 1");
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, host) != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+      cudaGetLastError();
+      return fail(h, CAVITY_ERR_INVALID_ARG, "step log: not page-locked host memory the device can address");
+    }
+    dev = (StepRecord *)pa.devicePointer;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  h->d_log = dev;
+  h->log_cap = host ? capacity : 0;
+  return build_graphs(h);  // the finalise launches in the graphs carry the log
+}
+
+int cavity_step_log_alloc(long long records, cavity_step_record **out) {
+  if (!out || records < 1 || records > (1LL << 32)) return CAVITY_ERR_INVALID_ARG;
+  *out = nullptr;
+  void *p = nullptr;
+  const size_t bytes = (size_t)records * sizeof(cavity_step_record);
+  if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    return CAVITY_ERR_OOM;
+  }
+  std::memset(p, 0, bytes);
+  *out = (cavity_step_record *)p;
+  return CAVITY_OK;
+}
+
+int cavity_step_log_free(cavity_step_record *p) {
+  if (p && cudaFreeHost(p) != cudaSuccess) return CAVITY_ERR_CUDA;
+  return CAVITY_OK;
 }
 
 int cavity_residual(cavity_t *h, double out[5]) {
