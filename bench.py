@@ -381,7 +381,10 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
         # device into page-locked host memory (the step log) as the step
         # finishes, read on the host after the final synchronisation; final
         # fields back to host
-        host0 = c.fields()
+        # the initial state and the final fields in page-locked host memory
+        host0 = torch.empty(tuple(c.fields().shape), dtype=torch.float64, pin_memory=True).numpy()
+        c.fields(out=host0)
+        host1 = torch.empty(host0.shape, dtype=torch.float64, pin_memory=True).numpy()
         e2e_steps = max(1, min(steps, 500))
         log = m.StepLog(e2e_steps)
         m.cavity_set_step_log(c.h, log)
@@ -390,7 +393,7 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
         t0 = time.perf_counter()
         c.set_fields(host0)
         c.step(e2e_steps)
-        res = c.fields()  # synchronises: every record is in host memory
+        res = c.fields(out=host1)  # synchronises: every record is in host memory
         recs = log.array.copy()
         t1 = time.perf_counter()
         barrier()

@@ -205,10 +205,15 @@ def _nfields(mask: int) -> int:
     return bin(mask & CAVITY_FIELD_ALL).count("1")
 
 
-def cavity_get_fields(h, shape: tuple[int, int, int], mask: int = CAVITY_FIELD_ALL) -> np.ndarray:
-    """Interior fields as an array [nf, nz, ny, nx] (shape = (nx, ny, nz))."""
+def cavity_get_fields(h, shape: tuple[int, int, int], mask: int = CAVITY_FIELD_ALL, out=None) -> np.ndarray:
+    """Interior fields as an array [nf, nz, ny, nx] (shape = (nx, ny, nz)); `out`: a C-contiguous
+    float64 array of that shape to fill (page-locked memory copies at the full link rate)."""
     nx, ny, nz = shape
-    out = np.empty((_nfields(mask), nz, ny, nx))
+    want = (_nfields(mask), nz, ny, nx)
+    if out is None:
+        out = np.empty(want)
+    elif out.shape != want or out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be a C-contiguous float64 array of shape %s" % (want,))
     _check(load_library().cavity_get_fields(h, int(mask), out.ctypes.data_as(_dp), out.size), h)
     return out
 
@@ -448,8 +453,8 @@ class Cavity:
         cavity_step(self.h, n)
         return self
 
-    def fields(self, mask: int = CAVITY_FIELD_ALL) -> np.ndarray:
-        return cavity_get_fields(self.h, self.shape, mask)
+    def fields(self, mask: int = CAVITY_FIELD_ALL, out=None) -> np.ndarray:
+        return cavity_get_fields(self.h, self.shape, mask, out)
 
     def set_fields(self, values, mask: int = CAVITY_FIELD_ALL) -> None:
         cavity_set_fields(self.h, values, mask)
