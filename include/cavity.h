@@ -379,8 +379,8 @@ CAVITY_API int cavity_measure_fp64_peak(int device, double *tflops);
  * Limit: ceil(nx/32) ceil(ny/8) ceil(nz/16) <= CAVITY_NOALLOC_MAX_TILES
  * (e.g. 256^3 fits, 512^3 does not); larger blocks return
  * CAVITY_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array and it
+ * device address (cudaGetSymbolAddress) with that device current.  All
+ * calls share the array and it
  * keeps the last call's contents (each call rewrites all it reads): calls
  * that overlap on the GPU (other streams, other threads) race and must not
  * be issued. */
