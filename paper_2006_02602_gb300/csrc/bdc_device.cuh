@@ -752,6 +752,7 @@ struct BcArgs {
   const CutFace *cuts;        // after a step with cut faces: the exchange of the new state, run by
   int ncuts;                  //   the CTAs after the finalise CTAs (null / 0: none)
   void *xbuf;
+  int nslices;                // k_finalize CTAs per cavity (1 .. kFinSlices)
   StepRecord *log;            // after a step: the step log (host memory), or null
   long long log_cap;          // its records per cavity
   int mode;                   // 0 after a step, 1 after init / set_fields,
@@ -807,9 +808,10 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
 // Finalise: one cavity's per-CTA partials reduced in a fixed order and its
 // state advanced (residual RMS, spectral maximum -> next dt, Nusselt numbers,
 // time, step count, centre pressure).  GB300's FP64 pipe does about two
-// lanes per clock per SM, so the FP64 sums are spread over kFinSlices CTAs
-// per cavity (contiguous slices of the partials), and the last of them
-// combines the slices in order.  Nusselt sums: the wall kernel's partials
+// lanes per clock per SM, so the FP64 sums are spread over up to kFinSlices
+// CTAs per cavity (BcArgs::nslices, contiguous slices of the partials, about
+// 128 partials a slice), and the last of them combines the slices in order;
+// with one slice that CTA goes straight on to the fold.  Nusselt sums: the wall kernel's partials
 // (modes 0, 1) or the step partials' slots 6 and 7, sums of
 // 3 T_w - 4 T_1 + T_2 (mode 4, FP32 step).  After a step of a decomposed
 // cavity, CTAs after the finalise CTAs exchange the new state's cut faces.
@@ -867,34 +869,39 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   // the next step kernel (a programmatic dependent) may start its prologue now;
   // it waits for this grid's completion before it reads the state advanced here
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if (blockIdx.x >= a.ncav * kFinSlices) {
+  const int nsl = a.nslices;
+  if (blockIdx.x >= a.ncav * nsl) {
     // the exchange of the new state's cut faces, beside the reductions
     const ExchArgs x{a.blocks, a.cuts, a.ncuts, (double *)a.xbuf, a.parity};
-    exchange_cta<S, kFinThreads>(x, blockIdx.x - a.ncav * kFinSlices);
+    exchange_cta<S, kFinThreads>(x, blockIdx.x - a.ncav * nsl);
     return;
   }
-  const int cav = blockIdx.x / kFinSlices, g = blockIdx.x % kFinSlices, tid = threadIdx.x;
+  const int cav = blockIdx.x / nsl, g = blockIdx.x % nsl, tid = threadIdx.x;
   const CavConst &C = a.cc[cav];
   const long long nt = C.tile_end - C.tile_begin, nb = a.mode == 4 ? 0 : C.bc_end - C.bc_begin;
   const long long ns = a.shell_end - a.shell_begin;
   double tf = 0.0;  // thread f < 8: this slice's total of field f
-  reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / kFinSlices, C.tile_begin + nt * (g + 1) / kFinSlices,
-                            C.bc_begin + nb * g / kFinSlices, C.bc_begin + nb * (g + 1) / kFinSlices,
-                            a.shell_begin + ns * g / kFinSlices, a.shell_begin + ns * (g + 1) / kFinSlices, tf, sh,
-                            tid);
-  double *my = mid + ((long long)cav * kFinSlices + g) * 8;
-  if (tid < 8) {
-    my[tid] = tf;
+  reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / nsl, C.tile_begin + nt * (g + 1) / nsl,
+                            C.bc_begin + nb * g / nsl, C.bc_begin + nb * (g + 1) / nsl,
+                            a.shell_begin + ns * g / nsl, a.shell_begin + ns * (g + 1) / nsl, tf, sh, tid);
+  if (nsl == 1) {
+    // the only slice: its totals go straight to the fold
+    if (tid < 8) shm[tid] = tf;
+  } else {
+    double *my = mid + ((long long)cav * kFinSlices + g) * 8;
+    if (tid < 8) {
+      my[tid] = tf;
+      __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) am_last = atomicAdd(a.counter + cav, 1u) == (unsigned int)nsl - 1u;
+    __syncthreads();
+    if (!am_last) return;
     __threadfence();
+    // the slice totals loaded in parallel
+    if (tid < nsl * 8) shm[tid] = mid[(long long)cav * kFinSlices * 8 + tid];
   }
-  __syncthreads();
-  if (tid == 0) am_last = atomicAdd(a.counter + cav, 1u) == (unsigned int)kFinSlices - 1u;
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // the slice totals and the centre pressure of the new state (at most 8
-  // nodes) loaded in parallel, then folded in order by one thread
-  if (tid < kFinSlices * 8) shm[tid] = mid[(long long)cav * kFinSlices * 8 + tid];
+  // the centre pressure of the new state (at most 8 nodes)
   if (a.mode != 1 && tid < C.ncentre) {
     const BlockDev &B = a.blocks[C.centre_blk[tid]];
     shc[tid] = load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[tid]);
@@ -906,7 +913,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   if (tid < 8) {
     const int f = tid;
     double t = shm[f];
-    for (int q = 1; q < kFinSlices; ++q) t = (f == 5) ? fmax(t, shm[q * 8 + f]) : t + shm[q * 8 + f];
+    for (int q = 1; q < nsl; ++q) t = (f == 5) ? fmax(t, shm[q * 8 + f]) : t + shm[q * 8 + f];
     if (a.mode == 4 && f >= 6) t *= (f == 6 ? 0.5 : -0.5) * C.ih[0] * C.inv_dT;  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
     sht[f] = t;
     if (a.mode != 1 && f < 5) st.res[f] = sqrt(t * C.inv_nint);

@@ -139,6 +139,7 @@ struct cavity {
   std::vector<CutFace> hcut;
   long long xbuf_elems = 0;
   int n_step = 0, n_bc = 0, n_cut = 0;
+  int nslices = kFinSlices;  // k_finalize CTAs per cavity: about 128 step partials a slice
   int n_coarse = 0;  // FP64 step tiles of KC planes (scheduled before the fine ones)
   int part_cap = 0;  // step partials allocated (CTAs)
 
@@ -262,6 +263,9 @@ void assign_tiles(cavity *h) {
   }
   h->n_step = tile;
   h->n_coarse = coarse;
+  int most = 0;  // the most tiles of one cavity
+  for (int c = 0; c < h->ncav; ++c) most = std::max(most, h->hcc[c].tile_end - h->hcc[c].tile_begin);
+  h->nslices = std::max(1, std::min(kFinSlices, ceil_div(most, 128)));
 }
 
 int build_layout(cavity *h) {
@@ -544,6 +548,7 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.log = mode == 1 || mode == 3 ? nullptr : h->d_log;  // after a step (modes 0, 4): the step log
   a.log_cap = h->log_cap;
   a.cuts = nullptr; a.ncuts = 0; a.xbuf = nullptr;
+  a.nslices = h->nslices;
   return a;
 }
 
@@ -621,7 +626,7 @@ void launch_spectral(cavity *h) {
 // unpack in one pass) beside the reductions: one launch after the step
 // instead of a finalise beside a pack and an unpack.
 void launch_bc_kernel(cavity *h, int parity, int mode) {
-  const int nfin = h->ncav * kFinSlices;
+  const int nfin = h->ncav * h->nslices;
   BcArgs b = bc_args(h, parity, h->f32 && mode == 0 ? 4 : mode);
   int grid = nfin;
   if (mode == 0 && h->n_cut > 0) {
@@ -696,7 +701,7 @@ int launch_step_overlapped(cavity *h, int parity) {
   k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(ba);
   ba.shell_begin = h->n_step;
   ba.shell_end = (long long)h->n_step + h->n_shell;
-  k_finalize<double><<<h->ncav * kFinSlices, kFinThreads, 0, h->stream>>>(ba, h->d_fin);
+  k_finalize<double><<<h->ncav * h->nslices, kFinThreads, 0, h->stream>>>(ba, h->d_fin);
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
