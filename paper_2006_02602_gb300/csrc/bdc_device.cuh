@@ -753,6 +753,7 @@ struct BcArgs {
   int ncuts;                  //   the CTAs after the finalise CTAs (null / 0: none)
   void *xbuf;
   int nslices;                // k_finalize CTAs per cavity (1 .. kFinSlices)
+  int wall_ctas;              // after an FP64 step: k_bc's CTAs, run in the finalise launch (0: none)
   StepRecord *log;            // after a step: the step log (host memory), or null
   long long log_cap;          // its records per cavity
   int mode;                   // 0 after a step, 1 after init / set_fields,
@@ -856,6 +857,8 @@ __device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long l
 
 template <class S, int NT>
 __device__ __forceinline__ void exchange_cta(const ExchArgs &a, int cta);
+template <class S>
+__device__ __forceinline__ int bc_cta(const BcArgs &a, int cta, bool reduce);
 
 // mid: [ncav][kFinSlices][8] slice totals; a.counter: per cavity, zero between launches
 template <class S>
@@ -869,37 +872,60 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   // the next step kernel (a programmatic dependent) may start its prologue now;
   // it waits for this grid's completion before it reads the state advanced here
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int nsl = a.nslices;
+  const int nsl = a.nslices, tid = threadIdx.x;
+  int cav;
   if (blockIdx.x >= a.ncav * nsl) {
-    // the exchange of the new state's cut faces, beside the reductions
-    const ExchArgs x{a.blocks, a.cuts, a.ncuts, (double *)a.xbuf, a.parity};
-    exchange_cta<S, kFinThreads>(x, blockIdx.x - a.ncav * nsl);
-    return;
-  }
-  const int cav = blockIdx.x / nsl, g = blockIdx.x % nsl, tid = threadIdx.x;
-  const CavConst &C = a.cc[cav];
-  const long long nt = C.tile_end - C.tile_begin, nb = a.mode == 4 ? 0 : C.bc_end - C.bc_begin;
-  const long long ns = a.shell_end - a.shell_begin;
-  double tf = 0.0;  // thread f < 8: this slice's total of field f
-  reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / nsl, C.tile_begin + nt * (g + 1) / nsl,
-                            C.bc_begin + nb * g / nsl, C.bc_begin + nb * (g + 1) / nsl,
-                            a.shell_begin + ns * g / nsl, a.shell_begin + ns * (g + 1) / nsl, tf, sh, tid);
-  if (nsl == 1) {
-    // the only slice: its totals go straight to the fold
-    if (tid < 8) shm[tid] = tf;
+    const int c = blockIdx.x - a.ncav * nsl;
+    if (c >= a.wall_ctas) {
+      // the exchange of the new state's cut faces, beside the reductions
+      const ExchArgs x{a.blocks, a.cuts, a.ncuts, (double *)a.xbuf, a.parity};
+      exchange_cta<S, kFinThreads>(x, c - a.wall_ctas);
+      return;
+    }
+    // a wall CTA (FP64 step): its walls and Nusselt partial, then it arrives
+    // at the cavity's counter like a slice (thread 0 wrote the partial)
+    cav = bc_cta<S>(a, c, true);
+    if (tid == 0) __threadfence();
   } else {
-    double *my = mid + ((long long)cav * kFinSlices + g) * 8;
-    if (tid < 8) {
-      my[tid] = tf;
+    cav = blockIdx.x / nsl;
+    const int g = blockIdx.x % nsl;
+    const CavConst &C = a.cc[cav];
+    const long long nt = C.tile_end - C.tile_begin;
+    const long long nb = (a.mode == 4 || a.wall_ctas) ? 0 : C.bc_end - C.bc_begin;
+    const long long ns = a.shell_end - a.shell_begin;
+    double tf = 0.0;  // thread f < 8: this slice's total of field f
+    reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / nsl, C.tile_begin + nt * (g + 1) / nsl,
+                              C.bc_begin + nb * g / nsl, C.bc_begin + nb * (g + 1) / nsl,
+                              a.shell_begin + ns * g / nsl, a.shell_begin + ns * (g + 1) / nsl, tf, sh, tid);
+    if (nsl == 1 && !a.wall_ctas) {
+      // the only CTA of the cavity: its totals go straight to the fold
+      if (tid < 8) shm[tid] = tf;
+    } else if (tid < 8) {
+      mid[((long long)cav * kFinSlices + g) * 8 + tid] = tf;
       __threadfence();
     }
+  }
+  const CavConst &C = a.cc[cav];
+  const int nwall = a.wall_ctas ? C.bc_end - C.bc_begin : 0;  // the cavity's wall CTAs in this launch
+  if (nsl + nwall > 1) {
     __syncthreads();
-    if (tid == 0) am_last = atomicAdd(a.counter + cav, 1u) == (unsigned int)nsl - 1u;
+    if (tid == 0) am_last = atomicAdd(a.counter + cav, 1u) == (unsigned int)(nsl + nwall) - 1u;
     __syncthreads();
     if (!am_last) return;
     __threadfence();
     // the slice totals loaded in parallel
     if (tid < nsl * 8) shm[tid] = mid[(long long)cav * kFinSlices * 8 + tid];
+  }
+  if (nwall) {
+    // the wall CTAs' Nusselt partials, in a fixed order (thread-strided, then warps in order)
+    double h = 0.0, c = 0.0;
+    for (int q = C.bc_begin + tid; q < C.bc_end; q += kFinThreads) {
+      h += a.bc_partials[2LL * q];
+      c += a.bc_partials[2LL * q + 1];
+    }
+    h = warp_sum(h);
+    c = warp_sum(c);
+    if ((tid & 31) == 0) { sh[(tid >> 5) * 2] = h; sh[(tid >> 5) * 2 + 1] = c; }
   }
   // the centre pressure of the new state (at most 8 nodes)
   if (a.mode != 1 && tid < C.ncentre) {
@@ -914,6 +940,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
     const int f = tid;
     double t = shm[f];
     for (int q = 1; q < nsl; ++q) t = (f == 5) ? fmax(t, shm[q * 8 + f]) : t + shm[q * 8 + f];
+    if (nwall && f >= 6)
+      for (int w = 0; w < kFinThreads / 32; ++w) t += sh[w * 2 + (f - 6)];
     if (a.mode == 4 && f >= 6) t *= (f == 6 ? 0.5 : -0.5) * C.ih[0] * C.inv_dT;  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
     sht[f] = t;
     if (a.mode != 1 && f < 5) st.res[f] = sqrt(t * C.inv_nint);
@@ -949,13 +977,18 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
 
 // k_bc: wall conditions of every wall face node and the Nusselt partials of
 // the x walls, one partial pair per CTA (reduced by k_finalize).
+// One CTA of the wall conditions: the wall nodes of kBcThreads positions of
+// one face (any block size: each thread takes every blockDim.x-th); with
+// `reduce`, the CTA's x-wall Nusselt partial (zeros for other faces).  Returns
+// the face's cavity.
 template <class S>
-__global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
+__device__ __forceinline__ int bc_cta(const BcArgs &a, int cta, bool reduce) {
   __shared__ double sh[(kBcThreads / 32) * 2];
-  const int cta = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x, nwarps = blockDim.x / 32;
+  int cav = 0;
   if (cta == 0 && tid == 0 && a.tile_counter) *a.tile_counter = 0u;  // the step kernel has finished
   if (cta == 0 && a.sfloor)
-    for (int c = tid; c < a.ncav; c += kBcThreads) a.sfloor[c] = 0u;
+    for (int c = tid; c < a.ncav; c += blockDim.x) a.sfloor[c] = 0u;
   double nu_h = 0.0, nu_c = 0.0;
   bool xwall = false;
   if (a.nfaces > 0) {
@@ -967,21 +1000,24 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
       if (m) fi = base + 31 - __clz(m);
     }
     const WallFace &F = a.faces[fi];
-    const int e = (cta - F.cta_begin) * kBcThreads + tid;
+    cav = F.cav;
     xwall = (F.face >> 1) == 0;
-    if (e < F.n1 * F.n2) {
-      const BlockDev &B = a.blocks[F.block];
-      apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
-                      nu_h, nu_c, a.mode == 1 ? (S *)B.base[a.parity ^ 1] : nullptr);
+    for (int sub = tid; sub < kBcThreads; sub += blockDim.x) {
+      const int e = (cta - F.cta_begin) * kBcThreads + sub;
+      if (e < F.n1 * F.n2) {
+        const BlockDev &B = a.blocks[F.block];
+        apply_wall<S>(B, a.cc[F.cav], (S *)B.base[a.parity], F.face, e % F.n1 + 1, e / F.n1 + 1, a.t_wall,
+                        nu_h, nu_c, a.mode == 1 ? (S *)B.base[a.parity ^ 1] : nullptr);
+      }
     }
   }
-  if (a.mode == 3) return;  // walls only (a stored state's walls made explicit), no reductions
+  if (!reduce) return cav;  // walls only (a stored state's walls made explicit), no reductions
   if (!xwall) {  // only the x walls carry Nusselt sums (a CTA covers one face)
     if (tid == 0) {
       a.bc_partials[2LL * cta] = 0.0;
       a.bc_partials[2LL * cta + 1] = 0.0;
     }
-    return;
+    return cav;
   }
   nu_h = warp_sum(nu_h);
   nu_c = warp_sum(nu_c);
@@ -989,10 +1025,16 @@ __global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
   __syncthreads();
   if (tid == 0) {
     double h = 0, c = 0;
-    for (int q = 0; q < kBcThreads / 32; ++q) { h += sh[2 * q]; c += sh[2 * q + 1]; }
+    for (int q = 0; q < nwarps; ++q) { h += sh[2 * q]; c += sh[2 * q + 1]; }
     a.bc_partials[2LL * cta] = h;
     a.bc_partials[2LL * cta + 1] = c;
   }
+  return cav;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kBcThreads) k_bc(BcArgs a) {
+  bc_cta<S>(a, blockIdx.x, a.mode != 3);
 }
 
 // ---------------------------------------------------------------------------

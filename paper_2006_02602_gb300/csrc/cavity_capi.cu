@@ -549,6 +549,7 @@ BcArgs bc_args(cavity *h, int parity, int mode) {
   a.log_cap = h->log_cap;
   a.cuts = nullptr; a.ncuts = 0; a.xbuf = nullptr;
   a.nslices = h->nslices;
+  a.wall_ctas = 0;
   return a;
 }
 
@@ -618,9 +619,12 @@ void launch_spectral(cavity *h) {
 
 // mode 0: after a step; mode 1: state refresh; 3: walls only.  The walls
 // kernel (k_bc) writes the walls and the Nusselt partials, k_finalize reduces
-// the partials and advances the state.  The FP32 step kernel applies the
-// walls where it reads them and leaves the Nusselt sums in its own partials,
-// so after its steps only k_finalize runs.  After a step of a decomposed
+// the partials and advances the state; after an FP64 step the wall CTAs run
+// inside the finalise launch, arriving at each cavity's completion counter
+// with the finalise CTAs, and the last to arrive folds their partials.  The
+// FP32 step kernel applies the walls where it reads them and leaves the
+// Nusselt sums in its own partials, so after its steps only k_finalize
+// runs.  After a step of a decomposed
 // cavity the finalise launch carries one more CTA per 256 cut-face
 // positions, which exchange the new state's cut faces (Section 4.5 pack and
 // unpack in one pass) beside the reductions: one launch after the step
@@ -629,6 +633,10 @@ void launch_bc_kernel(cavity *h, int parity, int mode) {
   const int nfin = h->ncav * h->nslices;
   BcArgs b = bc_args(h, parity, h->f32 && mode == 0 ? 4 : mode);
   int grid = nfin;
+  if (mode == 0 && !h->f32) {  // the FP64 walls and their Nusselt partials in the same launch
+    b.wall_ctas = h->n_bc;
+    grid += h->n_bc;
+  }
   if (mode == 0 && h->n_cut > 0) {
     b.cuts = h->d_cut;
     b.ncuts = (int)h->hcut.size();
@@ -643,8 +651,12 @@ void launch_bc_kernel(cavity *h, int parity, int mode) {
     k_bc<float><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
     if (mode != 3) k_finalize<float><<<nfin, kFinThreads, 0, h->stream>>>(bc_args(h, parity, mode), h->d_fin);
   } else {
+    if (mode == 0) {
+      k_finalize<double><<<grid, kFinThreads, 0, h->stream>>>(b, h->d_fin);
+      return;
+    }
     k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(bc_args(h, parity, mode));
-    if (mode != 3) k_finalize<double><<<grid, kFinThreads, 0, h->stream>>>(b, h->d_fin);
+    if (mode != 3) k_finalize<double><<<nfin, kFinThreads, 0, h->stream>>>(b, h->d_fin);
   }
 }
 
@@ -697,11 +709,12 @@ int launch_step_overlapped(cavity *h, int parity) {
   launch_step_f64(h, st);
   CK(cudaGetLastError());
   CK(cudaStreamWaitEvent(h->stream, h->ev_exch, 0));
+  // the finalise with the walls (and their Nusselt partials) in the same launch
   BcArgs ba = bc_args(h, parity ^ 1, 0);
-  k_bc<double><<<h->n_bc, kBcThreads, 0, h->stream>>>(ba);
+  ba.wall_ctas = h->n_bc;
   ba.shell_begin = h->n_step;
   ba.shell_end = (long long)h->n_step + h->n_shell;
-  k_finalize<double><<<h->ncav * h->nslices, kFinThreads, 0, h->stream>>>(ba, h->d_fin);
+  k_finalize<double><<<h->ncav * h->nslices + h->n_bc, kFinThreads, 0, h->stream>>>(ba, h->d_fin);
   CK(cudaGetLastError());
   return CAVITY_OK;
 }
