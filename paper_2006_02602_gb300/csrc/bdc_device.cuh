@@ -29,6 +29,7 @@ constexpr int kNF = 5;           // p, u, v, w, T
 constexpr int kMaxCentre = 8;    // 2^3 centre nodes at most
 constexpr int kPartStride = 8;   // doubles per step partial: 5 sums, sr max, pad
 constexpr int kBcThreads = 256;
+constexpr int kFinSlices = 16;   // k_finalize CTAs per cavity at most
 
 struct BlockDev {
   int nx, ny, nz;        // interior nodes of the block
@@ -82,6 +83,8 @@ struct CavConst {
   int centre_blk[kMaxCentre];
   long long centre_off[kMaxCentre];  // element offset of the node in its field array
   int tile_begin, tile_end;          // k_step CTAs of this cavity
+  int slice_q[kFinSlices + 1];       // k_finalize slice g reduces the step partials slice_q[g] .. slice_q[g+1]-1
+  double wscale[2];                  // FP32 step's sums of 3 T_w - 4 T_1 + T_2 -> hot, cold wall fluxes: +-h_x^-1 / (2 dT)
   int bc_begin, bc_end;              // k_bc CTAs of this cavity (all wall faces)
   long long wall_off;                // offset of this cavity's wall temperatures
 };
@@ -111,6 +114,8 @@ inline void set_cav_physics(CavConst &C, const int gn[3], const cavity_params &p
   C.inv_dT = 1.0 / (p.t_hot - p.t_cold);
   C.inv_nint = 1.0 / ((double)gn[0] * gn[1] * gn[2]);
   C.inv_nwall = 1.0 / ((double)gn[1] * gn[2]);
+  C.wscale[0] = 0.5 * C.ih[0] * C.inv_dT;
+  C.wscale[1] = -0.5 * C.ih[0] * C.inv_dT;
   for (int d = 0; d < 3; ++d) {
     C.dsc[d] = 0.5 * C.c4 * C.ih[d];
     C.nuhh[d] = C.nu * C.ihh[d];
@@ -762,6 +767,16 @@ struct BcArgs {
                               //   sums in the step partials
 };
 
+// x / 3 correctly rounded in three FP64 operations (a rounded reciprocal, then
+// one residual correction through fused multiply-adds: Markstein, IBM J. Res.
+// Dev. 34 (1990)), where a full division is a long dependent FP64 sequence on
+// GB300's narrow FP64 pipe.
+__device__ __forceinline__ double div3(double x) {
+  constexpr double y = 1.0 / 3.0;
+  const double q = x * y;
+  return fma(fma(-q, 3.0, x), y, q);
+}
+
 // Walls of one face node.  u = v = w = 0 and the isothermal T never change
 // between steps: they are written (into both buffer sets) only when `other`
 // is given (state refresh); every step rewrites p's wall and ghost values and
@@ -781,19 +796,24 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
   const long long N1 = W + s * step, N2 = W + 2 * s * step, G = W - s * step;
   const long long fs = B.fstride;
   constexpr int NP = Store<S>::NP;
+  // every load before the first store (the stores go to the wall and ghost
+  // nodes, the loads read interior ones, but the compiler cannot tell)
+  const double p1 = load_p<S>(base, fs, N1), p2 = load_p<S>(base, fs, N2);
+  const double T1 = load_T<S>(base, fs, N1), T2 = load_T<S>(base, fs, N2);
+  double tw = 0.0;
+  if (axis == 0) {
+    const int J = B.oy + c1, K = B.oz + c2;
+    const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
+    tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
+  }
   if (other) {
     base[NP * fs + W] = S(0); base[(NP + 1) * fs + W] = S(0); base[(NP + 2) * fs + W] = S(0);
     other[NP * fs + W] = S(0); other[(NP + 1) * fs + W] = S(0); other[(NP + 2) * fs + W] = S(0);
   }
-  const double p1 = load_p<S>(base, fs, N1), p2 = load_p<S>(base, fs, N2);
   const double pw = 2.0 * p1 - p2;
   store_p<S>(base, fs, W, pw);
   store_p<S>(base, fs, G, 2.0 * pw - p1);
-  const double T1 = load_T<S>(base, fs, N1), T2 = load_T<S>(base, fs, N2);
   if (axis == 0) {
-    const int J = B.oy + c1, K = B.oz + c2;
-    const long long widx = (long long)(J - 1) + (long long)C.gn[1] * (K - 1);
-    const double tw = t_wall[C.wall_off + (high ? (long long)C.gn[1] * C.gn[2] : 0) + widx];
     if (other) {
       store_T<S>(base, fs, W, tw);
       store_T<S>(other, fs, W, tw);
@@ -801,7 +821,7 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
     const double flux = (3.0 * tw - 4.0 * T1 + T2) * (0.5 * C.ih[0]) * C.inv_dT;
     if (high) nu_c += -flux; else nu_h += flux;
   } else {
-    store_T<S>(base, fs, W, (4.0 * T1 - T2) / 3.0);
+    store_T<S>(base, fs, W, div3(4.0 * T1 - T2));
   }
 }
 
@@ -809,20 +829,50 @@ __device__ __forceinline__ void apply_wall(const BlockDev &B, const CavConst &C,
 // Finalise: one cavity's per-CTA partials reduced in a fixed order and its
 // state advanced (residual RMS, spectral maximum -> next dt, Nusselt numbers,
 // time, step count, centre pressure).  GB300's FP64 pipe does about two
-// lanes per clock per SM, so the FP64 sums are spread over up to kFinSlices
-// CTAs per cavity (BcArgs::nslices, contiguous slices of the partials, about
-// 128 partials a slice), and the last of them combines the slices in order;
-// with one slice that CTA goes straight on to the fold.  Nusselt sums: the wall kernel's partials
-// (modes 0, 1) or the step partials' slots 6 and 7, sums of
+// lanes per clock per SM, and one dependent FP64 add costs tens of cycles,
+// so the FP64 sums are spread over up to kFinSlices CTAs per cavity
+// (BcArgs::nslices, contiguous slices of the partials, about 128 partials a
+// slice) and every sum is a shallow fixed tree: within a CTA the eight
+// fields are transposed through shared memory and summed by 16 threads each
+// (an 8-term tree, then four butterfly levels), and the last CTA of a cavity
+// combines the slice totals by the same butterfly.  Nusselt sums: the wall
+// kernel's partials (modes 0, 1) or the step partials' slots 6 and 7, sums of
 // 3 T_w - 4 T_1 + T_2 (mode 4, FP32 step).  After a step of a decomposed
 // cavity, CTAs after the finalise CTAs exchange the new state's cut faces.
-constexpr int kFinThreads = 128, kFinSlices = 16;
+constexpr int kFinThreads = 128;
 
+__device__ __forceinline__ double fin_comb(int f, double x, double y) { return f == 5 ? fmax(x, y) : x + y; }
+
+// Field f of the NT values in sv[f * NT ..] summed (f == 5: maximum) by the
+// 16 threads t = 16 f .. 16 f + 15 of the CTA: thread s of the group takes
+// values s, s + 16, .. s + 112 in a 3-level tree, then a butterfly over the
+// group; every thread of the group ends with the same total.
 template <int NT>
-__device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long long b0, long long b1,
-                             long long s0, long long s1, double &tot, double *sh, int tid) {
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (long long q = q0 + tid; q < q1; q += NT) {
+__device__ __forceinline__ double fin_tree(const double *sv, int f, int s) {
+  static_assert(NT == 128, "eight fields x 16 threads, eight values a thread");
+  const double *p = sv + f * NT + s;
+  const double a0 = fin_comb(f, p[0], p[16]), a1 = fin_comb(f, p[32], p[48]);
+  const double a2 = fin_comb(f, p[64], p[80]), a3 = fin_comb(f, p[96], p[112]);
+  double v = fin_comb(f, fin_comb(f, a0, a1), fin_comb(f, a2, a3));
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) v = fin_comb(f, v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One slice of a cavity's partials, thread tid's in thread-strided order.
+template <int NT>
+__device__ __forceinline__ void load_slice(const BcArgs &a, long long q0, long long q1, long long b0, long long b1,
+                                           long long s0, long long s1, int tid, double acc[8]) {
+  for (int f = 0; f < 8; ++f) acc[f] = 0.0;  // the spectral radius is positive: 0 is its identity too
+  long long q = q0 + tid;
+  if (q < q1) {  // the first partial is taken as it is, not added to zero
+    const double2 *pp = reinterpret_cast<const double2 *>(a.step_partials + q * kPartStride);
+    const double2 x0 = pp[0], x1 = pp[1], x2 = pp[2], x3 = pp[3];
+    acc[0] = x0.x; acc[1] = x0.y; acc[2] = x1.x; acc[3] = x1.y; acc[4] = x2.x; acc[5] = x2.y;
+    if (a.mode == 4) { acc[6] = x3.x; acc[7] = x3.y; }
+    q += NT;
+  }
+  for (; q < q1; q += NT) {
     const double *pp = a.step_partials + q * kPartStride;
     for (int f = 0; f < 5; ++f) acc[f] += pp[f];
     acc[5] = fmax(acc[5], pp[5]);
@@ -831,28 +881,25 @@ __device__ void reduce_slice(const BcArgs &a, long long q0, long long q1, long l
       acc[7] += pp[7];
     }
   }
-  for (long long q = s0 + tid; q < s1; q += NT) {  // shell-kernel partials
-    const double *pp = a.step_partials + q * kPartStride;
+  for (long long r = s0 + tid; r < s1; r += NT) {  // shell-kernel partials
+    const double *pp = a.step_partials + r * kPartStride;
     for (int f = 0; f < 5; ++f) acc[f] += pp[f];
     acc[5] = fmax(acc[5], pp[5]);
   }
-  for (long long q = b0 + tid; q < b1; q += NT) {
-    acc[6] += a.bc_partials[2 * q];
-    acc[7] += a.bc_partials[2 * q + 1];
+  for (long long r = b0 + tid; r < b1; r += NT) {
+    acc[6] += a.bc_partials[2 * r];
+    acc[7] += a.bc_partials[2 * r + 1];
   }
-  const int lane = tid & 31, wid = tid >> 5;
-  for (int f = 0; f < 8; ++f) acc[f] = (f == 5) ? warp_max(acc[f]) : warp_sum(acc[f]);
-  if (lane == 0)
-    for (int f = 0; f < 8; ++f) sh[wid * 8 + f] = acc[f];
+}
+
+// The CTA tree of the threads' slice sums: field f's total ends in threads
+// 16 f .. 16 f + 15.
+template <int NT>
+__device__ __forceinline__ double tree_slice(const double acc[8], double *sv, int tid) {
+#pragma unroll
+  for (int f = 0; f < 8; ++f) sv[f * NT + tid] = acc[f];
   __syncthreads();
-  // the warps' totals folded in warp order, field f by thread f (one thread's
-  // dependent FP64 chain is slow on this part's narrow FP64 pipe)
-  if (tid < 8) {
-    const int f = tid;
-    double t = sh[f];
-    for (int q = 1; q < NT / 32; ++q) t = (f == 5) ? fmax(t, sh[q * 8 + f]) : t + sh[q * 8 + f];
-    tot = t;
-  }
+  return fin_tree<NT>(sv, tid >> 4, tid & 15);
 }
 
 template <class S, int NT>
@@ -863,16 +910,20 @@ __device__ __forceinline__ int bc_cta(const BcArgs &a, int cta, bool reduce);
 // mid: [ncav][kFinSlices][8] slice totals; a.counter: per cavity, zero between launches
 template <class S>
 __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid) {
-  __shared__ double sh[kFinThreads / 32 * 8];
+  constexpr int NT = kFinThreads;
+  __shared__ double sv[8 * NT];
   __shared__ double shm[kFinSlices * 8];
   __shared__ double shc[8];
   __shared__ double sht[8];
+  __shared__ double sres[8];  // residual norms, Nusselt numbers, time: the step record's values
+  __shared__ double sdt;
+  __shared__ long long srec;
   __shared__ bool am_last;
-  static_assert(kFinSlices * 8 <= kFinThreads, "one slice total per thread");
+  static_assert(kFinSlices * 8 <= NT && kFinSlices == 16, "one slice total per thread, 16 threads a field");
   // the next step kernel (a programmatic dependent) may start its prologue now;
   // it waits for this grid's completion before it reads the state advanced here
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int nsl = a.nslices, tid = threadIdx.x;
+  const int nsl = a.nslices, tid = threadIdx.x, f = tid >> 4, s = tid & 15;
   int cav;
   if (blockIdx.x >= a.ncav * nsl) {
     const int c = blockIdx.x - a.ncav * nsl;
@@ -888,24 +939,44 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
     if (tid == 0) __threadfence();
   } else {
     cav = blockIdx.x / nsl;
-    const int g = blockIdx.x % nsl;
-    const CavConst &C = a.cc[cav];
-    const long long nt = C.tile_end - C.tile_begin;
-    const long long nb = (a.mode == 4 || a.wall_ctas) ? 0 : C.bc_end - C.bc_begin;
-    const long long ns = a.shell_end - a.shell_begin;
-    double tf = 0.0;  // thread f < 8: this slice's total of field f
-    reduce_slice<kFinThreads>(a, C.tile_begin + nt * g / nsl, C.tile_begin + nt * (g + 1) / nsl,
-                              C.bc_begin + nb * g / nsl, C.bc_begin + nb * (g + 1) / nsl,
-                              a.shell_begin + ns * g / nsl, a.shell_begin + ns * (g + 1) / nsl, tf, sh, tid);
+  }
+  const CavConst &C = a.cc[cav];
+  CavState &st = a.cs[cav];
+  const bool slice = blockIdx.x < a.ncav * nsl;
+  const int g = blockIdx.x - cav * nsl;
+  double acc[8];
+  if (slice) {
+    // slice bounds: the step partials' from the host's table; the wall and
+    // shell partials' (after a state refresh, the overlapped schedule) in
+    // 32-bit arithmetic (counts far below 2^27)
+    const unsigned nb = (a.mode == 4 || a.wall_ctas) ? 0u : (unsigned)(C.bc_end - C.bc_begin);
+    const unsigned ns = (unsigned)(a.shell_end - a.shell_begin);
+    load_slice<NT>(a, C.slice_q[g], C.slice_q[g + 1], C.bc_begin + nb * g / nsl, C.bc_begin + nb * (g + 1) / nsl,
+                   a.shell_begin + ns * g / nsl, a.shell_begin + ns * (g + 1) / nsl, tid, acc);
+  }
+  // loads for whichever CTA of the cavity comes last, issued while the
+  // partials are in flight and first used after the reductions: the new
+  // state's centre pressure (at most 8 nodes, written by the step kernel) and
+  // the state it advances (written only by that CTA)
+  double cp = 0.0, st_t = 0.0, st_dt = 0.0;
+  long long st_step = 0;
+  int st_flags = 0;
+  if (a.mode != 1 && tid < C.ncentre) {
+    const BlockDev &B = a.blocks[C.centre_blk[tid]];
+    cp = load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[tid]);
+  }
+  if (tid == 0 || tid == 3) { st_step = st.step; st_flags = st.flags; }
+  if (tid == 2) { st_t = st.t; st_dt = st.dt; }
+  if (slice) {
+    const double tf = tree_slice<NT>(acc, sv, tid);
     if (nsl == 1 && !a.wall_ctas) {
       // the only CTA of the cavity: its totals go straight to the fold
-      if (tid < 8) shm[tid] = tf;
-    } else if (tid < 8) {
-      mid[((long long)cav * kFinSlices + g) * 8 + tid] = tf;
+      if (s == 0) shm[f] = tf;
+    } else if (s == 0) {
+      mid[((long long)cav * kFinSlices + g) * 8 + f] = tf;
       __threadfence();
     }
   }
-  const CavConst &C = a.cc[cav];
   const int nwall = a.wall_ctas ? C.bc_end - C.bc_begin : 0;  // the cavity's wall CTAs in this launch
   if (nsl + nwall > 1) {
     __syncthreads();
@@ -916,61 +987,78 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
     // the slice totals loaded in parallel
     if (tid < nsl * 8) shm[tid] = mid[(long long)cav * kFinSlices * 8 + tid];
   }
+  if (tid < 8) shc[tid] = cp;
   if (nwall) {
-    // the wall CTAs' Nusselt partials, in a fixed order (thread-strided, then warps in order)
+    // the wall CTAs' Nusselt partials, thread-strided, into fields 6 and 7 of the tree
     double h = 0.0, c = 0.0;
-    for (int q = C.bc_begin + tid; q < C.bc_end; q += kFinThreads) {
+    for (int q = C.bc_begin + tid; q < C.bc_end; q += NT) {
       h += a.bc_partials[2LL * q];
       c += a.bc_partials[2LL * q + 1];
     }
-    h = warp_sum(h);
-    c = warp_sum(c);
-    if ((tid & 31) == 0) { sh[(tid >> 5) * 2] = h; sh[(tid >> 5) * 2 + 1] = c; }
-  }
-  // the centre pressure of the new state (at most 8 nodes)
-  if (a.mode != 1 && tid < C.ncentre) {
-    const BlockDev &B = a.blocks[C.centre_blk[tid]];
-    shc[tid] = load_p<S>((const S *)B.base[a.parity], B.fstride, C.centre_off[tid]);
+    sv[6 * NT + tid] = h;
+    sv[7 * NT + tid] = c;
   }
   __syncthreads();
-  CavState &st = a.cs[cav];
-  // the slice totals folded in slice order, field f by thread f; threads
-  // 0..4 take the residual norms
-  if (tid < 8) {
-    const int f = tid;
-    double t = shm[f];
-    for (int q = 1; q < nsl; ++q) t = (f == 5) ? fmax(t, shm[q * 8 + f]) : t + shm[q * 8 + f];
-    if (nwall && f >= 6)
-      for (int w = 0; w < kFinThreads / 32; ++w) t += sh[w * 2 + (f - 6)];
-    if (a.mode == 4 && f >= 6) t *= (f == 6 ? 0.5 : -0.5) * C.ih[0] * C.inv_dT;  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
+  // the slice totals of field f combined by its 16 threads (slice s in thread
+  // 16 f + s, a butterfly over the first nsl), then the wall partials' tree
+  double t = s < nsl ? shm[s * 8 + f] : 0.0;
+  for (int o = 1; o < nsl; o <<= 1) t = fin_comb(f, t, __shfl_xor_sync(0xffffffffu, t, o));
+  if (nwall && f >= 6) t += fin_tree<NT>(sv, f, s);
+  // one thread of each field group finishes its field (the FP64 chains run
+  // side by side): residual norms, dt, Nusselt numbers; threads 1 and 2 the
+  // centre pressure and the time
+  if (s == 0) {
     sht[f] = t;
-    if (a.mode != 1 && f < 5) st.res[f] = sqrt(t * C.inv_nint);
+    if (f < 5 && a.mode != 1) {
+      const double r = sqrt(t * C.inv_nint);
+      st.res[f] = r;
+      sres[f] = r;
+    }
+    if (f == 5) {
+      sdt = C.cfl / t;
+      st.dt = sdt;
+    }
+    if (f >= 6) {
+      if (a.mode == 4) t *= C.wscale[f - 6];  // sums of 3 T_w - 4 T_1 + T_2 -> wall fluxes
+      const double nu = t * C.inv_nwall;
+      sres[f - 1] = nu;  // slots 5, 6 of the record's tail
+      if (f == 6) st.nu_hot = nu; else st.nu_cold = nu;
+    }
   }
+  if (tid == 1 && a.mode != 1) {
+    // centre pressure of the new state, lexicographic (k, j, i) order; the
+    // count is 1, 2, 4 or 8 (one or two nodes per axis), so the scaling is exact
+    double csum = 0.0;
+    for (int m = 0; m < C.ncentre; ++m) csum += shc[m];
+    st.c = csum * (C.ncentre == 8 ? 0.125 : C.ncentre == 4 ? 0.25 : C.ncentre == 2 ? 0.5 : 1.0);
+  }
+  if (tid == 2 && a.mode != 1) {  // the time after this step
+    st_t += st_dt;
+    st.t = st_t;
+    sres[7] = st_t;
+  }
+  if (tid == 3 && a.log && a.mode != 1) srec = (st_step % a.log_cap) * a.ncav + cav;  // this step's log record
   __syncthreads();
   if (tid != 0) return;
   bool bad = !isfinite(sht[5]);
   if (a.mode != 1) {
-    for (int f = 0; f < 5; ++f) bad = bad || !isfinite(sht[f]);
-    st.t += st.dt;
-    st.step += 1;
-    // centre pressure of the new state, lexicographic (k, j, i) order
-    double csum = 0.0;
-    for (int m = 0; m < C.ncentre; ++m) csum += shc[m];
-    st.c = csum / (double)C.ncentre;
+    for (int q = 0; q < 5; ++q) bad = bad || !isfinite(sht[q]);
+    st_step += 1;
+    st.step = st_step;
   }
-  st.dt = C.cfl / sht[5];
-  st.nu_hot = sht[6] * C.inv_nwall;
-  st.nu_cold = sht[7] * C.inv_nwall;
-  if (bad) st.flags |= 1;
+  if (bad) {  // atomic: a timed-out wait of the next step kernel may set bit 1 meanwhile
+    st_flags |= 1;
+    atomicOr(&st.flags, 1);
+  }
   if (a.log && a.mode != 1) {  // this step's record, written to host memory
-    StepRecord &r = a.log[((st.step - 1) % a.log_cap) * a.ncav + cav];
-    r.step = st.step;
-    r.t = st.t;
-    r.dt = st.dt;
-    for (int f = 0; f < 5; ++f) r.res[f] = st.res[f];  // written by threads 0..4 before the barrier
-    r.nu_hot = st.nu_hot;
-    r.nu_cold = st.nu_cold;
-    r.flags = st.flags;
+    StepRecord &r = a.log[srec];
+    r.step = st_step;
+    r.t = sres[7];
+    r.dt = sdt;
+    for (int q = 0; q < 5; ++q) r.res[q] = sres[q];
+    r.nu_hot = sres[5];
+    r.nu_cold = sres[6];
+    r.flags = st_flags;
   }
   a.counter[cav] = 0u;
 }

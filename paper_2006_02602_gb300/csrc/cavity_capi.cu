@@ -266,6 +266,12 @@ void assign_tiles(cavity *h) {
   int most = 0;  // the most tiles of one cavity
   for (int c = 0; c < h->ncav; ++c) most = std::max(most, h->hcc[c].tile_end - h->hcc[c].tile_begin);
   h->nslices = std::max(1, std::min(kFinSlices, ceil_div(most, 128)));
+  for (int c = 0; c < h->ncav; ++c) {  // contiguous slices of each cavity's step partials
+    CavConst &C = h->hcc[c];
+    const long long nt = C.tile_end - C.tile_begin;
+    for (int g = 0; g <= kFinSlices; ++g)
+      C.slice_q[g] = C.tile_begin + (int)(nt * std::min(g, h->nslices) / h->nslices);
+  }
 }
 
 int build_layout(cavity *h) {
@@ -336,32 +342,44 @@ int build_layout(cavity *h) {
   h->field_bytes = total_elems * es;
   h->twall.assign((size_t)wall_off, 0.0);
   assign_tiles(h);
-  // wall faces (all, and the x walls alone), cut faces; contiguous per cavity
-  int bc = 0, cut = 0;
-  long long xoff = 0;
+  // wall faces, contiguous per cavity, and cut faces, each list with its x
+  // faces first: a CTA of an x face touches one 32-byte sector per node and
+  // array (its positions run along y) where the others' rows are contiguous,
+  // and launched first the x faces' CTAs spread over the SMs (the last
+  // exchange CTA after a 128^3 FP32 step in 2 x 2 x 2 blocks ended about
+  // 3 us earlier than with the faces in block order)
   h->hwall.clear();
   h->hcut.clear();
-  for (int c = 0; c < h->ncav; ++c) {
-    h->hcc[c].bc_begin = -1;
-  }
   for (int id = 0; id < h->nblocks; ++id) {
     const BlockDev &B = h->hb[id];
-    CavConst &C = h->hcc[B.cav];
     const int n[3] = {B.nx, B.ny, B.nz};
     for (int f = 0; f < 6; ++f) {
       const int a = f / 2;
       const int n1 = n[a == 0 ? 1 : 0], n2 = n[a == 2 ? 1 : 2];
-      if (B.wall[f]) {
-        h->hwall.push_back(WallFace{id, f, n1, n2, bc, B.cav});
-        if (C.bc_begin < 0) C.bc_begin = bc;
-        bc += ceil_div((long long)n1 * n2, kBcThreads);
-        C.bc_end = bc;
-      } else {
-        h->hcut.push_back(CutFace{id, f, B.nbr[f], n1, n2, cut, xoff});
-        cut += ceil_div((long long)n1 * n2, 256);
-        xoff += (long long)(h->na + h->np) * n1 * n2;
-      }
+      if (B.wall[f]) h->hwall.push_back(WallFace{id, f, n1, n2, 0, B.cav});
+      else h->hcut.push_back(CutFace{id, f, B.nbr[f], n1, n2, 0, 0});
     }
+  }
+  std::stable_sort(h->hwall.begin(), h->hwall.end(), [](const WallFace &x, const WallFace &y) {
+    return x.cav != y.cav ? x.cav < y.cav : x.face / 2 < y.face / 2;
+  });
+  std::stable_sort(h->hcut.begin(), h->hcut.end(),
+                   [](const CutFace &x, const CutFace &y) { return x.face / 2 < y.face / 2; });
+  int bc = 0, cut = 0;
+  long long xoff = 0;
+  for (int c = 0; c < h->ncav; ++c) h->hcc[c].bc_begin = -1;
+  for (WallFace &w : h->hwall) {
+    CavConst &C = h->hcc[w.cav];
+    w.cta_begin = bc;
+    if (C.bc_begin < 0) C.bc_begin = bc;
+    bc += ceil_div((long long)w.n1 * w.n2, kBcThreads);
+    C.bc_end = bc;
+  }
+  for (CutFace &c : h->hcut) {
+    c.cta_begin = cut;
+    c.buf_off = xoff;
+    cut += ceil_div((long long)c.nb * c.nc, 256);
+    xoff += (long long)(h->na + h->np) * c.nb * c.nc;
   }
   h->n_bc = bc;
   h->n_cut = cut;
