@@ -28,7 +28,7 @@ namespace bdc {
 constexpr int kNF = 5;           // p, u, v, w, T
 constexpr int kMaxCentre = 8;    // 2^3 centre nodes at most
 constexpr int kPartStride = 8;   // doubles per step partial: 5 sums, sr max, pad
-constexpr int kBcThreads = 256;
+constexpr int kBcThreads = 128;  // wall positions per k_bc CTA (one per thread)
 constexpr int kFinSlices = 16;   // k_finalize CTAs per cavity at most
 
 struct BlockDev {
@@ -86,6 +86,7 @@ struct CavConst {
   int slice_q[kFinSlices + 1];       // k_finalize slice g reduces the step partials slice_q[g] .. slice_q[g+1]-1
   double wscale[2];                  // FP32 step's sums of 3 T_w - 4 T_1 + T_2 -> hot, cold wall fluxes: +-h_x^-1 / (2 dT)
   int bc_begin, bc_end;              // k_bc CTAs of this cavity (all wall faces)
+  int bc_xend;                       // the x walls' CTAs (the Nusselt partials) come first: bc_begin .. bc_xend-1
   long long wall_off;                // offset of this cavity's wall temperatures
 };
 
@@ -991,7 +992,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
   if (nwall) {
     // the wall CTAs' Nusselt partials, thread-strided, into fields 6 and 7 of the tree
     double h = 0.0, c = 0.0;
-    for (int q = C.bc_begin + tid; q < C.bc_end; q += NT) {
+    for (int q = C.bc_begin + tid; q < C.bc_xend; q += NT) {  // the other walls' partials are zeros
       h += a.bc_partials[2LL * q];
       c += a.bc_partials[2LL * q + 1];
     }
@@ -1071,14 +1072,14 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BcArgs a, double *mid)
 // the face's cavity.
 template <class S>
 __device__ __forceinline__ int bc_cta(const BcArgs &a, int cta, bool reduce) {
-  __shared__ double sh[(kBcThreads / 32) * 2];
+  __shared__ double sh[kBcThreads / 32];
   const int tid = threadIdx.x, nwarps = blockDim.x / 32;
   int cav = 0;
   if (cta == 0 && tid == 0 && a.tile_counter) *a.tile_counter = 0u;  // the step kernel has finished
   if (cta == 0 && a.sfloor)
     for (int c = tid; c < a.ncav; c += blockDim.x) a.sfloor[c] = 0u;
   double nu_h = 0.0, nu_c = 0.0;
-  bool xwall = false;
+  bool xwall = false, xhigh = false;
   if (a.nfaces > 0) {
     // the face of this CTA: the last one whose first CTA is not after it (a warp-wide search)
     int fi = 0;
@@ -1090,6 +1091,7 @@ __device__ __forceinline__ int bc_cta(const BcArgs &a, int cta, bool reduce) {
     const WallFace &F = a.faces[fi];
     cav = F.cav;
     xwall = (F.face >> 1) == 0;
+    xhigh = F.face & 1;
     for (int sub = tid; sub < kBcThreads; sub += blockDim.x) {
       const int e = (cta - F.cta_begin) * kBcThreads + sub;
       if (e < F.n1 * F.n2) {
@@ -1107,15 +1109,15 @@ __device__ __forceinline__ int bc_cta(const BcArgs &a, int cta, bool reduce) {
     }
     return cav;
   }
-  nu_h = warp_sum(nu_h);
-  nu_c = warp_sum(nu_c);
-  if ((tid & 31) == 0) { sh[(tid >> 5) * 2] = nu_h; sh[(tid >> 5) * 2 + 1] = nu_c; }
+  // a CTA covers one face: the hot (low x) or the cold (high x) sum, the other is zero
+  const double v = warp_sum(xhigh ? nu_c : nu_h);
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
   __syncthreads();
   if (tid == 0) {
-    double h = 0, c = 0;
-    for (int q = 0; q < nwarps; ++q) { h += sh[2 * q]; c += sh[2 * q + 1]; }
-    a.bc_partials[2LL * cta] = h;
-    a.bc_partials[2LL * cta + 1] = c;
+    double t = 0;
+    for (int q = 0; q < nwarps; ++q) t += sh[q];
+    a.bc_partials[2LL * cta] = xhigh ? 0.0 : t;
+    a.bc_partials[2LL * cta + 1] = xhigh ? t : 0.0;
   }
   return cav;
 }

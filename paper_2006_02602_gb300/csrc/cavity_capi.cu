@@ -371,9 +371,10 @@ int build_layout(cavity *h) {
   for (WallFace &w : h->hwall) {
     CavConst &C = h->hcc[w.cav];
     w.cta_begin = bc;
-    if (C.bc_begin < 0) C.bc_begin = bc;
+    if (C.bc_begin < 0) C.bc_begin = C.bc_xend = bc;
     bc += ceil_div((long long)w.n1 * w.n2, kBcThreads);
     C.bc_end = bc;
+    if (w.face / 2 == 0) C.bc_xend = bc;
   }
   for (CutFace &c : h->hcut) {
     c.cta_begin = cut;
