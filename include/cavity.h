@@ -343,6 +343,18 @@ CAVITY_API int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]);
  * outside that range; CAVITY_ERR_OOM / CAVITY_ERR_CUDA on a CUDA error. */
 CAVITY_API int cavity_check_sqrt(const double *x, long long n, double *max_rel, long long *n_diff);
 
+/* Self-check of the division by 3 in the adiabatic wall value
+ * T_w = (4 T_1 - T_2) / 3 (the one-sided second-order zero-flux condition of
+ * Section 2) of the FP64 wall kernel: a rounded reciprocal of 3 and one
+ * residual correction through fused multiply-adds (Markstein 1990).  On the
+ * current CUDA device, evaluates it and CUDA's correctly rounded division for
+ * the n host values x (finite, |x| >= 4 DBL_MIN, so that the quotient is
+ * normal; copied in and out by the call, which synchronises) and returns in
+ * *n_diff the number of values where the two differ.
+ * CAVITY_ERR_INVALID_ARG for n < 1 or n > 2^26, a null pointer or a value
+ * outside that range; CAVITY_ERR_OOM / CAVITY_ERR_CUDA on a CUDA error. */
+CAVITY_API int cavity_check_div3(const double *x, long long n, long long *n_diff);
+
 /* Measurement (no counterpart in the paper): the FP64 FMA throughput of CUDA
  * device `device` in TFLOP/s (2 flops per FMA), the ceiling of the FP64 step
  * kernel, whose 190 FP64 operations per 80 bytes of state put it far on the

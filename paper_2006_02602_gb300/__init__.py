@@ -45,7 +45,7 @@ EXPORTED = (
     "cavity_exchange", "cavity_time_kernels", "cavity_step_block_noalloc", "cavity_sync", "cavity_destroy",
     "cavity_strerror", "cavity_last_error", "cavity_create_batch", "cavity_batch_size", "cavity_batch_state",
     "cavity_batch_get_fields", "cavity_autotune", "cavity_adjoint_forward", "cavity_adjoint_backward",
-    "cavity_set_time_stepping", "cavity_set_overlap", "cavity_check_sqrt", "cavity_test_wait_timeout",
+    "cavity_set_time_stepping", "cavity_set_overlap", "cavity_check_sqrt", "cavity_check_div3", "cavity_test_wait_timeout",
     "cavity_measure_fp64_peak", "cavity_adjoint_kernel_ms", "cavity_set_step_log", "cavity_step_log_alloc",
     "cavity_step_log_free",
 )
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "cavity_exchange": ([_H], ctypes.c_int),
         "cavity_time_kernels": ([_H, ctypes.c_int, _dp], ctypes.c_int),
         "cavity_check_sqrt": ([_dp, ctypes.c_longlong, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+        "cavity_check_div3": ([_dp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "cavity_set_time_stepping": ([_H, ctypes.c_int], ctypes.c_int),
         "cavity_set_overlap": ([_H, ctypes.c_int], ctypes.c_int),
         "cavity_create_batch": ([ctypes.POINTER(cavity_desc), ctypes.POINTER(cavity_params), ctypes.c_int,
@@ -288,6 +289,16 @@ def cavity_check_sqrt(x) -> tuple:
     nd = ctypes.c_longlong(0)
     _check(load_library().cavity_check_sqrt(x.ctypes.data_as(_dp), x.size, ctypes.byref(m), ctypes.byref(nd)))
     return m.value, nd.value
+
+
+def cavity_check_div3(x) -> int:
+    """Count of the finite values x (|x| >= 4 DBL_MIN) where the FP64 wall
+    kernel's division by 3 differs from CUDA's correctly rounded x / 3,
+    evaluated on the current CUDA device."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    nd = ctypes.c_longlong(0)
+    _check(load_library().cavity_check_div3(x.ctypes.data_as(_dp), x.size, ctypes.byref(nd)))
+    return nd.value
 
 
 def cavity_step_block_noalloc(q_in_ptr: int, q_out_ptr: int, shape, params: cavity_params, dt: float,

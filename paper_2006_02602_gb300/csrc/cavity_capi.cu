@@ -1056,6 +1056,13 @@ __global__ void k_check_sqrt(const double *x, long long n, double *rel) {
   rel[i] = s == r ? 0.0 : fabs(s - r) / r;
 }
 
+// cavity_check_div3: whether div3 equals CUDA's correctly rounded x / 3
+__global__ void k_check_div3(const double *x, long long n, unsigned char *diff) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  diff[i] = div3(x[i]) != x[i] / 3.0;
+}
+
 // Recomputation of a checkpointed segment without copies: points block 0 of
 // the step graph's descriptor table at two buffer sets -- base[0] (read) = b0,
 // base[1] (written) = b1 -- and, in the FP32 form, replaces the parity-0
@@ -1743,6 +1750,29 @@ int cavity_time_kernels(cavity_t *h, int nsteps, double ms[4]) {
   for (int q = 0; q < 4; ++q) ms[q] = acc[q] / nsteps;
   ms[2] = ms[3] = 0.0;
   return rc;
+}
+
+int cavity_check_div3(const double *x, long long n, long long *n_diff) {
+  if (!x || !n_diff || n < 1 || n > (1ll << 26)) return CAVITY_ERR_INVALID_ARG;
+  for (long long i = 0; i < n; ++i)
+    if (!(std::fabs(x[i]) >= 4.0 * DBL_MIN && std::fabs(x[i]) <= DBL_MAX)) return CAVITY_ERR_INVALID_ARG;
+  double *d = nullptr;
+  const size_t bytes = (size_t)n * sizeof(double);
+  cudaError_t e = cudaMalloc(&d, bytes + (size_t)n);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CAVITY_ERR_OOM : CAVITY_ERR_CUDA;
+  std::vector<unsigned char> diff((size_t)n);
+  e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_check_div3<<<(unsigned)((n + 255) / 256), 256>>>(d, n, (unsigned char *)(d + n));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(diff.data(), d + n, (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return CAVITY_ERR_CUDA;
+  long long nd = 0;
+  for (unsigned char c : diff) nd += c != 0;
+  *n_diff = nd;
+  return CAVITY_OK;
 }
 
 int cavity_check_sqrt(const double *x, long long n, double *max_rel, long long *n_diff) {

@@ -1,5 +1,7 @@
 """The FP64 step's Newton square root (wave speeds of Section 2) against
-CUDA's correctly rounded sqrt, through the C-ABI self-check."""
+CUDA's correctly rounded sqrt, and the FP64 wall kernel's division by 3
+(adiabatic walls) against CUDA's correctly rounded division, through the
+C-ABI self-checks."""
 import numpy as np
 import pytest
 
@@ -28,3 +30,20 @@ def test_check_rejects_values_outside_the_range(m):
     for bad in ([0.0], [-1.0], [np.inf], [np.nan], [1e-310]):
         with pytest.raises(m.CavityError):
             m.cavity_check_sqrt(np.array(bad))
+
+
+def test_division_by_three_is_correctly_rounded(m):
+    rng = np.random.default_rng(11)
+    # random significands and signs over the normal range, dense near the
+    # temperatures the walls see, and exact multiples of 3 and powers of two
+    bits = rng.integers(0, 1 << 52, 1 << 20, dtype=np.int64) | (rng.integers(1, 2046, 1 << 20, dtype=np.int64) << 52)
+    wide = bits.view(np.float64) * rng.choice([-1.0, 1.0], bits.size)
+    wide = wide[np.abs(wide) >= 4 * np.finfo(np.float64).tiny]
+    x = np.concatenate([wide, rng.uniform(-2.0, 2.0, 1 << 20), 3.0 * np.arange(1, 4097), 2.0 ** np.arange(-1000, 1000)])
+    assert m.cavity_check_div3(x) == 0
+
+
+def test_div3_check_rejects_values_outside_the_range(m):
+    for bad in ([0.0], [np.inf], [np.nan], [1e-310]):
+        with pytest.raises(m.CavityError):
+            m.cavity_check_div3(np.array(bad))
