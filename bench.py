@@ -329,7 +329,7 @@ def measure(m, torch, precision, workload, blocks, steps, warmup, rank, world, l
         if world > 1:
             torch.distributed.barrier()
 
-    tuned = m.cavity_autotune(c.h, 10) if precision == "fp32" else None  # FP32: the autotuner picks the shape
+    tuned = m.cavity_autotune(c.h, 20) if precision == "fp32" else None  # FP32: the autotuner picks the shape
     shape = (f"{tuned['tile_y']},{tuned['kc']},{tuned['ring']},{tuned['kernel_form']}" if tuned else FP64_SHAPE)
     c.step(warmup)
     c.sync()
@@ -422,7 +422,7 @@ def measure_batch(m, torch, steps, warmup, rank, world, local, stream):
                               noise_amp=workloads.CFG4["noise"], device=local, stream=stream.cuda_stream)
     pts = sum(a * b * c for a, b, c in sizes)
     both_buffers = pts * BYTES_PER_POINT["fp32"]
-    tuned = m.cavity_autotune(h, 10)
+    tuned = m.cavity_autotune(h, 20)
     m.cavity_step(h, warmup)
     m.cavity_sync(h)
     kms_before = m.cavity_time_kernels(h, 10)  # averaged with 10 steps after the timed region
@@ -468,7 +468,7 @@ def measure_adjoint(m, torch, rank, world, local, stream):
     c = m.Cavity(*n, precision=m.CAVITY_FP32_MIXED, seed=cfg["seed"] + rank, noise_amp=cfg["noise"], device=local,
                  stream=stream.cuda_stream, Ra=cfg["Ra"], Pr=cfg["Pr"])
     m.cavity_set_wall_temperature(c.h, 0, theta)
-    tuned = m.cavity_autotune(c.h, 10)  # the FP32 step's tile shape (forward and recomputation)
+    tuned = m.cavity_autotune(c.h, 20)  # the FP32 step's tile shape (forward and recomputation)
     # warm-up with the timed run's own step count and checkpoint interval, so
     # that the timed run reuses the checkpoint and segment memory
     m.cavity_adjoint_forward(c.h, cfg["steps"], cfg["ckpt"])

@@ -261,7 +261,8 @@ CAVITY_API int cavity_batch_get_fields(cavity_t *h, int cav, int field_mask, dou
 
 /* Autotuner of the FP32-mixed step kernel: times every compiled tile shape
  * (x-y tile extent, z-chunk length, ring depth) for `steps` graph-replayed
- * steps on this handle's own cavities and keeps the fastest.  The state is
+ * steps on this handle's own cavities, times the four fastest once more
+ * (each keeps its better time) and keeps the fastest.  The state is
  * saved before the trials and restored after them (the step counter and the
  * fields are as before the call).  out (optional) receives the chosen tile
  * height (8 or 16 rows of 32 nodes), z-chunk, ring depth, kernel form (3:
