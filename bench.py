@@ -59,11 +59,11 @@ ADJ_BYTES_PER_POINT = 68
 # (precision, workload, blocks, shape); the FP32 shape is the autotuner's
 # "TY,KC,R,form"
 FP64_SHAPE = "32x4x8"
-TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 114.855680e6 + 55.964416e6,
-           ("fp32", "cfg3", (1, 1, 1), "8,96,4,3"): 601.765888e6 + 434.956800e6,
-           ("fp32", "cfg3", (1, 1, 1), "8,64,4,3"): 570.362112e6 + 434.965760e6,
-           ("fp32", "cfg3", (1, 1, 1), "8,32,4,3"): 584.913920e6 + 434.615552e6,
-           ("fp32", "cfg4", None, "8,64,4,3"): 610.060800e6 + 324.751616e6}
+TRAFFIC = {("fp64", "cfg2", (2, 2, 2), FP64_SHAPE): 115.065344e6 + 55.689216e6,
+           ("fp32", "cfg3", (1, 1, 1), "8,96,4,3"): 613.445632e6 + 434.552064e6,
+           ("fp32", "cfg3", (1, 1, 1), "8,64,4,3"): 575.716096e6 + 435.488256e6,
+           ("fp32", "cfg3", (1, 1, 1), "8,32,4,3"): 585.227776e6 + 434.474240e6,
+           ("fp32", "cfg4", None, "8,64,4,3"): 612.079360e6 + 324.579072e6}
 F32_FORMS = {3: "k_step_f32q (two nodes per thread, f32x2; z neighbours below the plane in registers)"}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
