@@ -225,12 +225,14 @@ CAVITY_API int cavity_num_blocks(cavity_t *h);
  * = o + local index).  For checks of the ghost exchange. */
 CAVITY_API int cavity_get_block_array(cavity_t *h, int block, int field, double *host, size_t count, int dims[6]);
 
-/* The last packed buffer of one cut face of one block (Section 4.5 layout:
+/* The packed buffer of one cut face of one block (Section 4.5 layout:
  * p at depth 2 with depth fastest, then u, v, w, T at depth 1), widened to
  * FP64; count must equal 6*nb*nc (FP64 form) or 9*nb*nc (FP32-mixed form:
- * p_hi then p_lo at depth 2, then u, v, w, T_hi, T_lo at depth 1).
- * CAVITY_ERR_INVALID_ARG if the face is a
- * wall. */
+ * p_hi then p_lo at depth 2, then u, v, w, T_hi, T_lo at depth 1), packed
+ * from the current state by this call: the values every exchange of this
+ * state sends (the step's exchange writes the neighbour's ghost layers
+ * without the buffer).  Synchronises.  CAVITY_ERR_INVALID_ARG if the face is
+ * a wall. */
 CAVITY_API int cavity_get_face_buffer(cavity_t *h, int block, int face, double *host, size_t count);
 
 /* Pack and unpack every cut face of the current state (a7, a8 alone). */

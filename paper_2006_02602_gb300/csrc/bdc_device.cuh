@@ -1205,12 +1205,13 @@ __global__ void __launch_bounds__(256) k_unpack(ExchArgs a) {
     q[(long long)(NP + v) * B.fstride + v_node] = buf[2LL * NP * plane + (long long)v * plane + e];
 }
 
-// Pack and unpack in one pass, one CTA of NT threads per 256 face positions
-// (CutFace::cta_begin counts such CTAs): the same buffer entries and ghost
-// values as k_pack followed by k_unpack.  The step's exchange, run by the
-// finalise kernel's extra CTAs beside its reductions, so it is written for
-// latency: the face found by a warp-wide search, every value of the thread's
-// positions loaded before the first store.
+// The step's exchange, one CTA of NT threads per 256 face positions
+// (CutFace::cta_begin counts such CTAs): the ghost values k_pack followed by
+// k_unpack would write, copied straight from the sending block's layers (the
+// face buffer is packed only when asked for, by cavity_get_face_buffer).  Run
+// by the finalise kernel's extra CTAs beside its reductions, so it is written
+// for latency: the face found by a warp-wide search, every value of the
+// thread's positions loaded before the first store.
 template <class S, int NT>
 __device__ __forceinline__ void exchange_cta(const ExchArgs &a, int cta) {
   static_assert(256 % NT == 0, "positions per thread");
@@ -1228,7 +1229,6 @@ __device__ __forceinline__ void exchange_cta(const ExchArgs &a, int cta) {
   const int plane = F.nb * F.nc;
   const S *__restrict__ q = (const S *)B.base[a.parity];
   S *__restrict__ g = (S *)D.base[a.parity];
-  S *__restrict__ buf = (S *)a.buf + F.buf_off;
   const long long fs = B.fstride, fd = D.fstride;
   int e[NPOS];
   long long gp[NPOS], gv[NPOS], gstep = 0;
@@ -1254,16 +1254,11 @@ __device__ __forceinline__ void exchange_cta(const ExchArgs &a, int cta) {
     if (e[r] >= plane) continue;
 #pragma unroll
     for (int pa = 0; pa < NP; ++pa) {
-      buf[2LL * pa * plane + 2LL * e[r]] = x[r][2 * pa];
-      buf[2LL * pa * plane + 2LL * e[r] + 1] = x[r][2 * pa + 1];
       g[pa * fd + gp[r]] = x[r][2 * pa];
       g[pa * fd + gp[r] + gstep] = x[r][2 * pa + 1];
     }
 #pragma unroll
-    for (int v = 0; v < NA - NP; ++v) {
-      buf[2LL * NP * plane + (long long)v * plane + e[r]] = x[r][2 * NP + v];
-      g[(NP + v) * fd + gv[r]] = x[r][2 * NP + v];
-    }
+    for (int v = 0; v < NA - NP; ++v) g[(NP + v) * fd + gv[r]] = x[r][2 * NP + v];
   }
 }
 

@@ -1360,6 +1360,10 @@ int cavity_get_face_buffer(cavity_t *h, int block, int face, double *host, size_
     const size_t n = (size_t)(h->na + h->np) * c.nb * c.nc;
     if (count != n) return fail(h, CAVITY_ERR_INVALID_ARG, "count mismatch");
     DeviceGuard g(h->dev);
+    // the step's exchange writes the ghost layers directly: pack the current
+    // state's faces (the values every exchange of this state sends)
+    launch_pack(h, h->parity);
+    CK(cudaGetLastError());
     if (h->f32) {
       std::vector<float> tmp(n);
       CK(cudaMemcpyAsync(tmp.data(), (float *)h->d_xbuf + c.buf_off, n * sizeof(float), cudaMemcpyDeviceToHost,
