@@ -345,9 +345,10 @@ int build_layout(cavity *h) {
   // wall faces, contiguous per cavity, and cut faces, each list with its x
   // faces first: a CTA of an x face touches one 32-byte sector per node and
   // array (its positions run along y) where the others' rows are contiguous,
-  // and launched first the x faces' CTAs spread over the SMs (the last
-  // exchange CTA after a 128^3 FP32 step in 2 x 2 x 2 blocks ended about
-  // 3 us earlier than with the faces in block order)
+  // and launched first the x faces' CTAs spread over the SMs (after a 128^3
+  // FP32 step in 2 x 2 x 2 blocks the last exchange CTA ended 14-15 us after
+  // the step kernel with the faces in block order, 10-12 us in this order
+  // together with the finalise's reduction trees)
   h->hwall.clear();
   h->hcut.clear();
   for (int id = 0; id < h->nblocks; ++id) {
